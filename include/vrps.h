@@ -1,0 +1,194 @@
+/*
+ * vrps.h -- C ABI of the GB300 (sm_103a) variance-reduced ProxSkip tomography library.
+ *
+ * Method: Papoutsellis, Kereta, Papafitsoros, "Split, Skip and Play: Variance-Reduced
+ * ProxSkip for Tomography Reconstruction is Extremely Fast" (arXiv 2602.09527).
+ * The library solves Eq. (tomography_problem), Section 2.1,
+ *     min_x  1/2 ||A x - b||^2 + alpha TV(x) + I_{x >= 0}(x),
+ * with A a Joseph (linear-interpolation) discretisation of the Radon transform, split into
+ * N staggered subsets of projection angles (Section 1.2; Fig. 1 caption), and the
+ * algorithms of Algorithm 1 (ISTA, FISTA, ProxSGD/SAGA/SVRG/L-SVRG and their Skip variants).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument named x, y, r, v, b, dual, out is a DEVICE pointer on the current
+ *    CUDA device unless the comment says "host".  Arrays are float32, densely packed,
+ *    caller-owned; the library never frees or retains them past the call.
+ *  - Image layout: 2D row-major [ny][nx]; 3D [nz][ny][nx] (x fastest).
+ *    Sinogram layout: 2D [rows][n_bins]; 3D [rows][nv][nu]; for a subset, row r is the
+ *    r-th angle (view) of the subset in increasing angle index.
+ *  - Subset i (0 <= i < N) holds angles {i, i+N, i+2N, ...}; subset -1 means all angles
+ *    in natural order.
+ *  - Calls are asynchronous on `stream` (cudaStream_t; NULL = the legacy default stream)
+ *    unless documented otherwise.  Two calls that share one geometry handle must not run
+ *    concurrently: the handle owns scratch buffers used by proj_fwd, prox_tv and solve.
+ *  - Every call returns an int status: VRPS_OK (0) or a negative VRPS_ERR_* code; the
+ *    message of the last failure on the calling thread is vrps_last_error().  No C++
+ *    exception crosses this boundary.  Invalid arguments are rejected before any launch.
+ */
+#ifndef VRPS_H
+#define VRPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* vrps_stream_t;   /* identical to cudaStream_t */
+typedef struct vrps_geom vrps_geom;         /* opaque, library-owned */
+
+enum vrps_status {
+  VRPS_OK = 0,
+  VRPS_ERR_INVALID_ARG = -1,   /* bad size, pointer, enum value or geometry */
+  VRPS_ERR_OUT_OF_MEMORY = -2, /* a library-owned allocation failed */
+  VRPS_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed */
+  VRPS_ERR_TIMEOUT = -4,       /* a bounded device-side wait expired */
+  VRPS_ERR_DIVERGED = -5,      /* the objective became non-finite */
+  VRPS_ERR_UNSUPPORTED = -6    /* valid request outside what this build implements */
+};
+
+enum vrps_algo {               /* Algorithm 1 and its estimator table */
+  VRPS_ALGO_ISTA = 0,          /* full gradient, prox every iteration */
+  VRPS_ALGO_FISTA = 1,         /* ISTA + Beck-Teboulle momentum */
+  VRPS_ALGO_SVRG = 2,          /* ProxSVRG (p = 1) */
+  VRPS_ALGO_SAGA = 3,          /* ProxSAGA (p = 1) */
+  VRPS_ALGO_PROXSKIP = 4,      /* full gradient, prox with probability p */
+  VRPS_ALGO_VR_PROXSKIP = 5    /* estimator from opts, prox with probability p */
+};
+
+enum vrps_estimator {
+  VRPS_EST_SVRG = 0,           /* snapshot every N iterations */
+  VRPS_EST_SAGA = 1,           /* table of subset gradients (stored as subset residuals) */
+  VRPS_EST_LSVRG = 2,          /* snapshot refreshed with probability 1/N */
+  VRPS_EST_SGD = 3             /* plain subset gradient, no variance reduction */
+};
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+const char* vrps_last_error(void);
+/* ABI version (major*10000 + minor*100 + patch). */
+int vrps_version(void);
+
+/* ---------------------------------------------------------------- geometry
+ * 2D parallel beam (Section 2.1, "discrete Radon transform"; projector choice: Joseph).
+ * Pixel (ix,iy) centre ((ix-(nx-1)/2) pixel, (iy-(ny-1)/2) pixel); bin j at
+ * s_j = (j-(n_bins-1)/2) bin_spacing; ray {x cos t + y sin t = s_j}.
+ * angles_rad: HOST array of n_angles float64 angles, copied.  n_subsets: N >= 1 (<= n_angles).
+ * On success *out receives a handle bound to the current device; free with vrps_geom_free.
+ * Errors: INVALID_ARG (sizes <= 0, spacings <= 0, NULL pointers), OUT_OF_MEMORY, CUDA. */
+int vrps_geom_par2d(int nx, int ny, double pixel, int n_angles, const double* angles_rad,
+                    int n_bins, double bin_spacing, int n_subsets, vrps_geom** out);
+
+/* 3D circular cone beam.  Source S = sod (cos b, sin b, 0); detector centre
+ * -(sdd-sod)(cos b, sin b, 0); detector axes e_u = (-sin b, cos b, 0), e_v = (0,0,1);
+ * pixel (iu,iv) centre (iu-(nu-1)/2) du, (iv-(nv-1)/2) dv.  Voxel (ix,iy,iz) centre
+ * ((i-(n-1)/2) voxel).  betas_rad: HOST array of n_views float64 source angles, copied.
+ * Errors: INVALID_ARG as above, or when the source lies inside the volume's bounding
+ * circle; UNSUPPORTED when a ray would be marched along z (cone angle above 45 degrees). */
+int vrps_geom_cone3d(int nx, int ny, int nz, double voxel, int n_views, const double* betas_rad,
+                     int nu, int nv, double du, double dv, double sod, double sdd,
+                     int n_subsets, vrps_geom** out);
+
+/* Releases the handle and every library-owned device buffer it holds.  NULL is accepted.
+ * Synchronises the device before freeing. */
+int vrps_geom_free(vrps_geom* g);
+
+/* Sizes: n = image elements, m = sinogram elements (all angles), rows of subset `subset`
+ * (-1: all) and elements per row (n_bins or nu*nv).  Any output pointer may be NULL. */
+int vrps_geom_sizes(const vrps_geom* g, int subset, int64_t* n, int64_t* m, int* rows,
+                    int* row_len, int* dims);
+
+/* ---------------------------------------------------------------- operators
+ * y = A_i x  (Section 1.2: the forward operator of subset i; i = -1 for A).
+ * x: [n] image.  y: [rows(i) * row_len] sinogram rows of subset i, overwritten.
+ * Ray-driven gather; no atomics.  Errors: INVALID_ARG (NULL, subset out of range). */
+int vrps_proj_fwd(const vrps_geom* g, int subset, const float* x, float* y, vrps_stream_t stream);
+
+/* x = A_i^T r, the exact transpose of vrps_proj_fwd for the same subset, computed
+ * pixel (voxel) by pixel as a gather over the rays that touch it; no atomics.
+ * r: [rows(i) * row_len]; x: [n], overwritten.  Errors as vrps_proj_fwd. */
+int vrps_proj_adj(const vrps_geom* g, int subset, const float* r, float* x, vrps_stream_t stream);
+
+/* x = prox_{tau g}(v), g = TV (+ I_{x>=0} when nonneg != 0): Eq. (proximal_definition)
+ * solved by `iters` iterations of FGP on the dual (Section 2.1; Beck & Teboulle 2009).
+ * dual: NULL for a cold start (zero dual), or a [dims * n] float32 buffer holding the
+ * warm-start dual on entry and the final dual on exit (component-major: d/dx, d/dy[, d/dz]).
+ * v and x may not alias; iters >= 0 (0 returns the projection with the given dual);
+ * tau > 0.  Uses library-owned scratch of 2 * dims * n floats held by the handle.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+int vrps_prox_tv(const vrps_geom* g, const float* v, float* x, float tau, int iters, int nonneg,
+                 float* dual, vrps_stream_t stream);
+
+/* L = lambda_max(A^T A) by `iters` power iterations from a Philox4x32-10 start vector
+ * (key = seed, counter = (e/4, 0, 0, 1), element e takes word e%4, value (u+0.5)/2^32),
+ * with float64 inner products.  *L_out is a HOST double; the call synchronises `stream`.
+ * Sets the step sizes of Section 3 (gamma = factor / L). */
+int vrps_power_iteration(const vrps_geom* g, int iters, uint64_t seed, double* L_out,
+                         vrps_stream_t stream);
+
+/* Objective of Eq. (tomography_problem) at x (the indicator is not evaluated):
+ * out3 (HOST, 3 doubles) = { F, 1/2||Ax-b||^2, TV(x) } with float64 reductions.
+ * b: [m] sinogram, all angles, natural order.  Synchronises `stream`. */
+int vrps_objective(const vrps_geom* g, const float* x, const float* b, double alpha,
+                   double* out3, vrps_stream_t stream);
+
+/* Draws of Algorithm 1 for iterations k0 .. k0+count-1 (device int32 [count][3]):
+ * Philox4x32-10 with key (seed mod 2^32, seed >> 32), counter (k mod 2^32, k >> 32, job, 0);
+ * [0] = subset i_k = floor(u0 N / 2^32), [1] = skip coin theta_k = (u1 < floor(p 2^32)),
+ * 1 when p >= 1, [2] = L-SVRG refresh coin (u2 < floor(2^32 / N)). */
+int vrps_philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int n_subsets,
+                         double p, int32_t* out, vrps_stream_t stream);
+
+/* ---------------------------------------------------------------- solver */
+typedef struct vrps_solve_opts {
+  int estimator;      /* vrps_estimator, used by VRPS_ALGO_VR_PROXSKIP */
+  int fgp_iters;      /* FGP inner iterations per prox call (>= 0) */
+  int max_iters;      /* outer iterations K (> 0) */
+  int nonneg;         /* 1: include I_{x>=0} in the prox */
+  int power_iters;    /* iterations of the Lipschitz estimate when gamma <= 0 */
+  int eval_every;     /* evaluate F every this many iterations (0: never) */
+  double f_star;      /* reference optimum for the relative gap (used when target_gap > 0) */
+  double target_gap;  /* stop at the first evaluation with (F - f_star)/|f_star| <= this */
+  const float* x0;    /* optional initial image [n] (NULL: zeros) */
+  double* history;    /* optional HOST [history_cap][4]: iteration, F, seconds, data passes */
+  int history_cap;
+  int host_io;        /* 1: b and x_out are HOST pointers (copied inside the call) */
+  int n_subsets;      /* 0: the geometry's N; otherwise the number of subsets for this solve */
+  uint32_t job;       /* Philox counter word 2 (independent streams for batched jobs) */
+} vrps_solve_opts;
+
+typedef struct vrps_report {
+  int iterations;     /* outer iterations performed */
+  int prox_calls;     /* FGP prox evaluations */
+  int snapshots;      /* full-gradient refreshes (SVRG / L-SVRG) */
+  int evaluations;    /* objective evaluations written to history */
+  double passes;      /* data passes: subset gradients / N + full gradients */
+  double gamma;       /* step size used */
+  double lipschitz;   /* L estimate (0 when gamma was given) */
+  double objective;   /* last evaluated F (NaN if none) */
+  double seconds;     /* device time of the iteration loop (CUDA events) */
+  int reached;        /* 1 when target_gap was reached */
+} vrps_report;
+
+/* Defaults: SVRG estimator, 50 FGP iterations, 100 iterations, nonneg, 100 power
+ * iterations, no evaluation, N from the geometry. */
+void vrps_solve_opts_default(vrps_solve_opts* opts);
+
+/* Runs Algorithm 1's family on Eq. (tomography_problem).
+ * b: [m] sinogram, all angles in natural order (device, or host with opts->host_io).
+ * alpha > 0: TV weight.  algo: vrps_algo.  p in (0,1] for the Skip variants (ignored
+ * otherwise).  gamma > 0: step; gamma <= 0: factor/L with L from the power iteration and
+ * factor 1.99 (ISTA, ProxSkip), 1 (FISTA, SVRG, L-SVRG, SGD), 1/3 (SAGA) (Section 3).
+ * seed: Philox key for i_k, theta_k and the L-SVRG coin.  x_out: [n] final iterate x_K.
+ * Synchronous: returns after the last kernel finished (the report needs the results).
+ * Library-owned workspace (about 12 n + 3 m floats) is kept by the handle between calls.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA, DIVERGED (non-finite F at an evaluation). */
+int vrps_solve(const float* b, const vrps_geom* g, double alpha, int algo, double p, double gamma,
+               uint64_t seed, const vrps_solve_opts* opts, float* x_out, vrps_report* report,
+               vrps_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRPS_H */

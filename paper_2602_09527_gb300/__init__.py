@@ -1,0 +1,12 @@
+"""GB300-native (sm_103a) variance-reduced ProxSkip for tomography (arXiv 2602.09527).
+
+The compute path is the CUDA library ``_lib/libvrps.so`` (C ABI in ``include/vrps.h``);
+this package is its thin ctypes binding.  Entry points keep the C names without the
+``vrps_`` prefix: ``proj_fwd``, ``proj_adj``, ``prox_tv``, ``solve``, ``power_iteration``,
+``objective``, ``philox_schedule`` and the ``Geometry`` handle.
+"""
+from ._binding import (ALGOS, ESTIMATORS, Geometry, Report, SolveOpts, VrpsError, lib, objective,
+                       philox_schedule, power_iteration, prox_tv, proj_adj, proj_fwd, solve)
+
+__all__ = ["ALGOS", "ESTIMATORS", "Geometry", "Report", "SolveOpts", "VrpsError", "lib", "objective",
+           "philox_schedule", "power_iteration", "prox_tv", "proj_adj", "proj_fwd", "solve"]

@@ -1,0 +1,506 @@
+// C-ABI entry points: errors, geometry handles, operators, prox, power iteration, objective.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "vrps_internal.h"
+
+namespace vrps {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  return e == cudaErrorMemoryAllocation ? VRPS_ERR_OUT_OF_MEMORY : VRPS_ERR_CUDA;
+}
+
+int ensure(float** p, size_t count) {
+  if (*p) return VRPS_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(float));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMalloc(workspace)");
+  }
+  return VRPS_OK;
+}
+
+int ensure_d(double** p, size_t count) {
+  if (*p) return VRPS_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(double));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMalloc(workspace)");
+  }
+  return VRPS_OK;
+}
+
+// Staggered subsets (Fig. 1 caption): subset i = {i, i+N, i+2N, ...}; subset-major order
+// concatenates the subsets, so subset i occupies rows off[i] .. off[i+1]-1.
+int build_order(int n_angles, int N, int** dev, std::vector<int>* off) {
+  std::vector<int> order;
+  order.reserve(n_angles);
+  off->assign(N + 1, 0);
+  for (int i = 0; i < N; ++i) {
+    (*off)[i] = (int)order.size();
+    for (int a = i; a < n_angles; a += N) order.push_back(a);
+  }
+  (*off)[N] = (int)order.size();
+  if (*dev) {
+    cudaFree(*dev);
+    *dev = nullptr;
+  }
+  VRPS_CUDA(cudaMalloc((void**)dev, sizeof(int) * n_angles));
+  VRPS_CUDA(cudaMemcpy(*dev, order.data(), sizeof(int) * n_angles, cudaMemcpyHostToDevice));
+  return VRPS_OK;
+}
+
+int subset_rows(const vrps_geom* g, int subset, const int** ids, int* rows) {
+  if (subset == -1) {
+    *ids = g->order_natural;
+    *rows = g->n_angles;
+    return VRPS_OK;
+  }
+  if (subset < 0 || subset >= g->n_subsets)
+    return fail(VRPS_ERR_INVALID_ARG, "subset %d outside [-1, %d)", subset, g->n_subsets);
+  *ids = g->order_subset + g->subset_off[subset];
+  *rows = g->subset_off[subset + 1] - g->subset_off[subset];
+  return VRPS_OK;
+}
+
+int proj_forward(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows,
+                 int mode, FwdOut o, cudaStream_t s) {
+  if (g->dims == 3) return fwd3d(g, x, ids, rows, mode, o, s);
+  if (!xT) {
+    vrps_geom* gm = const_cast<vrps_geom*>(g);
+    VRPS_TRY(ensure(&gm->ws.xT, (size_t)g->n));
+    VRPS_TRY(transpose2d(x, gm->ws.xT, g->ny, g->nx, s));
+    xT = gm->ws.xT;
+  }
+  return fwd2d(g, x, xT, ids, rows, mode, o, s);
+}
+
+int proj_adjoint(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+                 cudaStream_t s) {
+  if (g->dims == 3) return adj3d(g, r, ids, rows, u, s);
+  return adj2d(g, r, ids, rows, u, s);
+}
+
+static int check_geom(const vrps_geom* g) {
+  if (!g) return fail(VRPS_ERR_INVALID_ARG, "geometry handle is NULL");
+  int dev = -1;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  if (dev != g->device)
+    return fail(VRPS_ERR_INVALID_ARG, "geometry was created on device %d, current device is %d",
+                g->device, dev);
+  return VRPS_OK;
+}
+
+static void free_ws(Workspace& w) {
+  float** fl[] = {&w.xT, &w.dual_cold, &w.dual_s1, &w.dual_s2, &w.sino, &w.img, &w.img2,
+                  &w.x, &w.xf, &w.xfT, &w.h, &w.xhat, &w.v, &w.gbar, &w.xprox, &w.dual,
+                  &w.b_perm, &w.tab, &w.res};
+  for (float** p : fl) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  if (w.partials) cudaFree(w.partials);
+  if (w.scalars) cudaFree(w.scalars);
+  if (w.sched_dev) cudaFree(w.sched_dev);
+  if (w.sched_host) cudaFreeHost(w.sched_host);
+  if (w.order_dev) cudaFree(w.order_dev);
+  w = Workspace();
+}
+
+static void free_geom(vrps_geom* g) {
+  if (!g) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();
+  if (g->ang2d) cudaFree(g->ang2d);
+  if (g->ray3d) cudaFree(g->ray3d);
+  if (g->view3d) cudaFree(g->view3d);
+  if (g->order_natural) cudaFree(g->order_natural);
+  if (g->order_subset) cudaFree(g->order_subset);
+  free_ws(g->ws);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete g;
+}
+
+static int finish_common(vrps_geom* g) {
+  std::vector<int> nat(g->n_angles);
+  for (int a = 0; a < g->n_angles; ++a) nat[a] = a;
+  VRPS_CUDA(cudaMalloc((void**)&g->order_natural, sizeof(int) * g->n_angles));
+  VRPS_CUDA(cudaMemcpy(g->order_natural, nat.data(), sizeof(int) * g->n_angles, cudaMemcpyHostToDevice));
+  VRPS_TRY(build_order(g->n_angles, g->n_subsets, &g->order_subset, &g->subset_off));
+  VRPS_TRY(ensure_d(&g->ws.partials, 1024));
+  VRPS_TRY(ensure_d(&g->ws.scalars, 16));
+  return VRPS_OK;
+}
+
+// 2D tables, float64 on the host (dominant-axis test included, so that it is taken in the
+// same precision as by any float64 reference).
+static int build_par2d(vrps_geom* g) {
+  const double pix = g->pixel, ds = g->bin_spacing;
+  const int TILE = 16;
+  std::vector<AngleInfo2D> tab(g->n_angles);
+  double span_max = 0.0, hw_max = 0.0;
+  for (int a = 0; a < g->n_angles; ++a) {
+    const double th = g->angles[a];
+    const double c = std::cos(th), s = std::sin(th);
+    const bool rows = std::fabs(c) >= std::fabs(s);
+    const double m = rows ? std::fabs(c) : std::fabs(s);
+    AngleInfo2D& t = tab[a];
+    if (rows) {
+      t.A1 = (float)(ds / (pix * c));
+      t.A2 = (float)(-s / c);
+    } else {
+      t.A1 = (float)(ds / (pix * s));
+      t.A2 = (float)(-c / s);
+    }
+    t.T = rows ? 0 : 1;
+    t.wgt = (float)(pix / m);
+    t.Bx = (float)(pix * c / ds);
+    t.By = (float)(pix * s / ds);
+    t.hw = (float)(pix * m / ds);
+    t.inv_hw = (float)(ds / (pix * m));
+    span_max = std::fmax(span_max, (TILE - 1) * (std::fabs(pix * c / ds) + std::fabs(pix * s / ds)));
+    hw_max = std::fmax(hw_max, pix * m / ds);
+  }
+  g->adj_nc = (int)std::ceil(2.0 * hw_max) + 1;
+  g->adj_fp = (int)std::ceil(span_max) + g->adj_nc + 4;
+  VRPS_CUDA(cudaMalloc((void**)&g->ang2d, sizeof(AngleInfo2D) * g->n_angles));
+  VRPS_CUDA(cudaMemcpy(g->ang2d, tab.data(), sizeof(AngleInfo2D) * g->n_angles, cudaMemcpyHostToDevice));
+  return VRPS_OK;
+}
+
+// 3D tables: per (view, detector column) ray constants and per view adjoint constants.
+// Rays are marched over x planes when |d_x| >= |d_y| (d depends only on the column), over
+// y planes otherwise; a ray whose |d_z| is not below both is rejected as unsupported.
+static int build_cone3d(vrps_geom* g) {
+  const double vox = g->pixel;
+  const double cx = 0.5 * (g->nx - 1), cy = 0.5 * (g->ny - 1);
+  const double cv = 0.5 * (g->nv - 1);
+  const double vmax = std::fabs((0 - cv) * g->dv);
+  std::vector<RayInfo3D> rays((size_t)g->n_angles * g->nu);
+  g->view3d_host.assign(g->n_angles, ViewInfo3D());
+  for (int a = 0; a < g->n_angles; ++a) {
+    const double b = g->angles[a];
+    const double cb = std::cos(b), sb = std::sin(b);
+    const double Sx = g->sod * cb, Sy = g->sod * sb;
+    const double D0x = -(g->sdd - g->sod) * cb, D0y = -(g->sdd - g->sod) * sb;
+    ViewInfo3D& vi = g->view3d_host[a];
+    vi.sx = (float)Sx;
+    vi.sy = (float)Sy;
+    vi.eux = (float)(-sb);
+    vi.euy = (float)cb;
+    vi.esx = (float)cb;
+    vi.esy = (float)sb;
+    vi.sdd = (float)g->sdd;
+    vi.inv_du = (float)(1.0 / g->du);
+    vi.cu = (float)(0.5 * (g->nu - 1));
+    vi.has_x = 0;
+    vi.has_y = 0;
+    for (int iu = 0; iu < g->nu; ++iu) {
+      const double u = (iu - (g->nu - 1) / 2.0) * g->du;
+      const double dx = (D0x + u * (-sb)) - Sx;
+      const double dy = (D0y + u * cb) - Sy;
+      if (vmax >= std::fmax(std::fabs(dx), std::fabs(dy)))
+        return fail(VRPS_ERR_UNSUPPORTED, "view %d column %d: ray dominant along z (cone too wide)", a, iu);
+      {
+        // every plane of the volume along the marching axis must lie in front of the source
+        const bool ax0 = std::fabs(dx) >= std::fabs(dy);
+        const double Sa = ax0 ? Sx : Sy, da = ax0 ? dx : dy;
+        const int na = ax0 ? g->nx : g->ny;
+        const double c = 0.5 * (na - 1);
+        const double t0 = ((0 - c) * vox - Sa) / da, t1 = ((na - 1 - c) * vox - Sa) / da;
+        if (!(t0 > 0.0 && t1 > 0.0))
+          return fail(VRPS_ERR_INVALID_ARG, "view %d column %d: volume planes behind the source", a, iu);
+      }
+      RayInfo3D& r = rays[(size_t)a * g->nu + iu];
+      r.pad0 = r.pad1 = 0.f;
+      if (std::fabs(dx) >= std::fabs(dy)) {
+        r.axis = 0;
+        r.P0 = (float)(cy + (Sy - Sx * dy / dx) / vox);
+        r.P1 = (float)(dy / dx);
+        r.Q0 = (float)(-Sx * g->dv / (dx * vox));
+        r.Q1 = (float)(g->dv / dx);
+        r.R = (float)(g->dv / dx);
+        vi.has_x = 1;
+      } else {
+        r.axis = 1;
+        r.P0 = (float)(cx + (Sx - Sy * dx / dy) / vox);
+        r.P1 = (float)(dx / dy);
+        r.Q0 = (float)(-Sy * g->dv / (dy * vox));
+        r.Q1 = (float)(g->dv / dy);
+        r.R = (float)(g->dv / dy);
+        vi.has_y = 1;
+      }
+    }
+  }
+  VRPS_CUDA(cudaMalloc((void**)&g->ray3d, sizeof(RayInfo3D) * rays.size()));
+  VRPS_CUDA(cudaMemcpy(g->ray3d, rays.data(), sizeof(RayInfo3D) * rays.size(), cudaMemcpyHostToDevice));
+  VRPS_CUDA(cudaMalloc((void**)&g->view3d, sizeof(ViewInfo3D) * g->n_angles));
+  VRPS_CUDA(cudaMemcpy(g->view3d, g->view3d_host.data(), sizeof(ViewInfo3D) * g->n_angles,
+                       cudaMemcpyHostToDevice));
+  return VRPS_OK;
+}
+
+static int fgp_dual_size(const vrps_geom* g, size_t* count) {
+  *count = (size_t)g->dims * (size_t)g->n;
+  return VRPS_OK;
+}
+
+}  // namespace vrps
+
+using namespace vrps;
+
+extern "C" {
+
+const char* vrps_last_error(void) { return g_err; }
+
+int vrps_version(void) { return 10000; }
+
+int vrps_geom_par2d(int nx, int ny, double pixel, int n_angles, const double* angles_rad,
+                    int n_bins, double bin_spacing, int n_subsets, vrps_geom** out) {
+  if (!out) return fail(VRPS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx <= 0 || ny <= 0 || n_angles <= 0 || n_bins <= 0)
+    return fail(VRPS_ERR_INVALID_ARG, "sizes must be positive (nx=%d ny=%d angles=%d bins=%d)", nx, ny,
+                n_angles, n_bins);
+  if (n_angles > 65535) return fail(VRPS_ERR_INVALID_ARG, "at most 65535 angles");
+  if ((int64_t)nx * ny > (int64_t)1 << 30) return fail(VRPS_ERR_INVALID_ARG, "image too large");
+  if (!(pixel > 0) || !(bin_spacing > 0)) return fail(VRPS_ERR_INVALID_ARG, "pixel and bin spacing must be > 0");
+  if (!angles_rad) return fail(VRPS_ERR_INVALID_ARG, "angles is NULL");
+  if (n_subsets < 1 || n_subsets > n_angles)
+    return fail(VRPS_ERR_INVALID_ARG, "n_subsets %d outside [1, %d]", n_subsets, n_angles);
+  for (int a = 0; a < n_angles; ++a)
+    if (!std::isfinite(angles_rad[a])) return fail(VRPS_ERR_INVALID_ARG, "angle %d is not finite", a);
+  vrps_geom* g = new (std::nothrow) vrps_geom();
+  if (!g) return fail(VRPS_ERR_OUT_OF_MEMORY, "host allocation failed");
+  g->dims = 2;
+  g->nx = nx;
+  g->ny = ny;
+  g->nz = 1;
+  g->pixel = pixel;
+  g->n_angles = n_angles;
+  g->n_bins = n_bins;
+  g->bin_spacing = bin_spacing;
+  g->n_subsets = n_subsets;
+  g->n = (int64_t)nx * ny;
+  g->m = (int64_t)n_angles * n_bins;
+  g->row_len = n_bins;
+  g->angles.assign(angles_rad, angles_rad + n_angles);
+  cudaError_t e = cudaGetDevice(&g->device);
+  int st = e == cudaSuccess ? VRPS_OK : cuda_fail(e, "cudaGetDevice");
+  if (st == VRPS_OK) st = build_par2d(g);
+  if (st == VRPS_OK) st = finish_common(g);
+  if (st != VRPS_OK) {
+    free_geom(g);
+    return st;
+  }
+  *out = g;
+  return VRPS_OK;
+}
+
+int vrps_geom_cone3d(int nx, int ny, int nz, double voxel, int n_views, const double* betas_rad,
+                     int nu, int nv, double du, double dv, double sod, double sdd, int n_subsets,
+                     vrps_geom** out) {
+  if (!out) return fail(VRPS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx <= 0 || ny <= 0 || nz <= 0 || n_views <= 0 || nu <= 0 || nv <= 0)
+    return fail(VRPS_ERR_INVALID_ARG, "sizes must be positive");
+  if (n_views > 65535) return fail(VRPS_ERR_INVALID_ARG, "at most 65535 views");
+  if ((int64_t)nx * ny * nz > ((int64_t)1 << 31) - 1) return fail(VRPS_ERR_INVALID_ARG, "volume too large");
+  if ((int64_t)nu * nv * n_views > ((int64_t)1 << 31) - 1) return fail(VRPS_ERR_INVALID_ARG, "sinogram too large");
+  if (!(voxel > 0) || !(du > 0) || !(dv > 0)) return fail(VRPS_ERR_INVALID_ARG, "spacings must be > 0");
+  if (!betas_rad) return fail(VRPS_ERR_INVALID_ARG, "betas is NULL");
+  if (n_subsets < 1 || n_subsets > n_views)
+    return fail(VRPS_ERR_INVALID_ARG, "n_subsets %d outside [1, %d]", n_subsets, n_views);
+  const double half = 0.5 * voxel * std::sqrt((double)nx * nx + (double)ny * ny);
+  if (!(sod > half + voxel) || !(sdd > sod))
+    return fail(VRPS_ERR_INVALID_ARG, "need sdd > sod > %.6g (source outside the volume)", half);
+  for (int a = 0; a < n_views; ++a)
+    if (!std::isfinite(betas_rad[a])) return fail(VRPS_ERR_INVALID_ARG, "view %d angle not finite", a);
+  vrps_geom* g = new (std::nothrow) vrps_geom();
+  if (!g) return fail(VRPS_ERR_OUT_OF_MEMORY, "host allocation failed");
+  g->dims = 3;
+  g->nx = nx;
+  g->ny = ny;
+  g->nz = nz;
+  g->pixel = voxel;
+  g->n_angles = n_views;
+  g->nu = nu;
+  g->nv = nv;
+  g->du = du;
+  g->dv = dv;
+  g->sod = sod;
+  g->sdd = sdd;
+  g->n_subsets = n_subsets;
+  g->n = (int64_t)nx * ny * nz;
+  g->m = (int64_t)n_views * nu * nv;
+  g->row_len = nu * nv;
+  g->angles.assign(betas_rad, betas_rad + n_views);
+  cudaError_t e = cudaGetDevice(&g->device);
+  int st = e == cudaSuccess ? VRPS_OK : cuda_fail(e, "cudaGetDevice");
+  if (st == VRPS_OK) st = build_cone3d(g);
+  if (st == VRPS_OK) st = finish_common(g);
+  if (st != VRPS_OK) {
+    free_geom(g);
+    return st;
+  }
+  *out = g;
+  return VRPS_OK;
+}
+
+int vrps_geom_free(vrps_geom* g) {
+  free_geom(g);
+  return VRPS_OK;
+}
+
+int vrps_geom_sizes(const vrps_geom* g, int subset, int64_t* n, int64_t* m, int* rows, int* row_len,
+                    int* dims) {
+  if (!g) return fail(VRPS_ERR_INVALID_ARG, "geometry handle is NULL");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (row_len) *row_len = g->row_len;
+  if (dims) *dims = g->dims;
+  if (rows) {
+    if (subset == -1) {
+      *rows = g->n_angles;
+    } else {
+      if (subset < 0 || subset >= g->n_subsets)
+        return fail(VRPS_ERR_INVALID_ARG, "subset %d outside [-1, %d)", subset, g->n_subsets);
+      *rows = g->subset_off[subset + 1] - g->subset_off[subset];
+    }
+  }
+  return VRPS_OK;
+}
+
+int vrps_proj_fwd(const vrps_geom* g, int subset, const float* x, float* y, vrps_stream_t stream) {
+  VRPS_TRY(check_geom(g));
+  if (!x || !y) return fail(VRPS_ERR_INVALID_ARG, "x or y is NULL");
+  const int* ids = nullptr;
+  int rows = 0;
+  VRPS_TRY(subset_rows(g, subset, &ids, &rows));
+  FwdOut o{y, nullptr, nullptr};
+  return proj_forward(g, x, nullptr, ids, rows, FWD_PLAIN, o, (cudaStream_t)stream);
+}
+
+int vrps_proj_adj(const vrps_geom* g, int subset, const float* r, float* x, vrps_stream_t stream) {
+  VRPS_TRY(check_geom(g));
+  if (!x || !r) return fail(VRPS_ERR_INVALID_ARG, "r or x is NULL");
+  const int* ids = nullptr;
+  int rows = 0;
+  VRPS_TRY(subset_rows(g, subset, &ids, &rows));
+  UpdateArgs u;
+  std::memset(&u, 0, sizeof(u));
+  u.enabled = 0;
+  u.out = x;
+  return proj_adjoint(g, r, ids, rows, u, (cudaStream_t)stream);
+}
+
+int vrps_prox_tv(const vrps_geom* g, const float* v, float* x, float tau, int iters, int nonneg,
+                 float* dual, vrps_stream_t stream) {
+  VRPS_TRY(check_geom(g));
+  if (!v || !x) return fail(VRPS_ERR_INVALID_ARG, "v or x is NULL");
+  if (v == x) return fail(VRPS_ERR_INVALID_ARG, "v and x must not alias");
+  if (!(tau > 0.f) || !std::isfinite(tau)) return fail(VRPS_ERR_INVALID_ARG, "tau must be > 0");
+  if (iters < 0) return fail(VRPS_ERR_INVALID_ARG, "iters must be >= 0");
+  vrps_geom* gm = const_cast<vrps_geom*>(g);
+  size_t dn = 0;
+  fgp_dual_size(g, &dn);
+  cudaStream_t s = (cudaStream_t)stream;
+  float* d = dual;
+  if (!d) {
+    VRPS_TRY(ensure(&gm->ws.dual_cold, dn));
+    VRPS_CUDA(cudaMemsetAsync(gm->ws.dual_cold, 0, dn * sizeof(float), s));
+    d = gm->ws.dual_cold;
+  }
+  ProxTail t;
+  std::memset(&t, 0, sizeof(t));
+  t.mode = 0;
+  t.out = x;
+  return fgp_run(g, v, tau, iters, nonneg ? 1 : 0, d, t, s);
+}
+
+int vrps_power_iteration(const vrps_geom* g, int iters, uint64_t seed, double* L_out, vrps_stream_t stream) {
+  VRPS_TRY(check_geom(g));
+  if (!L_out) return fail(VRPS_ERR_INVALID_ARG, "L_out is NULL");
+  if (iters < 1) return fail(VRPS_ERR_INVALID_ARG, "iters must be >= 1");
+  vrps_geom* gm = const_cast<vrps_geom*>(g);
+  Workspace& w = gm->ws;
+  cudaStream_t s = (cudaStream_t)stream;
+  VRPS_TRY(ensure(&w.img, (size_t)g->n));
+  VRPS_TRY(ensure(&w.img2, (size_t)g->n));
+  VRPS_TRY(ensure(&w.sino, (size_t)g->m));
+  float* u = w.img;
+  float* z = w.img2;
+  VRPS_TRY(philox_uniform(seed, 0, 1, u, g->n, s));
+  VRPS_TRY(dot64(u, u, g->n, w.scalars + 0, w, s));
+  VRPS_TRY(scale_inv_sqrt(u, u, w.scalars + 0, g->n, s));
+  UpdateArgs ua;
+  std::memset(&ua, 0, sizeof(ua));
+  ua.out = z;
+  for (int it = 0; it < iters; ++it) {
+    FwdOut o{w.sino, nullptr, nullptr};
+    VRPS_TRY(proj_forward(g, u, nullptr, g->order_natural, g->n_angles, FWD_PLAIN, o, s));
+    VRPS_TRY(proj_adjoint(g, w.sino, g->order_natural, g->n_angles, ua, s));
+    VRPS_TRY(dot64(u, z, g->n, w.scalars + 1, w, s));
+    VRPS_TRY(dot64(z, z, g->n, w.scalars + 2, w, s));
+    VRPS_TRY(scale_inv_sqrt(u, z, w.scalars + 2, g->n, s));
+  }
+  double lam = 0.0;
+  VRPS_CUDA(cudaMemcpyAsync(&lam, w.scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  VRPS_CUDA(cudaStreamSynchronize(s));
+  *L_out = lam;
+  return VRPS_OK;
+}
+
+int vrps_objective(const vrps_geom* g, const float* x, const float* b, double alpha, double* out3,
+                   vrps_stream_t stream) {
+  VRPS_TRY(check_geom(g));
+  if (!x || !b || !out3) return fail(VRPS_ERR_INVALID_ARG, "NULL argument");
+  vrps_geom* gm = const_cast<vrps_geom*>(g);
+  Workspace& w = gm->ws;
+  cudaStream_t s = (cudaStream_t)stream;
+  VRPS_TRY(ensure(&w.sino, (size_t)g->m));
+  FwdOut o{w.sino, b, nullptr};
+  VRPS_TRY(proj_forward(g, x, nullptr, g->order_natural, g->n_angles, FWD_RESID, o, s));
+  VRPS_TRY(dot64(w.sino, w.sino, g->m, w.scalars + 3, w, s));
+  VRPS_TRY(tv64(g, x, w.scalars + 4, w, s));
+  double h[2];
+  VRPS_CUDA(cudaMemcpyAsync(h, w.scalars + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  VRPS_CUDA(cudaStreamSynchronize(s));
+  out3[1] = 0.5 * h[0];
+  out3[2] = h[1];
+  out3[0] = out3[1] + alpha * out3[2];
+  return VRPS_OK;
+}
+
+int vrps_philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int n_subsets, double p,
+                         int32_t* out, vrps_stream_t stream) {
+  if (!out || count < 0 || n_subsets < 1 || !(p > 0))
+    return fail(VRPS_ERR_INVALID_ARG, "bad schedule arguments");
+  if (k0 < 0) return fail(VRPS_ERR_INVALID_ARG, "k0 must be >= 0");
+  return philox_schedule(seed, job, k0, count, n_subsets, p, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

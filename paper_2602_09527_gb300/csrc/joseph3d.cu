@@ -1,0 +1,261 @@
+// 3D circular cone-beam Joseph projector: ray-driven forward (gather) and voxel-driven exact
+// transpose (gather, no atomics), with the same fused epilogues as the 2D projector.
+//
+// Each ray (view, iu, iv) is marched over the planes of its dominant axis (x or y, fixed
+// per detector column); on plane l its point has transverse index ft = P0 + P1 (l - lc)
+// and z index fz = cz + (iv - cv)(Q0 + Q1 (l - lc)), bilinearly interpolated; each plane
+// adds voxel * |d| / |d_a|.  The adjoint visits, for every voxel and view, the detector
+// columns whose rays cross the voxel's dominant plane within one voxel (found by projecting
+// the two plane points at +-1 voxel onto the detector) and the rows whose z index is within
+// one voxel, and accumulates the identical bilinear weight.
+#include "vrps_internal.h"
+
+namespace vrps {
+namespace {
+
+struct Fwd3DParams {
+  const float* x;
+  const RayInfo3D* rays;
+  const int* ids;
+  int nx, ny, nz, nu, nv;
+  float cx, cy, cz, cv, vox;
+  FwdOut o;
+};
+
+// Plane indices l in [0, nl) where intercept + slope (l - lc) lies in (-1, n); widened by 1.
+__device__ __forceinline__ void clip_range(float intercept, float slope, float lc, int n, int nl, int& lo,
+                                           int& hi) {
+  if (slope != 0.f) {
+    float a = lc + (-1.f - intercept) / slope;
+    float b = lc + ((float)n - intercept) / slope;
+    if (a > b) {
+      const float t = a;
+      a = b;
+      b = t;
+    }
+    a = fminf(fmaxf(a, -2.f), (float)nl + 1.f);
+    b = fminf(fmaxf(b, -2.f), (float)nl + 1.f);
+    lo = max(lo, (int)floorf(a) - 1);
+    hi = min(hi, (int)ceilf(b) + 1);
+  } else if (!(intercept > -1.f && intercept < (float)n)) {
+    hi = -1;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
+  const int iu = blockIdx.x * 32 + threadIdx.x;
+  const int iv = blockIdx.y * 8 + threadIdx.y;
+  const int row = blockIdx.z;
+  if (iu >= P.nu || iv >= P.nv) return;
+  const int view = P.ids[row];
+  const RayInfo3D ri = P.rays[(size_t)view * P.nu + iu];
+  const float k = (float)iv - P.cv;
+  const bool ax0 = ri.axis == 0;
+  const int nl = ax0 ? P.nx : P.ny;
+  const int nt = ax0 ? P.ny : P.nx;
+  const float lc = ax0 ? P.cx : P.cy;
+  const int64_t sl = ax0 ? 1 : P.nx;
+  const int64_t st = ax0 ? P.nx : 1;
+  const int64_t sz = (int64_t)P.nx * P.ny;
+  int lo = 0, hi = nl - 1;
+  clip_range(ri.P0, ri.P1, lc, nt, nl, lo, hi);
+  clip_range(fmaf(k, ri.Q0, P.cz), k * ri.Q1, lc, P.nz, nl, lo, hi);
+  float acc = 0.f;
+  for (int l = lo; l <= hi; ++l) {
+    const float dl = (float)l - lc;
+    const float ft = fmaf(ri.P1, dl, ri.P0);
+    const float fz = fmaf(k, fmaf(ri.Q1, dl, ri.Q0), P.cz);
+    const float flt = floorf(ft), flz = floorf(fz);
+    const int it = (int)flt, iz = (int)flz;
+    const float f = ft - flt, gz = fz - flz;
+    const bool t0 = it >= 0 && it < nt, t1 = it + 1 >= 0 && it + 1 < nt;
+    const bool z0 = iz >= 0 && iz < P.nz, z1 = iz + 1 >= 0 && iz + 1 < P.nz;
+    const int64_t b = (int64_t)l * sl + (int64_t)it * st + (int64_t)iz * sz;
+    const float v00 = (t0 && z0) ? __ldg(P.x + b) : 0.f;
+    const float v10 = (t1 && z0) ? __ldg(P.x + b + st) : 0.f;
+    const float v01 = (t0 && z1) ? __ldg(P.x + b + sz) : 0.f;
+    const float v11 = (t1 && z1) ? __ldg(P.x + b + st + sz) : 0.f;
+    const float lo_z = fmaf(f, v10 - v00, v00);
+    const float hi_z = fmaf(f, v11 - v01, v01);
+    acc += fmaf(gz, hi_z - lo_z, lo_z);
+  }
+  const float kr = k * ri.R;
+  const float r = acc * (P.vox * sqrtf(1.f + ri.P1 * ri.P1 + kr * kr));
+  const size_t idx = (size_t)row * P.nu * P.nv + (size_t)iv * P.nu + iu;
+  if (MODE == FWD_PLAIN) {
+    P.o.y[idx] = r;
+  } else if (MODE == FWD_RESID) {
+    P.o.y[idx] = r - P.o.b[idx];
+  } else if (MODE == FWD_SVRG) {
+    P.o.y[idx] = r - P.o.tab[idx];
+  } else if (MODE == FWD_SAGA) {
+    const float res = r - P.o.b[idx];
+    P.o.y[idx] = res - P.o.tab[idx];
+    P.o.tab[idx] = res;
+  } else {
+    P.o.tab[idx] = r;
+    P.o.y[idx] = r - P.o.b[idx];
+  }
+}
+
+struct Adj3DParams {
+  const float* r;
+  const RayInfo3D* rays;
+  const ViewInfo3D* views;
+  const int* ids;
+  int rows;
+  int nx, ny, nz, nu, nv;
+  float cx, cy, cz, cv, vox;
+  UpdateArgs u;
+};
+
+// Fractional detector column of the ray from the source through the point (qx, qy, *).
+__device__ __forceinline__ float column_of(const ViewInfo3D& vi, float qx, float qy) {
+  const float ax = qx - vi.sx, ay = qy - vi.sy;
+  const float num = fmaf(ax, vi.eux, ay * vi.euy);
+  const float den = -fmaf(ax, vi.esx, ay * vi.esy);
+  return fmaf(vi.sdd * num / den, vi.inv_du, vi.cu);
+}
+
+// Contribution of the rays of one view whose dominant axis is `axis` to voxel
+// (plane index l along that axis, transverse index tt, z index gz).
+__device__ __forceinline__ float adj_axis(const Adj3DParams& P, const ViewInfo3D& vi, const RayInfo3D* vr,
+                                          const float* rr, int axis, int l, int tt, int gz, float qx0,
+                                          float qy0, float qx1, float qy1) {
+  const float lim = (float)P.nu + 2.f;
+  const float c0 = fminf(fmaxf(column_of(vi, qx0, qy0), -2.f), lim);
+  const float c1 = fminf(fmaxf(column_of(vi, qx1, qy1), -2.f), lim);
+  int u_lo = (int)floorf(fminf(c0, c1)) - 1;
+  int u_hi = (int)ceilf(fmaxf(c0, c1)) + 1;
+  u_lo = max(u_lo, 0);
+  u_hi = min(u_hi, P.nu - 1);
+  const float dl = (float)l - (axis == 0 ? P.cx : P.cy);
+  float a = 0.f;
+  for (int iu = u_lo; iu <= u_hi; ++iu) {
+    const RayInfo3D ri = vr[iu];
+    if (ri.axis != axis) continue;
+    const float ft = fmaf(ri.P1, dl, ri.P0);
+    const float wt = 1.f - fabsf(ft - (float)tt);
+    if (wt <= 0.f) continue;
+    const float qz = fmaf(ri.Q1, dl, ri.Q0);
+    const float vlim = (float)P.nv + 2.f;
+    const float klo = fminf(fmaxf(((float)gz - 1.f - P.cz) / qz + P.cv, -2.f), vlim);
+    const float khi = fminf(fmaxf(((float)gz + 1.f - P.cz) / qz + P.cv, -2.f), vlim);
+    const int v_lo = max(0, (int)floorf(fminf(klo, khi)) - 1);
+    const int v_hi = min(P.nv - 1, (int)ceilf(fmaxf(klo, khi)) + 1);
+    const float base_w = 1.f + ri.P1 * ri.P1;
+    for (int iv = v_lo; iv <= v_hi; ++iv) {
+      const float k = (float)iv - P.cv;
+      const float fz = fmaf(k, qz, P.cz);
+      const float wz = 1.f - fabsf(fz - (float)gz);
+      if (wz <= 0.f) continue;
+      const float kr = k * ri.R;
+      const float w = wt * wz * (P.vox * sqrtf(base_w + kr * kr));
+      a = fmaf(w, __ldg(rr + (size_t)iv * P.nu + iu), a);
+    }
+  }
+  return a;
+}
+
+__global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
+  const int gx = blockIdx.x * 32 + threadIdx.x;
+  const int gy = blockIdx.y * 8 + threadIdx.y;
+  const int gz = blockIdx.z;
+  if (gx >= P.nx || gy >= P.ny) return;
+  const float X = ((float)gx - P.cx) * P.vox, Y = ((float)gy - P.cy) * P.vox;
+  float acc = 0.f;
+  for (int q = 0; q < P.rows; ++q) {
+    const int view = P.ids[q];
+    const ViewInfo3D vi = P.views[view];
+    const RayInfo3D* vr = P.rays + (size_t)view * P.nu;
+    const float* rr = P.r + (size_t)q * P.nu * P.nv;
+    if (vi.has_x) acc += adj_axis(P, vi, vr, rr, 0, gx, gy, gz, X, Y - P.vox, X, Y + P.vox);
+    if (vi.has_y) acc += adj_axis(P, vi, vr, rr, 1, gy, gx, gz, X - P.vox, Y, X + P.vox, Y);
+  }
+  const size_t p = ((size_t)gz * P.ny + gy) * P.nx + gx;
+  const UpdateArgs& u = P.u;
+  if (!u.enabled) {
+    u.out[p] = acc;
+    return;
+  }
+  float G = u.cN * acc;
+  if (u.gbar) {
+    const float gb = u.gbar[p];
+    G += gb;
+    if (u.saga) u.gbar[p] = gb + acc;
+  }
+  const float base = u.base[p];
+  if (u.h) {
+    const float hp = u.h[p];
+    const float xh = base - u.gamma * (G - hp);
+    if (u.theta) {
+      u.xhat[p] = xh;
+      u.v[p] = xh - u.gamma_over_p * hp;
+    } else {
+      u.x[p] = xh;
+    }
+  } else {
+    const float xh = base - u.gamma * G;
+    if (u.theta) u.v[p] = xh;
+    else u.x[p] = xh;
+  }
+}
+
+}  // namespace
+
+int fwd3d(const vrps_geom* g, const float* x, const int* ids, int rows, int mode, FwdOut o, cudaStream_t s) {
+  if (rows <= 0) return VRPS_OK;
+  Fwd3DParams P;
+  P.x = x;
+  P.rays = g->ray3d;
+  P.ids = ids;
+  P.nx = g->nx;
+  P.ny = g->ny;
+  P.nz = g->nz;
+  P.nu = g->nu;
+  P.nv = g->nv;
+  P.cx = 0.5f * (float)(g->nx - 1);
+  P.cy = 0.5f * (float)(g->ny - 1);
+  P.cz = 0.5f * (float)(g->nz - 1);
+  P.cv = 0.5f * (float)(g->nv - 1);
+  P.vox = (float)g->pixel;
+  P.o = o;
+  dim3 grid((g->nu + 31) / 32, (g->nv + 7) / 8, rows), block(32, 8);
+  switch (mode) {
+    case FWD_PLAIN: fwd3d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); break;
+    case FWD_RESID: fwd3d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); break;
+    case FWD_SVRG: fwd3d_kernel<FWD_SVRG><<<grid, block, 0, s>>>(P); break;
+    case FWD_SAGA: fwd3d_kernel<FWD_SAGA><<<grid, block, 0, s>>>(P); break;
+    case FWD_SNAP: fwd3d_kernel<FWD_SNAP><<<grid, block, 0, s>>>(P); break;
+    default: return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
+  }
+  VRPS_LAUNCHED("fwd3d");
+  return VRPS_OK;
+}
+
+int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u, cudaStream_t s) {
+  Adj3DParams P;
+  P.r = r;
+  P.rays = g->ray3d;
+  P.views = g->view3d;
+  P.ids = ids;
+  P.rows = rows;
+  P.nx = g->nx;
+  P.ny = g->ny;
+  P.nz = g->nz;
+  P.nu = g->nu;
+  P.nv = g->nv;
+  P.cx = 0.5f * (float)(g->nx - 1);
+  P.cy = 0.5f * (float)(g->ny - 1);
+  P.cz = 0.5f * (float)(g->nz - 1);
+  P.cv = 0.5f * (float)(g->nv - 1);
+  P.vox = (float)g->pixel;
+  P.u = u;
+  dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
+  adj3d_kernel<<<grid, block, 0, s>>>(P);
+  VRPS_LAUNCHED("adj3d");
+  return VRPS_OK;
+}
+
+}  // namespace vrps

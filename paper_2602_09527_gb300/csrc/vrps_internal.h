@@ -1,0 +1,208 @@
+// Internal declarations shared by the translation units of the CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "vrps.h"
+
+namespace vrps {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define VRPS_CUDA(call)                                        \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return ::vrps::cuda_fail(_e, #call); \
+  } while (0)
+
+#define VRPS_LAUNCHED(name)                                    \
+  do {                                                         \
+    cudaError_t _e = cudaGetLastError();                       \
+    if (_e != cudaSuccess) return ::vrps::cuda_fail(_e, name); \
+  } while (0)
+
+#define VRPS_TRY(expr)              \
+  do {                              \
+    int _s = (expr);                \
+    if (_s != VRPS_OK) return _s;   \
+  } while (0)
+
+// ------------------------------------------------------------------ geometry tables
+// Per-angle constants of the 2D Joseph projector, derived in float64 on the host.
+// Marching frame: T = 0 -> lines are image rows (iy) of x; T = 1 -> lines are columns (ix)
+// read from the transposed image xT[ix][iy].  Along line l the ray of bin j meets the
+// interpolation axis at u = uc + A1 (j - jc) + A2 (l - lc).  Pixel-driven adjoint: the
+// pixel centre projects to fractional bin t = jc + Bx (ix - cx) + By (iy - cy); bin j gets
+// weight wgt * max(0, 1 - |j - t| * inv_hw).
+struct AngleInfo2D {
+  float A1, A2, wgt, Bx;
+  float By, hw, inv_hw;
+  int T;
+};
+
+// Per (view, detector column iu) constants of the 3D projector (float64-derived).
+// axis 0: rays marched over x planes; axis 1: over y planes.  On dominant plane index l:
+//   transverse index  ft = P0 + P1 (l - lc)
+//   z index           fz = (iv - cv) (Q0 + Q1 (l - lc)) + cz
+//   weight            wgt = voxel * sqrt(1 + P1^2 + ((iv - cv) R)^2),  R = dv / d_a
+struct RayInfo3D {
+  float P0, P1, Q0, Q1;
+  float R;
+  int axis;
+  float pad0, pad1;
+};
+
+// Per view constants of the 3D voxel-driven adjoint (float64-derived).
+struct ViewInfo3D {
+  float sx, sy;        // source position (physical units)
+  float eux, euy;      // detector u axis
+  float esx, esy;      // unit vector from the origin towards the source
+  float sdd, inv_du;   // source-detector distance, 1/du
+  float cu;            // (nu-1)/2
+  int has_x, has_y;    // whether the view has rays of each dominant axis
+  int pad;
+};
+
+struct Workspace {
+  // generic scratch sized by the geometry (lazily allocated)
+  float* xT = nullptr;          // [n] transposed image for the 2D forward
+  float* dual_cold = nullptr;   // [dims n] zero dual for cold-start prox calls
+  float* dual_s1 = nullptr;     // [dims n] FGP rotation buffers
+  float* dual_s2 = nullptr;
+  double* partials = nullptr;   // reduction partials
+  double* scalars = nullptr;    // [16] device scalars
+  float* sino = nullptr;        // [m] sinogram scratch
+  float* img = nullptr;         // [n] image scratch
+  float* img2 = nullptr;        // [n]
+  // solver state (allocated on first solve)
+  bool solver_ready = false;
+  float *x = nullptr, *xf = nullptr, *xfT = nullptr, *h = nullptr, *xhat = nullptr, *v = nullptr,
+        *gbar = nullptr, *xprox = nullptr, *dual = nullptr;
+  float *b_perm = nullptr, *tab = nullptr, *res = nullptr;
+  int32_t* sched_dev = nullptr;
+  int sched_cap = 0;
+  int32_t* sched_host = nullptr;   // pinned
+  int* order_dev = nullptr;        // subset-major angle order for the solver's N
+  int order_N = 0;
+  std::vector<int> order_off;      // N+1 row offsets of the subsets in subset-major order
+};
+
+}  // namespace vrps
+
+struct vrps_geom {
+  int dims = 2;
+  int nx = 0, ny = 0, nz = 1;
+  double pixel = 1.0;
+  int n_angles = 0;      // angles (2D) or views (3D)
+  int n_bins = 0;        // 2D bins
+  double bin_spacing = 1.0;
+  int nu = 0, nv = 0;
+  double du = 1.0, dv = 1.0, sod = 0.0, sdd = 0.0;
+  int n_subsets = 1;
+  int64_t n = 0, m = 0;
+  int row_len = 0;
+  int device = 0;
+  std::vector<double> angles;
+  // 2D tables
+  vrps::AngleInfo2D* ang2d = nullptr;
+  int adj_fp = 0;        // footprint slots per angle of the 2D adjoint tile
+  int adj_nc = 0;        // candidate bins per pixel and angle
+  // 3D tables
+  vrps::RayInfo3D* ray3d = nullptr;     // [n_views][nu]
+  vrps::ViewInfo3D* view3d = nullptr;   // [n_views]
+  std::vector<vrps::ViewInfo3D> view3d_host;
+  int adj3_nu = 0, adj3_nv = 0;         // candidate window of the 3D adjoint
+  // angle orders
+  int* order_natural = nullptr;   // [n_angles] 0..n_angles-1
+  int* order_subset = nullptr;    // [n_angles] subset-major for n_subsets
+  std::vector<int> subset_off;    // [n_subsets+1]
+  vrps::Workspace ws;
+};
+
+namespace vrps {
+
+// subset -> (device id list, row count, row offset within the subset-major order)
+int subset_rows(const vrps_geom* g, int subset, const int** ids, int* rows);
+int build_order(int n_angles, int N, int** dev, std::vector<int>* off);
+int ensure(float** p, size_t count);
+int ensure_d(double** p, size_t count);
+
+// ---- 2D projector (joseph2d.cu)
+enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_SVRG = 2, FWD_SAGA = 3, FWD_SNAP = 4 };
+struct FwdOut {
+  float* y;           // output rows
+  const float* b;     // data rows (RESID, SAGA, SNAP)
+  float* tab;         // table rows (SVRG read, SAGA read/write, SNAP write)
+};
+int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
+          FwdOut o, cudaStream_t s);
+int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s);
+
+// epilogue of the pixel-driven adjoint, fused ProxSkip update (Algorithm 1, x_hat line)
+struct UpdateArgs {
+  int enabled;            // 0: plain adjoint -> out
+  float* out;             // plain output
+  float cN;               // G = cN * g + gbar
+  float* gbar;            // may be null; SAGA updates it in place (gbar += g)
+  int saga;
+  const float* base;      // point the step starts from (x, or FISTA's y)
+  const float* h;         // control variate (null: not used)
+  float gamma, gamma_over_p;
+  int theta;
+  float* x;               // theta = 0: x <- x_hat
+  float* xT;              // and its transpose (may be null)
+  float* xhat;            // theta = 1 and h in use: keep x_hat
+  float* v;               // theta = 1: prox input
+};
+int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+          cudaStream_t s);
+
+// ---- 3D projector (joseph3d.cu)
+int fwd3d(const vrps_geom* g, const float* x, const int* ids, int rows, int mode, FwdOut o,
+          cudaStream_t s);
+int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+          cudaStream_t s);
+
+// ---- FGP (fgp.cu)
+struct ProxTail {
+  int mode;               // 0: out = x+;  1: solver tail
+  float* out;
+  float* x;               // solver: x <- x+
+  float* xT;              // and transposed (2D, may be null)
+  float* h;               // h += (p/gamma)(x+ - xhat) when non-null
+  const float* xhat;
+  float p_over_gamma;
+  float* xprox;           // copy of x+ (may be null)
+  float* y;               // FISTA: y <- x+ + mom (x+ - x_old); yT likewise
+  float* yT;
+  float mom;
+};
+int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
+            const ProxTail& tail, cudaStream_t s);
+
+// ---- reductions, Philox, misc (reduce.cu)
+int dot64(const float* a, const float* b, int64_t n, double* dst, Workspace& ws, cudaStream_t s);
+int tv64(const vrps_geom* g, const float* x, double* dst, Workspace& ws, cudaStream_t s);
+int philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int N, double p,
+                    int32_t* out, cudaStream_t s);
+int philox_uniform(uint64_t seed, uint32_t job, uint32_t tag, float* out, int64_t n, cudaStream_t s);
+int scale_inv_sqrt(float* dst, const float* src, const double* nrm2, int64_t n, cudaStream_t s);
+int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s);
+int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s);
+int fill(float* p, float v, int64_t n, cudaStream_t s);
+int copy_or_zero(float* dst, const float* src, int64_t n, cudaStream_t s);
+
+// projector dispatch (2D or 3D) used by the solver and the API
+int proj_forward(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows,
+                 int mode, FwdOut o, cudaStream_t s);
+int proj_adjoint(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+                 cudaStream_t s);
+
+}  // namespace vrps

@@ -1,0 +1,141 @@
+"""2D parallel-beam projector: CUDA path (through the C ABI) vs the float64 oracle.
+
+Tolerance: relative L2 error of a single FP32 projection <= 1e-5 against float64.
+Geometries span several tiles and ragged edges (odd sizes, unequal subsets, pixel and
+bin spacings != 1, angles exactly at 0, 45 and 90 degrees)."""
+import math
+
+import numpy as np
+import pytest
+
+from tests._gpu import dev, host, need_gpu, rel, torch
+
+import synthetic
+from oracle import joseph2d as J
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _vr():
+    need_gpu()
+    import paper_2602_09527_gb300 as vr
+    return vr
+
+
+GEOMS = {
+    "par2d_64": dict(nx=64, ny=64, pixel=1.0, angles=synthetic.uniform_angles(90, math.pi), nb=96, ds=1.0, N=10),
+    "ragged": dict(nx=37, ny=53, pixel=0.9, angles=np.concatenate([synthetic.uniform_angles(43, math.pi),
+                                                                   [math.pi / 4, math.pi / 2, 0.0, 3 * math.pi / 4]]),
+                   nb=61, ds=1.1, N=4),
+    "fine_bins": dict(nx=40, ny=24, pixel=1.0, angles=synthetic.uniform_angles(30, math.pi), nb=120, ds=0.45, N=3),
+}
+
+
+def _pair(name):
+    vr = _vr()
+    p = GEOMS[name]
+    g = vr.Geometry.par2d(p["nx"], p["ny"], p["pixel"], p["angles"], p["nb"], p["ds"], p["N"])
+    og = J.Geometry2D(p["nx"], p["ny"], p["pixel"], p["angles"], p["nb"], p["ds"], p["N"])
+    return vr, g, og
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_forward_every_subset(name):
+    vr, g, og = _pair(name)
+    x = np.random.default_rng(1).uniform(size=(og.ny, og.nx))
+    for i in list(range(og.n_subsets)) + [-1]:
+        ids = og.all_angles() if i == -1 else og.subset(i)
+        y = vr.proj_fwd(g, i, dev(x))
+        assert rel(host(y), J.forward(og, x, ids)) < TOL, (name, i)
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_adjoint_every_subset(name):
+    vr, g, og = _pair(name)
+    rng = np.random.default_rng(2)
+    for i in list(range(og.n_subsets)) + [-1]:
+        ids = og.all_angles() if i == -1 else og.subset(i)
+        r = rng.standard_normal((len(ids), og.n_bins))
+        x = vr.proj_adj(g, i, dev(r))
+        assert rel(host(x), J.adjoint(og, r, ids)) < TOL, (name, i)
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_adjoint_identity_fp32(name):
+    vr, g, og = _pair(name)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(og.n)
+    y = rng.standard_normal(og.m)
+    Ax = host(vr.proj_fwd(g, -1, dev(x)))
+    ATy = host(vr.proj_adj(g, -1, dev(y)))
+    xf = x.astype(np.float32).astype(np.float64)
+    yf = y.astype(np.float32).astype(np.float64)
+    lhs, rhs = float(Ax @ yf), float(xf @ ATy)
+    scale = float(np.abs(Ax).sum() * np.abs(yf).max())
+    assert abs(lhs - rhs) <= 2e-6 * scale
+
+
+def test_dense_matrix_small():
+    """Every column of A and every row of A^T from unit vectors, against the oracle's dense A."""
+    vr = _vr()
+    ang = [0.0, 0.3, math.pi / 4, 1.1, math.pi / 2, 2.0, 3 * math.pi / 4, 2.9]
+    g = vr.Geometry.par2d(6, 5, 1.0, ang, 9, 1.0, 2)
+    og = J.Geometry2D(6, 5, 1.0, ang, 9, 1.0, 2)
+    A = J.dense_matrix(og)
+    cols = torch.eye(og.n, device="cuda", dtype=torch.float32)
+    G = np.stack([host(vr.proj_fwd(g, -1, cols[c].contiguous())) for c in range(og.n)], axis=1)
+    assert np.max(np.abs(G - A)) < 1e-5
+    rows = torch.eye(og.m, device="cuda", dtype=torch.float32)
+    GT = np.stack([host(vr.proj_adj(g, -1, rows[r].contiguous())) for r in range(og.m)], axis=0)
+    assert np.max(np.abs(GT - A)) < 1e-5
+
+
+def test_degenerate_sizes():
+    vr = _vr()
+    for (nx, ny, nb, ang) in ((1, 1, 1, [0.0]), (1, 7, 3, [0.2, 1.4]), (9, 1, 5, [math.pi / 2]),
+                              (3, 3, 1, [math.pi / 4])):
+        g = vr.Geometry.par2d(nx, ny, 1.0, ang, nb, 1.0, 1)
+        og = J.Geometry2D(nx, ny, 1.0, ang, nb, 1.0, 1)
+        x = np.random.default_rng(nx * 10 + ny).uniform(size=(ny, nx))
+        y = host(vr.proj_fwd(g, -1, dev(x)))
+        ref = J.forward(og, x, og.all_angles())
+        assert np.max(np.abs(y - ref.ravel())) < 1e-5 * max(1.0, np.abs(ref).max())
+        r = np.random.default_rng(5).standard_normal(og.m)
+        a = host(vr.proj_adj(g, -1, dev(r)))
+        ref = J.adjoint(og, r.reshape(len(ang), nb), og.all_angles())
+        assert np.max(np.abs(a - ref.ravel())) < 1e-5 * max(1.0, np.abs(ref).max())
+
+
+def test_bad_subset_raises():
+    vr, g, og = _pair("par2d_64")
+    x = torch.zeros(og.n, device="cuda")
+    with pytest.raises(vr.VrpsError):
+        vr.proj_fwd(g, og.n_subsets, x, torch.zeros(10, device="cuda"))
+
+
+def test_full_size_512_sampled_angles():
+    """512^2, 720 angles, 768 bins, 20 subsets: the full forward on the GPU, checked row by
+    row on a sample of angles (both marching orientations, 45 and 90 degrees); the full
+    adjoint checked on single-angle sinograms and by the adjoint identity."""
+    vr = _vr()
+    spec = synthetic.Par2DSpec(512, 512, 1.0, synthetic.uniform_angles(720, math.pi), 768, 1.0, 20)
+    g = vr.Geometry.from_spec(spec)
+    og = J.Geometry2D.from_spec(spec)
+    x = synthetic.rasterize_ellipses(synthetic.random_ellipses(10, 256.0, np.random.default_rng(7)),
+                                     512, 512, 1.0)
+    y = host(vr.proj_fwd(g, -1, dev(x))).reshape(720, 768)
+    sample = [0, 1, 97, 180, 263, 360, 500, 719]
+    ref = J.forward(og, x, sample)
+    for k, a in enumerate(sample):
+        assert rel(y[a], ref[k]) < TOL, a
+    # adjoint of a sinogram supported on a few angles
+    rng = np.random.default_rng(8)
+    r = np.zeros((720, 768))
+    r[sample] = rng.standard_normal((len(sample), 768))
+    xa = host(vr.proj_adj(g, -1, dev(r)))
+    assert rel(xa, J.adjoint(og, r[sample], sample)) < TOL
+    # subset forward equals the matching rows of the full forward (same kernels, same rays)
+    ys = host(vr.proj_fwd(g, 7, dev(x))).reshape(-1, 768)
+    assert np.array_equal(ys, y[og.subset(7)])
