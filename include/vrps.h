@@ -98,6 +98,11 @@ int vrps_geom_free(vrps_geom* g);
 int vrps_geom_sizes(const vrps_geom* g, int subset, int64_t* n, int64_t* m, int* rows,
                     int* row_len, int* dims);
 
+/* Number of Joseph samples of subset `subset` (-1: all angles): pairs (ray, dominant-axis
+ * line or plane) at which at least one interpolation tap lies inside the image, counted on
+ * the host in float64.  One sample is one "ray-voxel" of the projector throughput metric. */
+int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
+
 /* ---------------------------------------------------------------- operators
  * y = A_i x  (Section 1.2: the forward operator of subset i; i = -1 for A).
  * x: [n] image.  y: [rows(i) * row_len] sinogram rows of subset i, overwritten.
@@ -138,6 +143,24 @@ int vrps_objective(const vrps_geom* g, const float* x, const float* b, double al
  * 1 when p >= 1, [2] = L-SVRG refresh coin (u2 < floor(2^32 / N)). */
 int vrps_philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int n_subsets,
                          double p, int32_t* out, vrps_stream_t stream);
+
+/* ---------------------------------------------------------------- instrumentation
+ * Launch accounting and kernel timing (no counterpart in the paper; used to measure the
+ * kernels against their roofline).  vrps_kernel_launches(): cumulative number of CUDA
+ * kernels this library has launched in the process.  While profiling is enabled every
+ * launch is bracketed by CUDA events recorded on the launching stream; vrps_profile_read
+ * synchronises the device, folds the elapsed times into per-kernel totals and copies up to
+ * `cap` entries (HOST array) with *count set to the number of kernel families seen.
+ * vrps_profile_enable(0) stops recording and clears the totals. */
+typedef struct vrps_kernel_stat {
+  char name[32];
+  uint64_t launches;
+  double total_ms;
+} vrps_kernel_stat;
+
+uint64_t vrps_kernel_launches(void);
+int vrps_profile_enable(int on);
+int vrps_profile_read(vrps_kernel_stat* out, int cap, int* count);
 
 /* ---------------------------------------------------------------- solver */
 typedef struct vrps_solve_opts {

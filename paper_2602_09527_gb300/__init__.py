@@ -5,8 +5,10 @@ this package is its thin ctypes binding.  Entry points keep the C names without 
 ``vrps_`` prefix: ``proj_fwd``, ``proj_adj``, ``prox_tv``, ``solve``, ``power_iteration``,
 ``objective``, ``philox_schedule`` and the ``Geometry`` handle.
 """
-from ._binding import (ALGOS, ESTIMATORS, Geometry, Report, SolveOpts, VrpsError, lib, objective,
-                       philox_schedule, power_iteration, prox_tv, proj_adj, proj_fwd, solve)
+from ._binding import (ALGOS, ESTIMATORS, Geometry, Report, SolveOpts, VrpsError, kernel_launches, lib,
+                       objective, philox_schedule, power_iteration, profile_enable, profile_read, prox_tv,
+                       proj_adj, proj_fwd, solve)
 
-__all__ = ["ALGOS", "ESTIMATORS", "Geometry", "Report", "SolveOpts", "VrpsError", "lib", "objective",
-           "philox_schedule", "power_iteration", "prox_tv", "proj_adj", "proj_fwd", "solve"]
+__all__ = ["ALGOS", "ESTIMATORS", "Geometry", "Report", "SolveOpts", "VrpsError", "kernel_launches", "lib",
+           "objective", "philox_schedule", "power_iteration", "profile_enable", "profile_read", "prox_tv",
+           "proj_adj", "proj_fwd", "solve"]

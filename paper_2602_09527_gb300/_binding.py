@@ -51,6 +51,10 @@ class Report(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"{_LIB_PATH} is missing: build it with "
@@ -66,6 +70,7 @@ def _load():
         "vrps_geom_cone3d": (i, [i, i, i, d, i, P(d), i, i, d, d, d, d, i, P(vp)]),
         "vrps_geom_free": (i, [vp]),
         "vrps_geom_sizes": (i, [vp, i, P(i64), P(i64), P(i), P(i), P(i)]),
+        "vrps_geom_samples": (i, [vp, i, P(i64)]),
         "vrps_proj_fwd": (i, [vp, i, vp, vp, vp]),
         "vrps_proj_adj": (i, [vp, i, vp, vp, vp]),
         "vrps_prox_tv": (i, [vp, vp, vp, ctypes.c_float, i, i, vp, vp]),
@@ -74,6 +79,9 @@ def _load():
         "vrps_philox_schedule": (i, [u64, u32, i64, i, i, d, vp, vp]),
         "vrps_solve_opts_default": (None, [P(SolveOpts)]),
         "vrps_solve": (i, [vp, vp, d, i, d, d, u64, P(SolveOpts), vp, P(Report), vp]),
+        "vrps_kernel_launches": (u64, []),
+        "vrps_profile_enable": (i, [i]),
+        "vrps_profile_read": (i, [P(KernelStat), i, P(i)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -174,6 +182,12 @@ class Geometry:
         _check(lib.vrps_geom_sizes(self.handle, int(subset), ctypes.byref(n), ctypes.byref(m),
                                    ctypes.byref(rows), ctypes.byref(rl), ctypes.byref(dims)))
         return Sizes(n.value, m.value, rows.value, rl.value, dims.value)
+
+    def samples(self, subset=-1) -> int:
+        """Joseph samples (ray-voxels) of a subset (vrps_geom_samples)."""
+        out = ctypes.c_int64()
+        _check(lib.vrps_geom_samples(self.handle, int(subset), ctypes.byref(out)))
+        return out.value
 
     def close(self):
         if self._h is not None:
@@ -288,3 +302,21 @@ def solve(b: torch.Tensor, g: Geometry, alpha: float, algo: str = "VR_PROXSKIP",
         for e in range(min(rep.evaluations, history_cap)):
             h.append([hist[4 * e + q] for q in range(4)])
     return x_out, rd, h
+
+
+def kernel_launches() -> int:
+    """Cumulative number of CUDA kernels launched by the library in this process."""
+    return int(lib.vrps_kernel_launches())
+
+
+def profile_enable(on: bool = True):
+    _check(lib.vrps_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} of the launches recorded while profiling was on."""
+    cap = 64
+    arr = (KernelStat * cap)()
+    cnt = ctypes.c_int()
+    _check(lib.vrps_profile_read(arr, cap, ctypes.byref(cnt)))
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms)) for k in range(min(cnt.value, cap))}

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 
 #include "vrps_internal.h"
 
@@ -176,6 +177,11 @@ static int build_par2d(vrps_geom* g) {
       t.A2 = (float)(-c / s);
     }
     t.T = rows ? 0 : 1;
+    const double two31 = 2147483648.0;
+    t.A1H = std::llround((rows ? ds / (pix * c) : ds / (pix * s)) * two31);
+    t.A2H = std::llround((rows ? -s / c : -c / s) * two31);
+    t.BxH = std::llround(pix * c / ds * two31);
+    t.ByH = std::llround(pix * s / ds * two31);
     t.wgt = (float)(pix / m);
     t.Bx = (float)(pix * c / ds);
     t.By = (float)(pix * s / ds);
@@ -394,6 +400,82 @@ int vrps_geom_sizes(const vrps_geom* g, int subset, int64_t* n, int64_t* m, int*
   return VRPS_OK;
 }
 
+// integers l in [0, nl) with lo < a + b (l - lc) < hi
+static void open_interval(double a, double b, double lc, double lo, double hi, double* l0, double* l1) {
+  if (b == 0.0) {
+    if (!(a > lo && a < hi)) {
+      *l0 = 1.0;
+      *l1 = 0.0;
+    }
+    return;
+  }
+  double t0 = lc + (lo - a) / b, t1 = lc + (hi - a) / b;
+  if (t0 > t1) std::swap(t0, t1);
+  *l0 = std::fmax(*l0, t0);
+  *l1 = std::fmin(*l1, t1);
+}
+
+static int64_t count_open(double l0, double l1, int nl) {
+  // integers strictly inside (l0, l1), clipped to [0, nl-1]
+  long long a = (long long)std::floor(l0) + 1, b = (long long)std::ceil(l1) - 1;
+  if (a < 0) a = 0;
+  if (b > nl - 1) b = nl - 1;
+  return b >= a ? (int64_t)(b - a + 1) : 0;
+}
+
+int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples) {
+  if (!g || !samples) return fail(VRPS_ERR_INVALID_ARG, "NULL argument");
+  std::vector<int> ids;
+  if (subset == -1) {
+    for (int a = 0; a < g->n_angles; ++a) ids.push_back(a);
+  } else {
+    if (subset < 0 || subset >= g->n_subsets) return fail(VRPS_ERR_INVALID_ARG, "bad subset %d", subset);
+    for (int a = subset; a < g->n_angles; a += g->n_subsets) ids.push_back(a);
+  }
+  int64_t total = 0;
+  if (g->dims == 2) {
+    const double pix = g->pixel, ds = g->bin_spacing, jc = 0.5 * (g->n_bins - 1);
+    for (int a : ids) {
+      const double c = std::cos(g->angles[a]), s = std::sin(g->angles[a]);
+      const bool rows = std::fabs(c) >= std::fabs(s);
+      const int ncols = rows ? g->nx : g->ny, nl = rows ? g->ny : g->nx;
+      const double A1 = rows ? ds / (pix * c) : ds / (pix * s), A2 = rows ? -s / c : -c / s;
+      const double uc = 0.5 * (ncols - 1), lc = 0.5 * (nl - 1);
+      for (int j = 0; j < g->n_bins; ++j) {
+        double l0 = -1e300, l1 = 1e300;
+        open_interval(uc + A1 * (j - jc), A2, lc, -1.0, (double)ncols, &l0, &l1);
+        total += count_open(l0, l1, nl);
+      }
+    }
+  } else {
+    const double vox = g->pixel, cv = 0.5 * (g->nv - 1), cz = 0.5 * (g->nz - 1);
+    for (int a : ids) {
+      const double cb = std::cos(g->angles[a]), sb = std::sin(g->angles[a]);
+      const double Sx = g->sod * cb, Sy = g->sod * sb;
+      const double D0x = -(g->sdd - g->sod) * cb, D0y = -(g->sdd - g->sod) * sb;
+      for (int iu = 0; iu < g->nu; ++iu) {
+        const double u = (iu - (g->nu - 1) / 2.0) * g->du;
+        const double dx = (D0x + u * (-sb)) - Sx, dy = (D0y + u * cb) - Sy;
+        const bool ax0 = std::fabs(dx) >= std::fabs(dy);
+        const double Sa = ax0 ? Sx : Sy, So = ax0 ? Sy : Sx, da = ax0 ? dx : dy, dd = ax0 ? dy : dx;
+        const int nl = ax0 ? g->nx : g->ny, nt = ax0 ? g->ny : g->nx;
+        const double lc = 0.5 * (nl - 1), tc = 0.5 * (nt - 1);
+        const double P0 = tc + (So - Sa * dd / da) / vox, P1 = dd / da;
+        const double Q0 = -Sa * g->dv / (da * vox), Q1 = g->dv / da;
+        for (int iv = 0; iv < g->nv; ++iv) {
+          const double k = iv - cv;
+          double l0 = -1e300, l1 = 1e300;
+          open_interval(P0, P1, lc, -1.0, (double)nt, &l0, &l1);
+          open_interval(cz + k * Q0, k * Q1, lc, -1.0, (double)g->nz, &l0, &l1);
+          if (l1 > l0) total += count_open(l0, l1, nl);
+        }
+      }
+    }
+  }
+  *samples = total;
+  return VRPS_OK;
+}
+
 int vrps_proj_fwd(const vrps_geom* g, int subset, const float* x, float* y, vrps_stream_t stream) {
   VRPS_TRY(check_geom(g));
   if (!x || !y) return fail(VRPS_ERR_INVALID_ARG, "x or y is NULL");
@@ -501,6 +583,117 @@ int vrps_philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int
     return fail(VRPS_ERR_INVALID_ARG, "bad schedule arguments");
   if (k0 < 0) return fail(VRPS_ERR_INVALID_ARG, "k0 must be >= 0");
   return philox_schedule(seed, job, k0, count, n_subsets, p, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ launch accounting
+#include <atomic>
+#include <map>
+#include <mutex>
+
+namespace vrps {
+namespace {
+struct PendingLaunch {
+  const char* name;
+  cudaEvent_t e0, e1;
+};
+struct ProfState {
+  std::atomic<uint64_t> launches{0};
+  std::atomic<bool> on{false};
+  std::mutex mu;
+  std::vector<PendingLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<uint64_t, double>> totals;
+};
+ProfState& prof() {
+  static ProfState* st = new ProfState();   // never destroyed: safe at process exit
+  return *st;
+}
+thread_local PendingLaunch t_open = {nullptr, nullptr, nullptr};
+
+cudaEvent_t take_event(ProfState& st) {
+  if (!st.pool.empty()) {
+    cudaEvent_t e = st.pool.back();
+    st.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+}  // namespace
+
+void launch_begin(const char* name, cudaStream_t s) {
+  ProfState& st = prof();
+  st.launches.fetch_add(1, std::memory_order_relaxed);
+  t_open.name = nullptr;
+  if (!st.on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(st.mu);
+  cudaEvent_t e0 = take_event(st), e1 = take_event(st);
+  if (!e0 || !e1) return;
+  cudaEventRecord(e0, s);
+  t_open = {name, e0, e1};
+}
+
+void launch_end(cudaStream_t s) {
+  if (!t_open.name) return;
+  ProfState& st = prof();
+  cudaEventRecord(t_open.e1, s);
+  std::lock_guard<std::mutex> lk(st.mu);
+  st.pending.push_back(t_open);
+  t_open.name = nullptr;
+}
+
+}  // namespace vrps
+
+extern "C" {
+
+uint64_t vrps_kernel_launches(void) { return vrps::prof().launches.load(); }
+
+int vrps_profile_enable(int on) {
+  vrps::ProfState& st = vrps::prof();
+  std::lock_guard<std::mutex> lk(st.mu);
+  if (!on) {
+    cudaDeviceSynchronize();
+    for (auto& p : st.pending) {
+      st.pool.push_back(p.e0);
+      st.pool.push_back(p.e1);
+    }
+    st.pending.clear();
+    st.totals.clear();
+  }
+  st.on.store(on != 0);
+  return VRPS_OK;
+}
+
+int vrps_profile_read(vrps_kernel_stat* out, int cap, int* count) {
+  vrps::ProfState& st = vrps::prof();
+  std::lock_guard<std::mutex> lk(st.mu);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return vrps::cuda_fail(e, "cudaDeviceSynchronize(profile)");
+  for (auto& p : st.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      auto& t = st.totals[p.name];
+      t.first += 1;
+      t.second += ms;
+    }
+    st.pool.push_back(p.e0);
+    st.pool.push_back(p.e1);
+  }
+  st.pending.clear();
+  int k = 0;
+  for (auto& kv : st.totals) {
+    if (out && k < cap) {
+      std::snprintf(out[k].name, sizeof(out[k].name), "%s", kv.first.c_str());
+      out[k].launches = kv.second.first;
+      out[k].total_ms = kv.second.second;
+    }
+    ++k;
+  }
+  if (count) *count = k;
+  return VRPS_OK;
 }
 
 }  // extern "C"

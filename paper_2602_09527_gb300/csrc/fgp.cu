@@ -231,12 +231,16 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     const int nxt = (k == 0) ? 1 : 3 - cur - prev;
     if (g->dims == 2) {
       dim3 grid((g->nx + FX - 1) / FX, (g->ny + FY - 1) / FY), block(FX, FY);
+      { LaunchScope _ls("fgp2d_iter", s);
       fgp2d_iter<<<grid, block, 0, s>>>(v, buf[cur], buf[prev], buf[nxt], g->nx, g->ny, tau, step,
                                        mom[k], nonneg);
+      }
     } else {
       Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
       dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
+      { LaunchScope _ls("fgp3d_iter", s);
       fgp3d_iter<<<grid, block, 0, s>>>(v, buf[cur], buf[prev], buf[nxt], D, tau, step, mom[k], nonneg);
+      }
     }
     VRPS_LAUNCHED("fgp_iter");
     prev = cur;
@@ -245,11 +249,15 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   float* wdst = (cur != 0) ? dual : nullptr;
   if (g->dims == 2) {
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32), block(32, 8);
+    { LaunchScope _ls("fgp2d_out", s);
     fgp2d_out<<<grid, block, 0, s>>>(v, buf[cur], wdst, g->nx, g->ny, tau, nonneg, tail);
+    }
   } else {
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
     dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
+    { LaunchScope _ls("fgp3d_out", s);
     fgp3d_out<<<grid, block, 0, s>>>(v, buf[cur], wdst, D, tau, nonneg, tail);
+    }
   }
   VRPS_LAUNCHED("fgp_out");
   return VRPS_OK;

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
   const float lc = 0.5f * (float)(nlines - 1);
   float acc = 0.f;
   if (j < P.nb) {
-    const float u0 = fmaf(in.A1, (float)j - P.jc, uc);
+    const float u0 = fmaf(in.A1, (float)j - P.jc, uc);   // line-range clipping only
     int lo = 0, hi = nlines - 1;
     if (in.A2 != 0.f) {
       // lines where the ray's interpolation point is in (-1, ncols); widened by one line
@@ -65,11 +65,14 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
     } else if (!(u0 > -1.f && u0 < (float)ncols)) {
       hi = -1;
     }
-    for (int l = lo + ph; l <= hi; l += FWD_PHASES) {
-      const float u = fmaf(in.A2, (float)l - lc, u0);
-      const float fl = floorf(u);
-      const int i0 = (int)fl;
-      const float f = u - fl;
+    // exact fixed-point walk along the ray: U = u * 2^32
+    const int l0 = lo + ph;
+    long long U = (long long)(ncols - 1) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
+                  in.A2H * (long long)(2 * l0 - (nlines - 1));
+    const long long dU = in.A2H * (2 * FWD_PHASES);
+    for (int l = l0; l <= hi; l += FWD_PHASES, U += dU) {
+      const int i0 = fix_floor(U);
+      const float f = fix_frac(U);
       const float* rp = img + (size_t)l * ncols;
       const float v0 = (i0 >= 0 && i0 < ncols) ? __ldg(rp + i0) : 0.f;
       const float v1 = (i0 + 1 >= 0 && i0 + 1 < ncols) ? __ldg(rp + i0 + 1) : 0.f;
@@ -115,26 +118,31 @@ struct Adj2DParams {
 __global__ void __launch_bounds__(ADJ_T* ADJ_T) adj2d_kernel(Adj2DParams P) {
   extern __shared__ float sm[];  // [chunk][fp]
   __shared__ int s_jlo[ADJ_CHUNK];
+  __shared__ int s_J0[ADJ_CHUNK];
+  __shared__ float s_F0[ADJ_CHUNK];
   __shared__ AngleInfo2D s_ang[ADJ_CHUNK];
   __shared__ float s_tile[ADJ_T][ADJ_T + 1];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_T + tx;
   const int ix0 = blockIdx.x * ADJ_T, iy0 = blockIdx.y * ADJ_T;
   const int ix = ix0 + tx, iy = iy0 + ty;
-  const float px = (float)ix - P.cx, py = (float)iy - P.cy;
-  const float pxa = (float)ix0 - P.cx, pxb = pxa + (float)(ADJ_T - 1);
-  const float pya = (float)iy0 - P.cy, pyb = pya + (float)(ADJ_T - 1);
+  const float ftx = (float)tx, fty = (float)ty;
   float acc = 0.f;
   for (int r0 = 0; r0 < P.rows; r0 += P.chunk) {
     const int nr = min(P.chunk, P.rows - r0);
     if (tid < nr) {
+      // exact fractional bin of the tile origin: t = J0 + F0 (fixed point), then the
+      // pixels of the tile only add small float offsets Bx tx + By ty
       const AngleInfo2D in = P.ang[P.ids[r0 + tid]];
       s_ang[tid] = in;
-      const float t00 = fmaf(in.By, pya, fmaf(in.Bx, pxa, P.jc));
-      const float t10 = fmaf(in.By, pya, fmaf(in.Bx, pxb, P.jc));
-      const float t01 = fmaf(in.By, pyb, fmaf(in.Bx, pxa, P.jc));
-      const float t11 = fmaf(in.By, pyb, fmaf(in.Bx, pxb, P.jc));
-      const float tmin = fminf(fminf(t00, t10), fminf(t01, t11));
-      s_jlo[tid] = (int)floorf(tmin - in.hw) - 1;
+      const long long T0 = (long long)(P.nb - 1) * 2147483648LL + in.BxH * (long long)(2 * ix0 - (P.nx - 1)) +
+                           in.ByH * (long long)(2 * iy0 - (P.ny - 1));
+      const int J0 = fix_floor(T0);
+      const float F0 = fix_frac(T0);
+      const float e = (float)(ADJ_T - 1);
+      const float tmin = F0 + fminf(0.f, in.Bx * e) + fminf(0.f, in.By * e);
+      s_J0[tid] = J0;
+      s_F0[tid] = F0;
+      s_jlo[tid] = J0 + (int)floorf(tmin - in.hw) - 1;
     }
     __syncthreads();
     for (int e = tid; e < nr * P.fp; e += ADJ_T * ADJ_T) {
@@ -145,15 +153,15 @@ __global__ void __launch_bounds__(ADJ_T* ADJ_T) adj2d_kernel(Adj2DParams P) {
     __syncthreads();
     for (int q = 0; q < nr; ++q) {
       const AngleInfo2D in = s_ang[q];
-      const float t = fmaf(in.By, py, fmaf(in.Bx, px, P.jc));
-      const int js = (int)floorf(t - in.hw) + 1;
-      const int jlo = s_jlo[q];
+      const float tr = fmaf(in.By, fty, fmaf(in.Bx, ftx, s_F0[q]));   // t - J0
+      const int js = (int)floorf(tr - in.hw) + 1;                      // first candidate - J0
+      const int off = s_J0[q] - s_jlo[q];
       const float* row = sm + q * P.fp;
       float a = 0.f;
       for (int c = 0; c < P.nc; ++c) {
-        const int j = js + c;
-        const int o = j - jlo;
-        const float w = fmaxf(0.f, 1.f - fabsf((float)j - t) * in.inv_hw);
+        const int jj = js + c;
+        const int o = jj + off;
+        const float w = fmaxf(0.f, 1.f - fabsf((float)jj - tr) * in.inv_hw);
         if (o >= 0 && o < P.fp) a = fmaf(w, row[o], a);
       }
       acc = fmaf(a, in.wgt, acc);
@@ -223,7 +231,9 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 
 int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s) {
   dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
+  { LaunchScope _ls("transpose_kernel", s);
   transpose_kernel<<<grid, block, 0, s>>>(in, out, ny, nx);
+  }
   VRPS_LAUNCHED("transpose2d");
   return VRPS_OK;
 }
@@ -243,11 +253,11 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.o = o;
   dim3 grid((g->n_bins + FWD_LANES - 1) / FWD_LANES, rows), block(FWD_LANES, FWD_PHASES);
   switch (mode) {
-    case FWD_PLAIN: fwd2d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); break;
-    case FWD_RESID: fwd2d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); break;
-    case FWD_SVRG: fwd2d_kernel<FWD_SVRG><<<grid, block, 0, s>>>(P); break;
-    case FWD_SAGA: fwd2d_kernel<FWD_SAGA><<<grid, block, 0, s>>>(P); break;
-    case FWD_SNAP: fwd2d_kernel<FWD_SNAP><<<grid, block, 0, s>>>(P); break;
+    case FWD_PLAIN: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); } break;
+    case FWD_RESID: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); } break;
+    case FWD_SVRG: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_SVRG><<<grid, block, 0, s>>>(P); } break;
+    case FWD_SAGA: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_SAGA><<<grid, block, 0, s>>>(P); } break;
+    case FWD_SNAP: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_SNAP><<<grid, block, 0, s>>>(P); } break;
     default: return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
   }
   VRPS_LAUNCHED("fwd2d");
@@ -274,7 +284,9 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.u = u;
   const size_t smem = sizeof(float) * (size_t)P.chunk * P.fp;
   dim3 grid((g->nx + ADJ_T - 1) / ADJ_T, (g->ny + ADJ_T - 1) / ADJ_T), block(ADJ_T, ADJ_T);
+  { LaunchScope _ls("adj2d_kernel", s);
   adj2d_kernel<<<grid, block, smem, s>>>(P);
+  }
   VRPS_LAUNCHED("adj2d");
   return VRPS_OK;
 }

@@ -223,11 +223,11 @@ int fwd3d(const vrps_geom* g, const float* x, const int* ids, int rows, int mode
   P.o = o;
   dim3 grid((g->nu + 31) / 32, (g->nv + 7) / 8, rows), block(32, 8);
   switch (mode) {
-    case FWD_PLAIN: fwd3d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); break;
-    case FWD_RESID: fwd3d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); break;
-    case FWD_SVRG: fwd3d_kernel<FWD_SVRG><<<grid, block, 0, s>>>(P); break;
-    case FWD_SAGA: fwd3d_kernel<FWD_SAGA><<<grid, block, 0, s>>>(P); break;
-    case FWD_SNAP: fwd3d_kernel<FWD_SNAP><<<grid, block, 0, s>>>(P); break;
+    case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s); fwd3d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); } break;
+    case FWD_RESID: { LaunchScope _ls("fwd3d_kernel", s); fwd3d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); } break;
+    case FWD_SVRG: { LaunchScope _ls("fwd3d_kernel", s); fwd3d_kernel<FWD_SVRG><<<grid, block, 0, s>>>(P); } break;
+    case FWD_SAGA: { LaunchScope _ls("fwd3d_kernel", s); fwd3d_kernel<FWD_SAGA><<<grid, block, 0, s>>>(P); } break;
+    case FWD_SNAP: { LaunchScope _ls("fwd3d_kernel", s); fwd3d_kernel<FWD_SNAP><<<grid, block, 0, s>>>(P); } break;
     default: return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
   }
   VRPS_LAUNCHED("fwd3d");
@@ -253,7 +253,9 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.vox = (float)g->pixel;
   P.u = u;
   dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
+  { LaunchScope _ls("adj3d_kernel", s);
   adj3d_kernel<<<grid, block, 0, s>>>(P);
+  }
   VRPS_LAUNCHED("adj3d");
   return VRPS_OK;
 }

@@ -134,17 +134,25 @@ __global__ void fill_kernel(float* p, float v, int64_t n) {
 }  // namespace
 
 int dot64(const float* a, const float* b, int64_t n, double* dst, Workspace& ws, cudaStream_t s) {
+  { LaunchScope _ls("dot_partial", s);
   dot_partial<<<NPART, RED_THREADS, 0, s>>>(a, b, n, ws.partials);
+  }
   VRPS_LAUNCHED("dot_partial");
+  { LaunchScope _ls("finalize", s);
   finalize<<<1, RED_THREADS, 0, s>>>(ws.partials, NPART, dst);
+  }
   VRPS_LAUNCHED("finalize");
   return VRPS_OK;
 }
 
 int tv64(const vrps_geom* g, const float* x, double* dst, Workspace& ws, cudaStream_t s) {
+  { LaunchScope _ls("tv_partial", s);
   tv_partial<<<NPART, RED_THREADS, 0, s>>>(x, g->nx, g->ny, g->nz, ws.partials);
+  }
   VRPS_LAUNCHED("tv_partial");
+  { LaunchScope _ls("finalize", s);
   finalize<<<1, RED_THREADS, 0, s>>>(ws.partials, NPART, dst);
+  }
   VRPS_LAUNCHED("finalize");
   return VRPS_OK;
 }
@@ -154,21 +162,27 @@ int philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int N, d
   if (count <= 0) return VRPS_OK;
   const int always = p >= 1.0 ? 1 : 0;
   const unsigned long long thr = always ? 0ull : (unsigned long long)std::floor(p * 4294967296.0);
+  { LaunchScope _ls("schedule_kernel", s);
   schedule_kernel<<<(count + 255) / 256, 256, 0, s>>>((uint32_t)seed, (uint32_t)(seed >> 32), job, k0, count,
                                                       (uint32_t)N, thr, always, out);
+  }
   VRPS_LAUNCHED("philox_schedule");
   return VRPS_OK;
 }
 
 int philox_uniform(uint64_t seed, uint32_t job, uint32_t tag, float* out, int64_t n, cudaStream_t s) {
   const int64_t blocks = ((n + 3) / 4 + 255) / 256;
+  { LaunchScope _ls("uniform_kernel", s);
   uniform_kernel<<<(unsigned)blocks, 256, 0, s>>>((uint32_t)seed, (uint32_t)(seed >> 32), job, tag, out, n);
+  }
   VRPS_LAUNCHED("philox_uniform");
   return VRPS_OK;
 }
 
 int scale_inv_sqrt(float* dst, const float* src, const double* nrm2, int64_t n, cudaStream_t s) {
+  { LaunchScope _ls("scale_kernel", s);
   scale_kernel<<<NPART, 256, 0, s>>>(dst, src, nrm2, n);
+  }
   VRPS_LAUNCHED("scale_inv_sqrt");
   return VRPS_OK;
 }
@@ -176,7 +190,9 @@ int scale_inv_sqrt(float* dst, const float* src, const double* nrm2, int64_t n, 
 int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s) {
   if (rows <= 0) return VRPS_OK;
   dim3 grid((row_len + 255) / 256 < 64 ? (row_len + 255) / 256 : 64, rows);
+  { LaunchScope _ls("gather_rows_kernel", s);
   gather_rows_kernel<<<grid, 256, 0, s>>>(src, dst, ids, row_len);
+  }
   VRPS_LAUNCHED("gather_rows");
   return VRPS_OK;
 }
@@ -184,13 +200,17 @@ int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_
 int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s) {
   if (rows <= 0) return VRPS_OK;
   dim3 grid((row_len + 255) / 256 < 64 ? (row_len + 255) / 256 : 64, rows);
+  { LaunchScope _ls("scatter_rows_kernel", s);
   scatter_rows_kernel<<<grid, 256, 0, s>>>(src, dst, ids, row_len);
+  }
   VRPS_LAUNCHED("scatter_rows");
   return VRPS_OK;
 }
 
 int fill(float* p, float v, int64_t n, cudaStream_t s) {
+  { LaunchScope _ls("fill_kernel", s);
   fill_kernel<<<NPART, 256, 0, s>>>(p, v, n);
+  }
   VRPS_LAUNCHED("fill");
   return VRPS_OK;
 }

@@ -34,6 +34,17 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_s != VRPS_OK) return _s;   \
   } while (0)
 
+// ------------------------------------------------------------------ launch accounting
+// Every kernel launch is wrapped in a LaunchScope: it counts the launch and, while
+// profiling is on, records CUDA events around it on the launching stream.
+void launch_begin(const char* name, cudaStream_t s);
+void launch_end(cudaStream_t s);
+struct LaunchScope {
+  cudaStream_t s;
+  LaunchScope(const char* name, cudaStream_t st) : s(st) { launch_begin(name, st); }
+  ~LaunchScope() { launch_end(s); }
+};
+
 // ------------------------------------------------------------------ geometry tables
 // Per-angle constants of the 2D Joseph projector, derived in float64 on the host.
 // Marching frame: T = 0 -> lines are image rows (iy) of x; T = 1 -> lines are columns (ix)
@@ -41,11 +52,24 @@ int cuda_fail(cudaError_t e, const char* what);
 // interpolation axis at u = uc + A1 (j - jc) + A2 (l - lc).  Pixel-driven adjoint: the
 // pixel centre projects to fractional bin t = jc + Bx (ix - cx) + By (iy - cy); bin j gets
 // weight wgt * max(0, 1 - |j - t| * inv_hw).
+//
+// Positions are carried in 64-bit fixed point with 32 fractional bits where float32 would
+// lose precision at large coordinates: A1H, A2H, BxH, ByH hold A1, A2, Bx, By times 2^31, so
+// that u * 2^32 = (ncols-1) 2^31 + A1H (2j-nb+1) + A2H (2l-nlines+1) is exact integer
+// arithmetic up to the rounding of the constants (2^-32 per unit step).
 struct AngleInfo2D {
+  long long A1H, A2H, BxH, ByH;
   float A1, A2, wgt, Bx;
   float By, hw, inv_hw;
   int T;
 };
+
+// Fixed-point helpers: value * 2^32 held in a 64-bit integer.
+__host__ __device__ __forceinline__ int fix_floor(long long v) { return (int)(v >> 32); }
+// fractional part in [0, 1) from the top 23 fraction bits (exact float construction)
+__device__ __forceinline__ float fix_frac(long long v) {
+  return __int_as_float(0x3f800000u | ((unsigned)(unsigned long long)v >> 9)) - 1.0f;
+}
 
 // Per (view, detector column iu) constants of the 3D projector (float64-derived).
 // axis 0: rays marched over x planes; axis 1: over y planes.  On dominant plane index l:

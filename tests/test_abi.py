@@ -17,9 +17,10 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2602_09527_gb300 import _build
-    _build.build()
-    return ctypes.CDLL(_build.LIB)
+    import __graft_entry__
+    b = __graft_entry__._build_module()
+    b.build()
+    return ctypes.CDLL(b.LIB)
 
 
 def test_header_declares_entry_points():
