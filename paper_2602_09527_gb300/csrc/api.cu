@@ -114,7 +114,7 @@ static int check_geom(const vrps_geom* g) {
 }
 
 static void free_ws(Workspace& w) {
-  float** fl[] = {&w.xT, &w.dual_cold, &w.dual_s1, &w.dual_s2, &w.sino, &w.img, &w.img2,
+  float** fl[] = {&w.xT, &w.dual_cold, &w.dual_s1, &w.dual_s2, &w.dual_s3, &w.dual_s4, &w.sino, &w.img, &w.img2,
                   &w.x, &w.xf, &w.xfT, &w.h, &w.xhat, &w.v, &w.gbar, &w.xprox, &w.dual,
                   &w.b_perm, &w.tab, &w.res};
   for (float** p : fl) {
@@ -160,7 +160,6 @@ static int finish_common(vrps_geom* g) {
 // same precision as by any float64 reference).
 static int build_par2d(vrps_geom* g) {
   const double pix = g->pixel, ds = g->bin_spacing;
-  const int TILE = 16;
   std::vector<AngleInfo2D> tab(g->n_angles);
   double span_max = 0.0, hw_max = 0.0;
   for (int a = 0; a < g->n_angles; ++a) {
@@ -187,10 +186,12 @@ static int build_par2d(vrps_geom* g) {
     t.By = (float)(pix * s / ds);
     t.hw = (float)(pix * m / ds);
     t.inv_hw = (float)(ds / (pix * m));
-    span_max = std::fmax(span_max, (TILE - 1) * (std::fabs(pix * c / ds) + std::fabs(pix * s / ds)));
+    span_max = std::fmax(span_max, (ADJ2D_TILE_X - 1) * std::fabs(pix * c / ds) +
+                                       (ADJ2D_TILE_Y - 1) * std::fabs(pix * s / ds));
     hw_max = std::fmax(hw_max, pix * m / ds);
   }
-  g->adj_nc = (int)std::ceil(2.0 * hw_max) + 1;
+  // hw <= 1: at most two bins lie strictly within hw of a pixel's projected centre
+  g->adj_nc = hw_max <= 1.0 ? 2 : (int)std::ceil(2.0 * hw_max) + 1;
   g->adj_fp = (int)std::ceil(span_max) + g->adj_nc + 4;
   VRPS_CUDA(cudaMalloc((void**)&g->ang2d, sizeof(AngleInfo2D) * g->n_angles));
   VRPS_CUDA(cudaMemcpy(g->ang2d, tab.data(), sizeof(AngleInfo2D) * g->n_angles, cudaMemcpyHostToDevice));

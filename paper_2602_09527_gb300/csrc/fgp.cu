@@ -5,9 +5,10 @@
 //   x    = P_+( v + tau div z )            (D^T = -div, forward differences, Neumann)
 //   w'   = P_B( z + D x / (4 d tau) )      (d = 2 or 3)
 //   z'   = w' + mom_k (w' - w)             (mom from t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2)
-// Kernels store only w_k and w_{k-1} and rebuild z on the fly, so one iteration reads
-// v, w_k, w_{k-1} and writes w_{k+1} (7 floats per pixel in 2D, 10 per voxel in 3D).
-// Three dual buffers rotate so that no launch writes a buffer another CTA still reads.
+// Kernels store only w_k and w_{k-1} and rebuild z on the fly.  2D runs FB_T iterations
+// per launch on shared-memory tiles (temporal blocking); 3D runs one iteration per launch
+// (reads v, w_k, w_{k-1}, writes w_{k+1}: 10 floats per voxel) with three rotating buffers,
+// so that no launch writes a buffer another CTA still reads.
 // The output kernel forms x+ = P_+(v + tau div w_K) and applies the fused tail of the
 // solver (x <- x+, h += (p/gamma)(x+ - x_hat), FISTA momentum, transposed copy).
 #include <cmath>
@@ -18,64 +19,115 @@
 namespace vrps {
 namespace {
 
-constexpr int FX = 32, FY = 8;
+// 2D: T iterations per launch (temporal blocking).  A CTA owns a TX x TY output tile and
+// loads v, w_k and w_{k-1} on the tile grown by T pixels on every side; each iteration
+// shrinks the region where values are exact by one pixel per side, so after T iterations
+// the tile itself holds w_{k+T} and w_{k+T-1}, which are written back.  Reads and writes go
+// to different buffer pairs, so neighbouring CTAs never see a half-updated dual.
+constexpr int FB_TX = 32, FB_TY = 16, FB_T = 8;
+constexpr int FB_THREADS = 256;
 
-__global__ void __launch_bounds__(FX* FY) fgp2d_iter(const float* __restrict__ v, const float* wc,
-                                                     const float* wp, float* __restrict__ wn, int nx,
-                                                     int ny, float tau, float step, float mom,
-                                                     int nonneg) {
-  __shared__ float z1[FY + 2][FX + 2];
-  __shared__ float z2[FY + 2][FX + 2];
-  __shared__ float xs[FY + 1][FX + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FX + tx;
-  const int ix0 = blockIdx.x * FX, iy0 = blockIdx.y * FY;
+struct MomBlock {
+  float c[FB_T];
+};
+
+template <int TX, int TY, int T>
+__global__ void __launch_bounds__(FB_THREADS) fgp2d_block(const float* __restrict__ v, const float* __restrict__ wc_g,
+                                                          const float* __restrict__ wp_g, float* __restrict__ wn_g,
+                                                          float* __restrict__ wq_g, int nx, int ny, float tau,
+                                                          float step, MomBlock mom, int nsteps, int nonneg) {
+  constexpr int EX = TX + 2 * T, EY = TY + 2 * T, NE = EX * EY;
+  extern __shared__ float smf[];
+  float* sv = smf;
+  float* c1 = sv + NE;   // current dual (2 components)
+  float* c2 = c1 + NE;
+  float* q1 = c2 + NE;   // previous dual; overwritten by the new one
+  float* q2 = q1 + NE;
+  float* sx = q2 + NE;   // primal x of the current iteration
+  const int tid = threadIdx.x;
+  const int ox = blockIdx.x * TX - T, oy = blockIdx.y * TY - T;
   const size_t n = (size_t)nx * ny;
-  for (int e = tid; e < (FX + 2) * (FY + 2); e += FX * FY) {
-    const int lx = e % (FX + 2), ly = e / (FX + 2);
-    const int gx = ix0 - 1 + lx, gy = iy0 - 1 + ly;
-    float a = 0.f, b = 0.f;
+  for (int e = tid; e < NE; e += FB_THREADS) {
+    const int lx = e % EX, ly = e / EX;
+    const int gx = ox + lx, gy = oy + ly;
+    float vv = 0.f, a = 0.f, b = 0.f, pa = 0.f, pb = 0.f;
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
       const size_t p = (size_t)gy * nx + gx;
-      const float c1 = wc[p], c2 = wc[n + p];
-      if (mom != 0.f) {
-        a = c1 + mom * (c1 - wp[p]);
-        b = c2 + mom * (c2 - wp[n + p]);
-      } else {
-        a = c1;
-        b = c2;
+      vv = v[p];
+      a = wc_g[p];
+      b = wc_g[n + p];
+      pa = wp_g[p];
+      pb = wp_g[n + p];
+    }
+    sv[e] = vv;
+    c1[e] = a;
+    c2[e] = b;
+    q1[e] = pa;
+    q2[e] = pb;
+  }
+  __syncthreads();
+  for (int s = 0; s < nsteps; ++s) {
+    const float m = mom.c[s];
+    // x on [s+1, EX-s) x [s+1, EY-s): needs z at i, i-1, i-EX (z rebuilt from cur and prev)
+    const int lo = s + 1;
+    const int wx = EX - s - lo, wy = EY - s - lo;
+    for (int e = tid; e < wx * wy; e += FB_THREADS) {
+      const int lx = lo + e % wx, ly = lo + e / wx;
+      const int gx = ox + lx, gy = oy + ly;
+      const int i = ly * EX + lx;
+      float xv = 0.f;
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        float d = 0.f;
+        if (gx < nx - 1) d += fmaf(m, c1[i] - q1[i], c1[i]);
+        if (gx > 0) d -= fmaf(m, c1[i - 1] - q1[i - 1], c1[i - 1]);
+        if (gy < ny - 1) d += fmaf(m, c2[i] - q2[i], c2[i]);
+        if (gy > 0) d -= fmaf(m, c2[i - EX] - q2[i - EX], c2[i - EX]);
+        xv = fmaf(tau, d, sv[i]);
+        if (nonneg) xv = fmaxf(xv, 0.f);
       }
+      sx[i] = xv;
     }
-    z1[ly][lx] = a;
-    z2[ly][lx] = b;
+    __syncthreads();
+    // w' on [s+1, EX-s-1) x [s+1, EY-s-1): needs x at i, i+1, i+EX and z at i
+    const int ux = wx - 1, uy = wy - 1;
+    for (int e = tid; e < ux * uy; e += FB_THREADS) {
+      const int lx = lo + e % ux, ly = lo + e / ux;
+      const int gx = ox + lx, gy = oy + ly;
+      const int i = ly * EX + lx;
+      float n1 = 0.f, n2 = 0.f;
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const float xc = sx[i];
+        const float d1 = gx < nx - 1 ? sx[i + 1] - xc : 0.f;
+        const float d2 = gy < ny - 1 ? sx[i + EX] - xc : 0.f;
+        const float z1 = fmaf(m, c1[i] - q1[i], c1[i]);
+        const float z2 = fmaf(m, c2[i] - q2[i], c2[i]);
+        const float g1 = fmaf(step, d1, z1), g2 = fmaf(step, d2, z2);
+        const float den = fmaxf(1.f, sqrtf(g1 * g1 + g2 * g2));
+        n1 = g1 / den;
+        n2 = g2 / den;
+      }
+      q1[i] = n1;
+      q2[i] = n2;
+    }
+    __syncthreads();
+    float* t1 = c1;
+    c1 = q1;
+    q1 = t1;
+    float* t2 = c2;
+    c2 = q2;
+    q2 = t2;
   }
-  __syncthreads();
-  for (int e = tid; e < (FX + 1) * (FY + 1); e += FX * FY) {
-    const int lx = e % (FX + 1), ly = e / (FX + 1);
-    const int gx = ix0 + lx, gy = iy0 + ly;
-    float xv = 0.f;
+  for (int e = tid; e < TX * TY; e += FB_THREADS) {
+    const int lx = T + e % TX, ly = T + e / TX;
+    const int gx = ox + lx, gy = oy + ly;
     if (gx < nx && gy < ny) {
-      float d = 0.f;
-      if (gx < nx - 1) d += z1[ly + 1][lx + 1];
-      if (gx > 0) d -= z1[ly + 1][lx];
-      if (gy < ny - 1) d += z2[ly + 1][lx + 1];
-      if (gy > 0) d -= z2[ly][lx + 1];
-      xv = fmaf(tau, d, v[(size_t)gy * nx + gx]);
-      if (nonneg) xv = fmaxf(xv, 0.f);
+      const size_t p = (size_t)gy * nx + gx;
+      const int i = ly * EX + lx;
+      wn_g[p] = c1[i];
+      wn_g[n + p] = c2[i];
+      wq_g[p] = q1[i];
+      wq_g[n + p] = q2[i];
     }
-    xs[ly][lx] = xv;
-  }
-  __syncthreads();
-  const int gx = ix0 + tx, gy = iy0 + ty;
-  if (gx < nx && gy < ny) {
-    const float xc = xs[ty][tx];
-    const float d1 = gx < nx - 1 ? xs[ty][tx + 1] - xc : 0.f;
-    const float d2 = gy < ny - 1 ? xs[ty + 1][tx] - xc : 0.f;
-    const float q1 = fmaf(step, d1, z1[ty + 1][tx + 1]);
-    const float q2 = fmaf(step, d2, z2[ty + 1][tx + 1]);
-    const float den = fmaxf(1.f, sqrtf(q1 * q1 + q2 * q2));
-    const size_t p = (size_t)gy * nx + gx;
-    wn[p] = q1 / den;
-    wn[n + p] = q2 / den;
   }
 }
 
@@ -207,10 +259,15 @@ __global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, co
 int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
             const ProxTail& tail, cudaStream_t s) {
   vrps_geom* gm = const_cast<vrps_geom*>(g);
+  Workspace& ws = gm->ws;
   const size_t dn = (size_t)g->dims * (size_t)g->n;
   if (iters > 0) {
-    VRPS_TRY(ensure(&gm->ws.dual_s1, dn));
-    VRPS_TRY(ensure(&gm->ws.dual_s2, dn));
+    VRPS_TRY(ensure(&ws.dual_s1, dn));
+    VRPS_TRY(ensure(&ws.dual_s2, dn));
+    if (g->dims == 2) {
+      VRPS_TRY(ensure(&ws.dual_s3, dn));
+      VRPS_TRY(ensure(&ws.dual_s4, dn));
+    }
   }
   // momentum coefficients in float64: t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2,
   // iteration k (k >= 1) extrapolates with (t_{k-1} - 1)/t_k, iteration 0 with 0.
@@ -225,38 +282,64 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     }
   }
   const float step = (float)(1.0 / (4.0 * g->dims * (double)tau));
-  float* buf[3] = {dual, gm->ws.dual_s1, gm->ws.dual_s2};
-  int cur = 0, prev = 0;
-  for (int k = 0; k < iters; ++k) {
-    const int nxt = (k == 0) ? 1 : 3 - cur - prev;
-    if (g->dims == 2) {
-      dim3 grid((g->nx + FX - 1) / FX, (g->ny + FY - 1) / FY), block(FX, FY);
-      { LaunchScope _ls("fgp2d_iter", s);
-      fgp2d_iter<<<grid, block, 0, s>>>(v, buf[cur], buf[prev], buf[nxt], g->nx, g->ny, tau, step,
-                                       mom[k], nonneg);
+  const float* w_final = dual;
+  if (g->dims == 2) {
+    // blocks of FB_T iterations; buffer pairs alternate (s1,s2) <-> (s3,s4)
+    const float* rc = dual;
+    const float* rp = dual;
+    float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
+    int which = 0;
+    constexpr int EX = FB_TX + 2 * FB_T, EY = FB_TY + 2 * FB_T;
+    const size_t smem = sizeof(float) * 6 * EX * EY;
+    static_assert(sizeof(float) * 6 * EX * EY <= 48 * 1024, "FGP tile exceeds the default shared-memory size");
+    dim3 grid((g->nx + FB_TX - 1) / FB_TX, (g->ny + FB_TY - 1) / FB_TY);
+    for (int k0 = 0; k0 < iters; k0 += FB_T) {
+      const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
+      MomBlock mb;
+      for (int q = 0; q < FB_T; ++q) mb.c[q] = q < ns ? mom[k0 + q] : 0.f;
+      float* wn = pairs[which][0];
+      float* wq = pairs[which][1];
+      {
+        LaunchScope _ls("fgp2d_block", s);
+        fgp2d_block<FB_TX, FB_TY, FB_T><<<grid, FB_THREADS, smem, s>>>(v, rc, rp, wn, wq, g->nx, g->ny, tau, step,
+                                                                        mb, ns, nonneg);
       }
-    } else {
+      VRPS_LAUNCHED("fgp2d_block");
+      rc = wn;
+      rp = wq;
+      which ^= 1;
+    }
+    w_final = rc;
+  } else {
+    float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};
+    int cur = 0, prev = 0;
+    for (int k = 0; k < iters; ++k) {
+      const int nxt = (k == 0) ? 1 : 3 - cur - prev;
       Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
       dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
-      { LaunchScope _ls("fgp3d_iter", s);
-      fgp3d_iter<<<grid, block, 0, s>>>(v, buf[cur], buf[prev], buf[nxt], D, tau, step, mom[k], nonneg);
+      {
+        LaunchScope _ls("fgp3d_iter", s);
+        fgp3d_iter<<<grid, block, 0, s>>>(v, buf[cur], buf[prev], buf[nxt], D, tau, step, mom[k], nonneg);
       }
+      VRPS_LAUNCHED("fgp_iter");
+      prev = cur;
+      cur = nxt;
     }
-    VRPS_LAUNCHED("fgp_iter");
-    prev = cur;
-    cur = nxt;
+    w_final = buf[cur];
   }
-  float* wdst = (cur != 0) ? dual : nullptr;
+  float* wdst = (w_final != dual) ? dual : nullptr;
   if (g->dims == 2) {
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32), block(32, 8);
-    { LaunchScope _ls("fgp2d_out", s);
-    fgp2d_out<<<grid, block, 0, s>>>(v, buf[cur], wdst, g->nx, g->ny, tau, nonneg, tail);
+    {
+      LaunchScope _ls("fgp2d_out", s);
+      fgp2d_out<<<grid, block, 0, s>>>(v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail);
     }
   } else {
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
     dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
-    { LaunchScope _ls("fgp3d_out", s);
-    fgp3d_out<<<grid, block, 0, s>>>(v, buf[cur], wdst, D, tau, nonneg, tail);
+    {
+      LaunchScope _ls("fgp3d_out", s);
+      fgp3d_out<<<grid, block, 0, s>>>(v, w_final, wdst, D, tau, nonneg, tail);
     }
   }
   VRPS_LAUNCHED("fgp_out");

@@ -18,8 +18,10 @@ namespace vrps {
 namespace {
 
 constexpr int FWD_LANES = 32;
-constexpr int FWD_PHASES = 8;
-constexpr int ADJ_T = 16;
+constexpr int FWD_PHASES = 16;
+constexpr int ADJ_TX = ADJ2D_TILE_X;   // pixel tile: 16 columns x 32 rows, 2 pixels per thread
+constexpr int ADJ_TY = ADJ2D_TILE_Y;
+constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_CHUNK = 64;
 
 struct Fwd2DParams {
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
   const int nlines = tr ? P.nx : P.ny;
   const float uc = 0.5f * (float)(ncols - 1);
   const float lc = 0.5f * (float)(nlines - 1);
-  float acc = 0.f;
+  float acc0 = 0.f, acc1 = 0.f;
   if (j < P.nb) {
     const float u0 = fmaf(in.A1, (float)j - P.jc, uc);   // line-range clipping only
     int lo = 0, hi = nlines - 1;
@@ -70,16 +72,35 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
     long long U = (long long)(ncols - 1) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
                   in.A2H * (long long)(2 * l0 - (nlines - 1));
     const long long dU = in.A2H * (2 * FWD_PHASES);
-    for (int l = l0; l <= hi; l += FWD_PHASES, U += dU) {
+    const float* rp = img + (size_t)l0 * ncols;
+    const size_t dp = (size_t)FWD_PHASES * ncols;
+    const unsigned nc = (unsigned)ncols;
+    int l = l0;
+#pragma unroll 2
+    for (; l + FWD_PHASES <= hi; l += 2 * FWD_PHASES) {
       const int i0 = fix_floor(U);
       const float f = fix_frac(U);
-      const float* rp = img + (size_t)l * ncols;
-      const float v0 = (i0 >= 0 && i0 < ncols) ? __ldg(rp + i0) : 0.f;
-      const float v1 = (i0 + 1 >= 0 && i0 + 1 < ncols) ? __ldg(rp + i0 + 1) : 0.f;
-      acc += fmaf(f, v1 - v0, v0);
+      const int i1 = fix_floor(U + dU);
+      const float f1 = fix_frac(U + dU);
+      const float* rq = rp + dp;
+      const float a0 = ((unsigned)i0 < nc) ? __ldg(rp + i0) : 0.f;
+      const float a1 = ((unsigned)(i0 + 1) < nc) ? __ldg(rp + i0 + 1) : 0.f;
+      const float b0 = ((unsigned)i1 < nc) ? __ldg(rq + i1) : 0.f;
+      const float b1 = ((unsigned)(i1 + 1) < nc) ? __ldg(rq + i1 + 1) : 0.f;
+      acc0 += fmaf(f, a1 - a0, a0);
+      acc1 += fmaf(f1, b1 - b0, b0);
+      U += 2 * dU;
+      rp += 2 * dp;
+    }
+    if (l <= hi) {
+      const int i0 = fix_floor(U);
+      const float f = fix_frac(U);
+      const float a0 = ((unsigned)i0 < nc) ? __ldg(rp + i0) : 0.f;
+      const float a1 = ((unsigned)(i0 + 1) < nc) ? __ldg(rp + i0 + 1) : 0.f;
+      acc0 += fmaf(f, a1 - a0, a0);
     }
   }
-  red[ph][lane] = acc;
+  red[ph][lane] = acc0 + acc1;
   __syncthreads();
   if (ph == 0 && j < P.nb) {
     float s = 0.f;
@@ -110,106 +131,144 @@ struct Adj2DParams {
   const int* ids;
   int rows;
   int nx, ny, nb;
-  float jc, cx, cy;
   int fp, nc, chunk;
   UpdateArgs u;
 };
 
-__global__ void __launch_bounds__(ADJ_T* ADJ_T) adj2d_kernel(Adj2DParams P) {
-  extern __shared__ float sm[];  // [chunk][fp]
+// Algorithm 1, estimator and x_hat lines for one pixel: G = cN g + gbar,
+// x_hat = base - gamma (G - h); theta = 0: x <- x_hat (returned for the transposed copy);
+// theta = 1: keep x_hat and write the prox input v = x_hat - (gamma/p) h.
+__device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, float g) {
+  float G = u.cN * g;
+  if (u.gbar) {
+    const float gb = u.gbar[p];
+    G += gb;
+    if (u.saga) u.gbar[p] = gb + g;
+  }
+  const float base = u.base[p];
+  if (u.h) {
+    const float hp = u.h[p];
+    const float xh = base - u.gamma * (G - hp);
+    if (u.theta) {
+      u.xhat[p] = xh;
+      u.v[p] = xh - u.gamma_over_p * hp;
+      return 0.f;
+    }
+    u.x[p] = xh;
+    return xh;
+  }
+  const float xh = base - u.gamma * G;
+  if (u.theta) {
+    u.v[p] = xh;
+    return 0.f;
+  }
+  u.x[p] = xh;
+  return xh;
+}
+
+// Pixel-driven transpose.  Per angle of a chunk, one thread stages the tile's detector
+// footprint: the tile origin's fractional bin t0 = J0 + F0 is exact (fixed point); the
+// footprint r[jlo .. jlo+fp) is copied to shared memory pre-multiplied by the angle's
+// length factor.  A pixel at tile offset (tx, ty) then has t - J0 = F0 + Bx tx + By ty (a
+// small float) and receives max(0, 1 - |j - t|/hw) r_j from the bins within hw of t.
+// NC = 2 covers hw <= 1 (bins not finer than pixels): two candidates, unrolled; NC = 0 is
+// the general loop over P.nc candidates.
+template <int NC>
+__global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
+  extern __shared__ float sm[];                  // [chunk][fp]
+  __shared__ float4 s_par[ADJ_CHUNK];            // Bx, By, (F0 - hw), 1/hw
+  __shared__ float s_c0[ADJ_CHUNK];              // 1 - hw
+  __shared__ int s_off[ADJ_CHUNK];               // J0 - jlo
   __shared__ int s_jlo[ADJ_CHUNK];
-  __shared__ int s_J0[ADJ_CHUNK];
-  __shared__ float s_F0[ADJ_CHUNK];
-  __shared__ AngleInfo2D s_ang[ADJ_CHUNK];
-  __shared__ float s_tile[ADJ_T][ADJ_T + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_T + tx;
-  const int ix0 = blockIdx.x * ADJ_T, iy0 = blockIdx.y * ADJ_T;
-  const int ix = ix0 + tx, iy = iy0 + ty;
+  __shared__ float s_wgt[ADJ_CHUNK];
+  __shared__ float s_tile[ADJ_TY][ADJ_TX + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_TX + tx;
+  const int ix0 = blockIdx.x * ADJ_TX, iy0 = blockIdx.y * ADJ_TY;
   const float ftx = (float)tx, fty = (float)ty;
-  float acc = 0.f;
+  const float half_rows = (float)(ADJ_TY / 2);
+  float acc0 = 0.f, acc1 = 0.f;                  // pixels (tx, ty) and (tx, ty + ADJ_TY/2)
   for (int r0 = 0; r0 < P.rows; r0 += P.chunk) {
     const int nr = min(P.chunk, P.rows - r0);
     if (tid < nr) {
-      // exact fractional bin of the tile origin: t = J0 + F0 (fixed point), then the
-      // pixels of the tile only add small float offsets Bx tx + By ty
       const AngleInfo2D in = P.ang[P.ids[r0 + tid]];
-      s_ang[tid] = in;
       const long long T0 = (long long)(P.nb - 1) * 2147483648LL + in.BxH * (long long)(2 * ix0 - (P.nx - 1)) +
                            in.ByH * (long long)(2 * iy0 - (P.ny - 1));
       const int J0 = fix_floor(T0);
       const float F0 = fix_frac(T0);
-      const float e = (float)(ADJ_T - 1);
-      const float tmin = F0 + fminf(0.f, in.Bx * e) + fminf(0.f, in.By * e);
-      s_J0[tid] = J0;
-      s_F0[tid] = F0;
-      s_jlo[tid] = J0 + (int)floorf(tmin - in.hw) - 1;
+      const float tmin = F0 + fminf(0.f, in.Bx * (float)(ADJ_TX - 1)) + fminf(0.f, in.By * (float)(ADJ_TY - 1));
+      const int jlo = J0 + (int)floorf(tmin - in.hw) - 1;
+      s_par[tid] = make_float4(in.Bx, in.By, F0 - in.hw, in.inv_hw);
+      s_c0[tid] = 1.f - in.hw;
+      s_off[tid] = J0 - jlo;
+      s_jlo[tid] = jlo;
+      s_wgt[tid] = in.wgt;
     }
     __syncthreads();
-    for (int e = tid; e < nr * P.fp; e += ADJ_T * ADJ_T) {
+    for (int e = tid; e < nr * P.fp; e += ADJ_THREADS) {
       const int q = e / P.fp;
       const int j = s_jlo[q] + (e - q * P.fp);
-      sm[e] = (j >= 0 && j < P.nb) ? __ldg(P.r + (size_t)(r0 + q) * P.nb + j) : 0.f;
+      sm[e] = (j >= 0 && j < P.nb) ? s_wgt[q] * __ldg(P.r + (size_t)(r0 + q) * P.nb + j) : 0.f;
     }
     __syncthreads();
     for (int q = 0; q < nr; ++q) {
-      const AngleInfo2D in = s_ang[q];
-      const float tr = fmaf(in.By, fty, fmaf(in.Bx, ftx, s_F0[q]));   // t - J0
-      const int js = (int)floorf(tr - in.hw) + 1;                      // first candidate - J0
-      const int off = s_J0[q] - s_jlo[q];
-      const float* row = sm + q * P.fp;
-      float a = 0.f;
-      for (int c = 0; c < P.nc; ++c) {
-        const int jj = js + c;
-        const int o = jj + off;
-        const float w = fmaxf(0.f, 1.f - fabsf((float)jj - tr) * in.inv_hw);
-        if (o >= 0 && o < P.fp) a = fmaf(w, row[o], a);
+      const float4 pr = s_par[q];
+      const float* row = sm + q * P.fp + s_off[q] + 1;   // row[floor(ua)] = first candidate
+      const float ua = fmaf(pr.y, fty, fmaf(pr.x, ftx, pr.z));   // (t - J0) - hw
+      const float ub = fmaf(pr.y, half_rows, ua);
+      if (NC == 2) {
+        const float c0 = s_c0[q];
+        {
+          const float fl = floorf(ua);
+          const float d0 = c0 - (ua - fl);
+          const float w0 = fmaxf(0.f, fmaf(-fabsf(d0), pr.w, 1.f));
+          const float w1 = fmaxf(0.f, fmaf(-(d0 + 1.f), pr.w, 1.f));
+          const float* rr = row + (int)fl;
+          acc0 = fmaf(w0, rr[0], acc0);
+          acc0 = fmaf(w1, rr[1], acc0);
+        }
+        {
+          const float fl = floorf(ub);
+          const float d0 = c0 - (ub - fl);
+          const float w0 = fmaxf(0.f, fmaf(-fabsf(d0), pr.w, 1.f));
+          const float w1 = fmaxf(0.f, fmaf(-(d0 + 1.f), pr.w, 1.f));
+          const float* rr = row + (int)fl;
+          acc1 = fmaf(w0, rr[0], acc1);
+          acc1 = fmaf(w1, rr[1], acc1);
+        }
+      } else {
+        const float hw = 1.f - s_c0[q];
+        const float fa = floorf(ua), fb = floorf(ub);
+        const float* ra = row + (int)fa;
+        const float* rb = row + (int)fb;
+        const float da = fa + 1.f - (ua + hw), db = fb + 1.f - (ub + hw);   // first candidate - t
+        for (int c = 0; c < P.nc; ++c) {
+          acc0 = fmaf(fmaxf(0.f, fmaf(-fabsf(da + (float)c), pr.w, 1.f)), ra[c], acc0);
+          acc1 = fmaf(fmaxf(0.f, fmaf(-fabsf(db + (float)c), pr.w, 1.f)), rb[c], acc1);
+        }
       }
-      acc = fmaf(a, in.wgt, acc);
     }
     __syncthreads();
   }
-  const bool inside = ix < P.nx && iy < P.ny;
-  const size_t p = (size_t)iy * P.nx + ix;
+  const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + ADJ_TY / 2;
+  const bool in0 = ix < P.nx && iy < P.ny, in1 = ix < P.nx && iy1 < P.ny;
+  const size_t p0 = (size_t)iy * P.nx + ix, p1 = (size_t)iy1 * P.nx + ix;
   const UpdateArgs& u = P.u;
   if (!u.enabled) {
-    if (inside) u.out[p] = acc;
+    if (in0) u.out[p0] = acc0;
+    if (in1) u.out[p1] = acc1;
     return;
   }
-  // Algorithm 1, estimator + x_hat lines: G = cN g + gbar; x_hat = base - gamma (G - h)
-  float xnew = 0.f;
-  if (inside) {
-    float G = u.cN * acc;
-    if (u.gbar) {
-      const float gb = u.gbar[p];
-      G += gb;
-      if (u.saga) u.gbar[p] = gb + acc;
-    }
-    const float base = u.base[p];
-    if (u.h) {
-      const float hp = u.h[p];
-      const float xh = base - u.gamma * (G - hp);
-      if (u.theta) {
-        u.xhat[p] = xh;
-        u.v[p] = xh - u.gamma_over_p * hp;
-      } else {
-        u.x[p] = xh;
-        xnew = xh;
-      }
-    } else {
-      const float xh = base - u.gamma * G;
-      if (u.theta) {
-        u.v[p] = xh;
-      } else {
-        u.x[p] = xh;
-        xnew = xh;
-      }
-    }
-  }
+  const float x0 = in0 ? update_pixel(u, p0, acc0) : 0.f;
+  const float x1 = in1 ? update_pixel(u, p1, acc1) : 0.f;
   if (!u.theta && u.xT) {
-    s_tile[ty][tx] = xnew;
+    s_tile[ty][tx] = x0;
+    s_tile[ty + ADJ_TY / 2][tx] = x1;
     __syncthreads();
-    const int ox = ix0 + ty, oy = iy0 + tx;
-    if (ox < P.nx && oy < P.ny) u.xT[(size_t)ox * P.ny + oy] = s_tile[tx][ty];
+    for (int e = tid; e < ADJ_TX * ADJ_TY; e += ADJ_THREADS) {
+      const int c = e / ADJ_TY, r = e - c * ADJ_TY;
+      const int ox = ix0 + c, oy = iy0 + r;
+      if (ox < P.nx && oy < P.ny) u.xT[(size_t)ox * P.ny + oy] = s_tile[r][c];
+    }
   }
 }
 
@@ -274,18 +333,21 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.nx = g->nx;
   P.ny = g->ny;
   P.nb = g->n_bins;
-  P.jc = 0.5f * (float)(g->n_bins - 1);
-  P.cx = 0.5f * (float)(g->nx - 1);
-  P.cy = 0.5f * (float)(g->ny - 1);
   P.fp = g->adj_fp;
   P.nc = g->adj_nc;
-  int chunk = (int)(48 * 1024 / (sizeof(float) * (size_t)g->adj_fp));
+  int chunk = (int)(96 * 1024 / (sizeof(float) * (size_t)g->adj_fp));
   P.chunk = chunk < ADJ_CHUNK ? (chunk < 1 ? 1 : chunk) : ADJ_CHUNK;
   P.u = u;
   const size_t smem = sizeof(float) * (size_t)P.chunk * P.fp;
-  dim3 grid((g->nx + ADJ_T - 1) / ADJ_T, (g->ny + ADJ_T - 1) / ADJ_T), block(ADJ_T, ADJ_T);
-  { LaunchScope _ls("adj2d_kernel", s);
-  adj2d_kernel<<<grid, block, smem, s>>>(P);
+  dim3 grid((g->nx + ADJ_TX - 1) / ADJ_TX, (g->ny + ADJ_TY - 1) / ADJ_TY), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
+  if (g->adj_nc == 2) {
+    if (smem > 48 * 1024) VRPS_CUDA(cudaFuncSetAttribute(adj2d_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope _ls("adj2d_kernel", s);
+    adj2d_kernel<2><<<grid, block, smem, s>>>(P);
+  } else {
+    if (smem > 48 * 1024) VRPS_CUDA(cudaFuncSetAttribute(adj2d_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope _ls("adj2d_kernel", s);
+    adj2d_kernel<0><<<grid, block, smem, s>>>(P);
   }
   VRPS_LAUNCHED("adj2d");
   return VRPS_OK;

@@ -198,7 +198,6 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   const float fgamma = (float)gamma, fgp = (float)(gamma / p), fpg = (float)(p / gamma);
   double t_fista = 1.0;
   int status = VRPS_OK;
-  double elapsed_eval = 0.0;
   int k = 0;
   for (; k < K; ++k) {
     const int i = w.sched_host[3 * k + 0];
@@ -313,7 +312,6 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
         row[3] = r.passes;
       }
       r.evaluations += 1;
-      (void)elapsed_eval;
       if (!std::isfinite(F)) {
         status = fail(VRPS_ERR_DIVERGED, "objective is not finite at iteration %d", k + 1);
         ++k;

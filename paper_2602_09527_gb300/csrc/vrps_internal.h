@@ -71,6 +71,10 @@ __device__ __forceinline__ float fix_frac(long long v) {
   return __int_as_float(0x3f800000u | ((unsigned)(unsigned long long)v >> 9)) - 1.0f;
 }
 
+// pixel tile of the 2D adjoint (the footprint size is derived from it on the host)
+constexpr int ADJ2D_TILE_X = 16;
+constexpr int ADJ2D_TILE_Y = 32;
+
 // Per (view, detector column iu) constants of the 3D projector (float64-derived).
 // axis 0: rays marched over x planes; axis 1: over y planes.  On dominant plane index l:
 //   transverse index  ft = P0 + P1 (l - lc)
@@ -100,6 +104,8 @@ struct Workspace {
   float* dual_cold = nullptr;   // [dims n] zero dual for cold-start prox calls
   float* dual_s1 = nullptr;     // [dims n] FGP rotation buffers
   float* dual_s2 = nullptr;
+  float* dual_s3 = nullptr;
+  float* dual_s4 = nullptr;
   double* partials = nullptr;   // reduction partials
   double* scalars = nullptr;    // [16] device scalars
   float* sino = nullptr;        // [m] sinogram scratch
