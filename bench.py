@@ -173,12 +173,15 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default="par2d_512", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--alpha", type=float, default=None, help="override the workload's TV weight")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     wl = args.workload
     w = WORKLOADS[wl]
+    if args.alpha is not None:
+        w["alpha"] = args.alpha
 
     if args.impl == "reference":
         return reference_arm(args, rank, world)

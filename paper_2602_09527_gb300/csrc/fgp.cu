@@ -20,113 +20,118 @@ namespace vrps {
 namespace {
 
 // 2D: T iterations per launch (temporal blocking).  A CTA owns a TX x TY output tile and
-// loads v, w_k and w_{k-1} on the tile grown by T pixels on every side; each iteration
-// shrinks the region where values are exact by one pixel per side, so after T iterations
-// the tile itself holds w_{k+T} and w_{k+T-1}, which are written back.  Reads and writes go
-// to different buffer pairs, so neighbouring CTAs never see a half-updated dual.
+// loads v, the dual w and the extrapolated dual z on the tile grown by T pixels on every
+// side; each iteration shrinks the region where values are exact by one pixel per side, so
+// after T iterations the tile itself holds w_{k+T} and z_{k+T}, which are written back.
+// Per iteration: x = P_+(v + tau div z) on the region, then per pixel
+// w' = P_B(z + step D x) and the next extrapolation z' = w' + mom' (w' - w), both in place
+// (each only reads its own pixel's w and z).  Reads and writes go to different buffer
+// pairs, so neighbouring CTAs never see a half-updated dual.
 constexpr int FB_TX = 32, FB_TY = 16, FB_T = 8;
-constexpr int FB_THREADS = 256;
+constexpr int FB_BX = 32, FB_BY = 8;   // threads
 
 struct MomBlock {
-  float c[FB_T];
+  float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
 };
 
 template <int TX, int TY, int T>
-__global__ void __launch_bounds__(FB_THREADS) fgp2d_block(const float* __restrict__ v, const float* __restrict__ wc_g,
-                                                          const float* __restrict__ wp_g, float* __restrict__ wn_g,
-                                                          float* __restrict__ wq_g, int nx, int ny, float tau,
-                                                          float step, MomBlock mom, int nsteps, int nonneg) {
+__global__ void __launch_bounds__(FB_BX* FB_BY) fgp2d_block(const float* __restrict__ v, const float* __restrict__ w_g,
+                                                            const float* __restrict__ z_g, float* __restrict__ wn_g,
+                                                            float* __restrict__ zn_g, int nx, int ny, float tau,
+                                                            float step, MomBlock mom, int nsteps, int nonneg) {
   constexpr int EX = TX + 2 * T, EY = TY + 2 * T, NE = EX * EY;
-  extern __shared__ float smf[];
-  float* sv = smf;
-  float* c1 = sv + NE;   // current dual (2 components)
-  float* c2 = c1 + NE;
-  float* q1 = c2 + NE;   // previous dual; overwritten by the new one
-  float* q2 = q1 + NE;
-  float* sx = q2 + NE;   // primal x of the current iteration
-  const int tid = threadIdx.x;
+  __shared__ float sv[NE], w1[NE], w2[NE], z1[NE], z2[NE], sx[NE];
+  const int tx = threadIdx.x, ty = threadIdx.y;
   const int ox = blockIdx.x * TX - T, oy = blockIdx.y * TY - T;
   const size_t n = (size_t)nx * ny;
-  for (int e = tid; e < NE; e += FB_THREADS) {
-    const int lx = e % EX, ly = e / EX;
-    const int gx = ox + lx, gy = oy + ly;
-    float vv = 0.f, a = 0.f, b = 0.f, pa = 0.f, pb = 0.f;
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-      const size_t p = (size_t)gy * nx + gx;
-      vv = v[p];
-      a = wc_g[p];
-      b = wc_g[n + p];
-      pa = wp_g[p];
-      pb = wp_g[n + p];
+  for (int ly = ty; ly < EY; ly += FB_BY) {
+    const int gy = oy + ly;
+    for (int lx = tx; lx < EX; lx += FB_BX) {
+      const int gx = ox + lx;
+      const int i = ly * EX + lx;
+      float vv = 0.f, a = 0.f, b = 0.f, za = 0.f, zb = 0.f;
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        const size_t p = (size_t)gy * nx + gx;
+        vv = v[p];
+        a = w_g[p];
+        b = w_g[n + p];
+        za = z_g[p];
+        zb = z_g[n + p];
+      }
+      sv[i] = vv;
+      w1[i] = a;
+      w2[i] = b;
+      z1[i] = za;
+      z2[i] = zb;
     }
-    sv[e] = vv;
-    c1[e] = a;
-    c2[e] = b;
-    q1[e] = pa;
-    q2[e] = pb;
   }
   __syncthreads();
   for (int s = 0; s < nsteps; ++s) {
-    const float m = mom.c[s];
-    // x on [s+1, EX-s) x [s+1, EY-s): needs z at i, i-1, i-EX (z rebuilt from cur and prev)
     const int lo = s + 1;
-    const int wx = EX - s - lo, wy = EY - s - lo;
-    for (int e = tid; e < wx * wy; e += FB_THREADS) {
-      const int lx = lo + e % wx, ly = lo + e / wx;
-      const int gx = ox + lx, gy = oy + ly;
-      const int i = ly * EX + lx;
-      float xv = 0.f;
-      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-        float d = 0.f;
-        if (gx < nx - 1) d += fmaf(m, c1[i] - q1[i], c1[i]);
-        if (gx > 0) d -= fmaf(m, c1[i - 1] - q1[i - 1], c1[i - 1]);
-        if (gy < ny - 1) d += fmaf(m, c2[i] - q2[i], c2[i]);
-        if (gy > 0) d -= fmaf(m, c2[i - EX] - q2[i - EX], c2[i - EX]);
-        xv = fmaf(tau, d, sv[i]);
-        if (nonneg) xv = fmaxf(xv, 0.f);
+    // x on [s+1, EX-s) x [s+1, EY-s): needs z at i, i-1, i-EX
+    for (int ly = lo + ty; ly < EY - s; ly += FB_BY) {
+      const int gy = oy + ly;
+      for (int lx = lo + tx; lx < EX - s; lx += FB_BX) {
+        const int gx = ox + lx;
+        const int i = ly * EX + lx;
+        float xv = 0.f;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+          float d = 0.f;
+          if (gx < nx - 1) d += z1[i];
+          if (gx > 0) d -= z1[i - 1];
+          if (gy < ny - 1) d += z2[i];
+          if (gy > 0) d -= z2[i - EX];
+          xv = fmaf(tau, d, sv[i]);
+          if (nonneg) xv = fmaxf(xv, 0.f);
+        }
+        sx[i] = xv;
       }
-      sx[i] = xv;
     }
     __syncthreads();
-    // w' on [s+1, EX-s-1) x [s+1, EY-s-1): needs x at i, i+1, i+EX and z at i
-    const int ux = wx - 1, uy = wy - 1;
-    for (int e = tid; e < ux * uy; e += FB_THREADS) {
-      const int lx = lo + e % ux, ly = lo + e / ux;
-      const int gx = ox + lx, gy = oy + ly;
-      const int i = ly * EX + lx;
-      float n1 = 0.f, n2 = 0.f;
-      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-        const float xc = sx[i];
-        const float d1 = gx < nx - 1 ? sx[i + 1] - xc : 0.f;
-        const float d2 = gy < ny - 1 ? sx[i + EX] - xc : 0.f;
-        const float z1 = fmaf(m, c1[i] - q1[i], c1[i]);
-        const float z2 = fmaf(m, c2[i] - q2[i], c2[i]);
-        const float g1 = fmaf(step, d1, z1), g2 = fmaf(step, d2, z2);
-        const float den = fmaxf(1.f, sqrtf(g1 * g1 + g2 * g2));
-        n1 = g1 / den;
-        n2 = g2 / den;
+    // w', z' on [s+1, EX-s-1) x [s+1, EY-s-1): needs x at i, i+1, i+EX and w, z at i
+    const float m = mom.c[s];
+    for (int ly = lo + ty; ly < EY - s - 1; ly += FB_BY) {
+      const int gy = oy + ly;
+      for (int lx = lo + tx; lx < EX - s - 1; lx += FB_BX) {
+        const int gx = ox + lx;
+        const int i = ly * EX + lx;
+        float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+          const float xc = sx[i];
+          const float d1 = gx < nx - 1 ? sx[i + 1] - xc : 0.f;
+          const float d2 = gy < ny - 1 ? sx[i + EX] - xc : 0.f;
+          const float g1 = fmaf(step, d1, z1[i]), g2 = fmaf(step, d2, z2[i]);
+          const float nrm = sqrtf(g1 * g1 + g2 * g2);
+          if (nrm > 1.f) {
+            n1 = g1 / nrm;
+            n2 = g2 / nrm;
+          } else {
+            n1 = g1;
+            n2 = g2;
+          }
+          m1 = fmaf(m, n1 - w1[i], n1);
+          m2 = fmaf(m, n2 - w2[i], n2);
+        }
+        w1[i] = n1;
+        w2[i] = n2;
+        z1[i] = m1;
+        z2[i] = m2;
       }
-      q1[i] = n1;
-      q2[i] = n2;
     }
     __syncthreads();
-    float* t1 = c1;
-    c1 = q1;
-    q1 = t1;
-    float* t2 = c2;
-    c2 = q2;
-    q2 = t2;
   }
-  for (int e = tid; e < TX * TY; e += FB_THREADS) {
-    const int lx = T + e % TX, ly = T + e / TX;
-    const int gx = ox + lx, gy = oy + ly;
-    if (gx < nx && gy < ny) {
-      const size_t p = (size_t)gy * nx + gx;
-      const int i = ly * EX + lx;
-      wn_g[p] = c1[i];
-      wn_g[n + p] = c2[i];
-      wq_g[p] = q1[i];
-      wq_g[n + p] = q2[i];
+  for (int ly = T + ty; ly < T + TY; ly += FB_BY) {
+    const int gy = oy + ly;
+    for (int lx = T + tx; lx < T + TX; lx += FB_BX) {
+      const int gx = ox + lx;
+      if (gx < nx && gy < ny) {
+        const size_t p = (size_t)gy * nx + gx;
+        const int i = ly * EX + lx;
+        wn_g[p] = w1[i];
+        wn_g[n + p] = w2[i];
+        zn_g[p] = z1[i];
+        zn_g[n + p] = z2[i];
+      }
     }
   }
 }
@@ -284,31 +289,31 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   const float step = (float)(1.0 / (4.0 * g->dims * (double)tau));
   const float* w_final = dual;
   if (g->dims == 2) {
-    // blocks of FB_T iterations; buffer pairs alternate (s1,s2) <-> (s3,s4)
-    const float* rc = dual;
-    const float* rp = dual;
+    // blocks of FB_T iterations; state (w, z) pairs alternate (s1,s2) <-> (s3,s4).  The
+    // first block starts from z = w (iteration 0 does not extrapolate).
+    const float* rw = dual;
+    const float* rz = dual;
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
     int which = 0;
-    constexpr int EX = FB_TX + 2 * FB_T, EY = FB_TY + 2 * FB_T;
-    const size_t smem = sizeof(float) * 6 * EX * EY;
-    static_assert(sizeof(float) * 6 * EX * EY <= 48 * 1024, "FGP tile exceeds the default shared-memory size");
-    dim3 grid((g->nx + FB_TX - 1) / FB_TX, (g->ny + FB_TY - 1) / FB_TY);
+    dim3 grid((g->nx + FB_TX - 1) / FB_TX, (g->ny + FB_TY - 1) / FB_TY), block(FB_BX, FB_BY);
     for (int k0 = 0; k0 < iters; k0 += FB_T) {
       const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
       MomBlock mb;
-      for (int q = 0; q < FB_T; ++q) mb.c[q] = q < ns ? mom[k0 + q] : 0.f;
+      // the z written after iteration k0+q feeds iteration k0+q+1: coefficient mom[k0+q+1]
+      for (int q = 0; q <= FB_T; ++q) mb.c[q] = (q < ns && k0 + q + 1 < iters) ? mom[k0 + q + 1] : 0.f;
       float* wn = pairs[which][0];
-      float* wq = pairs[which][1];
+      float* zn = pairs[which][1];
       {
         LaunchScope _ls("fgp2d_block", s);
-        fgp2d_block<FB_TX, FB_TY, FB_T><<<grid, FB_THREADS, smem, s>>>(v, rc, rp, wn, wq, g->nx, g->ny, tau, step,
-                                                                        mb, ns, nonneg);
+        fgp2d_block<FB_TX, FB_TY, FB_T><<<grid, block, 0, s>>>(v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns,
+                                                               nonneg);
       }
       VRPS_LAUNCHED("fgp2d_block");
-      rc = wn;
-      rp = wq;
+      rw = wn;
+      rz = zn;
       which ^= 1;
     }
+    const float* rc = rw;
     w_final = rc;
   } else {
     float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};

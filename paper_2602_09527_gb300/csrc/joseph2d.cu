@@ -18,7 +18,7 @@ namespace vrps {
 namespace {
 
 constexpr int FWD_LANES = 32;
-constexpr int FWD_PHASES = 16;
+constexpr int FWD_PHASES = 8;
 constexpr int ADJ_TX = ADJ2D_TILE_X;   // pixel tile: 16 columns x 32 rows, 2 pixels per thread
 constexpr int ADJ_TY = ADJ2D_TILE_Y;
 constexpr int ADJ_THREADS = 256;
@@ -75,29 +75,34 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
     const float* rp = img + (size_t)l0 * ncols;
     const size_t dp = (size_t)FWD_PHASES * ncols;
     const unsigned nc = (unsigned)ncols;
+    // four samples per trip, independent accumulators (keeps 8 loads in flight per thread)
     int l = l0;
-#pragma unroll 2
-    for (; l + FWD_PHASES <= hi; l += 2 * FWD_PHASES) {
-      const int i0 = fix_floor(U);
-      const float f = fix_frac(U);
-      const int i1 = fix_floor(U + dU);
-      const float f1 = fix_frac(U + dU);
-      const float* rq = rp + dp;
-      const float a0 = ((unsigned)i0 < nc) ? __ldg(rp + i0) : 0.f;
-      const float a1 = ((unsigned)(i0 + 1) < nc) ? __ldg(rp + i0 + 1) : 0.f;
-      const float b0 = ((unsigned)i1 < nc) ? __ldg(rq + i1) : 0.f;
-      const float b1 = ((unsigned)(i1 + 1) < nc) ? __ldg(rq + i1 + 1) : 0.f;
-      acc0 += fmaf(f, a1 - a0, a0);
-      acc1 += fmaf(f1, b1 - b0, b0);
-      U += 2 * dU;
-      rp += 2 * dp;
+    for (; l + 3 * FWD_PHASES <= hi; l += 4 * FWD_PHASES) {
+      float a[4], b[4], f[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long Uq = U + (long long)q * dU;
+        const int i0 = fix_floor(Uq);
+        f[q] = fix_frac(Uq);
+        const float* rq = rp + (size_t)q * dp;
+        a[q] = ((unsigned)i0 < nc) ? __ldg(rq + i0) : 0.f;
+        b[q] = ((unsigned)(i0 + 1) < nc) ? __ldg(rq + i0 + 1) : 0.f;
+      }
+      acc0 += fmaf(f[0], b[0] - a[0], a[0]);
+      acc1 += fmaf(f[1], b[1] - a[1], a[1]);
+      acc0 += fmaf(f[2], b[2] - a[2], a[2]);
+      acc1 += fmaf(f[3], b[3] - a[3], a[3]);
+      U += 4 * dU;
+      rp += 4 * dp;
     }
-    if (l <= hi) {
+    for (; l <= hi; l += FWD_PHASES) {
       const int i0 = fix_floor(U);
       const float f = fix_frac(U);
       const float a0 = ((unsigned)i0 < nc) ? __ldg(rp + i0) : 0.f;
       const float a1 = ((unsigned)(i0 + 1) < nc) ? __ldg(rp + i0 + 1) : 0.f;
       acc0 += fmaf(f, a1 - a0, a0);
+      U += dU;
+      rp += dp;
     }
   }
   red[ph][lane] = acc0 + acc1;
