@@ -122,6 +122,8 @@ static void free_ws(Workspace& w) {
     *p = nullptr;
   }
   if (w.partials) cudaFree(w.partials);
+  if (w.fwd_part) cudaFree(w.fwd_part);
+  if (w.fwd_count) cudaFree(w.fwd_count);
   if (w.scalars) cudaFree(w.scalars);
   if (w.sched_dev) cudaFree(w.sched_dev);
   if (w.sched_host) cudaFreeHost(w.sched_host);

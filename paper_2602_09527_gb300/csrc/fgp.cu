@@ -27,22 +27,98 @@ namespace {
 // w' = P_B(z + step D x) and the next extrapolation z' = w' + mom' (w' - w), both in place
 // (each only reads its own pixel's w and z).  Reads and writes go to different buffer
 // pairs, so neighbouring CTAs never see a half-updated dual.
-constexpr int FB_TX = 32, FB_TY = 16, FB_T = 8;
+constexpr int FB_TX = 32, FB_TY = 32, FB_T = 8;
 constexpr int FB_BX = 32, FB_BY = 8;   // threads
+constexpr int FB_EX = FB_TX + 2 * FB_T, FB_EY = FB_TY + 2 * FB_T, FB_NE = FB_EX * FB_EY;
+constexpr size_t FB_SMEM = sizeof(float) * 6 * FB_NE;
 
 struct MomBlock {
   float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
 };
 
-template <int TX, int TY, int T>
+// Projection onto the unit ball: g / max(1, |g|) with one correctly rounded 1/sqrt.
+__device__ __forceinline__ void ball2(float g1, float g2, float& n1, float& n2) {
+  const float q = g1 * g1 + g2 * g2;
+  if (q > 1.f) {
+    const float r = __frsqrt_rn(q);
+    n1 = g1 * r;
+    n2 = g2 * r;
+  } else {
+    n1 = g1;
+    n2 = g2;
+  }
+}
+
+// One block of nsteps FGP iterations on the shared-memory tile.  INTERIOR: the grown tile
+// lies strictly inside the image (no boundary or bounds tests needed).
+template <bool INTERIOR>
+__device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, float* z1, float* z2, float* sx, int ox,
+                                            int oy, int nx, int ny, float tau, float step, const MomBlock& mom,
+                                            int nsteps, int nonneg) {
+  constexpr int EX = FB_EX, EY = FB_EY;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int s = 0; s < nsteps; ++s) {
+    const int lo = s + 1;
+    // x on [s+1, EX-s) x [s+1, EY-s): needs z at i, i-1, i-EX
+    for (int ly = lo + ty; ly < EY - s; ly += FB_BY) {
+      const int gy = oy + ly;
+      for (int lx = lo + tx; lx < EX - s; lx += FB_BX) {
+        const int gx = ox + lx;
+        const int i = ly * EX + lx;
+        float xv = 0.f;
+        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+          float d = 0.f;
+          if (INTERIOR || gx < nx - 1) d += z1[i];
+          if (INTERIOR || gx > 0) d -= z1[i - 1];
+          if (INTERIOR || gy < ny - 1) d += z2[i];
+          if (INTERIOR || gy > 0) d -= z2[i - EX];
+          xv = fmaf(tau, d, sv[i]);
+          if (nonneg) xv = fmaxf(xv, 0.f);
+        }
+        sx[i] = xv;
+      }
+    }
+    __syncthreads();
+    // w', z' on [s+1, EX-s-1) x [s+1, EY-s-1): needs x at i, i+1, i+EX and w, z at i
+    const float m = mom.c[s];
+    for (int ly = lo + ty; ly < EY - s - 1; ly += FB_BY) {
+      const int gy = oy + ly;
+      for (int lx = lo + tx; lx < EX - s - 1; lx += FB_BX) {
+        const int gx = ox + lx;
+        const int i = ly * EX + lx;
+        float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
+        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+          const float xc = sx[i];
+          const float d1 = (INTERIOR || gx < nx - 1) ? sx[i + 1] - xc : 0.f;
+          const float d2 = (INTERIOR || gy < ny - 1) ? sx[i + EX] - xc : 0.f;
+          ball2(fmaf(step, d1, z1[i]), fmaf(step, d2, z2[i]), n1, n2);
+          m1 = fmaf(m, n1 - w1[i], n1);
+          m2 = fmaf(m, n2 - w2[i], n2);
+        }
+        w1[i] = n1;
+        w2[i] = n2;
+        z1[i] = m1;
+        z2[i] = m2;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(FB_BX* FB_BY) fgp2d_block(const float* __restrict__ v, const float* __restrict__ w_g,
                                                             const float* __restrict__ z_g, float* __restrict__ wn_g,
                                                             float* __restrict__ zn_g, int nx, int ny, float tau,
                                                             float step, MomBlock mom, int nsteps, int nonneg) {
-  constexpr int EX = TX + 2 * T, EY = TY + 2 * T, NE = EX * EY;
-  __shared__ float sv[NE], w1[NE], w2[NE], z1[NE], z2[NE], sx[NE];
+  constexpr int EX = FB_EX, EY = FB_EY, NE = FB_NE;
+  extern __shared__ float smf[];
+  float* sv = smf;
+  float* w1 = sv + NE;
+  float* w2 = w1 + NE;
+  float* z1 = w2 + NE;
+  float* z2 = z1 + NE;
+  float* sx = z2 + NE;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int ox = blockIdx.x * TX - T, oy = blockIdx.y * TY - T;
+  const int ox = blockIdx.x * FB_TX - FB_T, oy = blockIdx.y * FB_TY - FB_T;
   const size_t n = (size_t)nx * ny;
   for (int ly = ty; ly < EY; ly += FB_BY) {
     const int gy = oy + ly;
@@ -66,63 +142,14 @@ __global__ void __launch_bounds__(FB_BX* FB_BY) fgp2d_block(const float* __restr
     }
   }
   __syncthreads();
-  for (int s = 0; s < nsteps; ++s) {
-    const int lo = s + 1;
-    // x on [s+1, EX-s) x [s+1, EY-s): needs z at i, i-1, i-EX
-    for (int ly = lo + ty; ly < EY - s; ly += FB_BY) {
-      const int gy = oy + ly;
-      for (int lx = lo + tx; lx < EX - s; lx += FB_BX) {
-        const int gx = ox + lx;
-        const int i = ly * EX + lx;
-        float xv = 0.f;
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-          float d = 0.f;
-          if (gx < nx - 1) d += z1[i];
-          if (gx > 0) d -= z1[i - 1];
-          if (gy < ny - 1) d += z2[i];
-          if (gy > 0) d -= z2[i - EX];
-          xv = fmaf(tau, d, sv[i]);
-          if (nonneg) xv = fmaxf(xv, 0.f);
-        }
-        sx[i] = xv;
-      }
-    }
-    __syncthreads();
-    // w', z' on [s+1, EX-s-1) x [s+1, EY-s-1): needs x at i, i+1, i+EX and w, z at i
-    const float m = mom.c[s];
-    for (int ly = lo + ty; ly < EY - s - 1; ly += FB_BY) {
-      const int gy = oy + ly;
-      for (int lx = lo + tx; lx < EX - s - 1; lx += FB_BX) {
-        const int gx = ox + lx;
-        const int i = ly * EX + lx;
-        float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-          const float xc = sx[i];
-          const float d1 = gx < nx - 1 ? sx[i + 1] - xc : 0.f;
-          const float d2 = gy < ny - 1 ? sx[i + EX] - xc : 0.f;
-          const float g1 = fmaf(step, d1, z1[i]), g2 = fmaf(step, d2, z2[i]);
-          const float nrm = sqrtf(g1 * g1 + g2 * g2);
-          if (nrm > 1.f) {
-            n1 = g1 / nrm;
-            n2 = g2 / nrm;
-          } else {
-            n1 = g1;
-            n2 = g2;
-          }
-          m1 = fmaf(m, n1 - w1[i], n1);
-          m2 = fmaf(m, n2 - w2[i], n2);
-        }
-        w1[i] = n1;
-        w2[i] = n2;
-        z1[i] = m1;
-        z2[i] = m2;
-      }
-    }
-    __syncthreads();
-  }
-  for (int ly = T + ty; ly < T + TY; ly += FB_BY) {
+  const bool interior = ox >= 1 && oy >= 1 && ox + EX <= nx - 1 && oy + EY <= ny - 1;
+  if (interior)
+    fgp2d_steps<true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps, nonneg);
+  else
+    fgp2d_steps<false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps, nonneg);
+  for (int ly = FB_T + ty; ly < FB_T + FB_TY; ly += FB_BY) {
     const int gy = oy + ly;
-    for (int lx = T + tx; lx < T + TX; lx += FB_BX) {
+    for (int lx = FB_T + tx; lx < FB_T + FB_TX; lx += FB_BX) {
       const int gx = ox + lx;
       if (gx < nx && gy < ny) {
         const size_t p = (size_t)gy * nx + gx;
@@ -296,6 +323,7 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
     int which = 0;
     dim3 grid((g->nx + FB_TX - 1) / FB_TX, (g->ny + FB_TY - 1) / FB_TY), block(FB_BX, FB_BY);
+    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM));
     for (int k0 = 0; k0 < iters; k0 += FB_T) {
       const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
       MomBlock mb;
@@ -305,8 +333,7 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       float* zn = pairs[which][1];
       {
         LaunchScope _ls("fgp2d_block", s);
-        fgp2d_block<FB_TX, FB_TY, FB_T><<<grid, block, 0, s>>>(v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns,
-                                                               nonneg);
+        fgp2d_block<<<grid, block, FB_SMEM, s>>>(v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg);
       }
       VRPS_LAUNCHED("fgp2d_block");
       rw = wn;

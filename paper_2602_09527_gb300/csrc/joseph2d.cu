@@ -24,6 +24,8 @@ constexpr int ADJ_TY = ADJ2D_TILE_Y;
 constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_CHUNK = 64;
 
+constexpr int FWD_CHUNK = 128;   // dominant-axis lines per CTA (a ray longer than this is split)
+
 struct Fwd2DParams {
   const float* x;
   const float* xT;
@@ -31,6 +33,9 @@ struct Fwd2DParams {
   const int* ids;
   int nx, ny, nb;
   float jc;
+  int chunks;                 // CTAs per ray group along the lines (gridDim.z)
+  float* part;                // [rows][chunks][nb] partial sums (chunks > 1)
+  unsigned* count;            // [rows][groups] arrival counters, zero between launches
   FwdOut o;
 };
 
@@ -67,6 +72,9 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
     } else if (!(u0 > -1.f && u0 < (float)ncols)) {
       hi = -1;
     }
+    // this CTA's chunk of lines
+    lo = max(lo, (int)blockIdx.z * FWD_CHUNK);
+    hi = min(hi, (int)blockIdx.z * FWD_CHUNK + FWD_CHUNK - 1);
     // exact fixed-point walk along the ray: U = u * 2^32
     const int l0 = lo + ph;
     long long U = (long long)(ncols - 1) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
@@ -107,10 +115,30 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
   }
   red[ph][lane] = acc0 + acc1;
   __syncthreads();
-  if (ph == 0 && j < P.nb) {
-    float s = 0.f;
+  if (ph != 0) return;
+  float s = 0.f;
 #pragma unroll
-    for (int q = 0; q < FWD_PHASES; ++q) s += red[q][lane];
+  for (int q = 0; q < FWD_PHASES; ++q) s += red[q][lane];
+  if (P.chunks > 1) {
+    // publish this chunk's partial sums; the last CTA of the ray group adds all chunks in
+    // chunk order (deterministic) and runs the epilogue
+    const size_t pbase = ((size_t)row * P.chunks) * P.nb;
+    if (j < P.nb) P.part[pbase + (size_t)blockIdx.z * P.nb + j] = s;
+    __threadfence();
+    unsigned last = 0;
+    if (lane == 0) {
+      unsigned* cnt = P.count + (size_t)row * gridDim.x + blockIdx.x;
+      last = (atomicAdd(cnt, 1u) == (unsigned)(P.chunks - 1)) ? 1u : 0u;
+      if (last) *cnt = 0u;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    s = 0.f;
+    if (j < P.nb)
+      for (int c = 0; c < P.chunks; ++c) s += __ldcg(P.part + pbase + (size_t)c * P.nb + j);
+  }
+  if (j < P.nb) {
     const float r = s * in.wgt;
     const size_t idx = (size_t)row * P.nb + j;
     if (MODE == FWD_PLAIN) {
@@ -315,7 +343,22 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.nb = g->n_bins;
   P.jc = 0.5f * (float)(g->n_bins - 1);
   P.o = o;
-  dim3 grid((g->n_bins + FWD_LANES - 1) / FWD_LANES, rows), block(FWD_LANES, FWD_PHASES);
+  const int groups = (g->n_bins + FWD_LANES - 1) / FWD_LANES;
+  const int max_lines = g->nx > g->ny ? g->nx : g->ny;
+  P.chunks = (max_lines + FWD_CHUNK - 1) / FWD_CHUNK;
+  P.part = nullptr;
+  P.count = nullptr;
+  if (P.chunks > 1) {
+    vrps_geom* gm = const_cast<vrps_geom*>(g);
+    if (!gm->ws.fwd_part) {
+      VRPS_CUDA(cudaMalloc((void**)&gm->ws.fwd_part, sizeof(float) * (size_t)g->n_angles * P.chunks * g->n_bins));
+      VRPS_CUDA(cudaMalloc((void**)&gm->ws.fwd_count, sizeof(unsigned) * (size_t)g->n_angles * groups));
+      VRPS_CUDA(cudaMemset(gm->ws.fwd_count, 0, sizeof(unsigned) * (size_t)g->n_angles * groups));
+    }
+    P.part = gm->ws.fwd_part;
+    P.count = gm->ws.fwd_count;
+  }
+  dim3 grid(groups, rows, P.chunks), block(FWD_LANES, FWD_PHASES);
   switch (mode) {
     case FWD_PLAIN: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); } break;
     case FWD_RESID: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); } break;

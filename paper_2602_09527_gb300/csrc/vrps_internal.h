@@ -107,6 +107,8 @@ struct Workspace {
   float* dual_s3 = nullptr;
   float* dual_s4 = nullptr;
   double* partials = nullptr;   // reduction partials
+  float* fwd_part = nullptr;      // 2D forward: per-chunk partial ray sums
+  unsigned* fwd_count = nullptr;  // 2D forward: chunk arrival counters
   double* scalars = nullptr;    // [16] device scalars
   float* sino = nullptr;        // [m] sinogram scratch
   float* img = nullptr;         // [n] image scratch
