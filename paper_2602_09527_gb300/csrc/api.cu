@@ -178,6 +178,11 @@ static int build_par2d(vrps_geom* g) {
       t.A2 = (float)(-c / s);
     }
     t.T = rows ? 0 : 1;
+    {
+      const double a2 = rows ? -s / c : -c / s;
+      t.inv_A2 = a2 != 0.0 ? (float)(1.0 / a2) : 0.f;
+      t.pad[0] = t.pad[1] = t.pad[2] = 0;
+    }
     const double two31 = 2147483648.0;
     t.A1H = std::llround((rows ? ds / (pix * c) : ds / (pix * s)) * two31);
     t.A2H = std::llround((rows ? -s / c : -c / s) * two31);

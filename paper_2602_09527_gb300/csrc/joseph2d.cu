@@ -58,8 +58,8 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
     int lo = 0, hi = nlines - 1;
     if (in.A2 != 0.f) {
       // lines where the ray's interpolation point is in (-1, ncols); widened by one line
-      float la = lc + (-1.f - u0) / in.A2;
-      float lb = lc + ((float)ncols - u0) / in.A2;
+      float la = fmaf(-1.f - u0, in.inv_A2, lc);
+      float lb = fmaf((float)ncols - u0, in.inv_A2, lc);
       if (la > lb) {
         const float t = la;
         la = lb;

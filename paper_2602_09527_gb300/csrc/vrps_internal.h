@@ -60,8 +60,9 @@ struct LaunchScope {
 struct AngleInfo2D {
   long long A1H, A2H, BxH, ByH;
   float A1, A2, wgt, Bx;
-  float By, hw, inv_hw;
+  float By, hw, inv_hw, inv_A2;   // inv_A2 = 1/A2 (0 when A2 = 0)
   int T;
+  int pad[3];
 };
 
 // Fixed-point helpers: value * 2^32 held in a 64-bit integer.
