@@ -27,10 +27,19 @@ namespace {
 // w' = P_B(z + step D x) and the next extrapolation z' = w' + mom' (w' - w), both in place
 // (each only reads its own pixel's w and z).  Reads and writes go to different buffer
 // pairs, so neighbouring CTAs never see a half-updated dual.
-constexpr int FB_TX = 32, FB_TY = 32, FB_T = 8;
-constexpr int FB_BX = 32, FB_BY = 16;  // threads
-constexpr int FB_EX = FB_TX + 2 * FB_T, FB_EY = FB_TY + 2 * FB_T, FB_NE = FB_EX * FB_EY;
-constexpr size_t FB_SMEM = sizeof(float) * 6 * FB_NE;
+constexpr int FB_T = 8;   // iterations per launch (= halo width)
+
+// Tile shapes: TX x TY outputs per CTA of BX x BY threads.  Small images use small tiles so
+// that every SM holds several CTAs (the stencil is latency-bound there); the halo
+// recomputation this costs is cheap next to the latency it hides.
+template <int TX_, int TY_, int BX_, int BY_>
+struct FgpTile {
+  static constexpr int TX = TX_, TY = TY_, BX = BX_, BY = BY_;
+  static constexpr int EX = TX + 2 * FB_T, EY = TY + 2 * FB_T, NE = EX * EY;
+  static constexpr size_t SMEM = sizeof(float) * 6 * NE;
+};
+using TileSmall = FgpTile<16, 16, 32, 8>;
+using TileLarge = FgpTile<32, 32, 32, 16>;
 
 struct MomBlock {
   float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
@@ -52,11 +61,11 @@ __device__ __forceinline__ void ball2(float g1, float g2, float& n1, float& n2) 
 
 // One block of nsteps FGP iterations on the shared-memory tile.  INTERIOR: the grown tile
 // lies strictly inside the image (no boundary or bounds tests needed).
-template <bool INTERIOR, bool NONNEG>
+template <class TL, bool INTERIOR, bool NONNEG>
 __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, float* z1, float* z2, float* sx, int ox,
                                             int oy, int nx, int ny, float tau, float step, const MomBlock& mom,
                                             int nsteps) {
-  constexpr int EX = FB_EX, EY = FB_EY;
+  constexpr int EX = TL::EX, EY = TL::EY, FB_BX = TL::BX, FB_BY = TL::BY;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int s = 0; s < nsteps; ++s) {
     const int lo = s + 1;
@@ -106,11 +115,13 @@ __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, flo
   }
 }
 
-__global__ void __launch_bounds__(FB_BX* FB_BY) fgp2d_block(const float* __restrict__ v, const float* __restrict__ w_g,
-                                                            const float* __restrict__ z_g, float* __restrict__ wn_g,
-                                                            float* __restrict__ zn_g, int nx, int ny, float tau,
-                                                            float step, MomBlock mom, int nsteps, int nonneg) {
-  constexpr int EX = FB_EX, EY = FB_EY, NE = FB_NE;
+template <class TL>
+__global__ void __launch_bounds__(TL::BX* TL::BY) fgp2d_block(const float* __restrict__ v, const float* __restrict__ w_g,
+                                                              const float* __restrict__ z_g, float* __restrict__ wn_g,
+                                                              float* __restrict__ zn_g, int nx, int ny, float tau,
+                                                              float step, MomBlock mom, int nsteps, int nonneg) {
+  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, FB_BX = TL::BX, FB_BY = TL::BY, FB_TX = TL::TX,
+                FB_TY = TL::TY;
   extern __shared__ float smf[];
   float* sv = smf;
   float* w1 = sv + NE;
@@ -146,14 +157,14 @@ __global__ void __launch_bounds__(FB_BX* FB_BY) fgp2d_block(const float* __restr
   const bool interior = ox >= 1 && oy >= 1 && ox + EX <= nx - 1 && oy + EY <= ny - 1;
   if (nonneg) {
     if (interior)
-      fgp2d_steps<true, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+      fgp2d_steps<TL, true, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
     else
-      fgp2d_steps<false, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+      fgp2d_steps<TL, false, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
   } else {
     if (interior)
-      fgp2d_steps<true, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+      fgp2d_steps<TL, true, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
     else
-      fgp2d_steps<false, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+      fgp2d_steps<TL, false, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
   }
   for (int ly = FB_T + ty; ly < FB_T + FB_TY; ly += FB_BY) {
     const int gy = oy + ly;
@@ -330,8 +341,16 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     const float* rz = dual;
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
     int which = 0;
-    dim3 grid((g->nx + FB_TX - 1) / FB_TX, (g->ny + FB_TY - 1) / FB_TY), block(FB_BX, FB_BY);
-    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM));
+    int sms = 0;
+    VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+    const bool small = (long long)((g->nx + 31) / 32) * ((g->ny + 31) / 32) < 4LL * sms;
+    if (small) {
+      VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TileSmall::SMEM));
+    } else {
+      VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TileLarge::SMEM));
+    }
     for (int k0 = 0; k0 < iters; k0 += FB_T) {
       const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
       MomBlock mb;
@@ -341,7 +360,15 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       float* zn = pairs[which][1];
       {
         LaunchScope _ls("fgp2d_block", s);
-        fgp2d_block<<<grid, block, FB_SMEM, s>>>(v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg);
+        if (small) {
+          dim3 grid((g->nx + TileSmall::TX - 1) / TileSmall::TX, (g->ny + TileSmall::TY - 1) / TileSmall::TY);
+          fgp2d_block<TileSmall><<<grid, dim3(TileSmall::BX, TileSmall::BY), TileSmall::SMEM, s>>>(
+              v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg);
+        } else {
+          dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
+          fgp2d_block<TileLarge><<<grid, dim3(TileLarge::BX, TileLarge::BY), TileLarge::SMEM, s>>>(
+              v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg);
+        }
       }
       VRPS_LAUNCHED("fgp2d_block");
       rw = wn;
