@@ -65,50 +65,59 @@ template <class TL, bool INTERIOR, bool NONNEG>
 __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, float* z1, float* z2, float* sx, int ox,
                                             int oy, int nx, int ny, float tau, float step, const MomBlock& mom,
                                             int nsteps) {
-  constexpr int EX = TL::EX, EY = TL::EY, FB_BX = TL::BX, FB_BY = TL::BY;
+  constexpr int EX = TL::EX, EY = TL::EY, BX = TL::BX, BY = TL::BY;
+  constexpr int RY = (EY + BY - 1) / BY, RX = (EX + BX - 1) / BX;   // elements per thread
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int s = 0; s < nsteps; ++s) {
     const int lo = s + 1;
     // x on [s+1, EX-s) x [s+1, EY-s): needs z at i, i-1, i-EX
-    for (int ly = lo + ty; ly < EY - s; ly += FB_BY) {
-      const int gy = oy + ly;
-      for (int lx = lo + tx; lx < EX - s; lx += FB_BX) {
-        const int gx = ox + lx;
-        const int i = ly * EX + lx;
-        float xv = 0.f;
-        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
-          float d = 0.f;
-          if (INTERIOR || gx < nx - 1) d += z1[i];
-          if (INTERIOR || gx > 0) d -= z1[i - 1];
-          if (INTERIOR || gy < ny - 1) d += z2[i];
-          if (INTERIOR || gy > 0) d -= z2[i - EX];
-          xv = fmaf(tau, d, sv[i]);
-          if (NONNEG) xv = fmaxf(xv, 0.f);
+#pragma unroll
+    for (int a = 0; a < RY; ++a) {
+#pragma unroll
+      for (int b = 0; b < RX; ++b) {
+        const int ly = ty + a * BY, lx = tx + b * BX;
+        if (ly >= lo && ly < EY - s && lx >= lo && lx < EX - s) {
+          const int gx = ox + lx, gy = oy + ly;
+          const int i = ly * EX + lx;
+          float xv = 0.f;
+          if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+            float d = 0.f;
+            if (INTERIOR || gx < nx - 1) d += z1[i];
+            if (INTERIOR || gx > 0) d -= z1[i - 1];
+            if (INTERIOR || gy < ny - 1) d += z2[i];
+            if (INTERIOR || gy > 0) d -= z2[i - EX];
+            xv = fmaf(tau, d, sv[i]);
+            if (NONNEG) xv = fmaxf(xv, 0.f);
+          }
+          sx[i] = xv;
         }
-        sx[i] = xv;
       }
     }
     __syncthreads();
     // w', z' on [s+1, EX-s-1) x [s+1, EY-s-1): needs x at i, i+1, i+EX and w, z at i
     const float m = mom.c[s];
-    for (int ly = lo + ty; ly < EY - s - 1; ly += FB_BY) {
-      const int gy = oy + ly;
-      for (int lx = lo + tx; lx < EX - s - 1; lx += FB_BX) {
-        const int gx = ox + lx;
-        const int i = ly * EX + lx;
-        float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
-        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
-          const float xc = sx[i];
-          const float d1 = (INTERIOR || gx < nx - 1) ? sx[i + 1] - xc : 0.f;
-          const float d2 = (INTERIOR || gy < ny - 1) ? sx[i + EX] - xc : 0.f;
-          ball2(fmaf(step, d1, z1[i]), fmaf(step, d2, z2[i]), n1, n2);
-          m1 = fmaf(m, n1 - w1[i], n1);
-          m2 = fmaf(m, n2 - w2[i], n2);
+#pragma unroll
+    for (int a = 0; a < RY; ++a) {
+#pragma unroll
+      for (int b = 0; b < RX; ++b) {
+        const int ly = ty + a * BY, lx = tx + b * BX;
+        if (ly >= lo && ly < EY - s - 1 && lx >= lo && lx < EX - s - 1) {
+          const int gx = ox + lx, gy = oy + ly;
+          const int i = ly * EX + lx;
+          float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
+          if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+            const float xc = sx[i];
+            const float d1 = (INTERIOR || gx < nx - 1) ? sx[i + 1] - xc : 0.f;
+            const float d2 = (INTERIOR || gy < ny - 1) ? sx[i + EX] - xc : 0.f;
+            ball2(fmaf(step, d1, z1[i]), fmaf(step, d2, z2[i]), n1, n2);
+            m1 = fmaf(m, n1 - w1[i], n1);
+            m2 = fmaf(m, n2 - w2[i], n2);
+          }
+          w1[i] = n1;
+          w2[i] = n2;
+          z1[i] = m1;
+          z2[i] = m2;
         }
-        w1[i] = n1;
-        w2[i] = n2;
-        z1[i] = m1;
-        z2[i] = m2;
       }
     }
     __syncthreads();
