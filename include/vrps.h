@@ -124,6 +124,24 @@ int vrps_proj_adj(const vrps_geom* g, int subset, const float* r, float* x, vrps
 int vrps_prox_tv(const vrps_geom* g, const float* v, float* x, float tau, int iters, int nonneg,
                  float* dual, vrps_stream_t stream);
 
+/* Allocation-free variant of vrps_prox_tv for 2D images (the paper has no counterpart; it
+ * exists for callers that cannot let a library allocate device memory -- for example an
+ * application that owns the whole device-memory budget through its own pool, or a
+ * latency-critical loop where the implicit synchronisation of cudaMalloc is not acceptable).
+ * Same operation and arguments as vrps_prox_tv on an nx x ny image (v, x: [nx*ny], dual:
+ * NULL or [2*nx*ny], caller-owned device buffers), but no geometry handle and no
+ * allocation: the scratch lives in a fixed array in device global memory of
+ * VRPS_NOALLOC_MAX_PIXELS x 10 floats (about 10 MB), which every GPU that calls this keeps
+ * until the process exits.  nx*ny above VRPS_NOALLOC_MAX_PIXELS is rejected with
+ * INVALID_ARG.  The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream capture.
+ * All calls share the array, which keeps the last call's contents (a cold start clears
+ * its dual): calls that overlap on the GPU -- on different streams, or from different host
+ * threads -- race with each other and must be serialised by the caller. */
+#define VRPS_NOALLOC_MAX_PIXELS (512 * 512)
+int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, float tau, int iters, int nonneg,
+                           float* dual, vrps_stream_t stream);
+
 /* L = lambda_max(A^T A) by `iters` power iterations from a Philox4x32-10 start vector
  * (key = seed, counter = (e/4, 0, 0, 1), element e takes word e%4, value (u+0.5)/2^32),
  * with float64 inner products.  *L_out is a HOST double; the call synchronises `stream`.

@@ -7,8 +7,8 @@ this package is its thin ctypes binding.  Entry points keep the C names without 
 """
 from ._binding import (ALGOS, ESTIMATORS, Geometry, Report, SolveOpts, VrpsError, kernel_launches, lib,
                        objective, philox_schedule, power_iteration, profile_enable, profile_read, prox_tv,
-                       proj_adj, proj_fwd, solve)
+                       prox_tv2d_noalloc, proj_adj, proj_fwd, solve)
 
 __all__ = ["ALGOS", "ESTIMATORS", "Geometry", "Report", "SolveOpts", "VrpsError", "kernel_launches", "lib",
            "objective", "philox_schedule", "power_iteration", "profile_enable", "profile_read", "prox_tv",
-           "proj_adj", "proj_fwd", "solve"]
+           "prox_tv2d_noalloc", "proj_adj", "proj_fwd", "solve"]

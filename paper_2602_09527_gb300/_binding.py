@@ -74,6 +74,7 @@ def _load():
         "vrps_proj_fwd": (i, [vp, i, vp, vp, vp]),
         "vrps_proj_adj": (i, [vp, i, vp, vp, vp]),
         "vrps_prox_tv": (i, [vp, vp, vp, ctypes.c_float, i, i, vp, vp]),
+        "vrps_prox_tv2d_noalloc": (i, [i, i, vp, vp, ctypes.c_float, i, i, vp, vp]),
         "vrps_power_iteration": (i, [vp, i, u64, P(d), vp]),
         "vrps_objective": (i, [vp, vp, vp, d, P(d), vp]),
         "vrps_philox_schedule": (i, [u64, u32, i64, i, i, d, vp, vp]),
@@ -234,6 +235,19 @@ def prox_tv(g: Geometry, v: torch.Tensor, tau: float, iters: int, nonneg: bool =
     dp = _dev_ptr(dual, "dual", g.dims * g.n) if dual is not None else None
     _check(lib.vrps_prox_tv(g.handle, _dev_ptr(v, "v", g.n), _dev_ptr(x, "x", g.n), float(tau), int(iters),
                             1 if nonneg else 0, dp, _stream(stream)))
+    return x
+
+
+def prox_tv2d_noalloc(nx: int, ny: int, v: torch.Tensor, tau: float, iters: int, nonneg: bool = True,
+                      dual: torch.Tensor | None = None, x: torch.Tensor | None = None, stream=None):
+    """vrps_prox_tv2d_noalloc: the 2D prox without a geometry handle and without allocation
+    (fixed device scratch; see include/vrps.h for its limits)."""
+    n = int(nx) * int(ny)
+    if x is None:
+        x = torch.empty(n, device=v.device, dtype=torch.float32)
+    dp = _dev_ptr(dual, "dual", 2 * n) if dual is not None else None
+    _check(lib.vrps_prox_tv2d_noalloc(int(nx), int(ny), _dev_ptr(v, "v", n), _dev_ptr(x, "x", n), float(tau),
+                                      int(iters), 1 if nonneg else 0, dp, _stream(stream)))
     return x
 
 

@@ -12,6 +12,8 @@
 // The output kernel forms x+ = P_+(v + tau div w_K) and applies the fused tail of the
 // solver (x <- x+, h += (p/gamma)(x+ - x_hat), FISTA momentum, transposed copy).
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "vrps_internal.h"
@@ -423,3 +425,128 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
 }
 
 }  // namespace vrps
+
+// ---------------------------------------------------------------- allocation-free 2D prox
+// Some callers cannot let this library call cudaMalloc: an application that owns the whole
+// device-memory budget through its own pool, or a latency-critical loop in which the implicit
+// device synchronisation of an allocation is not acceptable.  vrps_prox_tv2d_noalloc serves
+// them with scratch held in a fixed array in device global memory instead of allocations.
+// The array belongs to the loaded library: every GPU that uses the entry point keeps it until
+// the process exits, and every call shares it.
+namespace vrps {
+namespace {
+
+constexpr long long NOALLOC_MAX_PIXELS = 512LL * 512LL;   // VRPS_NOALLOC_MAX_PIXELS
+// five dual-sized regions of 2 * NOALLOC_MAX_PIXELS floats: cold-start dual + four rotation
+// buffers of the temporally blocked iterations
+__device__ __align__(256) float g_noalloc_scratch[5 * 2 * NOALLOC_MAX_PIXELS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  In host code the array's name
+// only stands for a host-side shadow, so the address is looked up once per device (with that
+// device current) and cached.
+int noalloc_scratch(int dev, float** out) {
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(VRPS_ERR_UNSUPPORTED, "device index %d too large", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return VRPS_OK;
+}
+
+}  // namespace
+}  // namespace vrps
+
+extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, float tau, int iters, int nonneg,
+                                      float* dual, vrps_stream_t stream) {
+  using namespace vrps;
+  if (nx <= 0 || ny <= 0) return fail(VRPS_ERR_INVALID_ARG, "sizes must be positive (nx=%d ny=%d)", nx, ny);
+  if ((long long)nx * ny > NOALLOC_MAX_PIXELS)
+    return fail(VRPS_ERR_INVALID_ARG, "nx*ny = %lld exceeds the fixed scratch capacity of %lld pixels",
+                (long long)nx * ny, NOALLOC_MAX_PIXELS);
+  if (!v || !x) return fail(VRPS_ERR_INVALID_ARG, "v or x is NULL");
+  if (v == x) return fail(VRPS_ERR_INVALID_ARG, "v and x must not alias");
+  if (!(tau > 0.f) || !std::isfinite(tau)) return fail(VRPS_ERR_INVALID_ARG, "tau must be > 0");
+  if (iters < 0) return fail(VRPS_ERR_INVALID_ARG, "iters must be >= 0");
+  int dev = -1;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  float* base = nullptr;
+  VRPS_TRY(noalloc_scratch(dev, &base));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)nx * ny, dn = 2 * n;
+  const size_t cap = 2 * (size_t)NOALLOC_MAX_PIXELS;
+  float* cold = base;
+  float* pairs[2][2] = {{base + cap, base + 2 * cap}, {base + 3 * cap, base + 4 * cap}};
+  float* d = dual;
+  if (!d) {
+    // the shared array keeps the previous call's contents: a cold start clears its dual
+    VRPS_CUDA(cudaMemsetAsync(cold, 0, dn * sizeof(float), s));
+    d = cold;
+  }
+  const float step = (float)(1.0 / (8.0 * (double)tau));
+  int sms = 0;
+  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool small = (long long)((nx + 31) / 32) * ((ny + 31) / 32) < 4LL * sms;
+  if (small) {
+    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)TileSmall::SMEM));
+  } else {
+    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)TileLarge::SMEM));
+  }
+  // FGP momentum t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2; the z formed after iteration k
+  // uses (t_k - 1)/t_{k+1}
+  double t_cur = 1.0;
+  const float* rw = d;
+  const float* rz = d;
+  int which = 0;
+  for (int k0 = 0; k0 < iters; k0 += FB_T) {
+    const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
+    MomBlock mb;
+    for (int q = 0; q <= FB_T; ++q) {
+      mb.c[q] = 0.f;
+      if (q < ns) {
+        const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
+        if (k0 + q + 1 < iters) mb.c[q] = (float)((t_cur - 1.0) / t_next);
+        t_cur = t_next;
+      }
+    }
+    float* wn = pairs[which][0];
+    float* zn = pairs[which][1];
+    {
+      LaunchScope _ls("fgp2d_block", s);
+      if (small) {
+        dim3 grid((nx + TileSmall::TX - 1) / TileSmall::TX, (ny + TileSmall::TY - 1) / TileSmall::TY);
+        fgp2d_block<TileSmall><<<grid, dim3(TileSmall::BX, TileSmall::BY), TileSmall::SMEM, s>>>(
+            v, rw, rz, wn, zn, nx, ny, tau, step, mb, ns, nonneg ? 1 : 0);
+      } else {
+        dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
+        fgp2d_block<TileLarge><<<grid, dim3(TileLarge::BX, TileLarge::BY), TileLarge::SMEM, s>>>(
+            v, rw, rz, wn, zn, nx, ny, tau, step, mb, ns, nonneg ? 1 : 0);
+      }
+    }
+    VRPS_LAUNCHED("fgp2d_block");
+    rw = wn;
+    rz = zn;
+    which ^= 1;
+  }
+  ProxTail t;
+  std::memset(&t, 0, sizeof(t));
+  t.mode = 0;
+  t.out = x;
+  float* wdst = (rw != d && dual) ? dual : nullptr;
+  {
+    dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
+    LaunchScope _ls("fgp2d_out", s);
+    fgp2d_out<<<grid, block, 0, s>>>(v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t);
+  }
+  VRPS_LAUNCHED("fgp2d_out");
+  return VRPS_OK;
+}
