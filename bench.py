@@ -35,7 +35,9 @@ if ROOT not in sys.path:
 import synthetic  # noqa: E402
 
 WORKLOADS = {
-    "par2d_512": dict(n=512, n_angles=720, n_bins=768, n_subsets=20, noise="poisson", alpha=0.01,
+    # alpha = 1.0: the TV weight with the smallest reconstruction error against the phantom
+    # (sweep 0.002 .. 10 with long FISTA runs); the workload's description leaves it open
+    "par2d_512": dict(n=512, n_angles=720, n_bins=768, n_subsets=20, noise="poisson", alpha=1.0,
                       algo="VR_PROXSKIP", estimator="SVRG", p=0.1, fgp_iters=100, seed=20260209,
                       target_gap=1e-4, max_epochs=150),
     "par2d_64": dict(n=64, n_angles=90, n_bins=96, n_subsets=10, noise="gauss", alpha=0.01,
@@ -47,7 +49,7 @@ WORKLOADS = {
 # by the CPU oracle legs to scale a bounded sample up to a whole reconstruction.  Recorded from
 # the GPU replay of this workload; the GPU arm recomputes them every run.
 TRAJECTORY = {
-    "par2d_512": dict(iterations=None, prox_calls=None, snapshots=None),
+    "par2d_512": dict(iterations=1920, prox_calls=180, snapshots=96),
     "par2d_64": dict(iterations=None, prox_calls=None, snapshots=None),
 }
 
@@ -174,6 +176,9 @@ def main():
     ap.add_argument("--workload", default="par2d_512", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--alpha", type=float, default=None, help="override the workload's TV weight")
+    ap.add_argument("--profile-once", type=int, default=0, metavar="K",
+                    help="profiling driver: run K solver iterations of the workload once (no F* search, "
+                         "no timing) and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -194,6 +199,17 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2602_09527_gb300 as vr
+
+    if args.profile_once:
+        P = make_problem(wl, rank)
+        g = vr.Geometry.from_spec(P.spec)
+        b_dev = torch.tensor(P.b.astype(np.float32).ravel(), device="cuda")
+        L = vr.power_iteration(g, 100, seed=w["seed"])
+        vr.solve(b_dev, g, w["alpha"], w["algo"], p=w["p"], gamma=1.0 / L, seed=w["seed"], estimator=w["estimator"],
+                 fgp_iters=w["fgp_iters"], max_iters=args.profile_once)
+        torch.cuda.synchronize()
+        g.close()
+        return
 
     P = make_problem(wl, rank)
     g = vr.Geometry.from_spec(P.spec)

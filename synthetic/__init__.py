@@ -244,7 +244,7 @@ WORKLOADS_2D = {
     # 64^2, 90 angles over [0,180), 96 unit bins, 10 subsets, Gaussian 1 %
     "par2d_64": dict(n=64, n_angles=90, n_bins=96, n_subsets=10, noise="gauss", alpha=0.01),
     # 512^2, 720 angles, 768 bins, 20 subsets, Poisson I0 = 1e4 with max clean line integral 4
-    "par2d_512": dict(n=512, n_angles=720, n_bins=768, n_subsets=20, noise="poisson", alpha=0.01),
+    "par2d_512": dict(n=512, n_angles=720, n_bins=768, n_subsets=20, noise="poisson", alpha=1.0),
 }
 
 WORKLOADS_3D = {
