@@ -31,17 +31,17 @@ namespace {
 // pairs, so neighbouring CTAs never see a half-updated dual.
 constexpr int FB_T = 8;   // iterations per launch (= halo width)
 
-// Tile shapes: TX x TY outputs per CTA of BX x BY threads.  Small images use small tiles so
-// that every SM holds several CTAs (the stencil is latency-bound there); the halo
-// recomputation this costs is cheap next to the latency it hides.
-template <int TX_, int TY_, int BX_, int BY_>
+// Tile: TX x TY outputs per CTA of NT threads; the grown tile (EX x EY elements) is walked
+// in NS linear slots per thread (slot e = tid + k NT).  Each slot carries the depth at which
+// it leaves the shrinking valid region, so one compare decides whether it works in a step.
+template <int TX_, int TY_, int NT_>
 struct FgpTile {
-  static constexpr int TX = TX_, TY = TY_, BX = BX_, BY = BY_;
+  static constexpr int TX = TX_, TY = TY_, NT = NT_;
   static constexpr int EX = TX + 2 * FB_T, EY = TY + 2 * FB_T, NE = EX * EY;
+  static constexpr int NS = (NE + NT - 1) / NT;
   static constexpr size_t SMEM = sizeof(float) * 6 * NE;
 };
-using TileSmall = FgpTile<16, 16, 32, 8>;
-using TileLarge = FgpTile<32, 32, 32, 16>;
+using TileLarge = FgpTile<32, 32, 512>;
 
 struct MomBlock {
   float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
@@ -67,59 +67,58 @@ template <class TL, bool INTERIOR, bool NONNEG>
 __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, float* z1, float* z2, float* sx, int ox,
                                             int oy, int nx, int ny, float tau, float step, const MomBlock& mom,
                                             int nsteps) {
-  constexpr int EX = TL::EX, EY = TL::EY, BX = TL::BX, BY = TL::BY;
-  constexpr int RY = (EY + BY - 1) / BY, RX = (EX + BX - 1) / BX;   // elements per thread
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT, NS = TL::NS;
+  const int tid = threadIdx.x;
+  // x at step s needs z at i-1, i-EX: valid on [s+1, EX-s); w' also needs x at i+1, i+EX:
+  // valid on [s+1, EX-s-1).  dx / dw = largest step at which the slot is still inside.
+  int dx[NS], dw[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int e = tid + k * NT;
+    const int lx = e % EX, ly = e / EX;
+    const int a = min(lx - 1, ly - 1);
+    dx[k] = e < NE ? min(a, min(EX - 1 - lx, EY - 1 - ly)) : -1;
+    dw[k] = e < NE ? min(a, min(EX - 2 - lx, EY - 2 - ly)) : -1;
+  }
   for (int s = 0; s < nsteps; ++s) {
-    const int lo = s + 1;
-    // x on [s+1, EX-s) x [s+1, EY-s): needs z at i, i-1, i-EX
 #pragma unroll
-    for (int a = 0; a < RY; ++a) {
-#pragma unroll
-      for (int b = 0; b < RX; ++b) {
-        const int ly = ty + a * BY, lx = tx + b * BX;
-        if (ly >= lo && ly < EY - s && lx >= lo && lx < EX - s) {
-          const int gx = ox + lx, gy = oy + ly;
-          const int i = ly * EX + lx;
-          float xv = 0.f;
-          if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
-            float d = 0.f;
-            if (INTERIOR || gx < nx - 1) d += z1[i];
-            if (INTERIOR || gx > 0) d -= z1[i - 1];
-            if (INTERIOR || gy < ny - 1) d += z2[i];
-            if (INTERIOR || gy > 0) d -= z2[i - EX];
-            xv = fmaf(tau, d, sv[i]);
-            if (NONNEG) xv = fmaxf(xv, 0.f);
-          }
-          sx[i] = xv;
+    for (int k = 0; k < NS; ++k) {
+      if (dx[k] >= s) {
+        const int i = tid + k * NT;
+        float xv = 0.f;
+        const int gx = ox + i % EX, gy = oy + i / EX;
+        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+          float d = 0.f;
+          if (INTERIOR || gx < nx - 1) d += z1[i];
+          if (INTERIOR || gx > 0) d -= z1[i - 1];
+          if (INTERIOR || gy < ny - 1) d += z2[i];
+          if (INTERIOR || gy > 0) d -= z2[i - EX];
+          xv = fmaf(tau, d, sv[i]);
+          if (NONNEG) xv = fmaxf(xv, 0.f);
         }
+        sx[i] = xv;
       }
     }
     __syncthreads();
-    // w', z' on [s+1, EX-s-1) x [s+1, EY-s-1): needs x at i, i+1, i+EX and w, z at i
     const float m = mom.c[s];
 #pragma unroll
-    for (int a = 0; a < RY; ++a) {
-#pragma unroll
-      for (int b = 0; b < RX; ++b) {
-        const int ly = ty + a * BY, lx = tx + b * BX;
-        if (ly >= lo && ly < EY - s - 1 && lx >= lo && lx < EX - s - 1) {
-          const int gx = ox + lx, gy = oy + ly;
-          const int i = ly * EX + lx;
-          float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
-          if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
-            const float xc = sx[i];
-            const float d1 = (INTERIOR || gx < nx - 1) ? sx[i + 1] - xc : 0.f;
-            const float d2 = (INTERIOR || gy < ny - 1) ? sx[i + EX] - xc : 0.f;
-            ball2(fmaf(step, d1, z1[i]), fmaf(step, d2, z2[i]), n1, n2);
-            m1 = fmaf(m, n1 - w1[i], n1);
-            m2 = fmaf(m, n2 - w2[i], n2);
-          }
-          w1[i] = n1;
-          w2[i] = n2;
-          z1[i] = m1;
-          z2[i] = m2;
+    for (int k = 0; k < NS; ++k) {
+      if (dw[k] >= s) {
+        const int i = tid + k * NT;
+        float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
+        const int gx = ox + i % EX, gy = oy + i / EX;
+        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+          const float xc = sx[i];
+          const float d1 = (INTERIOR || gx < nx - 1) ? sx[i + 1] - xc : 0.f;
+          const float d2 = (INTERIOR || gy < ny - 1) ? sx[i + EX] - xc : 0.f;
+          ball2(fmaf(step, d1, z1[i]), fmaf(step, d2, z2[i]), n1, n2);
+          m1 = fmaf(m, n1 - w1[i], n1);
+          m2 = fmaf(m, n2 - w2[i], n2);
         }
+        w1[i] = n1;
+        w2[i] = n2;
+        z1[i] = m1;
+        z2[i] = m2;
       }
     }
     __syncthreads();
@@ -127,12 +126,11 @@ __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, flo
 }
 
 template <class TL>
-__global__ void __launch_bounds__(TL::BX* TL::BY) fgp2d_block(const float* __restrict__ v, const float* __restrict__ w_g,
-                                                              const float* __restrict__ z_g, float* __restrict__ wn_g,
-                                                              float* __restrict__ zn_g, int nx, int ny, float tau,
-                                                              float step, MomBlock mom, int nsteps, int nonneg) {
-  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, FB_BX = TL::BX, FB_BY = TL::BY, FB_TX = TL::TX,
-                FB_TY = TL::TY;
+__global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ v, const float* __restrict__ w_g,
+                                                      const float* __restrict__ z_g, float* __restrict__ wn_g,
+                                                      float* __restrict__ zn_g, int nx, int ny, float tau, float step,
+                                                      MomBlock mom, int nsteps, int nonneg) {
+  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT;
   extern __shared__ float smf[];
   float* sv = smf;
   float* w1 = sv + NE;
@@ -140,29 +138,25 @@ __global__ void __launch_bounds__(TL::BX* TL::BY) fgp2d_block(const float* __res
   float* z1 = w2 + NE;
   float* z2 = z1 + NE;
   float* sx = z2 + NE;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int ox = blockIdx.x * FB_TX - FB_T, oy = blockIdx.y * FB_TY - FB_T;
+  const int tid = threadIdx.x;
+  const int ox = blockIdx.x * TL::TX - FB_T, oy = blockIdx.y * TL::TY - FB_T;
   const size_t n = (size_t)nx * ny;
-  for (int ly = ty; ly < EY; ly += FB_BY) {
-    const int gy = oy + ly;
-    for (int lx = tx; lx < EX; lx += FB_BX) {
-      const int gx = ox + lx;
-      const int i = ly * EX + lx;
-      float vv = 0.f, a = 0.f, b = 0.f, za = 0.f, zb = 0.f;
-      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-        const size_t p = (size_t)gy * nx + gx;
-        vv = v[p];
-        a = w_g[p];
-        b = w_g[n + p];
-        za = z_g[p];
-        zb = z_g[n + p];
-      }
-      sv[i] = vv;
-      w1[i] = a;
-      w2[i] = b;
-      z1[i] = za;
-      z2[i] = zb;
+  for (int i = tid; i < NE; i += NT) {
+    const int gx = ox + i % EX, gy = oy + i / EX;
+    float vv = 0.f, a = 0.f, b = 0.f, za = 0.f, zb = 0.f;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      const size_t p = (size_t)gy * nx + gx;
+      vv = v[p];
+      a = w_g[p];
+      b = w_g[n + p];
+      za = z_g[p];
+      zb = z_g[n + p];
     }
+    sv[i] = vv;
+    w1[i] = a;
+    w2[i] = b;
+    z1[i] = za;
+    z2[i] = zb;
   }
   __syncthreads();
   const bool interior = ox >= 1 && oy >= 1 && ox + EX <= nx - 1 && oy + EY <= ny - 1;
@@ -177,18 +171,16 @@ __global__ void __launch_bounds__(TL::BX* TL::BY) fgp2d_block(const float* __res
     else
       fgp2d_steps<TL, false, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
   }
-  for (int ly = FB_T + ty; ly < FB_T + FB_TY; ly += FB_BY) {
-    const int gy = oy + ly;
-    for (int lx = FB_T + tx; lx < FB_T + FB_TX; lx += FB_BX) {
-      const int gx = ox + lx;
-      if (gx < nx && gy < ny) {
-        const size_t p = (size_t)gy * nx + gx;
-        const int i = ly * EX + lx;
-        wn_g[p] = w1[i];
-        wn_g[n + p] = w2[i];
-        zn_g[p] = z1[i];
-        zn_g[n + p] = z2[i];
-      }
+  for (int q = tid; q < TL::TX * TL::TY; q += NT) {
+    const int lx = FB_T + q % TL::TX, ly = FB_T + q / TL::TX;
+    const int gx = ox + lx, gy = oy + ly;
+    if (gx < nx && gy < ny) {
+      const size_t p = (size_t)gy * nx + gx;
+      const int i = ly * EX + lx;
+      wn_g[p] = w1[i];
+      wn_g[n + p] = w2[i];
+      zn_g[p] = z1[i];
+      zn_g[n + p] = z2[i];
     }
   }
 }
@@ -352,16 +344,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     const float* rz = dual;
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
     int which = 0;
-    int sms = 0;
-    VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
-    const bool small = (long long)((g->nx + 31) / 32) * ((g->ny + 31) / 32) < 4LL * sms;
-    if (small) {
-      VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TileSmall::SMEM));
-    } else {
-      VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TileLarge::SMEM));
-    }
+    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)TileLarge::SMEM));
     for (int k0 = 0; k0 < iters; k0 += FB_T) {
       const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
       MomBlock mb;
@@ -371,15 +355,9 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       float* zn = pairs[which][1];
       {
         LaunchScope _ls("fgp2d_block", s);
-        if (small) {
-          dim3 grid((g->nx + TileSmall::TX - 1) / TileSmall::TX, (g->ny + TileSmall::TY - 1) / TileSmall::TY);
-          fgp2d_block<TileSmall><<<grid, dim3(TileSmall::BX, TileSmall::BY), TileSmall::SMEM, s>>>(
-              v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg);
-        } else {
-          dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
-          fgp2d_block<TileLarge><<<grid, dim3(TileLarge::BX, TileLarge::BY), TileLarge::SMEM, s>>>(
-              v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg);
-        }
+        dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
+        fgp2d_block<TileLarge><<<grid, TileLarge::NT, TileLarge::SMEM, s>>>(v, rw, rz, wn, zn, g->nx, g->ny, tau,
+                                                                           step, mb, ns, nonneg);
       }
       VRPS_LAUNCHED("fgp2d_block");
       rw = wn;
@@ -491,16 +469,8 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
     d = cold;
   }
   const float step = (float)(1.0 / (8.0 * (double)tau));
-  int sms = 0;
-  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const bool small = (long long)((nx + 31) / 32) * ((ny + 31) / 32) < 4LL * sms;
-  if (small) {
-    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)TileSmall::SMEM));
-  } else {
-    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)TileLarge::SMEM));
-  }
+  VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TileLarge::SMEM));
   // FGP momentum t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2; the z formed after iteration k
   // uses (t_k - 1)/t_{k+1}
   double t_cur = 1.0;
@@ -522,15 +492,9 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
     float* zn = pairs[which][1];
     {
       LaunchScope _ls("fgp2d_block", s);
-      if (small) {
-        dim3 grid((nx + TileSmall::TX - 1) / TileSmall::TX, (ny + TileSmall::TY - 1) / TileSmall::TY);
-        fgp2d_block<TileSmall><<<grid, dim3(TileSmall::BX, TileSmall::BY), TileSmall::SMEM, s>>>(
-            v, rw, rz, wn, zn, nx, ny, tau, step, mb, ns, nonneg ? 1 : 0);
-      } else {
-        dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
-        fgp2d_block<TileLarge><<<grid, dim3(TileLarge::BX, TileLarge::BY), TileLarge::SMEM, s>>>(
-            v, rw, rz, wn, zn, nx, ny, tau, step, mb, ns, nonneg ? 1 : 0);
-      }
+      dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
+      fgp2d_block<TileLarge><<<grid, TileLarge::NT, TileLarge::SMEM, s>>>(v, rw, rz, wn, zn, nx, ny, tau, step, mb,
+                                                                         ns, nonneg ? 1 : 0);
     }
     VRPS_LAUNCHED("fgp2d_block");
     rw = wn;

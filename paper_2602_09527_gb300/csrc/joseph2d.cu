@@ -18,13 +18,12 @@ namespace vrps {
 namespace {
 
 constexpr int FWD_LANES = 32;
-constexpr int FWD_PHASES = 8;
-constexpr int ADJ_TX = ADJ2D_TILE_X;   // pixel tile: 16 columns x 32 rows, 2 pixels per thread
+constexpr int FWD_WARPS = 4;     // independent warp items per CTA
+constexpr int FWD_CHUNK = 64;    // dominant-axis lines per warp item
+constexpr int ADJ_TX = ADJ2D_TILE_X;   // pixel tile: 16 columns x 32 rows
 constexpr int ADJ_TY = ADJ2D_TILE_Y;
 constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_CHUNK = 64;
-
-constexpr int FWD_CHUNK = 128;   // dominant-axis lines per CTA (a ray longer than this is split)
 
 struct Fwd2DParams {
   const float* x;
@@ -33,18 +32,25 @@ struct Fwd2DParams {
   const int* ids;
   int nx, ny, nb;
   float jc;
-  int chunks;                 // CTAs per ray group along the lines (gridDim.z)
+  int groups, chunks, items;  // items = rows * groups * chunks
   float* part;                // [rows][chunks][nb] partial sums (chunks > 1)
   unsigned* count;            // [rows][groups] arrival counters, zero between launches
   FwdOut o;
 };
 
+// One warp item = 32 consecutive bins of one angle over FWD_CHUNK consecutive lines.
+// Items are independent warps, so short and long rays balance across the GPU; the chunks of
+// a ray group are added by whichever warp finishes last, in chunk order (deterministic).
 template <int MODE>
-__global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DParams P) {
-  __shared__ float red[FWD_PHASES][FWD_LANES + 1];
-  const int lane = threadIdx.x, ph = threadIdx.y;
-  const int j = blockIdx.x * FWD_LANES + lane;
-  const int row = blockIdx.y;
+__global__ void __launch_bounds__(FWD_LANES * FWD_WARPS) fwd2d_kernel(Fwd2DParams P) {
+  const int lane = threadIdx.x;
+  const int item = blockIdx.x * FWD_WARPS + threadIdx.y;
+  if (item >= P.items) return;
+  const int chunk = item % P.chunks;
+  const int t = item / P.chunks;
+  const int group = t % P.groups;
+  const int row = t / P.groups;
+  const int j = group * FWD_LANES + lane;
   const AngleInfo2D in = P.ang[P.ids[row]];
   const bool tr = in.T != 0;
   const float* __restrict__ img = tr ? P.xT : P.x;
@@ -55,15 +61,15 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
   float acc0 = 0.f, acc1 = 0.f;
   if (j < P.nb) {
     const float u0 = fmaf(in.A1, (float)j - P.jc, uc);   // line-range clipping only
-    int lo = 0, hi = nlines - 1;
+    int lo = chunk * FWD_CHUNK, hi = min(nlines - 1, lo + FWD_CHUNK - 1);
     if (in.A2 != 0.f) {
       // lines where the ray's interpolation point is in (-1, ncols); widened by one line
       float la = fmaf(-1.f - u0, in.inv_A2, lc);
       float lb = fmaf((float)ncols - u0, in.inv_A2, lc);
       if (la > lb) {
-        const float t = la;
+        const float q = la;
         la = lb;
-        lb = t;
+        lb = q;
       }
       la = fminf(fmaxf(la, -2.f), (float)nlines + 1.f);
       lb = fminf(fmaxf(lb, -2.f), (float)nlines + 1.f);
@@ -72,27 +78,21 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
     } else if (!(u0 > -1.f && u0 < (float)ncols)) {
       hi = -1;
     }
-    // this CTA's chunk of lines
-    lo = max(lo, (int)blockIdx.z * FWD_CHUNK);
-    hi = min(hi, (int)blockIdx.z * FWD_CHUNK + FWD_CHUNK - 1);
     // exact fixed-point walk along the ray: U = u * 2^32
-    const int l0 = lo + ph;
     long long U = (long long)(ncols - 1) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
-                  in.A2H * (long long)(2 * l0 - (nlines - 1));
-    const long long dU = in.A2H * (2 * FWD_PHASES);
-    const float* rp = img + (size_t)l0 * ncols;
-    const size_t dp = (size_t)FWD_PHASES * ncols;
+                  in.A2H * (long long)(2 * lo - (nlines - 1));
+    const long long dU = 2 * in.A2H;
+    const float* rp = img + (size_t)lo * ncols;
     const unsigned nc = (unsigned)ncols;
-    // four samples per trip, independent accumulators (keeps 8 loads in flight per thread)
-    int l = l0;
-    for (; l + 3 * FWD_PHASES <= hi; l += 4 * FWD_PHASES) {
+    int l = lo;
+    for (; l + 3 <= hi; l += 4) {
       float a[4], b[4], f[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const long long Uq = U + (long long)q * dU;
         const int i0 = fix_floor(Uq);
         f[q] = fix_frac(Uq);
-        const float* rq = rp + (size_t)q * dp;
+        const float* rq = rp + (size_t)q * ncols;
         a[q] = ((unsigned)i0 < nc) ? __ldg(rq + i0) : 0.f;
         b[q] = ((unsigned)(i0 + 1) < nc) ? __ldg(rq + i0 + 1) : 0.f;
       }
@@ -101,33 +101,28 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_PHASES) fwd2d_kernel(Fwd2DPara
       acc0 += fmaf(f[2], b[2] - a[2], a[2]);
       acc1 += fmaf(f[3], b[3] - a[3], a[3]);
       U += 4 * dU;
-      rp += 4 * dp;
+      rp += 4 * (size_t)ncols;
     }
-    for (; l <= hi; l += FWD_PHASES) {
+    for (; l <= hi; ++l) {
       const int i0 = fix_floor(U);
       const float f = fix_frac(U);
       const float a0 = ((unsigned)i0 < nc) ? __ldg(rp + i0) : 0.f;
       const float a1 = ((unsigned)(i0 + 1) < nc) ? __ldg(rp + i0 + 1) : 0.f;
       acc0 += fmaf(f, a1 - a0, a0);
       U += dU;
-      rp += dp;
+      rp += ncols;
     }
   }
-  red[ph][lane] = acc0 + acc1;
-  __syncthreads();
-  if (ph != 0) return;
-  float s = 0.f;
-#pragma unroll
-  for (int q = 0; q < FWD_PHASES; ++q) s += red[q][lane];
+  float s = acc0 + acc1;
   if (P.chunks > 1) {
-    // publish this chunk's partial sums; the last CTA of the ray group adds all chunks in
+    // publish this chunk's partial sums; the last warp of the ray group adds all chunks in
     // chunk order (deterministic) and runs the epilogue
     const size_t pbase = ((size_t)row * P.chunks) * P.nb;
-    if (j < P.nb) P.part[pbase + (size_t)blockIdx.z * P.nb + j] = s;
+    if (j < P.nb) P.part[pbase + (size_t)chunk * P.nb + j] = s;
     __threadfence();
     unsigned last = 0;
     if (lane == 0) {
-      unsigned* cnt = P.count + (size_t)row * gridDim.x + blockIdx.x;
+      unsigned* cnt = P.count + (size_t)row * P.groups + group;
       last = (atomicAdd(cnt, 1u) == (unsigned)(P.chunks - 1)) ? 1u : 0u;
       if (last) *cnt = 0u;
     }
@@ -206,20 +201,21 @@ __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, flo
 // small float) and receives max(0, 1 - |j - t|/hw) r_j from the bins within hw of t.
 // NC = 2 covers hw <= 1 (bins not finer than pixels): two candidates, unrolled; NC = 0 is
 // the general loop over P.nc candidates.
-template <int NC>
+template <int NC, int PPT>
 __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
+  constexpr int TY = (ADJ_THREADS / ADJ_TX) * PPT;   // tile rows: 16 (one pixel per thread) or 32
   extern __shared__ float sm[];                  // [chunk][fp]
   __shared__ float4 s_par[ADJ_CHUNK];            // Bx, By, (F0 - hw), 1/hw
   __shared__ float s_c0[ADJ_CHUNK];              // 1 - hw
   __shared__ int s_off[ADJ_CHUNK];               // J0 - jlo
   __shared__ int s_jlo[ADJ_CHUNK];
   __shared__ float s_wgt[ADJ_CHUNK];
-  __shared__ float s_tile[ADJ_TY][ADJ_TX + 1];
+  __shared__ float s_tile[TY][ADJ_TX + 1];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_TX + tx;
-  const int ix0 = blockIdx.x * ADJ_TX, iy0 = blockIdx.y * ADJ_TY;
+  const int ix0 = blockIdx.x * ADJ_TX, iy0 = blockIdx.y * TY;
   const float ftx = (float)tx, fty = (float)ty;
-  const float half_rows = (float)(ADJ_TY / 2);
-  float acc0 = 0.f, acc1 = 0.f;                  // pixels (tx, ty) and (tx, ty + ADJ_TY/2)
+  const float half_rows = (float)(TY / 2);
+  float acc0 = 0.f, acc1 = 0.f;                  // pixels (tx, ty) and, with PPT = 2, (tx, ty + TY/2)
   for (int r0 = 0; r0 < P.rows; r0 += P.chunk) {
     const int nr = min(P.chunk, P.rows - r0);
     if (tid < nr) {
@@ -228,7 +224,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
                            in.ByH * (long long)(2 * iy0 - (P.ny - 1));
       const int J0 = fix_floor(T0);
       const float F0 = fix_frac(T0);
-      const float tmin = F0 + fminf(0.f, in.Bx * (float)(ADJ_TX - 1)) + fminf(0.f, in.By * (float)(ADJ_TY - 1));
+      const float tmin = F0 + fminf(0.f, in.Bx * (float)(ADJ_TX - 1)) + fminf(0.f, in.By * (float)(TY - 1));
       const int jlo = J0 + (int)floorf(tmin - in.hw) - 1;
       s_par[tid] = make_float4(in.Bx, in.By, F0 - in.hw, in.inv_hw);
       s_c0[tid] = 1.f - in.hw;
@@ -259,7 +255,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
           acc0 = fmaf(w0, rr[0], acc0);
           acc0 = fmaf(w1, rr[1], acc0);
         }
-        {
+        if (PPT == 2) {
           const float fl = floorf(ub);
           const float d0 = c0 - (ub - fl);
           const float w0 = fmaxf(0.f, fmaf(-fabsf(d0), pr.w, 1.f));
@@ -276,14 +272,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
         const float da = fa + 1.f - (ua + hw), db = fb + 1.f - (ub + hw);   // first candidate - t
         for (int c = 0; c < P.nc; ++c) {
           acc0 = fmaf(fmaxf(0.f, fmaf(-fabsf(da + (float)c), pr.w, 1.f)), ra[c], acc0);
-          acc1 = fmaf(fmaxf(0.f, fmaf(-fabsf(db + (float)c), pr.w, 1.f)), rb[c], acc1);
+          if (PPT == 2) acc1 = fmaf(fmaxf(0.f, fmaf(-fabsf(db + (float)c), pr.w, 1.f)), rb[c], acc1);
         }
       }
     }
     __syncthreads();
   }
-  const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + ADJ_TY / 2;
-  const bool in0 = ix < P.nx && iy < P.ny, in1 = ix < P.nx && iy1 < P.ny;
+  const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + TY / 2;
+  const bool in0 = ix < P.nx && iy < P.ny, in1 = PPT == 2 && ix < P.nx && iy1 < P.ny;
   const size_t p0 = (size_t)iy * P.nx + ix, p1 = (size_t)iy1 * P.nx + ix;
   const UpdateArgs& u = P.u;
   if (!u.enabled) {
@@ -295,10 +291,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
   const float x1 = in1 ? update_pixel(u, p1, acc1) : 0.f;
   if (!u.theta && u.xT) {
     s_tile[ty][tx] = x0;
-    s_tile[ty + ADJ_TY / 2][tx] = x1;
+    if (PPT == 2) s_tile[ty + TY / 2][tx] = x1;
     __syncthreads();
-    for (int e = tid; e < ADJ_TX * ADJ_TY; e += ADJ_THREADS) {
-      const int c = e / ADJ_TY, r = e - c * ADJ_TY;
+    for (int e = tid; e < ADJ_TX * TY; e += ADJ_THREADS) {
+      const int c = e / TY, r = e - c * TY;
       const int ox = ix0 + c, oy = iy0 + r;
       if (ox < P.nx && oy < P.ny) u.xT[(size_t)ox * P.ny + oy] = s_tile[r][c];
     }
@@ -343,22 +339,23 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.nb = g->n_bins;
   P.jc = 0.5f * (float)(g->n_bins - 1);
   P.o = o;
-  const int groups = (g->n_bins + FWD_LANES - 1) / FWD_LANES;
+  P.groups = (g->n_bins + FWD_LANES - 1) / FWD_LANES;
   const int max_lines = g->nx > g->ny ? g->nx : g->ny;
   P.chunks = (max_lines + FWD_CHUNK - 1) / FWD_CHUNK;
+  P.items = rows * P.groups * P.chunks;
   P.part = nullptr;
   P.count = nullptr;
   if (P.chunks > 1) {
     vrps_geom* gm = const_cast<vrps_geom*>(g);
     if (!gm->ws.fwd_part) {
       VRPS_CUDA(cudaMalloc((void**)&gm->ws.fwd_part, sizeof(float) * (size_t)g->n_angles * P.chunks * g->n_bins));
-      VRPS_CUDA(cudaMalloc((void**)&gm->ws.fwd_count, sizeof(unsigned) * (size_t)g->n_angles * groups));
-      VRPS_CUDA(cudaMemset(gm->ws.fwd_count, 0, sizeof(unsigned) * (size_t)g->n_angles * groups));
+      VRPS_CUDA(cudaMalloc((void**)&gm->ws.fwd_count, sizeof(unsigned) * (size_t)g->n_angles * P.groups));
+      VRPS_CUDA(cudaMemset(gm->ws.fwd_count, 0, sizeof(unsigned) * (size_t)g->n_angles * P.groups));
     }
     P.part = gm->ws.fwd_part;
     P.count = gm->ws.fwd_count;
   }
-  dim3 grid(groups, rows, P.chunks), block(FWD_LANES, FWD_PHASES);
+  dim3 grid((P.items + FWD_WARPS - 1) / FWD_WARPS), block(FWD_LANES, FWD_WARPS);
   switch (mode) {
     case FWD_PLAIN: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); } break;
     case FWD_RESID: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); } break;
@@ -387,15 +384,22 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.chunk = chunk < ADJ_CHUNK ? (chunk < 1 ? 1 : chunk) : ADJ_CHUNK;
   P.u = u;
   const size_t smem = sizeof(float) * (size_t)P.chunk * P.fp;
-  dim3 grid((g->nx + ADJ_TX - 1) / ADJ_TX, (g->ny + ADJ_TY - 1) / ADJ_TY), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
+  // one pixel per thread unless that already fills the GPU twice over (then two)
+  int sms = 0;
+  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+  const bool two = (long long)g->nx * g->ny > 2LL * sms * 2048;
+  const int ty = (ADJ_THREADS / ADJ_TX) * (two ? 2 : 1);
+  dim3 grid((g->nx + ADJ_TX - 1) / ADJ_TX, (g->ny + ty - 1) / ty), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
+  auto launch = [&](auto kern) -> int {
+    if (smem > 48 * 1024) VRPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope _ls("adj2d_kernel", s);
+    kern<<<grid, block, smem, s>>>(P);
+    return VRPS_OK;
+  };
   if (g->adj_nc == 2) {
-    if (smem > 48 * 1024) VRPS_CUDA(cudaFuncSetAttribute(adj2d_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LaunchScope _ls("adj2d_kernel", s);
-    adj2d_kernel<2><<<grid, block, smem, s>>>(P);
+    VRPS_TRY(two ? launch(adj2d_kernel<2, 2>) : launch(adj2d_kernel<2, 1>));
   } else {
-    if (smem > 48 * 1024) VRPS_CUDA(cudaFuncSetAttribute(adj2d_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LaunchScope _ls("adj2d_kernel", s);
-    adj2d_kernel<0><<<grid, block, smem, s>>>(P);
+    VRPS_TRY(two ? launch(adj2d_kernel<0, 2>) : launch(adj2d_kernel<0, 1>));
   }
   VRPS_LAUNCHED("adj2d");
   return VRPS_OK;
