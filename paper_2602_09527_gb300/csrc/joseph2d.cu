@@ -46,8 +46,10 @@ __global__ void __launch_bounds__(FWD_LANES * FWD_WARPS) fwd2d_kernel(Fwd2DParam
   const int lane = threadIdx.x;
   const int item = blockIdx.x * FWD_WARPS + threadIdx.y;
   if (item >= P.items) return;
-  const int chunk = item % P.chunks;
-  const int t = item / P.chunks;
+  // chunk-major item order: warps running at the same time read the same band of lines
+  const int per_chunk = P.items / P.chunks;
+  const int chunk = item / per_chunk;
+  const int t = item - chunk * per_chunk;
   const int group = t % P.groups;
   const int row = t / P.groups;
   const int j = group * FWD_LANES + lane;
@@ -384,10 +386,10 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.chunk = chunk < ADJ_CHUNK ? (chunk < 1 ? 1 : chunk) : ADJ_CHUNK;
   P.u = u;
   const size_t smem = sizeof(float) * (size_t)P.chunk * P.fp;
-  // one pixel per thread unless that already fills the GPU twice over (then two)
+  // two pixels per thread (shared per-angle parameters) unless the image is very small
   int sms = 0;
   VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
-  const bool two = (long long)g->nx * g->ny > 2LL * sms * 2048;
+  const bool two = (long long)g->nx * g->ny > 512LL * sms;
   const int ty = (ADJ_THREADS / ADJ_TX) * (two ? 2 : 1);
   dim3 grid((g->nx + ADJ_TX - 1) / ADJ_TX, (g->ny + ty - 1) / ty), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
   auto launch = [&](auto kern) -> int {
