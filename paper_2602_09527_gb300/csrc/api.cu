@@ -124,6 +124,7 @@ static void free_ws(Workspace& w) {
   if (w.partials) cudaFree(w.partials);
   if (w.fwd_part) cudaFree(w.fwd_part);
   if (w.fwd_count) cudaFree(w.fwd_count);
+  if (w.dev_error) cudaFree(w.dev_error);
   if (w.scalars) cudaFree(w.scalars);
   if (w.sched_dev) cudaFree(w.sched_dev);
   if (w.sched_host) cudaFreeHost(w.sched_host);

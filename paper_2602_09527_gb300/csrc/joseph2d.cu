@@ -10,6 +10,7 @@
 // the tile's footprint on the detector (at most fp bins) is staged in shared memory, then
 // each pixel sums w_j r_j over the <= nc bins whose ray passes within one interpolation
 // cell of its centre, with the Joseph weight of that (ray, pixel) pair.  No atomics.
+#include <cstdint>
 #include <cstring>
 
 #include "vrps_internal.h"
@@ -18,12 +19,13 @@ namespace vrps {
 namespace {
 
 constexpr int FWD_LANES = 32;
-constexpr int FWD_WARPS = 4;     // independent warp items per CTA
-constexpr int FWD_CHUNK = 64;    // dominant-axis lines per warp item
-constexpr int ADJ_TX = ADJ2D_TILE_X;   // pixel tile: 16 columns x 32 rows
+constexpr int FWD_THREADS = 256;
+constexpr int FWD_BAND_BYTES = 64 * 1024;   // shared-memory band of image lines per CTA
+constexpr int ADJ_TX = ADJ2D_TILE_X;        // pixel tile: 16 columns x 32 rows
 constexpr int ADJ_TY = ADJ2D_TILE_Y;
 constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_CHUNK = 64;
+constexpr unsigned WAIT_LIMIT = 1u << 22;   // bounded mbarrier polls before giving up
 
 struct Fwd2DParams {
   const float* x;
@@ -32,110 +34,165 @@ struct Fwd2DParams {
   const int* ids;
   int nx, ny, nb;
   float jc;
-  int groups, chunks, items;  // items = rows * groups * chunks
-  float* part;                // [rows][chunks][nb] partial sums (chunks > 1)
-  unsigned* count;            // [rows][groups] arrival counters, zero between launches
+  int band;                   // lines per band
+  int bands;                  // gridDim.x
+  float* part;                // [rows][bands][nb] partial sums
+  unsigned* count;            // [rows] arrival counters, zero between launches
+  unsigned* err;              // device error word
   FwdOut o;
 };
 
-// One warp item = 32 consecutive bins of one angle over FWD_CHUNK consecutive lines.
-// Items are independent warps, so short and long rays balance across the GPU; the chunks of
-// a ray group are added by whichever warp finishes last, in chunk order (deterministic).
-template <int MODE>
-__global__ void __launch_bounds__(FWD_LANES * FWD_WARPS) fwd2d_kernel(Fwd2DParams P) {
-  const int lane = threadIdx.x;
-  const int item = blockIdx.x * FWD_WARPS + threadIdx.y;
-  if (item >= P.items) return;
-  // chunk-major item order: warps running at the same time read the same band of lines
-  const int per_chunk = P.items / P.chunks;
-  const int chunk = item / per_chunk;
-  const int t = item - chunk * per_chunk;
-  const int group = t % P.groups;
-  const int row = t / P.groups;
-  const int j = group * FWD_LANES + lane;
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_addr(const void* p) {
+  unsigned long long g;
+  asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(p));
+  return g;
+}
+
+// TMA bulk copy global -> shared completing on an mbarrier (transaction bytes).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(global_addr(src)), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Forward projector, one CTA per (angle row, band of `band` dominant-axis lines).  The band
+// -- `band` consecutive rows of x (rows-marched angles) or of x^T (columns-marched angles) --
+// is one contiguous block of memory, fetched into shared memory by a single TMA bulk copy;
+// the CTA's eight warps then walk all n_bins rays of the angle through it, 32 bins per warp
+// pass, in 64-bit fixed point.  Each ray's band sum goes to a partial buffer; the CTA that
+// completes a row last adds the bands in band order (deterministic) and runs the epilogue.
+template <int MODE, bool BULK>
+__global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
+  extern __shared__ __align__(128) float band[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = blockIdx.x, row = blockIdx.y;
   const AngleInfo2D in = P.ang[P.ids[row]];
   const bool tr = in.T != 0;
   const float* __restrict__ img = tr ? P.xT : P.x;
   const int ncols = tr ? P.ny : P.nx;
   const int nlines = tr ? P.nx : P.ny;
+  const int l0 = c * P.band;
+  const int nl = min(P.band, nlines - l0);   // lines of this band (may be <= 0)
+  bool ok = true;
+  if (nl > 0) {
+    const float* src = img + (size_t)l0 * ncols;
+    if (BULK) {
+      if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncthreads();
+      if (tid == 0) bulk_load(band, src, (unsigned)(nl * ncols * sizeof(float)), &bar);
+      unsigned it = 0;
+      while (!mbar_try_wait(&bar, 0) && ++it < WAIT_LIMIT) {
+      }
+      ok = it < WAIT_LIMIT;
+      if (!ok) {
+        // record the failure, give the copy in flight a second bounded chance to land in
+        // shared memory before this CTA retires, and compute nothing from the band
+        if (tid == 0) atomicOr(P.err, 1u);
+        unsigned it2 = 0;
+        while (!mbar_try_wait(&bar, 0) && ++it2 < WAIT_LIMIT) {
+        }
+      }
+    } else {
+      for (int e = tid; e < nl * ncols; e += FWD_THREADS) band[e] = __ldg(src + e);
+      __syncthreads();
+    }
+  }
   const float uc = 0.5f * (float)(ncols - 1);
   const float lc = 0.5f * (float)(nlines - 1);
-  float acc0 = 0.f, acc1 = 0.f;
-  if (j < P.nb) {
-    const float u0 = fmaf(in.A1, (float)j - P.jc, uc);   // line-range clipping only
-    int lo = chunk * FWD_CHUNK, hi = min(nlines - 1, lo + FWD_CHUNK - 1);
-    if (in.A2 != 0.f) {
-      // lines where the ray's interpolation point is in (-1, ncols); widened by one line
-      float la = fmaf(-1.f - u0, in.inv_A2, lc);
-      float lb = fmaf((float)ncols - u0, in.inv_A2, lc);
-      if (la > lb) {
-        const float q = la;
-        la = lb;
-        lb = q;
+  const size_t pbase = (size_t)row * P.bands * P.nb + (size_t)c * P.nb;
+  const unsigned nc = (unsigned)ncols;
+  for (int j0 = warp * FWD_LANES; j0 < P.nb; j0 += FWD_THREADS) {
+    const int j = j0 + lane;
+    float acc0 = 0.f, acc1 = 0.f;
+    if (j < P.nb && nl > 0 && ok) {
+      const float u0 = fmaf(in.A1, (float)j - P.jc, uc);   // line-range clipping only
+      int lo = l0, hi = l0 + nl - 1;
+      if (in.A2 != 0.f) {
+        float la = fmaf(-1.f - u0, in.inv_A2, lc);
+        float lb = fmaf((float)ncols - u0, in.inv_A2, lc);
+        if (la > lb) {
+          const float q = la;
+          la = lb;
+          lb = q;
+        }
+        la = fminf(fmaxf(la, -2.f), (float)nlines + 1.f);
+        lb = fminf(fmaxf(lb, -2.f), (float)nlines + 1.f);
+        lo = max(lo, (int)floorf(la) - 1);
+        hi = min(hi, (int)ceilf(lb) + 1);
+      } else if (!(u0 > -1.f && u0 < (float)ncols)) {
+        hi = -1;
       }
-      la = fminf(fmaxf(la, -2.f), (float)nlines + 1.f);
-      lb = fminf(fmaxf(lb, -2.f), (float)nlines + 1.f);
-      lo = max(lo, (int)floorf(la) - 1);
-      hi = min(hi, (int)ceilf(lb) + 1);
-    } else if (!(u0 > -1.f && u0 < (float)ncols)) {
-      hi = -1;
-    }
-    // exact fixed-point walk along the ray: U = u * 2^32
-    long long U = (long long)(ncols - 1) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
-                  in.A2H * (long long)(2 * lo - (nlines - 1));
-    const long long dU = 2 * in.A2H;
-    const float* rp = img + (size_t)lo * ncols;
-    const unsigned nc = (unsigned)ncols;
-    int l = lo;
-    for (; l + 3 <= hi; l += 4) {
-      float a[4], b[4], f[4];
+      // exact fixed-point walk along the ray: U = u * 2^32
+      long long U = (long long)(ncols - 1) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
+                    in.A2H * (long long)(2 * lo - (nlines - 1));
+      const long long dU = 2 * in.A2H;
+      const float* rp = band + (size_t)(lo - l0) * ncols;
+      int l = lo;
+      for (; l + 3 <= hi; l += 4) {
+        float a[4], b[4], f[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const long long Uq = U + (long long)q * dU;
-        const int i0 = fix_floor(Uq);
-        f[q] = fix_frac(Uq);
-        const float* rq = rp + (size_t)q * ncols;
-        a[q] = ((unsigned)i0 < nc) ? __ldg(rq + i0) : 0.f;
-        b[q] = ((unsigned)(i0 + 1) < nc) ? __ldg(rq + i0 + 1) : 0.f;
+        for (int q = 0; q < 4; ++q) {
+          const long long Uq = U + (long long)q * dU;
+          const int i0 = fix_floor(Uq);
+          f[q] = fix_frac(Uq);
+          const float* rq = rp + q * ncols;
+          a[q] = ((unsigned)i0 < nc) ? rq[i0] : 0.f;
+          b[q] = ((unsigned)(i0 + 1) < nc) ? rq[i0 + 1] : 0.f;
+        }
+        acc0 += fmaf(f[0], b[0] - a[0], a[0]);
+        acc1 += fmaf(f[1], b[1] - a[1], a[1]);
+        acc0 += fmaf(f[2], b[2] - a[2], a[2]);
+        acc1 += fmaf(f[3], b[3] - a[3], a[3]);
+        U += 4 * dU;
+        rp += 4 * ncols;
       }
-      acc0 += fmaf(f[0], b[0] - a[0], a[0]);
-      acc1 += fmaf(f[1], b[1] - a[1], a[1]);
-      acc0 += fmaf(f[2], b[2] - a[2], a[2]);
-      acc1 += fmaf(f[3], b[3] - a[3], a[3]);
-      U += 4 * dU;
-      rp += 4 * (size_t)ncols;
+      for (; l <= hi; ++l) {
+        const int i0 = fix_floor(U);
+        const float f = fix_frac(U);
+        const float a0 = ((unsigned)i0 < nc) ? rp[i0] : 0.f;
+        const float a1 = ((unsigned)(i0 + 1) < nc) ? rp[i0 + 1] : 0.f;
+        acc0 += fmaf(f, a1 - a0, a0);
+        U += dU;
+        rp += ncols;
+      }
     }
-    for (; l <= hi; ++l) {
-      const int i0 = fix_floor(U);
-      const float f = fix_frac(U);
-      const float a0 = ((unsigned)i0 < nc) ? __ldg(rp + i0) : 0.f;
-      const float a1 = ((unsigned)(i0 + 1) < nc) ? __ldg(rp + i0 + 1) : 0.f;
-      acc0 += fmaf(f, a1 - a0, a0);
-      U += dU;
-      rp += ncols;
-    }
+    if (j < P.nb) P.part[pbase + j] = acc0 + acc1;
   }
-  float s = acc0 + acc1;
-  if (P.chunks > 1) {
-    // publish this chunk's partial sums; the last warp of the ray group adds all chunks in
-    // chunk order (deterministic) and runs the epilogue
-    const size_t pbase = ((size_t)row * P.chunks) * P.nb;
-    if (j < P.nb) P.part[pbase + (size_t)chunk * P.nb + j] = s;
-    __threadfence();
-    unsigned last = 0;
-    if (lane == 0) {
-      unsigned* cnt = P.count + (size_t)row * P.groups + group;
-      last = (atomicAdd(cnt, 1u) == (unsigned)(P.chunks - 1)) ? 1u : 0u;
-      if (last) *cnt = 0u;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    __threadfence();
-    s = 0.f;
-    if (j < P.nb)
-      for (int c = 0; c < P.chunks; ++c) s += __ldcg(P.part + pbase + (size_t)c * P.nb + j);
+  // the last CTA of this row adds the bands in order and applies the epilogue
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned prev = atomicAdd(P.count + row, 1u);
+    s_last = prev == (unsigned)(P.bands - 1) ? 1u : 0u;
+    if (s_last) P.count[row] = 0u;
   }
-  if (j < P.nb) {
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const size_t rbase = (size_t)row * P.bands * P.nb;
+  for (int j = tid; j < P.nb; j += FWD_THREADS) {
+    float s = 0.f;
+    for (int q = 0; q < P.bands; ++q) s += __ldcg(P.part + rbase + (size_t)q * P.nb + j);
     const float r = s * in.wgt;
     const size_t idx = (size_t)row * P.nb + j;
     if (MODE == FWD_PLAIN) {
@@ -341,29 +398,49 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.nb = g->n_bins;
   P.jc = 0.5f * (float)(g->n_bins - 1);
   P.o = o;
-  P.groups = (g->n_bins + FWD_LANES - 1) / FWD_LANES;
-  const int max_lines = g->nx > g->ny ? g->nx : g->ny;
-  P.chunks = (max_lines + FWD_CHUNK - 1) / FWD_CHUNK;
-  P.items = rows * P.groups * P.chunks;
-  P.part = nullptr;
-  P.count = nullptr;
-  if (P.chunks > 1) {
-    vrps_geom* gm = const_cast<vrps_geom*>(g);
-    if (!gm->ws.fwd_part) {
-      VRPS_CUDA(cudaMalloc((void**)&gm->ws.fwd_part, sizeof(float) * (size_t)g->n_angles * P.chunks * g->n_bins));
-      VRPS_CUDA(cudaMalloc((void**)&gm->ws.fwd_count, sizeof(unsigned) * (size_t)g->n_angles * P.groups));
-      VRPS_CUDA(cudaMemset(gm->ws.fwd_count, 0, sizeof(unsigned) * (size_t)g->n_angles * P.groups));
-    }
-    P.part = gm->ws.fwd_part;
-    P.count = gm->ws.fwd_count;
+  const int maxw = g->nx > g->ny ? g->nx : g->ny;   // widest line (row of x or of x^T)
+  const int maxl = maxw;
+  int band = FWD_BAND_BYTES / (int)(sizeof(float) * maxw);
+  if (band < 1) band = 1;
+  if (band > maxl) band = maxl;
+  P.band = band;
+  P.bands = (maxl + band - 1) / band;
+  vrps_geom* gm = const_cast<vrps_geom*>(g);
+  Workspace& ws = gm->ws;
+  if (!ws.fwd_part || ws.fwd_bands != P.bands) {
+    if (ws.fwd_part) cudaFree(ws.fwd_part);
+    ws.fwd_part = nullptr;
+    VRPS_CUDA(cudaMalloc((void**)&ws.fwd_part, sizeof(float) * (size_t)g->n_angles * P.bands * g->n_bins));
+    ws.fwd_bands = P.bands;
   }
-  dim3 grid((P.items + FWD_WARPS - 1) / FWD_WARPS), block(FWD_LANES, FWD_WARPS);
+  if (!ws.fwd_count) {
+    VRPS_CUDA(cudaMalloc((void**)&ws.fwd_count, sizeof(unsigned) * (size_t)g->n_angles));
+    VRPS_CUDA(cudaMemset(ws.fwd_count, 0, sizeof(unsigned) * (size_t)g->n_angles));
+  }
+  if (!ws.dev_error) {
+    VRPS_CUDA(cudaMalloc((void**)&ws.dev_error, sizeof(unsigned)));
+    VRPS_CUDA(cudaMemset(ws.dev_error, 0, sizeof(unsigned)));
+  }
+  P.part = ws.fwd_part;
+  P.count = ws.fwd_count;
+  P.err = ws.dev_error;
+  // the bulk copy needs 16-byte aligned rows: line lengths that are multiples of 4 floats
+  const bool bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
+  const size_t smem = sizeof(float) * (size_t)band * maxw;
+  dim3 grid(P.bands, rows), block(FWD_THREADS);
+  auto launch = [&](auto kern) -> int {
+    if (smem > 48 * 1024)
+      VRPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope _ls("fwd2d_kernel", s);
+    kern<<<grid, block, smem, s>>>(P);
+    return VRPS_OK;
+  };
   switch (mode) {
-    case FWD_PLAIN: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_PLAIN><<<grid, block, 0, s>>>(P); } break;
-    case FWD_RESID: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_RESID><<<grid, block, 0, s>>>(P); } break;
-    case FWD_SVRG: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_SVRG><<<grid, block, 0, s>>>(P); } break;
-    case FWD_SAGA: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_SAGA><<<grid, block, 0, s>>>(P); } break;
-    case FWD_SNAP: { LaunchScope _ls("fwd2d_kernel", s); fwd2d_kernel<FWD_SNAP><<<grid, block, 0, s>>>(P); } break;
+    case FWD_PLAIN: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_PLAIN, true>) : launch(fwd2d_kernel<FWD_PLAIN, false>)); break;
+    case FWD_RESID: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_RESID, true>) : launch(fwd2d_kernel<FWD_RESID, false>)); break;
+    case FWD_SVRG: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_SVRG, true>) : launch(fwd2d_kernel<FWD_SVRG, false>)); break;
+    case FWD_SAGA: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_SAGA, true>) : launch(fwd2d_kernel<FWD_SAGA, false>)); break;
+    case FWD_SNAP: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_SNAP, true>) : launch(fwd2d_kernel<FWD_SNAP, false>)); break;
     default: return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
   }
   VRPS_LAUNCHED("fwd2d");

@@ -108,8 +108,10 @@ struct Workspace {
   float* dual_s3 = nullptr;
   float* dual_s4 = nullptr;
   double* partials = nullptr;   // reduction partials
-  float* fwd_part = nullptr;      // 2D forward: per-chunk partial ray sums
-  unsigned* fwd_count = nullptr;  // 2D forward: chunk arrival counters
+  float* fwd_part = nullptr;      // 2D forward: per-band partial ray sums
+  unsigned* fwd_count = nullptr;  // 2D forward: band arrival counters (one per angle row)
+  int fwd_bands = 0;              // bands the partial buffer was sized for
+  unsigned* dev_error = nullptr;  // device-side error word (bounded waits that expired)
   double* scalars = nullptr;    // [16] device scalars
   float* sino = nullptr;        // [m] sinogram scratch
   float* img = nullptr;         // [n] image scratch
