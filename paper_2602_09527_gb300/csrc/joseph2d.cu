@@ -72,10 +72,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 
 // Forward projector, one CTA per (angle row, band of `band` dominant-axis lines).  The band
 // -- `band` consecutive rows of x (rows-marched angles) or of x^T (columns-marched angles) --
-// is one contiguous block of memory, fetched into shared memory by a single TMA bulk copy;
-// the CTA's eight warps then walk all n_bins rays of the angle through it, 32 bins per warp
-// pass, in 64-bit fixed point.  Each ray's band sum goes to a partial buffer; the CTA that
-// completes a row last adds the bands in band order (deterministic) and runs the epilogue.
+// is copied row by row into shared memory by TMA bulk copies, with FWD_PAD zero columns on
+// both sides of every row so that the taps of any sample whose point lies in (-1, ncols) are
+// read without bounds tests.  The CTA's eight warps walk all n_bins rays of the angle through
+// the band, 32 bins per warp pass.  Positions: every trip of four lines re-anchors exactly
+// from the 64-bit fixed-point walk (u = I + F); the four samples of the trip add A2 k to F
+// in float (|F + A2 k| < 5, error ~1e-7 pixel).  Each ray's band sum goes to a partial
+// buffer; the CTA that completes a row last adds the bands in band order (deterministic) and
+// runs the epilogue.
+constexpr int FWD_PAD = 4;   // zero floats left and right of each staged line (16 bytes)
+
 template <int MODE, bool BULK>
 __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
   extern __shared__ __align__(128) float band[];
@@ -88,39 +94,58 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
   const float* __restrict__ img = tr ? P.xT : P.x;
   const int ncols = tr ? P.ny : P.nx;
   const int nlines = tr ? P.nx : P.ny;
+  const int stride = ncols + 2 * FWD_PAD;
   const int l0 = c * P.band;
   const int nl = min(P.band, nlines - l0);   // lines of this band (may be <= 0)
   bool ok = true;
   if (nl > 0) {
     const float* src = img + (size_t)l0 * ncols;
+    for (int e = tid; e < nl * 2 * FWD_PAD; e += FWD_THREADS) {   // zero margins
+      const int L = e / (2 * FWD_PAD), q = e - L * 2 * FWD_PAD;
+      band[L * stride + (q < FWD_PAD ? q : ncols + q)] = 0.f;
+    }
     if (BULK) {
       if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       __syncthreads();
-      if (tid == 0) bulk_load(band, src, (unsigned)(nl * ncols * sizeof(float)), &bar);
+      if (tid == 0) {
+        const unsigned row_bytes = (unsigned)(ncols * sizeof(float));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
+                     "r"(row_bytes * (unsigned)nl)
+                     : "memory");
+        for (int L = 0; L < nl; ++L)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_addr(band + L * stride + FWD_PAD)),
+              "l"(global_addr(src + (size_t)L * ncols)), "r"(row_bytes), "r"(smem_addr(&bar))
+              : "memory");
+      }
       unsigned it = 0;
       while (!mbar_try_wait(&bar, 0) && ++it < WAIT_LIMIT) {
       }
       ok = it < WAIT_LIMIT;
       if (!ok) {
-        // record the failure, give the copy in flight a second bounded chance to land in
+        // record the failure, give the copies in flight a second bounded chance to land in
         // shared memory before this CTA retires, and compute nothing from the band
         if (tid == 0) atomicOr(P.err, 1u);
         unsigned it2 = 0;
         while (!mbar_try_wait(&bar, 0) && ++it2 < WAIT_LIMIT) {
         }
       }
+      __syncthreads();   // the zero margins written above
     } else {
-      for (int e = tid; e < nl * ncols; e += FWD_THREADS) band[e] = __ldg(src + e);
+      for (int e = tid; e < nl * ncols; e += FWD_THREADS) {
+        const int L = e / ncols;
+        band[L * stride + FWD_PAD + (e - L * ncols)] = __ldg(src + e);
+      }
       __syncthreads();
     }
   }
   const float uc = 0.5f * (float)(ncols - 1);
   const float lc = 0.5f * (float)(nlines - 1);
   const size_t pbase = (size_t)row * P.bands * P.nb + (size_t)c * P.nb;
-  const unsigned nc = (unsigned)ncols;
   for (int j0 = warp * FWD_LANES; j0 < P.nb; j0 += FWD_THREADS) {
     const int j = j0 + lane;
     float acc0 = 0.f, acc1 = 0.f;
@@ -142,38 +167,39 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
       } else if (!(u0 > -1.f && u0 < (float)ncols)) {
         hi = -1;
       }
-      // exact fixed-point walk along the ray: U = u * 2^32
-      long long U = (long long)(ncols - 1) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
-                    in.A2H * (long long)(2 * lo - (nlines - 1));
-      const long long dU = 2 * in.A2H;
-      const float* rp = band + (size_t)(lo - l0) * ncols;
+      // exact fixed-point walk along the ray: U = u * 2^32; FWD_PAD shifts into the padded row
+      long long U = (long long)(ncols - 1 + 2 * FWD_PAD) * 2147483648LL +
+                    in.A1H * (long long)(2 * j - (P.nb - 1)) + in.A2H * (long long)(2 * lo - (nlines - 1));
+      const long long dU4 = 8 * in.A2H;   // four lines
+      const float A2 = in.A2;
+      int rb = (lo - l0) * stride;          // shared-memory offset of the current line
       int l = lo;
       for (; l + 3 <= hi; l += 4) {
-        float a[4], b[4], f[4];
+        const int I = fix_floor(U) + rb;
+        const float F = fix_frac(U);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const long long Uq = U + (long long)q * dU;
-          const int i0 = fix_floor(Uq);
-          f[q] = fix_frac(Uq);
-          const float* rq = rp + q * ncols;
-          a[q] = ((unsigned)i0 < nc) ? rq[i0] : 0.f;
-          b[q] = ((unsigned)(i0 + 1) < nc) ? rq[i0 + 1] : 0.f;
+          const float ur = fmaf(A2, (float)q, F);
+          const float fl = floorf(ur);
+          const float f = ur - fl;
+          const float* t = band + (I + q * stride + (int)fl);
+          const float a = t[0], b = t[1];
+          if (q & 1) acc1 += fmaf(f, b - a, a);
+          else acc0 += fmaf(f, b - a, a);
         }
-        acc0 += fmaf(f[0], b[0] - a[0], a[0]);
-        acc1 += fmaf(f[1], b[1] - a[1], a[1]);
-        acc0 += fmaf(f[2], b[2] - a[2], a[2]);
-        acc1 += fmaf(f[3], b[3] - a[3], a[3]);
-        U += 4 * dU;
-        rp += 4 * ncols;
+        U += dU4;
+        rb += 4 * stride;
       }
-      for (; l <= hi; ++l) {
-        const int i0 = fix_floor(U);
-        const float f = fix_frac(U);
-        const float a0 = ((unsigned)i0 < nc) ? rp[i0] : 0.f;
-        const float a1 = ((unsigned)(i0 + 1) < nc) ? rp[i0 + 1] : 0.f;
-        acc0 += fmaf(f, a1 - a0, a0);
-        U += dU;
-        rp += ncols;
+      {
+        const int I = fix_floor(U) + rb;
+        const float F = fix_frac(U);
+        for (int q = 0; l <= hi; ++l, ++q) {
+          const float ur = fmaf(A2, (float)q, F);
+          const float fl = floorf(ur);
+          const float f = ur - fl;
+          const float* t = band + (I + q * stride + (int)fl);
+          acc0 += fmaf(f, t[1] - t[0], t[0]);
+        }
       }
     }
     if (j < P.nb) P.part[pbase + j] = acc0 + acc1;
@@ -400,7 +426,7 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.o = o;
   const int maxw = g->nx > g->ny ? g->nx : g->ny;   // widest line (row of x or of x^T)
   const int maxl = maxw;
-  int band = FWD_BAND_BYTES / (int)(sizeof(float) * maxw);
+  int band = FWD_BAND_BYTES / (int)(sizeof(float) * (maxw + 2 * FWD_PAD));
   if (band < 1) band = 1;
   if (band > maxl) band = maxl;
   P.band = band;
@@ -426,7 +452,7 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.err = ws.dev_error;
   // the bulk copy needs 16-byte aligned rows: line lengths that are multiples of 4 floats
   const bool bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
-  const size_t smem = sizeof(float) * (size_t)band * maxw;
+  const size_t smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD);
   dim3 grid(P.bands, rows), block(FWD_THREADS);
   auto launch = [&](auto kern) -> int {
     if (smem > 48 * 1024)
