@@ -3,6 +3,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 
@@ -30,6 +32,20 @@ int fail(int code, const char* fmt, ...) {
 int cuda_fail(cudaError_t e, const char* what) {
   set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
   return e == cudaErrorMemoryAllocation ? VRPS_ERR_OUT_OF_MEMORY : VRPS_ERR_CUDA;
+}
+
+int smem_opt_in(const void* kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return VRPS_OK;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{kern, dev}];
+  if (have >= bytes) return VRPS_OK;
+  VRPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+  return VRPS_OK;
 }
 
 int ensure(float** p, size_t count) {
@@ -149,6 +165,7 @@ static void free_geom(vrps_geom* g) {
 }
 
 static int finish_common(vrps_geom* g) {
+  VRPS_CUDA(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
   std::vector<int> nat(g->n_angles);
   for (int a = 0; a < g->n_angles; ++a) nat[a] = a;
   VRPS_CUDA(cudaMalloc((void**)&g->order_natural, sizeof(int) * g->n_angles));

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ 
                                                       const float* __restrict__ z_g, float* __restrict__ wn_g,
                                                       float* __restrict__ zn_g, int nx, int ny, float tau, float step,
                                                       MomBlock mom, int nsteps, int nonneg) {
+  pdl_prologue();
   constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT;
   extern __shared__ float smf[];
   float* sv = smf;
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ 
 __global__ void __launch_bounds__(256) fgp2d_out(const float* __restrict__ v, const float* __restrict__ w,
                                                  float* wdst, int nx, int ny, float tau, int nonneg,
                                                  ProxTail t) {
+  pdl_prologue();
   __shared__ float tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   const size_t n = (size_t)nx * ny;
@@ -266,6 +268,7 @@ __device__ __forceinline__ float x3(const float* __restrict__ v, const float* wc
 __global__ void __launch_bounds__(256) fgp3d_iter(const float* __restrict__ v, const float* wc,
                                                   const float* wp, float* __restrict__ wn, Dims3 D,
                                                   float tau, float step, float mom, int nonneg) {
+  pdl_prologue();
   const int gx = blockIdx.x * 32 + threadIdx.x;
   const int gy = blockIdx.y * 8 + threadIdx.y;
   const int gz = blockIdx.z;
@@ -286,6 +289,7 @@ __global__ void __launch_bounds__(256) fgp3d_iter(const float* __restrict__ v, c
 
 __global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, const float* __restrict__ w,
                                                  float* wdst, Dims3 D, float tau, int nonneg, ProxTail t) {
+  pdl_prologue();
   const int gx = blockIdx.x * 32 + threadIdx.x;
   const int gy = blockIdx.y * 8 + threadIdx.y;
   const int gz = blockIdx.z;
@@ -323,18 +327,9 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       VRPS_TRY(ensure(&ws.dual_s4, dn));
     }
   }
-  // momentum coefficients in float64: t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2,
-  // iteration k (k >= 1) extrapolates with (t_{k-1} - 1)/t_k, iteration 0 with 0.
-  std::vector<float> mom(iters > 0 ? iters : 1, 0.f);
-  {
-    double t = 1.0, tprev = 1.0;
-    for (int k = 0; k < iters; ++k) {
-      if (k >= 1) mom[k] = (float)((tprev - 1.0) / t);
-      const double tn = (1.0 + std::sqrt(1.0 + 4.0 * t * t)) / 2.0;
-      tprev = t;
-      t = tn;
-    }
-  }
+  // momentum in float64: t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2; the z formed after
+  // iteration k extrapolates with (t_k - 1)/t_{k+1} (iteration 0 itself uses z = w)
+  double t_cur = 1.0;
   const float step = (float)(1.0 / (4.0 * g->dims * (double)tau));
   const float* w_final = dual;
   if (g->dims == 2) {
@@ -344,20 +339,25 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     const float* rz = dual;
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
     int which = 0;
-    VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)TileLarge::SMEM));
+    VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLarge>, TileLarge::SMEM));
     for (int k0 = 0; k0 < iters; k0 += FB_T) {
       const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
       MomBlock mb;
-      // the z written after iteration k0+q feeds iteration k0+q+1: coefficient mom[k0+q+1]
-      for (int q = 0; q <= FB_T; ++q) mb.c[q] = (q < ns && k0 + q + 1 < iters) ? mom[k0 + q + 1] : 0.f;
+      for (int q = 0; q <= FB_T; ++q) {
+        mb.c[q] = 0.f;
+        if (q < ns) {
+          const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
+          if (k0 + q + 1 < iters) mb.c[q] = (float)((t_cur - 1.0) / t_next);
+          t_cur = t_next;
+        }
+      }
       float* wn = pairs[which][0];
       float* zn = pairs[which][1];
       {
         LaunchScope _ls("fgp2d_block", s);
         dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
-        fgp2d_block<TileLarge><<<grid, TileLarge::NT, TileLarge::SMEM, s>>>(v, rw, rz, wn, zn, g->nx, g->ny, tau,
-                                                                           step, mb, ns, nonneg);
+        VRPS_CUDA(launch_pdl(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, g->nx, g->ny, tau,
+                                                                           step, mb, ns, nonneg));
       }
       VRPS_LAUNCHED("fgp2d_block");
       rw = wn;
@@ -369,13 +369,21 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   } else {
     float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};
     int cur = 0, prev = 0;
+    double t_prev = 1.0;
     for (int k = 0; k < iters; ++k) {
       const int nxt = (k == 0) ? 1 : 3 - cur - prev;
+      // iteration k extrapolates with (t_{k-1} - 1)/t_k (0 for k = 0, 1)
+      float mk = 0.f;
+      if (k >= 1) {
+        mk = (float)((t_prev - 1.0) / t_cur);
+      }
+      t_prev = t_cur;
+      t_cur = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
       Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
       dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
       {
         LaunchScope _ls("fgp3d_iter", s);
-        fgp3d_iter<<<grid, block, 0, s>>>(v, buf[cur], buf[prev], buf[nxt], D, tau, step, mom[k], nonneg);
+        VRPS_CUDA(launch_pdl(fgp3d_iter, dim3(grid), dim3(block), (size_t)(0), s, v, buf[cur], buf[prev], buf[nxt], D, tau, step, mk, nonneg));
       }
       VRPS_LAUNCHED("fgp_iter");
       prev = cur;
@@ -388,14 +396,14 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32), block(32, 8);
     {
       LaunchScope _ls("fgp2d_out", s);
-      fgp2d_out<<<grid, block, 0, s>>>(v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail);
+      VRPS_CUDA(launch_pdl(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail));
     }
   } else {
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
     dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
     {
       LaunchScope _ls("fgp3d_out", s);
-      fgp3d_out<<<grid, block, 0, s>>>(v, w_final, wdst, D, tau, nonneg, tail);
+      VRPS_CUDA(launch_pdl(fgp3d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, D, tau, nonneg, tail));
     }
   }
   VRPS_LAUNCHED("fgp_out");
@@ -493,8 +501,8 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
     {
       LaunchScope _ls("fgp2d_block", s);
       dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
-      fgp2d_block<TileLarge><<<grid, TileLarge::NT, TileLarge::SMEM, s>>>(v, rw, rz, wn, zn, nx, ny, tau, step, mb,
-                                                                         ns, nonneg ? 1 : 0);
+      VRPS_CUDA(launch_pdl(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, nx, ny, tau, step, mb,
+                                                                         ns, nonneg ? 1 : 0));
     }
     VRPS_LAUNCHED("fgp2d_block");
     rw = wn;
@@ -509,7 +517,7 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
   {
     dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
     LaunchScope _ls("fgp2d_out", s);
-    fgp2d_out<<<grid, block, 0, s>>>(v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t);
+    VRPS_CUDA(launch_pdl(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t));
   }
   VRPS_LAUNCHED("fgp2d_out");
   return VRPS_OK;

@@ -84,6 +84,7 @@ constexpr int FWD_PAD = 4;   // zero floats left and right of each staged line (
 
 template <int MODE, bool BULK>
 __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
+  pdl_prologue();
   extern __shared__ __align__(128) float band[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned s_last;
@@ -288,6 +289,7 @@ __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, flo
 // the general loop over P.nc candidates.
 template <int NC, int PPT>
 __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
+  pdl_prologue();
   constexpr int TY = (ADJ_THREADS / ADJ_TX) * PPT;   // tile rows: 16 (one pixel per thread) or 32
   extern __shared__ float sm[];                  // [chunk][fp]
   __shared__ float4 s_par[ADJ_CHUNK];            // Bx, By, (F0 - hw), 1/hw
@@ -387,6 +389,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
 }
 
 __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx) {
+  pdl_prologue();
   __shared__ float t[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int k = threadIdx.y; k < 32; k += 8) {
@@ -405,7 +408,7 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s) {
   dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
   { LaunchScope _ls("transpose_kernel", s);
-  transpose_kernel<<<grid, block, 0, s>>>(in, out, ny, nx);
+  VRPS_CUDA(launch_pdl(transpose_kernel, dim3(grid), dim3(block), (size_t)(0), s, in, out, ny, nx));
   }
   VRPS_LAUNCHED("transpose2d");
   return VRPS_OK;
@@ -455,10 +458,9 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   const size_t smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD);
   dim3 grid(P.bands, rows), block(FWD_THREADS);
   auto launch = [&](auto kern) -> int {
-    if (smem > 48 * 1024)
-      VRPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("fwd2d_kernel", s);
-    kern<<<grid, block, smem, s>>>(P);
+    VRPS_CUDA(launch_pdl(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };
   switch (mode) {
@@ -490,15 +492,13 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.u = u;
   const size_t smem = sizeof(float) * (size_t)P.chunk * P.fp;
   // two pixels per thread (shared per-angle parameters) unless the image is very small
-  int sms = 0;
-  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
-  const bool two = (long long)g->nx * g->ny > 512LL * sms;
+  const bool two = (long long)g->nx * g->ny > 512LL * g->sms;
   const int ty = (ADJ_THREADS / ADJ_TX) * (two ? 2 : 1);
   dim3 grid((g->nx + ADJ_TX - 1) / ADJ_TX, (g->ny + ty - 1) / ty), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
   auto launch = [&](auto kern) -> int {
-    if (smem > 48 * 1024) VRPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("adj2d_kernel", s);
-    kern<<<grid, block, smem, s>>>(P);
+    VRPS_CUDA(launch_pdl(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };
   if (g->adj_nc == 2) {

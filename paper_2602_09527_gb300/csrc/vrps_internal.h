@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "vrps.h"
@@ -44,6 +45,37 @@ struct LaunchScope {
   LaunchScope(const char* name, cudaStream_t st) : s(st) { launch_begin(name, st); }
   ~LaunchScope() { launch_end(s); }
 };
+
+// ------------------------------------------------------------------ dependent launches
+// Every kernel of the library starts with pdl_prologue(): it waits until the preceding grid
+// in the stream has completed and its memory is visible (so data dependencies are exactly
+// those of plain stream order), then lets the next grid be scheduled.  Kernels are launched
+// with programmatic stream serialisation (launch_pdl), so a kernel's launch and CTA dispatch
+// overlap the tail of the kernel before it instead of following its completion.
+__device__ __forceinline__ void pdl_prologue() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// Opt a kernel into `bytes` of dynamic shared memory on the current device (cached: the
+// runtime call is made once per kernel, device and size).
+int smem_opt_in(const void* kern, size_t bytes);
 
 // ------------------------------------------------------------------ geometry tables
 // Per-angle constants of the 2D Joseph projector, derived in float64 on the host.
@@ -144,6 +176,7 @@ struct vrps_geom {
   int64_t n = 0, m = 0;
   int row_len = 0;
   int device = 0;
+  int sms = 0;           // multiprocessors of that device
   std::vector<double> angles;
   // 2D tables
   vrps::AngleInfo2D* ang2d = nullptr;
