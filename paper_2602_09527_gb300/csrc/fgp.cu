@@ -130,7 +130,6 @@ __global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ 
                                                       const float* __restrict__ z_g, float* __restrict__ wn_g,
                                                       float* __restrict__ zn_g, int nx, int ny, float tau, float step,
                                                       MomBlock mom, int nsteps, int nonneg) {
-  pdl_prologue();
   constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT;
   extern __shared__ float smf[];
   float* sv = smf;
@@ -190,7 +189,6 @@ __global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ 
 __global__ void __launch_bounds__(256) fgp2d_out(const float* __restrict__ v, const float* __restrict__ w,
                                                  float* wdst, int nx, int ny, float tau, int nonneg,
                                                  ProxTail t) {
-  pdl_prologue();
   __shared__ float tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   const size_t n = (size_t)nx * ny;
@@ -268,7 +266,6 @@ __device__ __forceinline__ float x3(const float* __restrict__ v, const float* wc
 __global__ void __launch_bounds__(256) fgp3d_iter(const float* __restrict__ v, const float* wc,
                                                   const float* wp, float* __restrict__ wn, Dims3 D,
                                                   float tau, float step, float mom, int nonneg) {
-  pdl_prologue();
   const int gx = blockIdx.x * 32 + threadIdx.x;
   const int gy = blockIdx.y * 8 + threadIdx.y;
   const int gz = blockIdx.z;
@@ -289,7 +286,6 @@ __global__ void __launch_bounds__(256) fgp3d_iter(const float* __restrict__ v, c
 
 __global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, const float* __restrict__ w,
                                                  float* wdst, Dims3 D, float tau, int nonneg, ProxTail t) {
-  pdl_prologue();
   const int gx = blockIdx.x * 32 + threadIdx.x;
   const int gy = blockIdx.y * 8 + threadIdx.y;
   const int gz = blockIdx.z;
@@ -356,7 +352,7 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       {
         LaunchScope _ls("fgp2d_block", s);
         dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
-        VRPS_CUDA(launch_pdl(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, g->nx, g->ny, tau,
+        VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, g->nx, g->ny, tau,
                                                                            step, mb, ns, nonneg));
       }
       VRPS_LAUNCHED("fgp2d_block");
@@ -383,7 +379,7 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
       {
         LaunchScope _ls("fgp3d_iter", s);
-        VRPS_CUDA(launch_pdl(fgp3d_iter, dim3(grid), dim3(block), (size_t)(0), s, v, buf[cur], buf[prev], buf[nxt], D, tau, step, mk, nonneg));
+        VRPS_CUDA(launch_kernel(fgp3d_iter, dim3(grid), dim3(block), (size_t)(0), s, v, buf[cur], buf[prev], buf[nxt], D, tau, step, mk, nonneg));
       }
       VRPS_LAUNCHED("fgp_iter");
       prev = cur;
@@ -396,14 +392,14 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32), block(32, 8);
     {
       LaunchScope _ls("fgp2d_out", s);
-      VRPS_CUDA(launch_pdl(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail));
+      VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail));
     }
   } else {
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
     dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
     {
       LaunchScope _ls("fgp3d_out", s);
-      VRPS_CUDA(launch_pdl(fgp3d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, D, tau, nonneg, tail));
+      VRPS_CUDA(launch_kernel(fgp3d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, D, tau, nonneg, tail));
     }
   }
   VRPS_LAUNCHED("fgp_out");
@@ -501,7 +497,7 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
     {
       LaunchScope _ls("fgp2d_block", s);
       dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
-      VRPS_CUDA(launch_pdl(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, nx, ny, tau, step, mb,
+      VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, nx, ny, tau, step, mb,
                                                                          ns, nonneg ? 1 : 0));
     }
     VRPS_LAUNCHED("fgp2d_block");
@@ -517,7 +513,7 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
   {
     dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
     LaunchScope _ls("fgp2d_out", s);
-    VRPS_CUDA(launch_pdl(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t));
+    VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t));
   }
   VRPS_LAUNCHED("fgp2d_out");
   return VRPS_OK;

@@ -84,7 +84,6 @@ constexpr int FWD_PAD = 4;   // zero floats left and right of each staged line (
 
 template <int MODE, bool BULK>
 __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
-  pdl_prologue();
   extern __shared__ __align__(128) float band[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned s_last;
@@ -289,7 +288,6 @@ __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, flo
 // the general loop over P.nc candidates.
 template <int NC, int PPT>
 __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
-  pdl_prologue();
   constexpr int TY = (ADJ_THREADS / ADJ_TX) * PPT;   // tile rows: 16 (one pixel per thread) or 32
   extern __shared__ float sm[];                  // [chunk][fp]
   __shared__ float4 s_par[ADJ_CHUNK];            // Bx, By, (F0 - hw), 1/hw
@@ -389,7 +387,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
 }
 
 __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx) {
-  pdl_prologue();
   __shared__ float t[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int k = threadIdx.y; k < 32; k += 8) {
@@ -408,7 +405,7 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s) {
   dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
   { LaunchScope _ls("transpose_kernel", s);
-  VRPS_CUDA(launch_pdl(transpose_kernel, dim3(grid), dim3(block), (size_t)(0), s, in, out, ny, nx));
+  VRPS_CUDA(launch_kernel(transpose_kernel, dim3(grid), dim3(block), (size_t)(0), s, in, out, ny, nx));
   }
   VRPS_LAUNCHED("transpose2d");
   return VRPS_OK;
@@ -460,7 +457,7 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("fwd2d_kernel", s);
-    VRPS_CUDA(launch_pdl(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
+    VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };
   switch (mode) {
@@ -498,7 +495,7 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("adj2d_kernel", s);
-    VRPS_CUDA(launch_pdl(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
+    VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };
   if (g->adj_nc == 2) {

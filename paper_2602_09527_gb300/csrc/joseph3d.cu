@@ -44,7 +44,6 @@ __device__ __forceinline__ void clip_range(float intercept, float slope, float l
 
 template <int MODE>
 __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
-  pdl_prologue();
   const int iu = blockIdx.x * 32 + threadIdx.x;
   const int iv = blockIdx.y * 8 + threadIdx.y;
   const int row = blockIdx.z;
@@ -160,7 +159,6 @@ __device__ __forceinline__ float adj_axis(const Adj3DParams& P, const ViewInfo3D
 }
 
 __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
-  pdl_prologue();
   const int gx = blockIdx.x * 32 + threadIdx.x;
   const int gy = blockIdx.y * 8 + threadIdx.y;
   const int gz = blockIdx.z;
@@ -225,11 +223,11 @@ int fwd3d(const vrps_geom* g, const float* x, const int* ids, int rows, int mode
   P.o = o;
   dim3 grid((g->nu + 31) / 32, (g->nv + 7) / 8, rows), block(32, 8);
   switch (mode) {
-    case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_pdl(fwd3d_kernel<FWD_PLAIN>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_RESID: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_pdl(fwd3d_kernel<FWD_RESID>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_SVRG: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_pdl(fwd3d_kernel<FWD_SVRG>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_SAGA: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_pdl(fwd3d_kernel<FWD_SAGA>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_SNAP: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_pdl(fwd3d_kernel<FWD_SNAP>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_PLAIN>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_RESID: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_RESID>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_SVRG: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SVRG>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_SAGA: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SAGA>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_SNAP: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SNAP>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
     default: return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
   }
   VRPS_LAUNCHED("fwd3d");
@@ -256,7 +254,7 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.u = u;
   dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
   { LaunchScope _ls("adj3d_kernel", s);
-  VRPS_CUDA(launch_pdl(adj3d_kernel, dim3(grid), dim3(block), (size_t)(0), s, P));
+  VRPS_CUDA(launch_kernel(adj3d_kernel, dim3(grid), dim3(block), (size_t)(0), s, P));
   }
   VRPS_LAUNCHED("adj3d");
   return VRPS_OK;

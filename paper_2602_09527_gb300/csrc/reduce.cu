@@ -29,7 +29,6 @@ __device__ __forceinline__ double block_sum(double v) {
 __global__ void __launch_bounds__(RED_THREADS) dot_partial(const float* __restrict__ a,
                                                            const float* __restrict__ b, int64_t n,
                                                            double* part) {
-  pdl_prologue();
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * RED_THREADS)
@@ -39,7 +38,6 @@ __global__ void __launch_bounds__(RED_THREADS) dot_partial(const float* __restri
 }
 
 __global__ void __launch_bounds__(RED_THREADS) finalize(const double* part, int np, double* dst) {
-  pdl_prologue();
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += RED_THREADS) s += part[i];
   s = block_sum(s);
@@ -49,7 +47,6 @@ __global__ void __launch_bounds__(RED_THREADS) finalize(const double* part, int 
 // isotropic TV: sum over pixels of ||forward differences||_2 (zero at the last index)
 __global__ void __launch_bounds__(RED_THREADS) tv_partial(const float* __restrict__ x, int nx, int ny,
                                                           int nz, double* part) {
-  pdl_prologue();
   const int64_t n = (int64_t)nx * ny * nz;
   const int64_t nxy = (int64_t)nx * ny;
   double s = 0.0;
@@ -86,7 +83,6 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 
 __global__ void schedule_kernel(uint32_t k0lo, uint32_t k1hi, uint32_t job, int64_t kbase, int count,
                                 uint32_t N, unsigned long long thr, int always, int32_t* out) {
-  pdl_prologue();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   const uint64_t k = (uint64_t)kbase + (uint64_t)q;
@@ -98,7 +94,6 @@ __global__ void schedule_kernel(uint32_t k0lo, uint32_t k1hi, uint32_t job, int6
 
 __global__ void uniform_kernel(uint32_t key0, uint32_t key1, uint32_t job, uint32_t tag, float* out,
                                int64_t n) {
-  pdl_prologue();
   const int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (blk * 4 >= n) return;
   const uint4 w = philox10(make_uint4((uint32_t)blk, (uint32_t)((uint64_t)blk >> 32), job, tag), key0, key1);
@@ -110,7 +105,6 @@ __global__ void uniform_kernel(uint32_t key0, uint32_t key1, uint32_t job, uint3
 }
 
 __global__ void scale_kernel(float* dst, const float* src, const double* nrm2, int64_t n) {
-  pdl_prologue();
   const double inv = 1.0 / sqrt(*nrm2);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (float)((double)src[i] * inv);
@@ -118,7 +112,6 @@ __global__ void scale_kernel(float* dst, const float* src, const double* nrm2, i
 
 __global__ void gather_rows_kernel(const float* __restrict__ src, float* __restrict__ dst, const int* ids,
                                    int row_len) {
-  pdl_prologue();
   const int r = blockIdx.y;
   const size_t so = (size_t)ids[r] * row_len, d0 = (size_t)r * row_len;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < row_len; j += gridDim.x * blockDim.x)
@@ -127,7 +120,6 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, float* __restr
 
 __global__ void scatter_rows_kernel(const float* __restrict__ src, float* __restrict__ dst, const int* ids,
                                     int row_len) {
-  pdl_prologue();
   const int r = blockIdx.y;
   const size_t d0 = (size_t)ids[r] * row_len, so = (size_t)r * row_len;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < row_len; j += gridDim.x * blockDim.x)
@@ -135,7 +127,6 @@ __global__ void scatter_rows_kernel(const float* __restrict__ src, float* __rest
 }
 
 __global__ void fill_kernel(float* p, float v, int64_t n) {
-  pdl_prologue();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
 }
@@ -144,11 +135,11 @@ __global__ void fill_kernel(float* p, float v, int64_t n) {
 
 int dot64(const float* a, const float* b, int64_t n, double* dst, Workspace& ws, cudaStream_t s) {
   { LaunchScope _ls("dot_partial", s);
-  VRPS_CUDA(launch_pdl(dot_partial, dim3(NPART), dim3(RED_THREADS), (size_t)(0), s, a, b, n, ws.partials));
+  VRPS_CUDA(launch_kernel(dot_partial, dim3(NPART), dim3(RED_THREADS), (size_t)(0), s, a, b, n, ws.partials));
   }
   VRPS_LAUNCHED("dot_partial");
   { LaunchScope _ls("finalize", s);
-  VRPS_CUDA(launch_pdl(finalize, dim3(1), dim3(RED_THREADS), (size_t)(0), s, ws.partials, NPART, dst));
+  VRPS_CUDA(launch_kernel(finalize, dim3(1), dim3(RED_THREADS), (size_t)(0), s, ws.partials, NPART, dst));
   }
   VRPS_LAUNCHED("finalize");
   return VRPS_OK;
@@ -156,11 +147,11 @@ int dot64(const float* a, const float* b, int64_t n, double* dst, Workspace& ws,
 
 int tv64(const vrps_geom* g, const float* x, double* dst, Workspace& ws, cudaStream_t s) {
   { LaunchScope _ls("tv_partial", s);
-  VRPS_CUDA(launch_pdl(tv_partial, dim3(NPART), dim3(RED_THREADS), (size_t)(0), s, x, g->nx, g->ny, g->nz, ws.partials));
+  VRPS_CUDA(launch_kernel(tv_partial, dim3(NPART), dim3(RED_THREADS), (size_t)(0), s, x, g->nx, g->ny, g->nz, ws.partials));
   }
   VRPS_LAUNCHED("tv_partial");
   { LaunchScope _ls("finalize", s);
-  VRPS_CUDA(launch_pdl(finalize, dim3(1), dim3(RED_THREADS), (size_t)(0), s, ws.partials, NPART, dst));
+  VRPS_CUDA(launch_kernel(finalize, dim3(1), dim3(RED_THREADS), (size_t)(0), s, ws.partials, NPART, dst));
   }
   VRPS_LAUNCHED("finalize");
   return VRPS_OK;
@@ -172,7 +163,7 @@ int philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int N, d
   const int always = p >= 1.0 ? 1 : 0;
   const unsigned long long thr = always ? 0ull : (unsigned long long)std::floor(p * 4294967296.0);
   { LaunchScope _ls("schedule_kernel", s);
-  VRPS_CUDA(launch_pdl(schedule_kernel, dim3((count + 255) / 256), dim3(256), (size_t)(0), s, (uint32_t)seed, (uint32_t)(seed >> 32), job, k0, count,
+  VRPS_CUDA(launch_kernel(schedule_kernel, dim3((count + 255) / 256), dim3(256), (size_t)(0), s, (uint32_t)seed, (uint32_t)(seed >> 32), job, k0, count,
                                                       (uint32_t)N, thr, always, out));
   }
   VRPS_LAUNCHED("philox_schedule");
@@ -182,7 +173,7 @@ int philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int N, d
 int philox_uniform(uint64_t seed, uint32_t job, uint32_t tag, float* out, int64_t n, cudaStream_t s) {
   const int64_t blocks = ((n + 3) / 4 + 255) / 256;
   { LaunchScope _ls("uniform_kernel", s);
-  VRPS_CUDA(launch_pdl(uniform_kernel, dim3((unsigned)blocks), dim3(256), (size_t)(0), s, (uint32_t)seed, (uint32_t)(seed >> 32), job, tag, out, n));
+  VRPS_CUDA(launch_kernel(uniform_kernel, dim3((unsigned)blocks), dim3(256), (size_t)(0), s, (uint32_t)seed, (uint32_t)(seed >> 32), job, tag, out, n));
   }
   VRPS_LAUNCHED("philox_uniform");
   return VRPS_OK;
@@ -190,7 +181,7 @@ int philox_uniform(uint64_t seed, uint32_t job, uint32_t tag, float* out, int64_
 
 int scale_inv_sqrt(float* dst, const float* src, const double* nrm2, int64_t n, cudaStream_t s) {
   { LaunchScope _ls("scale_kernel", s);
-  VRPS_CUDA(launch_pdl(scale_kernel, dim3(NPART), dim3(256), (size_t)(0), s, dst, src, nrm2, n));
+  VRPS_CUDA(launch_kernel(scale_kernel, dim3(NPART), dim3(256), (size_t)(0), s, dst, src, nrm2, n));
   }
   VRPS_LAUNCHED("scale_inv_sqrt");
   return VRPS_OK;
@@ -200,7 +191,7 @@ int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_
   if (rows <= 0) return VRPS_OK;
   dim3 grid((row_len + 255) / 256 < 64 ? (row_len + 255) / 256 : 64, rows);
   { LaunchScope _ls("gather_rows_kernel", s);
-  VRPS_CUDA(launch_pdl(gather_rows_kernel, dim3(grid), dim3(256), (size_t)(0), s, src, dst, ids, row_len));
+  VRPS_CUDA(launch_kernel(gather_rows_kernel, dim3(grid), dim3(256), (size_t)(0), s, src, dst, ids, row_len));
   }
   VRPS_LAUNCHED("gather_rows");
   return VRPS_OK;
@@ -210,7 +201,7 @@ int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row
   if (rows <= 0) return VRPS_OK;
   dim3 grid((row_len + 255) / 256 < 64 ? (row_len + 255) / 256 : 64, rows);
   { LaunchScope _ls("scatter_rows_kernel", s);
-  VRPS_CUDA(launch_pdl(scatter_rows_kernel, dim3(grid), dim3(256), (size_t)(0), s, src, dst, ids, row_len));
+  VRPS_CUDA(launch_kernel(scatter_rows_kernel, dim3(grid), dim3(256), (size_t)(0), s, src, dst, ids, row_len));
   }
   VRPS_LAUNCHED("scatter_rows");
   return VRPS_OK;
@@ -218,7 +209,7 @@ int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row
 
 int fill(float* p, float v, int64_t n, cudaStream_t s) {
   { LaunchScope _ls("fill_kernel", s);
-  VRPS_CUDA(launch_pdl(fill_kernel, dim3(NPART), dim3(256), (size_t)(0), s, p, v, n));
+  VRPS_CUDA(launch_kernel(fill_kernel, dim3(NPART), dim3(256), (size_t)(0), s, p, v, n));
   }
   VRPS_LAUNCHED("fill");
   return VRPS_OK;
