@@ -130,7 +130,7 @@ static int check_geom(const vrps_geom* g) {
 }
 
 static void free_ws(Workspace& w) {
-  float** fl[] = {&w.xT, &w.dual_cold, &w.dual_s1, &w.dual_s2, &w.dual_s3, &w.dual_s4, &w.sino, &w.img, &w.img2,
+  float** fl[] = {&w.xT, &w.dual_cold, &w.dual_s1, &w.dual_s2, &w.dual_s3, &w.dual_s4, &w.sino, &w.sino2, &w.img, &w.img2,
                   &w.x, &w.xf, &w.xfT, &w.h, &w.xhat, &w.v, &w.gbar, &w.xprox, &w.dual,
                   &w.b_perm, &w.tab, &w.res};
   for (float** p : fl) {
@@ -232,6 +232,7 @@ static int build_cone3d(vrps_geom* g) {
   const double cv = 0.5 * (g->nv - 1);
   const double vmax = std::fabs((0 - cv) * g->dv);
   std::vector<RayInfo3D> rays((size_t)g->n_angles * g->nu);
+  double qz_min = 1e300;
   g->view3d_host.assign(g->n_angles, ViewInfo3D());
   for (int a = 0; a < g->n_angles; ++a) {
     const double b = g->angles[a];
@@ -268,6 +269,13 @@ static int build_cone3d(vrps_geom* g) {
       }
       RayInfo3D& r = rays[(size_t)a * g->nu + iu];
       r.pad0 = r.pad1 = 0.f;
+      {
+        // smallest z-index step per detector row over the volume's planes (adjoint window)
+        const bool ax0 = std::fabs(dx) >= std::fabs(dy);
+        const double Sa = ax0 ? Sx : Sy, da = ax0 ? dx : dy;
+        const double half = 0.5 * ((ax0 ? g->nx : g->ny) - 1) * vox;
+        for (double X : {-half, half}) qz_min = std::fmin(qz_min, g->dv * ((X - Sa) / da) / vox);
+      }
       if (std::fabs(dx) >= std::fabs(dy)) {
         r.axis = 0;
         r.P0 = (float)(cy + (Sy - Sx * dy / dx) / vox);
@@ -287,6 +295,9 @@ static int build_cone3d(vrps_geom* g) {
       }
     }
   }
+  // rows within one voxel of a voxel's centre in z: an open window of 2/qz rows
+  g->adj3_ncv = (int)std::ceil(2.0 / qz_min);
+  if (g->adj3_ncv < 2) g->adj3_ncv = 2;
   VRPS_CUDA(cudaMalloc((void**)&g->ray3d, sizeof(RayInfo3D) * rays.size()));
   VRPS_CUDA(cudaMemcpy(g->ray3d, rays.data(), sizeof(RayInfo3D) * rays.size(), cudaMemcpyHostToDevice));
   VRPS_CUDA(cudaMalloc((void**)&g->view3d, sizeof(ViewInfo3D) * g->n_angles));

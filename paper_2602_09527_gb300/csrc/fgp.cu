@@ -263,25 +263,106 @@ __device__ __forceinline__ float x3(const float* __restrict__ v, const float* wc
   return nonneg ? fmaxf(xv, 0.f) : xv;
 }
 
-__global__ void __launch_bounds__(256) fgp3d_iter(const float* __restrict__ v, const float* wc,
-                                                  const float* wp, float* __restrict__ wn, Dims3 D,
-                                                  float tau, float step, float mom, int nonneg) {
-  const int gx = blockIdx.x * 32 + threadIdx.x;
-  const int gy = blockIdx.y * 8 + threadIdx.y;
-  const int gz = blockIdx.z;
-  if (gx >= D.nx || gy >= D.ny) return;
-  const size_t p = ((size_t)gz * D.ny + gy) * D.nx + gx;
-  const float xc = x3(v, wc, wp, D, gx, gy, gz, tau, mom, nonneg);
-  const float d1 = gx < D.nx - 1 ? x3(v, wc, wp, D, gx + 1, gy, gz, tau, mom, nonneg) - xc : 0.f;
-  const float d2 = gy < D.ny - 1 ? x3(v, wc, wp, D, gx, gy + 1, gz, tau, mom, nonneg) - xc : 0.f;
-  const float d3 = gz < D.nz - 1 ? x3(v, wc, wp, D, gx, gy, gz + 1, tau, mom, nonneg) - xc : 0.f;
-  const float q1 = fmaf(step, d1, zval(wc, wp, p, mom));
-  const float q2 = fmaf(step, d2, zval(wc, wp, D.n + p, mom));
-  const float q3 = fmaf(step, d3, zval(wc, wp, 2 * D.n + p, mom));
-  const float den = fmaxf(1.f, sqrtf(q1 * q1 + q2 * q2 + q3 * q3));
-  wn[p] = q1 / den;
-  wn[D.n + p] = q2 / den;
-  wn[2 * D.n + p] = q3 / den;
+// One FGP iteration in 3D as a 2.5-D streaming stencil.  A CTA owns a F3_TX x F3_TY tile of
+// z columns and walks a chunk of F3_ZC planes.  Per plane it builds the extrapolated dual
+// z = w_k + mom (w_k - w_{k-1}) on the tile grown by one voxel, then x = P_+(v + tau div z)
+// on the tile grown by one voxel on the + sides; the new dual of plane g is finished once x of
+// plane g+1 exists.  Each voxel's v, w_k, w_{k-1} are read about once (plus the tile halo)
+// and w_{k+1} written once: 10 floats per voxel per iteration.
+constexpr int F3_TX = 32, F3_TY = 16, F3_ZC = 64;
+constexpr int F3_HX = F3_TX + 2, F3_HY = F3_TY + 2;   // z tile with a one-voxel halo
+constexpr int F3_XX = F3_TX + 1, F3_XY = F3_TY + 1;   // x tile with the + halo
+
+__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
+                                                             const float* __restrict__ wp, float* __restrict__ wn,
+                                                             Dims3 D, float tau, float step, float mom, int nonneg) {
+  __shared__ float zs[3][F3_HY][F3_HX];   // extrapolated dual of the current plane (+ halo)
+  __shared__ float z3p[F3_HY][F3_HX];     // z-component of the previous plane
+  __shared__ float xs[2][F3_XY][F3_XX];   // x of two consecutive planes
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * F3_TX + tx;
+  const int ix0 = blockIdx.x * F3_TX, iy0 = blockIdx.y * F3_TY;
+  const int zb = blockIdx.z * F3_ZC, ze = min(zb + F3_ZC, D.nz);
+  const size_t nxy = (size_t)D.nx * D.ny;
+  auto load_z = [&](int g) {
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) {
+      const int ly = e / F3_HX, lx = e - ly * F3_HX;
+      const int gx = ix0 + lx - 1, gy = iy0 + ly - 1;
+      float a = 0.f, b = 0.f, c = 0.f;
+      if (gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny) {
+        const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
+        a = zval(wc, wp, p, mom);
+        b = zval(wc, wp, D.n + p, mom);
+        c = zval(wc, wp, 2 * D.n + p, mom);
+      }
+      zs[0][ly][lx] = a;
+      zs[1][ly][lx] = b;
+      zs[2][ly][lx] = c;
+    }
+  };
+  auto comp_x = [&](int g, float (*xb)[F3_XX]) {
+    for (int e = tid; e < F3_XX * F3_XY; e += F3_TX * F3_TY) {
+      const int ly = e / F3_XX, lx = e - ly * F3_XX;
+      const int gx = ix0 + lx, gy = iy0 + ly;
+      float xv = 0.f;
+      if (gx < D.nx && gy < D.ny) {
+        const int hx = lx + 1, hy = ly + 1;
+        float d = 0.f;
+        if (gx < D.nx - 1) d += zs[0][hy][hx];
+        if (gx > 0) d -= zs[0][hy][hx - 1];
+        if (gy < D.ny - 1) d += zs[1][hy][hx];
+        if (gy > 0) d -= zs[1][hy - 1][hx];
+        if (g < D.nz - 1) d += zs[2][hy][hx];
+        if (g > 0) d -= z3p[hy][hx];
+        xv = fmaf(tau, d, v[(size_t)g * nxy + (size_t)gy * D.nx + gx]);
+        if (nonneg) xv = fmaxf(xv, 0.f);
+      }
+      xb[ly][lx] = xv;
+    }
+  };
+  // prologue: z3 of the plane below the chunk, then plane zb and its x
+  if (zb > 0) {
+    load_z(zb - 1);
+    __syncthreads();
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
+  } else {
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = 0.f;
+  }
+  __syncthreads();
+  load_z(zb);
+  __syncthreads();
+  comp_x(zb, xs[0]);
+  __syncthreads();
+  const int gx = ix0 + tx, gy = iy0 + ty;
+  const bool own = gx < D.nx && gy < D.ny;
+  float zo0 = zs[0][ty + 1][tx + 1], zo1 = zs[1][ty + 1][tx + 1], zo2 = zs[2][ty + 1][tx + 1];
+  for (int g = zb; g < ze; ++g) {
+    const int cur = (g - zb) & 1, nxt = cur ^ 1;
+    if (g + 1 < D.nz) {
+      for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
+      __syncthreads();
+      load_z(g + 1);
+      __syncthreads();
+      comp_x(g + 1, xs[nxt]);
+      __syncthreads();
+    }
+    if (own) {
+      const float xc = xs[cur][ty][tx];
+      const float d1 = gx < D.nx - 1 ? xs[cur][ty][tx + 1] - xc : 0.f;
+      const float d2 = gy < D.ny - 1 ? xs[cur][ty + 1][tx] - xc : 0.f;
+      const float d3 = g < D.nz - 1 ? xs[nxt][ty][tx] - xc : 0.f;
+      const float q1 = fmaf(step, d1, zo0), q2 = fmaf(step, d2, zo1), q3 = fmaf(step, d3, zo2);
+      const float den = fmaxf(1.f, sqrtf(q1 * q1 + q2 * q2 + q3 * q3));
+      const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
+      wn[p] = q1 / den;
+      wn[D.n + p] = q2 / den;
+      wn[2 * D.n + p] = q3 / den;
+    }
+    if (g + 1 < D.nz) {
+      zo0 = zs[0][ty + 1][tx + 1];
+      zo1 = zs[1][ty + 1][tx + 1];
+      zo2 = zs[2][ty + 1][tx + 1];
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, const float* __restrict__ w,
@@ -376,10 +457,11 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       t_prev = t_cur;
       t_cur = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
       Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
-      dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
+      dim3 grid((g->nx + F3_TX - 1) / F3_TX, (g->ny + F3_TY - 1) / F3_TY, (g->nz + F3_ZC - 1) / F3_ZC);
       {
-        LaunchScope _ls("fgp3d_iter", s);
-        VRPS_CUDA(launch_kernel(fgp3d_iter, dim3(grid), dim3(block), (size_t)(0), s, v, buf[cur], buf[prev], buf[nxt], D, tau, step, mk, nonneg));
+        LaunchScope _ls("fgp3d_stream", s);
+        VRPS_CUDA(launch_kernel(fgp3d_stream, grid, dim3(F3_TX, F3_TY), (size_t)0, s, v, (const float*)buf[cur],
+                                (const float*)buf[prev], buf[nxt], D, tau, step, mk, nonneg));
       }
       VRPS_LAUNCHED("fgp_iter");
       prev = cur;

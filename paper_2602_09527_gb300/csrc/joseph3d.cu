@@ -81,21 +81,23 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
     acc += fmaf(gz, hi_z - lo_z, lo_z);
   }
   const float kr = k * ri.R;
-  const float r = acc * (P.vox * sqrtf(1.f + ri.P1 * ri.P1 + kr * kr));
+  const float wgt = P.vox * sqrtf(1.f + ri.P1 * ri.P1 + kr * kr);
+  const float r = acc * wgt;
+  const float ys = P.o.prescale ? wgt : 1.f;   // ray factor carried into the adjoint's input
   const size_t idx = (size_t)row * P.nu * P.nv + (size_t)iv * P.nu + iu;
   if (MODE == FWD_PLAIN) {
-    P.o.y[idx] = r;
+    P.o.y[idx] = r * ys;
   } else if (MODE == FWD_RESID) {
-    P.o.y[idx] = r - P.o.b[idx];
+    P.o.y[idx] = (r - P.o.b[idx]) * ys;
   } else if (MODE == FWD_SVRG) {
-    P.o.y[idx] = r - P.o.tab[idx];
+    P.o.y[idx] = (r - P.o.tab[idx]) * ys;
   } else if (MODE == FWD_SAGA) {
     const float res = r - P.o.b[idx];
-    P.o.y[idx] = res - P.o.tab[idx];
+    P.o.y[idx] = (res - P.o.tab[idx]) * ys;
     P.o.tab[idx] = res;
   } else {
     P.o.tab[idx] = r;
-    P.o.y[idx] = r - P.o.b[idx];
+    P.o.y[idx] = (r - P.o.b[idx]) * ys;
   }
 }
 
@@ -118,87 +120,110 @@ __device__ __forceinline__ float column_of(const ViewInfo3D& vi, float qx, float
   return fmaf(vi.sdd * num / den, vi.inv_du, vi.cu);
 }
 
-// Contribution of the rays of one view whose dominant axis is `axis` to voxel
-// (plane index l along that axis, transverse index tt, z index gz).
-__device__ __forceinline__ float adj_axis(const Adj3DParams& P, const ViewInfo3D& vi, const RayInfo3D* vr,
-                                          const float* rr, int axis, int l, int tt, int gz, float qx0,
-                                          float qy0, float qx1, float qy1) {
-  const float lim = (float)P.nu + 2.f;
-  const float c0 = fminf(fmaxf(column_of(vi, qx0, qy0), -2.f), lim);
-  const float c1 = fminf(fmaxf(column_of(vi, qx1, qy1), -2.f), lim);
-  int u_lo = (int)floorf(fminf(c0, c1)) - 1;
-  int u_hi = (int)ceilf(fmaxf(c0, c1)) + 1;
-  u_lo = max(u_lo, 0);
-  u_hi = min(u_hi, P.nu - 1);
-  const float dl = (float)l - (axis == 0 ? P.cx : P.cy);
-  float a = 0.f;
-  for (int iu = u_lo; iu <= u_hi; ++iu) {
-    const RayInfo3D ri = vr[iu];
-    if (ri.axis != axis) continue;
-    const float ft = fmaf(ri.P1, dl, ri.P0);
-    const float wt = 1.f - fabsf(ft - (float)tt);
-    if (wt <= 0.f) continue;
-    const float qz = fmaf(ri.Q1, dl, ri.Q0);
-    const float vlim = (float)P.nv + 2.f;
-    const float klo = fminf(fmaxf(((float)gz - 1.f - P.cz) / qz + P.cv, -2.f), vlim);
-    const float khi = fminf(fmaxf(((float)gz + 1.f - P.cz) / qz + P.cv, -2.f), vlim);
-    const int v_lo = max(0, (int)floorf(fminf(klo, khi)) - 1);
-    const int v_hi = min(P.nv - 1, (int)ceilf(fmaxf(klo, khi)) + 1);
-    const float base_w = 1.f + ri.P1 * ri.P1;
-    for (int iv = v_lo; iv <= v_hi; ++iv) {
-      const float k = (float)iv - P.cv;
-      const float fz = fmaf(k, qz, P.cz);
-      const float wz = 1.f - fabsf(fz - (float)gz);
-      if (wz <= 0.f) continue;
-      const float kr = k * ri.R;
-      const float w = wt * wz * (P.vox * sqrtf(base_w + kr * kr));
-      a = fmaf(w, __ldg(rr + (size_t)iv * P.nu + iu), a);
-    }
-  }
-  return a;
+constexpr int ADJ3_ZC = 16;   // voxels of one z column handled by a thread
+
+// r[row][iv][iu] <- r times the ray length factor voxel |d|/|d_a| (input of adj3d_kernel)
+__global__ void __launch_bounds__(256) prescale3d_kernel(const float* __restrict__ r, float* __restrict__ out,
+                                                         const RayInfo3D* rays, const int* ids, int nu, int nv,
+                                                         float cv, float vox) {
+  const int iu = blockIdx.x * 32 + threadIdx.x;
+  const int iv = blockIdx.y * 8 + threadIdx.y;
+  const int row = blockIdx.z;
+  if (iu >= nu || iv >= nv) return;
+  const RayInfo3D ri = rays[(size_t)ids[row] * nu + iu];
+  const float kr = ((float)iv - cv) * ri.R;
+  const size_t idx = (size_t)row * nu * nv + (size_t)iv * nu + iu;
+  out[idx] = r[idx] * (vox * sqrtf(1.f + ri.P1 * ri.P1 + kr * kr));
 }
 
+// Voxel-driven transpose of the 3D Joseph projector.  A thread owns ADJ3_ZC voxels of one z
+// column.  For each view and each dominant axis it projects the voxel's plane points at
+// +-1 voxel onto the detector to bound the candidate columns iu; for every column whose ray
+// meets the voxel's plane within one voxel (transverse weight wt, the same for the whole z
+// column) it adds, voxel by voxel, wt * wz * r over the detector rows iv whose ray passes
+// within one voxel in z.  r arrives pre-multiplied by the ray length factors.
+template <int NCV>
 __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
   const int gx = blockIdx.x * 32 + threadIdx.x;
   const int gy = blockIdx.y * 8 + threadIdx.y;
-  const int gz = blockIdx.z;
+  const int z0 = blockIdx.z * ADJ3_ZC;
   if (gx >= P.nx || gy >= P.ny) return;
   const float X = ((float)gx - P.cx) * P.vox, Y = ((float)gy - P.cy) * P.vox;
-  float acc = 0.f;
+  float acc[ADJ3_ZC];
+#pragma unroll
+  for (int z = 0; z < ADJ3_ZC; ++z) acc[z] = 0.f;
+  const float lim = (float)P.nu + 2.f;
+  const float vlim = (float)P.nv + 2.f;
   for (int q = 0; q < P.rows; ++q) {
     const int view = P.ids[q];
     const ViewInfo3D vi = P.views[view];
     const RayInfo3D* vr = P.rays + (size_t)view * P.nu;
     const float* rr = P.r + (size_t)q * P.nu * P.nv;
-    if (vi.has_x) acc += adj_axis(P, vi, vr, rr, 0, gx, gy, gz, X, Y - P.vox, X, Y + P.vox);
-    if (vi.has_y) acc += adj_axis(P, vi, vr, rr, 1, gy, gx, gz, X - P.vox, Y, X + P.vox, Y);
-  }
-  const size_t p = ((size_t)gz * P.ny + gy) * P.nx + gx;
-  const UpdateArgs& u = P.u;
-  if (!u.enabled) {
-    u.out[p] = acc;
-    return;
-  }
-  float G = u.cN * acc;
-  if (u.gbar) {
-    const float gb = u.gbar[p];
-    G += gb;
-    if (u.saga) u.gbar[p] = gb + acc;
-  }
-  const float base = u.base[p];
-  if (u.h) {
-    const float hp = u.h[p];
-    const float xh = base - u.gamma * (G - hp);
-    if (u.theta) {
-      u.xhat[p] = xh;
-      u.v[p] = xh - u.gamma_over_p * hp;
-    } else {
-      u.x[p] = xh;
+    for (int axis = 0; axis < 2; ++axis) {
+      if (axis == 0 ? !vi.has_x : !vi.has_y) continue;
+      const int tt = axis == 0 ? gy : gx;
+      const float dl = axis == 0 ? (float)gx - P.cx : (float)gy - P.cy;
+      const float c0 = fminf(fmaxf(axis == 0 ? column_of(vi, X, Y - P.vox) : column_of(vi, X - P.vox, Y), -2.f), lim);
+      const float c1 = fminf(fmaxf(axis == 0 ? column_of(vi, X, Y + P.vox) : column_of(vi, X + P.vox, Y), -2.f), lim);
+      const int u_lo = max(0, (int)floorf(fminf(c0, c1)) - 1);
+      const int u_hi = min(P.nu - 1, (int)ceilf(fmaxf(c0, c1)) + 1);
+      for (int iu = u_lo; iu <= u_hi; ++iu) {
+        const RayInfo3D ri = vr[iu];
+        if (ri.axis != axis) continue;
+        const float wt = 1.f - fabsf(fmaf(ri.P1, dl, ri.P0) - (float)tt);
+        if (wt <= 0.f) continue;
+        const float qz = fmaf(ri.Q1, dl, ri.Q0);   // z-index step per detector row (> 0)
+        const float iq = 1.f / qz;
+        const float* col = rr + iu;
+#pragma unroll
+        for (int z = 0; z < ADJ3_ZC; ++z) {
+          const float gzf = (float)(z0 + z);
+          const float klo = fminf(fmaxf(fmaf(gzf - 1.f - P.cz, iq, P.cv), -2.f), vlim);
+          const int ivs = (int)floorf(klo) + 1;   // first row whose ray passes above gz - 1
+          float a = 0.f;
+#pragma unroll
+          for (int c = 0; c < NCV; ++c) {
+            const int iv = ivs + c;
+            const float wz = 1.f - fabsf(fmaf((float)iv - P.cv, qz, P.cz) - gzf);
+            if (wz > 0.f && (unsigned)iv < (unsigned)P.nv) a = fmaf(wz, __ldg(col + (size_t)iv * P.nu), a);
+          }
+          acc[z] = fmaf(wt, a, acc[z]);
+        }
+      }
     }
-  } else {
-    const float xh = base - u.gamma * G;
-    if (u.theta) u.v[p] = xh;
-    else u.x[p] = xh;
+  }
+  const UpdateArgs& u = P.u;
+#pragma unroll
+  for (int z = 0; z < ADJ3_ZC; ++z) {
+    const int gz = z0 + z;
+    if (gz >= P.nz) break;
+    const size_t p = ((size_t)gz * P.ny + gy) * P.nx + gx;
+    const float g = acc[z];
+    if (!u.enabled) {
+      u.out[p] = g;
+      continue;
+    }
+    float G = u.cN * g;
+    if (u.gbar) {
+      const float gb = u.gbar[p];
+      G += gb;
+      if (u.saga) u.gbar[p] = gb + g;
+    }
+    const float base = u.base[p];
+    if (u.h) {
+      const float hp = u.h[p];
+      const float xh = base - u.gamma * (G - hp);
+      if (u.theta) {
+        u.xhat[p] = xh;
+        u.v[p] = xh - u.gamma_over_p * hp;
+      } else {
+        u.x[p] = xh;
+      }
+    } else {
+      const float xh = base - u.gamma * G;
+      if (u.theta) u.v[p] = xh;
+      else u.x[p] = xh;
+    }
   }
 }
 
@@ -236,7 +261,6 @@ int fwd3d(const vrps_geom* g, const float* x, const int* ids, int rows, int mode
 
 int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u, cudaStream_t s) {
   Adj3DParams P;
-  P.r = r;
   P.rays = g->ray3d;
   P.views = g->view3d;
   P.ids = ids;
@@ -252,9 +276,30 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.cv = 0.5f * (float)(g->nv - 1);
   P.vox = (float)g->pixel;
   P.u = u;
-  dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
-  { LaunchScope _ls("adj3d_kernel", s);
-  VRPS_CUDA(launch_kernel(adj3d_kernel, dim3(grid), dim3(block), (size_t)(0), s, P));
+  P.r = r;
+  if (!u.prescaled && rows > 0) {
+    vrps_geom* gm = const_cast<vrps_geom*>(g);
+    VRPS_TRY(ensure(&gm->ws.sino2, (size_t)g->m));
+    dim3 pg((g->nu + 31) / 32, (g->nv + 7) / 8, rows), pb(32, 8);
+    {
+      LaunchScope _ls("prescale3d_kernel", s);
+      VRPS_CUDA(launch_kernel(prescale3d_kernel, pg, pb, (size_t)0, s, r, gm->ws.sino2, (const RayInfo3D*)g->ray3d,
+                              ids, g->nu, g->nv, P.cv, P.vox));
+    }
+    VRPS_LAUNCHED("prescale3d");
+    P.r = gm->ws.sino2;
+  }
+  dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + ADJ3_ZC - 1) / ADJ3_ZC), block(32, 8);
+  LaunchScope _ls("adj3d_kernel", s);
+  switch (g->adj3_ncv) {
+    case 2: VRPS_CUDA(launch_kernel(adj3d_kernel<2>, grid, block, (size_t)0, s, P)); break;
+    case 3: VRPS_CUDA(launch_kernel(adj3d_kernel<3>, grid, block, (size_t)0, s, P)); break;
+    case 4: VRPS_CUDA(launch_kernel(adj3d_kernel<4>, grid, block, (size_t)0, s, P)); break;
+    case 5: VRPS_CUDA(launch_kernel(adj3d_kernel<5>, grid, block, (size_t)0, s, P)); break;
+    case 6: VRPS_CUDA(launch_kernel(adj3d_kernel<6>, grid, block, (size_t)0, s, P)); break;
+    case 7: VRPS_CUDA(launch_kernel(adj3d_kernel<7>, grid, block, (size_t)0, s, P)); break;
+    case 8: VRPS_CUDA(launch_kernel(adj3d_kernel<8>, grid, block, (size_t)0, s, P)); break;
+    default: return fail(VRPS_ERR_UNSUPPORTED, "detector rows much finer than voxels (%d candidates)", g->adj3_ncv);
   }
   VRPS_LAUNCHED("adj3d");
   return VRPS_OK;

@@ -194,6 +194,8 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   VRPS_CUDA(cudaEventCreate(&ev0));
   VRPS_CUDA(cudaEventCreate(&ev1));
   VRPS_CUDA(cudaEventRecord(ev0, s));
+  // 3D: forwards that feed an adjoint leave the ray length factor on their residual
+  const int pre = g->dims == 3 ? 1 : 0;
   const float tau = (float)(gamma * alpha / p);
   const float fgamma = (float)gamma, fgp = (float)(gamma / p), fpg = (float)(p / gamma);
   double t_fista = 1.0;
@@ -211,6 +213,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     UpdateArgs ua;
     std::memset(&ua, 0, sizeof(ua));
     ua.enabled = 1;
+    ua.prescaled = pre;
     ua.base = xf;
     ua.h = skip ? w.h : nullptr;
     ua.gamma = fgamma;
@@ -222,19 +225,19 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     ua.v = w.v;
 
     if (est == EST_FULL) {
-      FwdOut fo{w.res, w.b_perm, nullptr};
+      FwdOut fo{w.res, w.b_perm, nullptr, pre};
       VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_RESID, fo, s));
       ua.cN = 1.f;
       VRPS_TRY(proj_adjoint(g, w.res, order, g->n_angles, ua, s));
       r.passes += 1.0;
     } else if (est == VRPS_EST_SGD) {
-      FwdOut fo{w.res, b_i, nullptr};
+      FwdOut fo{w.res, b_i, nullptr, pre};
       VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_RESID, fo, s));
       ua.cN = (float)N;
       VRPS_TRY(proj_adjoint(g, w.res, ids_i, rows_i, ua, s));
       r.passes += 1.0 / N;
     } else if (est == VRPS_EST_SAGA) {
-      FwdOut fo{w.res, b_i, tab_i};
+      FwdOut fo{w.res, b_i, tab_i, pre};
       VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_SAGA, fo, s));
       ua.cN = (float)N;
       ua.gbar = w.gbar;
@@ -245,11 +248,12 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
       const bool refresh = est == VRPS_EST_SVRG ? (k % N == 0) : (k == 0 || coin != 0);
       if (refresh) {
         // snapshot x~ = x_k: store A x~ (subset-major), gbar = A^T (A x~ - b); then G = gbar
-        FwdOut fo{w.res, w.b_perm, w.tab};
+        FwdOut fo{w.res, w.b_perm, w.tab, pre};
         VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_SNAP, fo, s));
         UpdateArgs pa;
         std::memset(&pa, 0, sizeof(pa));
         pa.out = w.gbar;
+        pa.prescaled = pre;
         VRPS_TRY(proj_adjoint(g, w.res, order, g->n_angles, pa, s));
         ua.cN = 0.f;
         ua.gbar = w.gbar;
@@ -257,7 +261,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
         r.snapshots += 1;
         r.passes += 1.0;
       } else {
-        FwdOut fo{w.res, nullptr, tab_i};
+        FwdOut fo{w.res, nullptr, tab_i, pre};
         VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_SVRG, fo, s));
         ua.cN = (float)N;
         ua.gbar = w.gbar;

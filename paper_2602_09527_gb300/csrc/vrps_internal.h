@@ -137,6 +137,7 @@ struct Workspace {
   unsigned* dev_error = nullptr;  // device-side error word (bounded waits that expired)
   double* scalars = nullptr;    // [16] device scalars
   float* sino = nullptr;        // [m] sinogram scratch
+  float* sino2 = nullptr;       // [m] second sinogram scratch (3D adjoint prescaling)
   float* img = nullptr;         // [n] image scratch
   float* img2 = nullptr;        // [n]
   // solver state (allocated on first solve)
@@ -177,7 +178,7 @@ struct vrps_geom {
   vrps::RayInfo3D* ray3d = nullptr;     // [n_views][nu]
   vrps::ViewInfo3D* view3d = nullptr;   // [n_views]
   std::vector<vrps::ViewInfo3D> view3d_host;
-  int adj3_nu = 0, adj3_nv = 0;         // candidate window of the 3D adjoint
+  int adj3_ncv = 0;                     // detector-row candidates per voxel of the 3D adjoint
   // angle orders
   int* order_natural = nullptr;   // [n_angles] 0..n_angles-1
   int* order_subset = nullptr;    // [n_angles] subset-major for n_subsets
@@ -199,6 +200,7 @@ struct FwdOut {
   float* y;           // output rows
   const float* b;     // data rows (RESID, SAGA, SNAP)
   float* tab;         // table rows (SVRG read, SAGA read/write, SNAP write)
+  int prescale = 0;   // 3D: write y times the ray's length factor (input of a prescaled adjoint)
 };
 int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
           FwdOut o, cudaStream_t s);
@@ -219,6 +221,7 @@ struct UpdateArgs {
   float* xT;              // and its transpose (may be null)
   float* xhat;            // theta = 1 and h in use: keep x_hat
   float* v;               // theta = 1: prox input
+  int prescaled;          // 3D: r already carries the ray length factors (see FwdOut::prescale)
 };
 int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
           cudaStream_t s);

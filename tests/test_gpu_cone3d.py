@@ -31,6 +31,10 @@ SMALL = synthetic.Cone3DSpec(nx=21, ny=18, nz=13, voxel=0.5, betas=synthetic.uni
 SCALED = synthetic.Cone3DSpec(nx=64, ny=64, nz=64, voxel=2.0, betas=synthetic.uniform_angles(36, 2 * math.pi),
                               nu=96, nv=96, du=4.0, dv=4.0, sod=500.0, sdd=1000.0, n_subsets=6)
 
+# ragged against the adjoint's 32 x 8 x 16 voxel tiles and the prox's 32 x 16 x 64 chunks
+RAGGED = synthetic.Cone3DSpec(nx=45, ny=19, nz=37, voxel=0.5, betas=synthetic.uniform_angles(8, 2 * math.pi),
+                              nu=61, nv=52, du=0.8, dv=0.8, sod=60.0, sdd=120.0, n_subsets=2)
+
 
 def _pair(spec):
     vr = _vr()
@@ -54,6 +58,19 @@ def test_adjoint_small_every_subset():
         r = rng.standard_normal((len(ids), og.nv, og.nu))
         x = vr.proj_adj(g, i, dev(r))
         assert rel(host(x), J.adjoint(og, r, ids)) < TOL, i
+
+
+def test_ragged_tiles_every_subset():
+    vr, g, og = _pair(RAGGED)
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0.0, 1.0, size=(37, 19, 45))
+    for s_ in range(2):
+        rows = list(range(s_, 8, 2))
+        y = host(vr.proj_fwd(g, s_, dev(x))).reshape(len(rows), 52, 61)
+        assert rel(y, J.forward(og, x, rows)) < TOL, s_
+        r = rng.standard_normal((len(rows), 52, 61))
+        xa = host(vr.proj_adj(g, s_, dev(r)))
+        assert rel(xa, J.adjoint(og, r, rows)) < TOL, s_
 
 
 def test_adjoint_identity_fp32():

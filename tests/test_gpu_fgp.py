@@ -64,7 +64,7 @@ def test_fgp2d_full_size_100_iters():
     assert rel(host(x), ref) < TOL
 
 
-@pytest.mark.parametrize("shape", [(16, 20, 24), (5, 33, 9), (1, 1, 3)])
+@pytest.mark.parametrize("shape", [(16, 20, 24), (5, 33, 9), (1, 1, 3), (130, 37, 70)])
 @pytest.mark.parametrize("iters", [0, 1, 4, 30])
 def test_fgp3d(shape, iters):
     nz, ny, nx = shape
