@@ -103,13 +103,13 @@ int subset_rows(const vrps_geom* g, int subset, const int** ids, int* rows) {
 
 int proj_forward(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows,
                  int mode, FwdOut o, cudaStream_t s) {
-  if (g->dims == 3) return fwd3d(g, x, ids, rows, mode, o, s);
   if (!xT) {
     vrps_geom* gm = const_cast<vrps_geom*>(g);
     VRPS_TRY(ensure(&gm->ws.xT, (size_t)g->n));
-    VRPS_TRY(transpose2d(x, gm->ws.xT, g->ny, g->nx, s));
+    VRPS_TRY(transpose2d(x, gm->ws.xT, g->ny, g->nx, s, g->dims == 3 ? g->nz : 1));
     xT = gm->ws.xT;
   }
+  if (g->dims == 3) return fwd3d(g, x, xT, ids, rows, mode, o, s);
   return fwd2d(g, x, xT, ids, rows, mode, o, s);
 }
 
@@ -268,7 +268,7 @@ static int build_cone3d(vrps_geom* g) {
           return fail(VRPS_ERR_INVALID_ARG, "view %d column %d: volume planes behind the source", a, iu);
       }
       RayInfo3D& r = rays[(size_t)a * g->nu + iu];
-      r.pad0 = r.pad1 = 0.f;
+      r.pad = 0;
       {
         // smallest z-index step per detector row over the volume's planes (adjoint window)
         const bool ax0 = std::fabs(dx) >= std::fabs(dy);
@@ -276,23 +276,31 @@ static int build_cone3d(vrps_geom* g) {
         const double half = 0.5 * ((ax0 ? g->nx : g->ny) - 1) * vox;
         for (double X : {-half, half}) qz_min = std::fmin(qz_min, g->dv * ((X - Sa) / da) / vox);
       }
+      // transverse index P0 + P1 (l - lc) and z step per row Q0 + Q1 (l - lc) on plane l
+      double P0, P1, Q0, Q1, lc;
       if (std::fabs(dx) >= std::fabs(dy)) {
         r.axis = 0;
-        r.P0 = (float)(cy + (Sy - Sx * dy / dx) / vox);
-        r.P1 = (float)(dy / dx);
-        r.Q0 = (float)(-Sx * g->dv / (dx * vox));
-        r.Q1 = (float)(g->dv / dx);
-        r.R = (float)(g->dv / dx);
+        P0 = cy + (Sy - Sx * dy / dx) / vox;
+        P1 = dy / dx;
+        Q0 = -Sx * g->dv / (dx * vox);
+        Q1 = g->dv / dx;
+        lc = cx;
         vi.has_x = 1;
       } else {
         r.axis = 1;
-        r.P0 = (float)(cx + (Sx - Sy * dx / dy) / vox);
-        r.P1 = (float)(dx / dy);
-        r.Q0 = (float)(-Sy * g->dv / (dy * vox));
-        r.Q1 = (float)(g->dv / dy);
-        r.R = (float)(g->dv / dy);
+        P0 = cx + (Sx - Sy * dx / dy) / vox;
+        P1 = dx / dy;
+        Q0 = -Sy * g->dv / (dy * vox);
+        Q1 = g->dv / dy;
+        lc = cy;
         vi.has_y = 1;
       }
+      r.PF0 = std::llround(std::ldexp(P0 - P1 * lc, 32));
+      r.PF1 = std::llround(std::ldexp(P1, 32));
+      r.QF0 = std::llround(std::ldexp(Q0 - Q1 * lc, 32));
+      r.QF1 = std::llround(std::ldexp(Q1, 32));
+      r.P1 = (float)P1;
+      r.R = (float)Q1;
     }
   }
   // rows within one voxel of a voxel's centre in z: an open window of 2/qz rows

@@ -389,6 +389,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
 __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx) {
   __shared__ float t[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  in += (size_t)blockIdx.z * nx * ny;   // one [ny][nx] slice per blockIdx.z
+  out += (size_t)blockIdx.z * nx * ny;
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int x = bx + threadIdx.x, y = by + k;
     if (x < nx && y < ny) t[k][threadIdx.x] = in[(size_t)y * nx + x];
@@ -402,8 +404,8 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 
 }  // namespace
 
-int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s) {
-  dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
+int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s, int slices) {
+  dim3 grid((nx + 31) / 32, (ny + 31) / 32, slices), block(32, 8);
   { LaunchScope _ls("transpose_kernel", s);
   VRPS_CUDA(launch_kernel(transpose_kernel, dim3(grid), dim3(block), (size_t)(0), s, in, out, ny, nx));
   }

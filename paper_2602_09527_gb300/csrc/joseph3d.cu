@@ -2,9 +2,11 @@
 // transpose (gather, no atomics), with the same fused epilogues as the 2D projector.
 //
 // Each ray (view, iu, iv) is marched over the planes of its dominant axis (x or y, fixed
-// per detector column); on plane l its point has transverse index ft = P0 + P1 (l - lc)
-// and z index fz = cz + (iv - cv)(Q0 + Q1 (l - lc)), bilinearly interpolated; each plane
-// adds voxel * |d| / |d_a|.  The adjoint visits, for every voxel and view, the detector
+// per detector column); on plane l its point has transverse index ft = P0 + P1 l and z index
+// fz = cz + (iv - cv)(Q0 + Q1 l), both carried in 64-bit fixed point, bilinearly
+// interpolated; each plane adds voxel * |d| / |d_a|.  Rays marched over x planes read the
+// volume transposed in (x, y), so that for either axis the 32 lanes of a warp (adjacent
+// detector columns) read along a contiguous row.  The adjoint visits, for every voxel and view, the detector
 // columns whose rays cross the voxel's dominant plane within one voxel (found by projecting
 // the two plane points at +-1 voxel onto the detector) and the rows whose z index is within
 // one voxel, and accumulates the identical bilinear weight.
@@ -14,7 +16,8 @@ namespace vrps {
 namespace {
 
 struct Fwd3DParams {
-  const float* x;
+  const float* x;    // [nz][ny][nx]
+  const float* xT;   // [nz][nx][ny]
   const RayInfo3D* rays;
   const int* ids;
   int nx, ny, nz, nu, nv;
@@ -42,6 +45,8 @@ __device__ __forceinline__ void clip_range(float intercept, float slope, float l
   }
 }
 
+constexpr float TWO_M32 = 2.3283064365386963e-10f;   // 2^-32
+
 template <int MODE>
 __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
   const int iu = blockIdx.x * 32 + threadIdx.x;
@@ -51,31 +56,33 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
   const int view = P.ids[row];
   const RayInfo3D ri = P.rays[(size_t)view * P.nu + iu];
   const float k = (float)iv - P.cv;
+  const long long k2 = 2LL * iv - (P.nv - 1);   // 2 (iv - cv), exact
   const bool ax0 = ri.axis == 0;
   const int nl = ax0 ? P.nx : P.ny;
   const int nt = ax0 ? P.ny : P.nx;
-  const float lc = ax0 ? P.cx : P.cy;
-  const int64_t sl = ax0 ? 1 : P.nx;
-  const int64_t st = ax0 ? P.nx : 1;
+  const float* vol = ax0 ? P.xT : P.x;          // transverse index contiguous in both cases
+  const int64_t sl = nt;
   const int64_t sz = (int64_t)P.nx * P.ny;
   int lo = 0, hi = nl - 1;
-  clip_range(ri.P0, ri.P1, lc, nt, nl, lo, hi);
-  clip_range(fmaf(k, ri.Q0, P.cz), k * ri.Q1, lc, P.nz, nl, lo, hi);
+  const float q0 = __ll2float_rn(ri.QF0) * TWO_M32, q1 = __ll2float_rn(ri.QF1) * TWO_M32;
+  clip_range(__ll2float_rn(ri.PF0) * TWO_M32, ri.P1, 0.f, nt, nl, lo, hi);
+  clip_range(fmaf(k, q0, P.cz), k * q1, 0.f, P.nz, nl, lo, hi);
   float acc = 0.f;
-  for (int l = lo; l <= hi; ++l) {
-    const float dl = (float)l - lc;
-    const float ft = fmaf(ri.P1, dl, ri.P0);
-    const float fz = fmaf(k, fmaf(ri.Q1, dl, ri.Q0), P.cz);
-    const float flt = floorf(ft), flz = floorf(fz);
-    const int it = (int)flt, iz = (int)flz;
-    const float f = ft - flt, gz = fz - flz;
+  // transverse position in units of 2^-32, z position in units of 2^-33
+  long long ft = ri.PF0 + ri.PF1 * lo;
+  const long long zstep = k2 * ri.QF1;
+  long long fz = ((long long)(P.nz - 1) << 32) + k2 * ri.QF0 + zstep * lo;
+  for (int l = lo; l <= hi; ++l, ft += ri.PF1, fz += zstep) {
+    const int it = (int)(ft >> 32), iz = (int)(fz >> 33);
+    const float f = (float)(unsigned)ft * TWO_M32;
+    const float gz = (float)(unsigned)(fz >> 1) * TWO_M32;
     const bool t0 = it >= 0 && it < nt, t1 = it + 1 >= 0 && it + 1 < nt;
     const bool z0 = iz >= 0 && iz < P.nz, z1 = iz + 1 >= 0 && iz + 1 < P.nz;
-    const int64_t b = (int64_t)l * sl + (int64_t)it * st + (int64_t)iz * sz;
-    const float v00 = (t0 && z0) ? __ldg(P.x + b) : 0.f;
-    const float v10 = (t1 && z0) ? __ldg(P.x + b + st) : 0.f;
-    const float v01 = (t0 && z1) ? __ldg(P.x + b + sz) : 0.f;
-    const float v11 = (t1 && z1) ? __ldg(P.x + b + st + sz) : 0.f;
+    const int64_t b = (int64_t)l * sl + (int64_t)it + (int64_t)iz * sz;
+    const float v00 = (t0 && z0) ? __ldg(vol + b) : 0.f;
+    const float v10 = (t1 && z0) ? __ldg(vol + b + 1) : 0.f;
+    const float v01 = (t0 && z1) ? __ldg(vol + b + sz) : 0.f;
+    const float v11 = (t1 && z1) ? __ldg(vol + b + 1 + sz) : 0.f;
     const float lo_z = fmaf(f, v10 - v00, v00);
     const float hi_z = fmaf(f, v11 - v01, v01);
     acc += fmaf(gz, hi_z - lo_z, lo_z);
@@ -162,7 +169,8 @@ __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
     for (int axis = 0; axis < 2; ++axis) {
       if (axis == 0 ? !vi.has_x : !vi.has_y) continue;
       const int tt = axis == 0 ? gy : gx;
-      const float dl = axis == 0 ? (float)gx - P.cx : (float)gy - P.cy;
+      const long long gl = axis == 0 ? gx : gy;
+      const long long tt32 = (long long)tt << 32;
       const float c0 = fminf(fmaxf(axis == 0 ? column_of(vi, X, Y - P.vox) : column_of(vi, X - P.vox, Y), -2.f), lim);
       const float c1 = fminf(fmaxf(axis == 0 ? column_of(vi, X, Y + P.vox) : column_of(vi, X + P.vox, Y), -2.f), lim);
       const int u_lo = max(0, (int)floorf(fminf(c0, c1)) - 1);
@@ -170,22 +178,29 @@ __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
       for (int iu = u_lo; iu <= u_hi; ++iu) {
         const RayInfo3D ri = vr[iu];
         if (ri.axis != axis) continue;
-        const float wt = 1.f - fabsf(fmaf(ri.P1, dl, ri.P0) - (float)tt);
-        if (wt <= 0.f) continue;
-        const float qz = fmaf(ri.Q1, dl, ri.Q0);   // z-index step per detector row (> 0)
-        const float iq = 1.f / qz;
+        const long long dt = ri.PF0 + ri.PF1 * gl - tt32;   // (transverse - tt) 2^32, exact
+        if (dt <= -(1LL << 32) || dt >= (1LL << 32)) continue;
+        const float wt = 1.f - fabsf(__ll2float_rn(dt) * TWO_M32);
+        // z-index step per detector row (> 0) as an unevaluated sum qh + ql
+        const long long qf = ri.QF0 + ri.QF1 * gl;
+        const float qh = __ll2float_rn(qf) * TWO_M32;
+        const float ql = __ll2float_rn(qf - __float2ll_rn(qh * 4294967296.f)) * TWO_M32;
+        const float iq = 1.f / qh;
         const float* col = rr + iu;
 #pragma unroll
         for (int z = 0; z < ADJ3_ZC; ++z) {
-          const float gzf = (float)(z0 + z);
-          const float klo = fminf(fmaxf(fmaf(gzf - 1.f - P.cz, iq, P.cv), -2.f), vlim);
+          const float czg = P.cz - (float)(z0 + z);   // exact
+          const float klo = fminf(fmaxf(fmaf(-1.f - czg, iq, P.cv), -2.f), vlim);
           const int ivs = (int)floorf(klo) + 1;   // first row whose ray passes above gz - 1
+          const float ks = (float)ivs - P.cv;     // exact
+          float e = fmaf(ks, ql, fmaf(ks, qh, czg));   // fz(ivs) - gz
           float a = 0.f;
 #pragma unroll
           for (int c = 0; c < NCV; ++c) {
             const int iv = ivs + c;
-            const float wz = 1.f - fabsf(fmaf((float)iv - P.cv, qz, P.cz) - gzf);
+            const float wz = 1.f - fabsf(e);
             if (wz > 0.f && (unsigned)iv < (unsigned)P.nv) a = fmaf(wz, __ldg(col + (size_t)iv * P.nu), a);
+            e += qh;
           }
           acc[z] = fmaf(wt, a, acc[z]);
         }
@@ -229,10 +244,12 @@ __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
 
 }  // namespace
 
-int fwd3d(const vrps_geom* g, const float* x, const int* ids, int rows, int mode, FwdOut o, cudaStream_t s) {
+int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode, FwdOut o,
+          cudaStream_t s) {
   if (rows <= 0) return VRPS_OK;
   Fwd3DParams P;
   P.x = x;
+  P.xT = xT;
   P.rays = g->ray3d;
   P.ids = ids;
   P.nx = g->nx;

@@ -104,11 +104,17 @@ constexpr int ADJ2D_TILE_Y = 32;
 //   transverse index  ft = P0 + P1 (l - lc)
 //   z index           fz = (iv - cv) (Q0 + Q1 (l - lc)) + cz
 //   weight            wgt = voxel * sqrt(1 + P1^2 + ((iv - cv) R)^2),  R = dv / d_a
+// Per (view, detector column) ray constants of the 3D projector.  On plane l of the ray's
+// dominant axis (l = 0 .. n-1, not centred) the transverse voxel index is (PF0 + PF1 l) 2^-32
+// and the z-index step per detector row is qz(l) = (QF0 + QF1 l) 2^-32: 64-bit fixed point, so
+// positions stay exact to ~1e-9 voxel at any distance from the volume centre.
 struct RayInfo3D {
-  float P0, P1, Q0, Q1;
-  float R;
-  int axis;
-  float pad0, pad1;
+  long long PF0, PF1;
+  long long QF0, QF1;
+  float P1;   // transverse slope (ray length factor)
+  float R;    // z slope per detector row relative to the dominant axis (ray length factor)
+  int axis;   // 0: marched over x planes, 1: over y planes
+  int pad;
 };
 
 // Per view constants of the 3D voxel-driven adjoint (float64-derived).
@@ -204,7 +210,7 @@ struct FwdOut {
 };
 int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
           FwdOut o, cudaStream_t s);
-int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s);
+int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s, int slices = 1);
 
 // epilogue of the pixel-driven adjoint, fused ProxSkip update (Algorithm 1, x_hat line)
 struct UpdateArgs {
@@ -227,7 +233,7 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
           cudaStream_t s);
 
 // ---- 3D projector (joseph3d.cu)
-int fwd3d(const vrps_geom* g, const float* x, const int* ids, int rows, int mode, FwdOut o,
+int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode, FwdOut o,
           cudaStream_t s);
 int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
           cudaStream_t s);

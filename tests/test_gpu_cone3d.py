@@ -73,6 +73,30 @@ def test_ragged_tiles_every_subset():
         assert rel(xa, J.adjoint(og, r, rows)) < TOL, s_
 
 
+def test_full_size_sampled_views():
+    """The 256^3 / 384^2 / 360-view geometry the 3D bench runs: subset 0 (12 views) forward on a
+    random volume, compared on three sampled views, and the adjoint of random data placed on
+    two of its views (zero-mean data: no smoothing hides position errors)."""
+    w = synthetic.WORKLOADS_3D["cone3d_256"]
+    spec = synthetic.Cone3DSpec(nx=w["n"], ny=w["n"], nz=w["n"], voxel=w["voxel"],
+                                betas=synthetic.uniform_angles(w["n_views"], 2 * math.pi), nu=w["det"],
+                                nv=w["det"], du=w["d"], dv=w["d"], sod=w["sod"], sdd=w["sdd"],
+                                n_subsets=w["n_subsets"])
+    vr, g, og = _pair(spec)
+    n, d, N = w["n"], w["det"], w["n_subsets"]
+    rows = list(range(0, w["n_views"], N))
+    rng = np.random.default_rng(21)
+    x = rng.uniform(0.0, 1.0, size=(n, n, n))
+    y = host(vr.proj_fwd(g, 0, dev(x))).reshape(len(rows), d, d)
+    for r_i in (0, 4, 7):        # 0, 120 and 210 degrees
+        assert rel(y[r_i], J.forward(og, x, [rows[r_i]])[0]) < TOL, r_i
+    r = np.zeros((len(rows), d, d))
+    pick = [3, 5]                # 90 and 150 degrees
+    r[pick] = rng.standard_normal((2, d, d))
+    xa = host(vr.proj_adj(g, 0, dev(r)))
+    assert rel(xa, J.adjoint(og, r[pick], [rows[i] for i in pick])) < TOL
+
+
 def test_adjoint_identity_fp32():
     vr, g, og = _pair(SMALL)
     rng = np.random.default_rng(3)
