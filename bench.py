@@ -45,6 +45,16 @@ WORKLOADS = {
                      target_gap=1e-4, max_epochs=150),
 }
 
+# 3D cone-beam workload (optional, not the default line): 256^3 voxels of 0.5, 360 views over
+# 360 deg, 384^2 detector of pixel 1, SOD 500, SDD 1000, 30 subsets, ProxSVRGSkip p = 0.1 with
+# 50 3D FGP iterations.  Metric: seconds per epoch (N = 30 subset iterations from x0 = 0,
+# including the epoch's SVRG snapshot and its prox calls).
+WORKLOADS_3D = {
+    "cone3d_256": dict(n=256, voxel=0.5, n_views=360, det=384, d=1.0, sod=500.0, sdd=1000.0, n_subsets=30,
+                       alpha=0.01, algo="VR_PROXSKIP", estimator="SVRG", p=0.1, fgp_iters=50, seed=20260209,
+                       epochs=1),
+}
+
 # Iteration counts of the replayed trajectory (same seed and draws on any machine), used only
 # by the CPU oracle legs to scale a bounded sample up to a whole reconstruction.  Recorded from
 # the GPU replay of this workload; the GPU arm recomputes them every run.
@@ -153,18 +163,202 @@ def oracle_extrapolate(samp, counts, N):
 
 
 # --------------------------------------------------------------------------- roofline
-def algorithmic_bytes(kernel, g, rows_subset):
-    """Algorithmic DRAM bytes of one launch (float32, each array touched once)."""
-    n, nb = g.n, g.desc.get("n_bins", 0)
-    if kernel == "fgp2d_iter":       # read v, w_k(2), w_{k-1}(2); write w_{k+1}(2)
-        return 28 * n
-    if kernel == "fgp2d_out":        # read v, w(2), x, xhat, h; write x, xT, h
-        return 36 * n
-    if kernel == "adj2d_kernel":     # read dr (m_i), x, h, gbar; write x + xT (skip) or v + xhat
-        return 4 * rows_subset * nb + 20 * n
-    if kernel == "fwd2d_kernel":     # read x or xT (n), table (m_i); write dr (m_i)
-        return 4 * n + 8 * rows_subset * nb
-    return None
+def roofline_of(prof, peaks):
+    """Roofline entry of the kernel family with the largest share of device time: achieved =
+    its launches' algorithmic bytes (reported by the library per launch) / their event time."""
+    tot_ms = sum(v[1] for v in prof.values())
+    name, (launches, ms, nbytes) = max(prof.items(), key=lambda kv: kv[1][1])
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    if nbytes <= 0:
+        return None
+    avg_s = ms / 1e3 / max(launches, 1)
+    per_launch = nbytes / max(launches, 1)
+    ach = per_launch / avg_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "peak_source": src,
+            "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": NCU_TRAFFIC.get(name),
+            "bytes_per_launch": round(per_launch), "avg_launch_us": round(avg_s * 1e6, 3),
+            "share": round(ms / tot_ms, 4)}
+
+
+def kernel_table(prof):
+    tot_ms = sum(v[1] for v in prof.values())
+    out = {}
+    for k, (n, ms, nb) in prof.items():
+        out[k] = {"launches": n, "ms": round(ms, 4), "share": round(ms / tot_ms, 4)}
+        if nb > 0:
+            out[k]["gbs"] = round(nb / (ms / 1e3) / 1e9, 1)
+    return out
+
+
+def load_peaks():
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pk_path)) if os.path.exists(pk_path) else {}
+
+
+# --------------------------------------------------------------------------- 3D workload
+def make_problem3(wl, rank):
+    w = WORKLOADS_3D[wl]
+    return synthetic.make_problem_3d(w["n"], w["voxel"], w["n_views"], w["det"], w["d"], w["sod"], w["sdd"],
+                                     w["n_subsets"], seed=w["seed"] + rank, alpha=w["alpha"])
+
+
+def oracle_sample_3d(wl, spec):
+    """Time the float64 oracle on one view's forward and adjoint and two FGP iterations of
+    the 3D workload; oracle_epoch_3d scales these to one epoch."""
+    from oracle import joseph3d, tv
+    w = WORKLOADS_3D[wl]
+    og = joseph3d.GeometryCone.from_spec(spec)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(0, 1, size=og.shape())
+    t0 = time.perf_counter()
+    y = joseph3d.forward(og, x, [0])
+    joseph3d.adjoint(og, y, [0])
+    t1 = time.perf_counter()
+    tv.fgp(x, 1e-3, 2)
+    t2 = time.perf_counter()
+    return {"t_view": t1 - t0, "t_fgp_iter": (t2 - t1) / 2, "sample_s": t2 - t0,
+            "views_per_subset": w["n_views"] // w["n_subsets"]}
+
+
+def oracle_epoch_3d(samp, w):
+    """One epoch of the oracle's ProxSVRGSkip: N - 1 subset iterations with two subset
+    gradients each (at x and at the snapshot), one full gradient, p N prox calls."""
+    N = w["n_subsets"]
+    grad_views = (N - 1) * 2 * samp["views_per_subset"] + w["n_views"]
+    return grad_views * samp["t_view"] + w["p"] * N * w["fgp_iters"] * samp["t_fgp_iter"]
+
+
+def bench_3d(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2602_09527_gb300 as vr
+    wl = args.workload
+    w = WORKLOADS_3D[wl]
+    P = make_problem3(wl, rank)
+    g = vr.Geometry.from_spec(P.spec)
+    N = w["n_subsets"]
+    iters = w["epochs"] * N
+    b_dev = torch.tensor(P.b.astype(np.float32).ravel(), device="cuda")
+    L = vr.power_iteration(g, 30, seed=w["seed"])
+    gamma = 1.0 / L
+
+    def run_once(bb=b_dev, k=iters):
+        return vr.solve(bb, g, w["alpha"], w["algo"], p=w["p"], gamma=gamma, seed=w["seed"],
+                        estimator=w["estimator"], fgp_iters=w["fgp_iters"], max_iters=k)
+
+    if args.profile_once:
+        run_once(k=args.profile_once)
+        torch.cuda.synchronize()
+        g.close()
+        return
+    b_host = torch.tensor(P.b.astype(np.float32).ravel()).pin_memory()
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)
+    for _ in range(args.warmup):
+        run_once()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    launches0 = vr.kernel_launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, rep, _ = run_once()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+    launches = (vr.kernel_launches() - launches0) // args.steps
+    total = sum(times)
+    if dist is not None:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    sec_epoch = total / args.steps / w["epochs"]
+    e2e = []
+    for _ in range(2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run_once(bb=b_host)
+        e2e.append(time.perf_counter() - t0)
+    vr.profile_enable(True)
+    run_once()
+    prof = vr.profile_read()
+    vr.profile_enable(False)
+    peaks = load_peaks()
+    samples_sub = g.samples(0)
+    xs = torch.rand(g.n, device="cuda")
+    ys = vr.proj_fwd(g, 0, xs)
+    for _ in range(2):
+        vr.proj_fwd(g, 0, xs, ys)
+        vr.proj_adj(g, 0, ys, xs)
+    vr.profile_enable(True)
+    for _ in range(5):
+        vr.proj_fwd(g, 0, xs, ys)
+        vr.proj_adj(g, 0, ys, xs)
+    pp = vr.profile_read()
+    vr.profile_enable(False)
+    t_fwd = pp["fwd3d_kernel"][1] / pp["fwd3d_kernel"][0] / 1e3
+    t_adj = (pp["adj3d_kernel"][1] + pp["prescale3d_kernel"][1]) / pp["adj3d_kernel"][0] / 1e3
+    t_tr = pp.get("transpose_kernel", (1, 0.0, 0))[1] / max(pp.get("transpose_kernel", (1, 0.0, 0))[0], 1) / 1e3
+    gvox = 2 * samples_sub / (t_fwd + t_tr + t_adj) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        samp = oracle_sample_3d(wl, P.spec)
+        cpu = {"value": round(oracle_epoch_3d(samp, w), 1), "unit": "s per epoch", "cores": 1, "kind": "oracle",
+               "sample": (f"float64 oracle on this host: one view forward + adjoint ({samp['t_view']:.2f} s) and "
+                          f"two 3D FGP iterations ({2 * samp['t_fgp_iter']:.2f} s) at full size, scaled to one "
+                          f"epoch ({N - 1} x 2 subset gradients of {samp['views_per_subset']} views, one full "
+                          f"gradient, {w['p'] * N:g} prox calls of {w['fgp_iters']} iterations)")}
+    out = {
+        "metric": "s per epoch (3D cone-beam, 30 subset iterations)",
+        "value": round(sec_epoch, 6),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total / args.steps * 1e3, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded ellipsoid phantom, analytic cone-beam projections, Gaussian noise 1%)",
+        "config": {"workload": wl, "volume": f"{w['n']}^3", "voxel": w["voxel"], "views": w["n_views"],
+                   "detector": f"{w['det']}x{w['det']}", "sod": w["sod"], "sdd": w["sdd"], "subsets": N,
+                   "algo": "ProxSVRGSkip", "p": w["p"], "fgp_iters": w["fgp_iters"], "alpha": w["alpha"],
+                   "gamma": "1/L (30 power iterations)", "epochs_per_step": w["epochs"],
+                   "prox_calls": rep["prox_calls"], "snapshots": rep["snapshots"],
+                   "l2": "flushed between steps (256 MB write); working set > L2", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(statistics.mean(e2e) / w["epochs"], 6), "unit": "s",
+                "h2d_bytes_per_step": 4 * g.m, "d2h_bytes_per_step": 4 * g.n},
+        "gpu_launches": int(launches),
+        "roofline": roofline_of(prof, peaks),
+        "kernels": kernel_table(prof),
+        "projector": {"metric": "G ray-voxel/s", "value": round(gvox, 3), "samples_per_subset": samples_sub,
+                      "fwd_us": round(t_fwd * 1e6, 1), "transpose_us": round(t_tr * 1e6, 1),
+                      "adj_us": round(t_adj * 1e6, 1),
+                      "what": "subset 0 (12 views x 384^2): 2 x Joseph samples / (transpose + forward + "
+                              "prescale + adjoint kernel time)"},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
@@ -173,7 +367,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--workload", default="par2d_512", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="par2d_512", choices=list(WORKLOADS) + list(WORKLOADS_3D))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--alpha", type=float, default=None, help="override the workload's TV weight")
     ap.add_argument("--profile-once", type=int, default=0, metavar="K",
@@ -184,12 +378,14 @@ def main():
         args.warmup = 3
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     wl = args.workload
-    w = WORKLOADS[wl]
+    w = WORKLOADS[wl] if wl in WORKLOADS else WORKLOADS_3D[wl]
     if args.alpha is not None:
         w["alpha"] = args.alpha
 
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if wl in WORKLOADS_3D:
+        return bench_3d(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -288,26 +484,9 @@ def main():
     run_once()
     prof = vr.profile_read()
     vr.profile_enable(False)
-    tot_ms = sum(v[1] for v in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_launch, dom_ms) = dom
-    rows_subset = w["n_angles"] // N
-    ab = algorithmic_bytes(dom_name, g, rows_subset)
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    avg_s = dom_ms / 1e3 / max(dom_launch, 1)
-    roofline = None
-    if ab is not None:
-        ach = ab / avg_s / 1e9
-        roofline = {"kernel": dom_name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
-                    "peak_source": peak_src, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
-                    "traffic": NCU_TRAFFIC.get(dom_name), "bytes_per_launch": ab,
-                    "avg_launch_us": round(avg_s * 1e6, 3), "share": round(dom_ms / tot_ms, 4)}
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot_ms, 4)} for k, v in prof.items()}
+    peaks = load_peaks()
+    roofline = roofline_of(prof, peaks)
+    kernels = kernel_table(prof)
 
     # projector throughput (G ray-voxel/s): subset forward and adjoint kernels, each launch
     # timed by CUDA events around it (library profiling), so host call overhead is excluded
@@ -383,6 +562,8 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     wl = args.workload
+    if wl in WORKLOADS_3D:
+        return reference_arm_3d(args, wl)
     w = WORKLOADS[wl]
     counts = TRAJECTORY[wl]
     if counts["iterations"] is None:
@@ -422,6 +603,26 @@ def reference_arm(args, rank, world):
         "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
+
+
+def reference_arm_3d(args, wl):
+    w = WORKLOADS_3D[wl]
+    spec = synthetic.Cone3DSpec(nx=w["n"], ny=w["n"], nz=w["n"], voxel=w["voxel"],
+                                betas=synthetic.uniform_angles(w["n_views"], 2 * math.pi), nu=w["det"], nv=w["det"],
+                                du=w["d"], dv=w["d"], sod=w["sod"], sdd=w["sdd"], n_subsets=w["n_subsets"])
+    for _ in range(args.warmup):
+        oracle_sample_3d(wl, spec)
+    vals = [oracle_epoch_3d(oracle_sample_3d(wl, spec), w) for _ in range(args.steps)]
+    v = statistics.mean(vals)
+    print(json.dumps({
+        "impl": "reference", "metric": "s per epoch (3D cone-beam, 30 subset iterations)", "value": round(v, 1),
+        "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded ellipsoid phantom)", "config": {"workload": wl},
+        "cpu_baseline": {"value": round(v, 1), "unit": "s per epoch", "cores": 1, "kind": "oracle",
+                         "sample": "per step: one view forward + adjoint and two 3D FGP iterations at full size, "
+                                   "scaled to one epoch"},
+        "e2e": {"value": round(v, 1), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 if __name__ == "__main__":

@@ -168,12 +168,15 @@ int vrps_philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int
  * kernels this library has launched in the process.  While profiling is enabled every
  * launch is bracketed by CUDA events recorded on the launching stream; vrps_profile_read
  * synchronises the device, folds the elapsed times into per-kernel totals and copies up to
- * `cap` entries (HOST array) with *count set to the number of kernel families seen.
+ * `cap` entries (HOST array) with *count set to the number of kernel families seen.  `bytes`
+ * sums the launches' algorithmic DRAM traffic: each float32 array the launch must read or
+ * write, counted once (0 for kernels that state none).
  * vrps_profile_enable(0) stops recording and clears the totals. */
 typedef struct vrps_kernel_stat {
   char name[32];
   uint64_t launches;
   double total_ms;
+  double bytes;
 } vrps_kernel_stat;
 
 uint64_t vrps_kernel_launches(void);

@@ -52,7 +52,8 @@ class Report(ctypes.Structure):
 
 
 class KernelStat(ctypes.Structure):
-    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 def _load():
@@ -328,9 +329,11 @@ def profile_enable(on: bool = True):
 
 
 def profile_read() -> dict:
-    """{kernel name: (launches, total ms)} of the launches recorded while profiling was on."""
+    """{kernel name: (launches, total ms, algorithmic bytes)} of the launches recorded while
+    profiling was on."""
     cap = 64
     arr = (KernelStat * cap)()
     cnt = ctypes.c_int()
     _check(lib.vrps_profile_read(arr, cap, ctypes.byref(cnt)))
-    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms)) for k in range(min(cnt.value, cap))}
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms), float(arr[k].bytes))
+            for k in range(min(cnt.value, cap))}

@@ -642,6 +642,12 @@ namespace {
 struct PendingLaunch {
   const char* name;
   cudaEvent_t e0, e1;
+  double bytes;
+};
+struct Totals {
+  uint64_t launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
 };
 struct ProfState {
   std::atomic<uint64_t> launches{0};
@@ -649,13 +655,13 @@ struct ProfState {
   std::mutex mu;
   std::vector<PendingLaunch> pending;
   std::vector<cudaEvent_t> pool;
-  std::map<std::string, std::pair<uint64_t, double>> totals;
+  std::map<std::string, Totals> totals;
 };
 ProfState& prof() {
   static ProfState* st = new ProfState();   // never destroyed: safe at process exit
   return *st;
 }
-thread_local PendingLaunch t_open = {nullptr, nullptr, nullptr};
+thread_local PendingLaunch t_open = {nullptr, nullptr, nullptr, 0.0};
 
 cudaEvent_t take_event(ProfState& st) {
   if (!st.pool.empty()) {
@@ -669,7 +675,7 @@ cudaEvent_t take_event(ProfState& st) {
 }
 }  // namespace
 
-void launch_begin(const char* name, cudaStream_t s) {
+void launch_begin(const char* name, cudaStream_t s, double bytes) {
   ProfState& st = prof();
   st.launches.fetch_add(1, std::memory_order_relaxed);
   t_open.name = nullptr;
@@ -678,7 +684,7 @@ void launch_begin(const char* name, cudaStream_t s) {
   cudaEvent_t e0 = take_event(st), e1 = take_event(st);
   if (!e0 || !e1) return;
   cudaEventRecord(e0, s);
-  t_open = {name, e0, e1};
+  t_open = {name, e0, e1, bytes};
 }
 
 void launch_end(cudaStream_t s) {
@@ -721,8 +727,9 @@ int vrps_profile_read(vrps_kernel_stat* out, int cap, int* count) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
       auto& t = st.totals[p.name];
-      t.first += 1;
-      t.second += ms;
+      t.launches += 1;
+      t.ms += ms;
+      t.bytes += p.bytes;
     }
     st.pool.push_back(p.e0);
     st.pool.push_back(p.e1);
@@ -732,8 +739,9 @@ int vrps_profile_read(vrps_kernel_stat* out, int cap, int* count) {
   for (auto& kv : st.totals) {
     if (out && k < cap) {
       std::snprintf(out[k].name, sizeof(out[k].name), "%s", kv.first.c_str());
-      out[k].launches = kv.second.first;
-      out[k].total_ms = kv.second.second;
+      out[k].launches = kv.second.launches;
+      out[k].total_ms = kv.second.ms;
+      out[k].bytes = kv.second.bytes;
     }
     ++k;
   }

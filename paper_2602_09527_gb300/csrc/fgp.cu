@@ -431,7 +431,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       float* wn = pairs[which][0];
       float* zn = pairs[which][1];
       {
-        LaunchScope _ls("fgp2d_block", s);
+        // read v, w and z (one array when z = w), write w and z
+        LaunchScope _ls("fgp2d_block", s, 4.0 * g->n * (rz == rw ? 7 : 9));
         dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
         VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, g->nx, g->ny, tau,
                                                                            step, mb, ns, nonneg));
@@ -459,7 +460,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
       dim3 grid((g->nx + F3_TX - 1) / F3_TX, (g->ny + F3_TY - 1) / F3_TY, (g->nz + F3_ZC - 1) / F3_ZC);
       {
-        LaunchScope _ls("fgp3d_stream", s);
+        // read v, w_k (and w_{k-1} when extrapolating), write w_{k+1}
+        LaunchScope _ls("fgp3d_stream", s, 4.0 * g->n * (mk != 0.f ? 10 : 7));
         VRPS_CUDA(launch_kernel(fgp3d_stream, grid, dim3(F3_TX, F3_TY), (size_t)0, s, v, (const float*)buf[cur],
                                 (const float*)buf[prev], buf[nxt], D, tau, step, mk, nonneg));
       }
@@ -473,14 +475,14 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   if (g->dims == 2) {
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32), block(32, 8);
     {
-      LaunchScope _ls("fgp2d_out", s);
+      LaunchScope _ls("fgp2d_out", s, 4.0 * g->n * (wdst ? 5 : 3) + tail_bytes(tail, (size_t)g->n));
       VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail));
     }
   } else {
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
     dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
     {
-      LaunchScope _ls("fgp3d_out", s);
+      LaunchScope _ls("fgp3d_out", s, 4.0 * g->n * (wdst ? 7 : 4) + tail_bytes(tail, (size_t)g->n));
       VRPS_CUDA(launch_kernel(fgp3d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, D, tau, nonneg, tail));
     }
   }
@@ -577,7 +579,7 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
     float* wn = pairs[which][0];
     float* zn = pairs[which][1];
     {
-      LaunchScope _ls("fgp2d_block", s);
+      LaunchScope _ls("fgp2d_block", s, 4.0 * nx * ny * (rz == rw ? 7 : 9));
       dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
       VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, nx, ny, tau, step, mb,
                                                                          ns, nonneg ? 1 : 0));
@@ -594,7 +596,7 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
   float* wdst = (rw != d && dual) ? dual : nullptr;
   {
     dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
-    LaunchScope _ls("fgp2d_out", s);
+    LaunchScope _ls("fgp2d_out", s, 4.0 * nx * ny * (wdst ? 5 : 3) + tail_bytes(t, (size_t)nx * ny));
     VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t));
   }
   VRPS_LAUNCHED("fgp2d_out");

@@ -406,7 +406,7 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 
 int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s, int slices) {
   dim3 grid((nx + 31) / 32, (ny + 31) / 32, slices), block(32, 8);
-  { LaunchScope _ls("transpose_kernel", s);
+  { LaunchScope _ls("transpose_kernel", s, 8.0 * nx * ny * slices);
   VRPS_CUDA(launch_kernel(transpose_kernel, dim3(grid), dim3(block), (size_t)(0), s, in, out, ny, nx));
   }
   VRPS_LAUNCHED("transpose2d");
@@ -458,7 +458,7 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   dim3 grid(P.bands, rows), block(FWD_THREADS);
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
-    LaunchScope _ls("fwd2d_kernel", s);
+    LaunchScope _ls("fwd2d_kernel", s, 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->n_bins));
     VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };
@@ -496,7 +496,7 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   dim3 grid((g->nx + ADJ_TX - 1) / ADJ_TX, (g->ny + ty - 1) / ty), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
-    LaunchScope _ls("adj2d_kernel", s);
+    LaunchScope _ls("adj2d_kernel", s, 4.0 * rows * g->n_bins + update_bytes(u, (size_t)g->n));
     VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };

@@ -264,12 +264,13 @@ int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.vox = (float)g->pixel;
   P.o = o;
   dim3 grid((g->nu + 31) / 32, (g->nv + 7) / 8, rows), block(32, 8);
+  const double fb = 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->nu * g->nv);
   switch (mode) {
-    case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_PLAIN>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_RESID: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_RESID>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_SVRG: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SVRG>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_SAGA: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SAGA>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
-    case FWD_SNAP: { LaunchScope _ls("fwd3d_kernel", s); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SNAP>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_PLAIN>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_RESID: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_RESID>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_SVRG: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SVRG>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_SAGA: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SAGA>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
+    case FWD_SNAP: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_SNAP>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
     default: return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
   }
   VRPS_LAUNCHED("fwd3d");
@@ -299,7 +300,7 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
     VRPS_TRY(ensure(&gm->ws.sino2, (size_t)g->m));
     dim3 pg((g->nu + 31) / 32, (g->nv + 7) / 8, rows), pb(32, 8);
     {
-      LaunchScope _ls("prescale3d_kernel", s);
+      LaunchScope _ls("prescale3d_kernel", s, 8.0 * rows * g->nu * g->nv);
       VRPS_CUDA(launch_kernel(prescale3d_kernel, pg, pb, (size_t)0, s, r, gm->ws.sino2, (const RayInfo3D*)g->ray3d,
                               ids, g->nu, g->nv, P.cv, P.vox));
     }
@@ -307,7 +308,7 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
     P.r = gm->ws.sino2;
   }
   dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + ADJ3_ZC - 1) / ADJ3_ZC), block(32, 8);
-  LaunchScope _ls("adj3d_kernel", s);
+  LaunchScope _ls("adj3d_kernel", s, 4.0 * rows * g->nu * g->nv + update_bytes(u, (size_t)g->n));
   switch (g->adj3_ncv) {
     case 2: VRPS_CUDA(launch_kernel(adj3d_kernel<2>, grid, block, (size_t)0, s, P)); break;
     case 3: VRPS_CUDA(launch_kernel(adj3d_kernel<3>, grid, block, (size_t)0, s, P)); break;

@@ -134,7 +134,7 @@ __global__ void fill_kernel(float* p, float v, int64_t n) {
 }  // namespace
 
 int dot64(const float* a, const float* b, int64_t n, double* dst, Workspace& ws, cudaStream_t s) {
-  { LaunchScope _ls("dot_partial", s);
+  { LaunchScope _ls("dot_partial", s, (a == b ? 4.0 : 8.0) * n);
   VRPS_CUDA(launch_kernel(dot_partial, dim3(NPART), dim3(RED_THREADS), (size_t)(0), s, a, b, n, ws.partials));
   }
   VRPS_LAUNCHED("dot_partial");
@@ -146,7 +146,7 @@ int dot64(const float* a, const float* b, int64_t n, double* dst, Workspace& ws,
 }
 
 int tv64(const vrps_geom* g, const float* x, double* dst, Workspace& ws, cudaStream_t s) {
-  { LaunchScope _ls("tv_partial", s);
+  { LaunchScope _ls("tv_partial", s, 4.0 * g->n);
   VRPS_CUDA(launch_kernel(tv_partial, dim3(NPART), dim3(RED_THREADS), (size_t)(0), s, x, g->nx, g->ny, g->nz, ws.partials));
   }
   VRPS_LAUNCHED("tv_partial");
@@ -172,7 +172,7 @@ int philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int N, d
 
 int philox_uniform(uint64_t seed, uint32_t job, uint32_t tag, float* out, int64_t n, cudaStream_t s) {
   const int64_t blocks = ((n + 3) / 4 + 255) / 256;
-  { LaunchScope _ls("uniform_kernel", s);
+  { LaunchScope _ls("uniform_kernel", s, 4.0 * n);
   VRPS_CUDA(launch_kernel(uniform_kernel, dim3((unsigned)blocks), dim3(256), (size_t)(0), s, (uint32_t)seed, (uint32_t)(seed >> 32), job, tag, out, n));
   }
   VRPS_LAUNCHED("philox_uniform");
@@ -180,7 +180,7 @@ int philox_uniform(uint64_t seed, uint32_t job, uint32_t tag, float* out, int64_
 }
 
 int scale_inv_sqrt(float* dst, const float* src, const double* nrm2, int64_t n, cudaStream_t s) {
-  { LaunchScope _ls("scale_kernel", s);
+  { LaunchScope _ls("scale_kernel", s, 8.0 * n);
   VRPS_CUDA(launch_kernel(scale_kernel, dim3(NPART), dim3(256), (size_t)(0), s, dst, src, nrm2, n));
   }
   VRPS_LAUNCHED("scale_inv_sqrt");
@@ -190,7 +190,7 @@ int scale_inv_sqrt(float* dst, const float* src, const double* nrm2, int64_t n, 
 int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s) {
   if (rows <= 0) return VRPS_OK;
   dim3 grid((row_len + 255) / 256 < 64 ? (row_len + 255) / 256 : 64, rows);
-  { LaunchScope _ls("gather_rows_kernel", s);
+  { LaunchScope _ls("gather_rows_kernel", s, 8.0 * rows * row_len);
   VRPS_CUDA(launch_kernel(gather_rows_kernel, dim3(grid), dim3(256), (size_t)(0), s, src, dst, ids, row_len));
   }
   VRPS_LAUNCHED("gather_rows");
@@ -200,7 +200,7 @@ int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_
 int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s) {
   if (rows <= 0) return VRPS_OK;
   dim3 grid((row_len + 255) / 256 < 64 ? (row_len + 255) / 256 : 64, rows);
-  { LaunchScope _ls("scatter_rows_kernel", s);
+  { LaunchScope _ls("scatter_rows_kernel", s, 8.0 * rows * row_len);
   VRPS_CUDA(launch_kernel(scatter_rows_kernel, dim3(grid), dim3(256), (size_t)(0), s, src, dst, ids, row_len));
   }
   VRPS_LAUNCHED("scatter_rows");
@@ -208,7 +208,7 @@ int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row
 }
 
 int fill(float* p, float v, int64_t n, cudaStream_t s) {
-  { LaunchScope _ls("fill_kernel", s);
+  { LaunchScope _ls("fill_kernel", s, 4.0 * n);
   VRPS_CUDA(launch_kernel(fill_kernel, dim3(NPART), dim3(256), (size_t)(0), s, p, v, n));
   }
   VRPS_LAUNCHED("fill");

@@ -38,11 +38,13 @@ int cuda_fail(cudaError_t e, const char* what);
 // ------------------------------------------------------------------ launch accounting
 // Every kernel launch is wrapped in a LaunchScope: it counts the launch and, while
 // profiling is on, records CUDA events around it on the launching stream.
-void launch_begin(const char* name, cudaStream_t s);
+// `bytes` is the launch's algorithmic DRAM traffic (every array it must read or write,
+// touched once, float32), summed per kernel family for the roofline; 0 where not stated.
+void launch_begin(const char* name, cudaStream_t s, double bytes);
 void launch_end(cudaStream_t s);
 struct LaunchScope {
   cudaStream_t s;
-  LaunchScope(const char* name, cudaStream_t st) : s(st) { launch_begin(name, st); }
+  LaunchScope(const char* name, cudaStream_t st, double bytes = 0.0) : s(st) { launch_begin(name, st, bytes); }
   ~LaunchScope() { launch_end(s); }
 };
 
@@ -232,6 +234,30 @@ struct UpdateArgs {
 int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
           cudaStream_t s);
 
+// Algorithmic bytes of the image-side epilogue of an adjoint launch over n pixels.
+inline double update_bytes(const UpdateArgs& u, size_t n) {
+  const double f = 4.0 * (double)n;
+  if (!u.enabled) return f;                        // write out
+  double b = f;                                    // read base
+  if (u.gbar) b += u.saga ? 2 * f : f;             // read gbar (SAGA: and write it)
+  if (u.h) b += f;                                 // read h
+  if (u.theta) b += u.h ? 2 * f : f;               // write v (and x_hat)
+  else b += u.xT ? 2 * f : f;                      // write x (and its transpose)
+  return b;
+}
+
+// Algorithmic bytes of a forward launch's sinogram epilogue over m_i rays (FwdMode).
+inline double fwd_mode_bytes(int mode, size_t mi) {
+  const double f = 4.0 * (double)mi;
+  switch (mode) {
+    case FWD_PLAIN: return f;          // write y
+    case FWD_RESID: return 2 * f;      // read b, write y
+    case FWD_SVRG: return 2 * f;       // read A x~, write y
+    case FWD_SAGA: return 4 * f;       // read b, table; write y, table
+    default: return 3 * f;             // snapshot: read b; write table, y
+  }
+}
+
 // ---- 3D projector (joseph3d.cu)
 int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode, FwdOut o,
           cudaStream_t s);
@@ -254,6 +280,18 @@ struct ProxTail {
 };
 int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
             const ProxTail& tail, cudaStream_t s);
+
+// Algorithmic bytes of the prox output launch's tail over n pixels (beyond reading v, w).
+inline double tail_bytes(const ProxTail& t, size_t n) {
+  const double f = 4.0 * (double)n;
+  if (t.mode == 0) return f;                       // write out
+  double b = 2 * f;                                // read and write x
+  if (t.h) b += 3 * f;                             // read h, x_hat; write h
+  if (t.xprox) b += f;
+  if (t.y) b += f;
+  if (t.y ? t.yT : t.xT) b += f;                   // transposed copy
+  return b;
+}
 
 // ---- reductions, Philox, misc (reduce.cu)
 int dot64(const float* a, const float* b, int64_t n, double* dst, Workspace& ws, cudaStream_t s);
