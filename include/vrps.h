@@ -199,7 +199,16 @@ typedef struct vrps_solve_opts {
   int host_io;        /* 1: b and x_out are HOST pointers (copied inside the call) */
   int n_subsets;      /* 0: the geometry's N; otherwise the number of subsets for this solve */
   uint32_t job;       /* Philox counter word 2 (independent streams for batched jobs) */
+  int storage;        /* vrps_storage of the solver's copy of b and of the estimator table
+                       * (SVRG: A x~; SAGA: residual rows); arithmetic is float32 either way */
+  int correction_epochs; /* with BF16 storage: the last correction_epochs * N iterations switch
+                       * to float32 storage, starting from an exact float32 full gradient
+                       * (SVRG: a snapshot; SAGA: the table rebuilt at the current point;
+                       * 0: no switch; the whole run must then be longer than the switch) */
 } vrps_solve_opts;
+
+/* Storage of sinogram-sized solver state (not in the paper: a precision/footprint choice). */
+typedef enum vrps_storage { VRPS_STORAGE_FP32 = 0, VRPS_STORAGE_BF16 = 1 } vrps_storage;
 
 typedef struct vrps_report {
   int iterations;     /* outer iterations performed */

@@ -36,6 +36,7 @@ class SolveOpts(ctypes.Structure):
         ("f_star", ctypes.c_double), ("target_gap", ctypes.c_double),
         ("x0", ctypes.c_void_p), ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int),
         ("host_io", ctypes.c_int), ("n_subsets", ctypes.c_int), ("job", ctypes.c_uint32),
+        ("storage", ctypes.c_int), ("correction_epochs", ctypes.c_int),
     ]
 
 
@@ -277,7 +278,7 @@ def solve(b: torch.Tensor, g: Geometry, alpha: float, algo: str = "VR_PROXSKIP",
           max_iters: int = 100, nonneg: bool = True, power_iters: int = 100, eval_every: int = 0,
           f_star: float = 0.0, target_gap: float = 0.0, x0: torch.Tensor | None = None,
           history_cap: int = 0, n_subsets: int = 0, job: int = 0, x_out: torch.Tensor | None = None,
-          stream=None):
+          storage: str = "FP32", correction_epochs: int = 0, stream=None):
     """vrps_solve.  b and x_out on the GPU, or both on the host (then the copies happen
     inside the call).  Returns (x_out, report dict, history array [evaluations, 4])."""
     host_io = not b.is_cuda
@@ -288,6 +289,8 @@ def solve(b: torch.Tensor, g: Geometry, alpha: float, algo: str = "VR_PROXSKIP",
     o.power_iters, o.eval_every = int(power_iters), int(eval_every)
     o.f_star, o.target_gap = float(f_star), float(target_gap)
     o.host_io, o.n_subsets, o.job = 1 if host_io else 0, int(n_subsets), int(job)
+    o.storage = {"FP32": 0, "BF16": 1}[storage.upper()]
+    o.correction_epochs = int(correction_epochs)
     if host_io:
         bp = _host_ptr(b, "b", g.m)
         if x_out is None:

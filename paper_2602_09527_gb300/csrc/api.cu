@@ -132,7 +132,7 @@ static int check_geom(const vrps_geom* g) {
 static void free_ws(Workspace& w) {
   float** fl[] = {&w.xT, &w.dual_cold, &w.dual_s1, &w.dual_s2, &w.dual_s3, &w.dual_s4, &w.sino, &w.sino2, &w.img, &w.img2,
                   &w.x, &w.xf, &w.xfT, &w.h, &w.xhat, &w.v, &w.gbar, &w.xprox, &w.dual,
-                  &w.b_perm, &w.tab, &w.res};
+                  &w.b_perm, &w.tab, &w.res, &w.b16, &w.tab16};
   for (float** p : fl) {
     if (*p) cudaFree(*p);
     *p = nullptr;

@@ -221,19 +221,20 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
     for (int q = 0; q < P.bands; ++q) s += __ldcg(P.part + rbase + (size_t)q * P.nb + j);
     const float r = s * in.wgt;
     const size_t idx = (size_t)row * P.nb + j;
+    const int bf = P.o.bf16;
     if (MODE == FWD_PLAIN) {
       P.o.y[idx] = r;
     } else if (MODE == FWD_RESID) {
-      P.o.y[idx] = r - P.o.b[idx];
+      P.o.y[idx] = r - ld_store(P.o.b, idx, bf);
     } else if (MODE == FWD_SVRG) {
-      P.o.y[idx] = r - P.o.tab[idx];
+      P.o.y[idx] = r - ld_store(P.o.tab, idx, bf);
     } else if (MODE == FWD_SAGA) {
-      const float res = r - P.o.b[idx];
-      P.o.y[idx] = res - P.o.tab[idx];
-      P.o.tab[idx] = res;
+      const float res = r - ld_store(P.o.b, idx, bf);
+      P.o.y[idx] = res - ld_store(P.o.tab, idx, bf);
+      st_store(P.o.tab, idx, res, bf);
     } else {  // FWD_SNAP
-      P.o.tab[idx] = r;
-      P.o.y[idx] = r - P.o.b[idx];
+      st_store(P.o.tab, idx, r, bf);
+      P.o.y[idx] = r - ld_store(P.o.b, idx, bf);
     }
   }
 }
@@ -458,7 +459,7 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   dim3 grid(P.bands, rows), block(FWD_THREADS);
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
-    LaunchScope _ls("fwd2d_kernel", s, 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->n_bins));
+    LaunchScope _ls("fwd2d_kernel", s, 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->n_bins, o.bf16));
     VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };

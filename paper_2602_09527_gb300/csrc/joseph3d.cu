@@ -92,19 +92,20 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
   const float r = acc * wgt;
   const float ys = P.o.prescale ? wgt : 1.f;   // ray factor carried into the adjoint's input
   const size_t idx = (size_t)row * P.nu * P.nv + (size_t)iv * P.nu + iu;
+  const int bf = P.o.bf16;
   if (MODE == FWD_PLAIN) {
     P.o.y[idx] = r * ys;
   } else if (MODE == FWD_RESID) {
-    P.o.y[idx] = (r - P.o.b[idx]) * ys;
+    P.o.y[idx] = (r - ld_store(P.o.b, idx, bf)) * ys;
   } else if (MODE == FWD_SVRG) {
-    P.o.y[idx] = (r - P.o.tab[idx]) * ys;
+    P.o.y[idx] = (r - ld_store(P.o.tab, idx, bf)) * ys;
   } else if (MODE == FWD_SAGA) {
-    const float res = r - P.o.b[idx];
-    P.o.y[idx] = (res - P.o.tab[idx]) * ys;
-    P.o.tab[idx] = res;
+    const float res = r - ld_store(P.o.b, idx, bf);
+    P.o.y[idx] = (res - ld_store(P.o.tab, idx, bf)) * ys;
+    st_store(P.o.tab, idx, res, bf);
   } else {
-    P.o.tab[idx] = r;
-    P.o.y[idx] = (r - P.o.b[idx]) * ys;
+    st_store(P.o.tab, idx, r, bf);
+    P.o.y[idx] = (r - ld_store(P.o.b, idx, bf)) * ys;
   }
 }
 
@@ -160,7 +161,8 @@ __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
 #pragma unroll
   for (int z = 0; z < ADJ3_ZC; ++z) acc[z] = 0.f;
   const float lim = (float)P.nu + 2.f;
-  const float vlim = (float)P.nv + 2.f;
+  const float kmax = (float)(P.nv - NCV - 1);   // first candidate row clamped to [0, nv - NCV]
+  const float czg0 = P.cz - (float)z0;          // exact
   for (int q = 0; q < P.rows; ++q) {
     const int view = P.ids[q];
     const ViewInfo3D vi = P.views[view];
@@ -187,19 +189,22 @@ __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
         const float ql = __ll2float_rn(qf - __float2ll_rn(qh * 4294967296.f)) * TWO_M32;
         const float iq = 1.f / qh;
         const float* col = rr + iu;
+        // row window of voxel z: rows above klo(z) = (z0 + z - 1 - cz) / qz + cv; its first
+        // row is clamped into the detector, so every candidate row exists and rows outside
+        // the window get weight max(0, 1 - |e|) = 0
+        const float klo0 = fmaf(-1.f - czg0, iq, P.cv);
 #pragma unroll
         for (int z = 0; z < ADJ3_ZC; ++z) {
-          const float czg = P.cz - (float)(z0 + z);   // exact
-          const float klo = fminf(fmaxf(fmaf(-1.f - czg, iq, P.cv), -2.f), vlim);
-          const int ivs = (int)floorf(klo) + 1;   // first row whose ray passes above gz - 1
-          const float ks = (float)ivs - P.cv;     // exact
-          float e = fmaf(ks, ql, fmaf(ks, qh, czg));   // fz(ivs) - gz
+          const float klo = fminf(fmaxf(fmaf((float)z, iq, klo0), -1.f), kmax);
+          const float fl = floorf(klo);
+          const float ks = fl + (1.f - P.cv);                  // first row - cv (exact)
+          const int ivs = (int)fl + 1;
+          float e = fmaf(ks, ql, fmaf(ks, qh, czg0 - (float)z));   // fz(first row) - gz
+          const float* rp = col + ivs * P.nu;
           float a = 0.f;
 #pragma unroll
           for (int c = 0; c < NCV; ++c) {
-            const int iv = ivs + c;
-            const float wz = 1.f - fabsf(e);
-            if (wz > 0.f && (unsigned)iv < (unsigned)P.nv) a = fmaf(wz, __ldg(col + (size_t)iv * P.nu), a);
+            a = fmaf(fmaxf(1.f - fabsf(e), 0.f), __ldg(rp + c * P.nu), a);
             e += qh;
           }
           acc[z] = fmaf(wt, a, acc[z]);
@@ -264,7 +269,7 @@ int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.vox = (float)g->pixel;
   P.o = o;
   dim3 grid((g->nu + 31) / 32, (g->nv + 7) / 8, rows), block(32, 8);
-  const double fb = 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->nu * g->nv);
+  const double fb = 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->nu * g->nv, o.bf16);
   switch (mode) {
     case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_PLAIN>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
     case FWD_RESID: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_RESID>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
@@ -307,6 +312,9 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
     VRPS_LAUNCHED("prescale3d");
     P.r = gm->ws.sino2;
   }
+  if (g->adj3_ncv > g->nv)
+    return fail(VRPS_ERR_UNSUPPORTED, "detector of %d rows is shorter than the %d-row adjoint window", g->nv,
+                g->adj3_ncv);
   dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + ADJ3_ZC - 1) / ADJ3_ZC), block(32, 8);
   LaunchScope _ls("adj3d_kernel", s, 4.0 * rows * g->nu * g->nv + update_bytes(u, (size_t)g->n));
   switch (g->adj3_ncv) {

@@ -126,6 +126,11 @@ __global__ void scatter_rows_kernel(const float* __restrict__ src, float* __rest
     dst[d0 + j] = src[so + j];
 }
 
+__global__ void bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+
 __global__ void fill_kernel(float* p, float v, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -204,6 +209,14 @@ int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row
   VRPS_CUDA(launch_kernel(scatter_rows_kernel, dim3(grid), dim3(256), (size_t)(0), s, src, dst, ids, row_len));
   }
   VRPS_LAUNCHED("scatter_rows");
+  return VRPS_OK;
+}
+
+int to_bf16(const float* src, void* dst, int64_t n, cudaStream_t s) {
+  { LaunchScope _ls("bf16_kernel", s, 6.0 * n);
+  VRPS_CUDA(launch_kernel(bf16_kernel, dim3(NPART), dim3(256), (size_t)(0), s, src, (__nv_bfloat16*)dst, n));
+  }
+  VRPS_LAUNCHED("to_bf16");
   return VRPS_OK;
 }
 

@@ -30,7 +30,7 @@ struct State {
   float *x, *xf, *xfT, *h, *xhat, *v, *gbar, *xprox, *dual, *b_perm, *tab, *res;
 };
 
-int alloc_solver(vrps_geom* g, bool fista) {
+int alloc_solver(vrps_geom* g, bool fista, bool bf16) {
   Workspace& w = g->ws;
   const size_t n = (size_t)g->n, m = (size_t)g->m;
   VRPS_TRY(ensure(&w.x, n));
@@ -46,6 +46,10 @@ int alloc_solver(vrps_geom* g, bool fista) {
   VRPS_TRY(ensure(&w.sino, m));
   if (g->dims == 2) VRPS_TRY(ensure(&w.xfT, n));
   if (fista) VRPS_TRY(ensure(&w.xf, n));
+  if (bf16) {
+    VRPS_TRY(ensure(&w.b16, (m + 1) / 2));
+    VRPS_TRY(ensure(&w.tab16, (m + 1) / 2));
+  }
   return VRPS_OK;
 }
 
@@ -93,6 +97,9 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   if (!skip) p = 1.0;
   if (!std::isfinite(gamma)) return fail(VRPS_ERR_INVALID_ARG, "gamma is not finite");
   if (o.history && o.history_cap <= 0) return fail(VRPS_ERR_INVALID_ARG, "history_cap must be > 0");
+  if (o.storage != VRPS_STORAGE_FP32 && o.storage != VRPS_STORAGE_BF16)
+    return fail(VRPS_ERR_INVALID_ARG, "bad storage %d", o.storage);
+  if (o.correction_epochs < 0) return fail(VRPS_ERR_INVALID_ARG, "correction_epochs must be >= 0");
   vrps_geom* g = const_cast<vrps_geom*>(gc);
   {
     int dev = -1;
@@ -109,7 +116,8 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   const bool fista = algo == VRPS_ALGO_FISTA;
   cudaStream_t s = (cudaStream_t)stream;
   Workspace& w = g->ws;
-  VRPS_TRY(alloc_solver(g, fista));
+  const bool bf_run = o.storage == VRPS_STORAGE_BF16;
+  VRPS_TRY(alloc_solver(g, fista, bf_run));
   const int64_t n = g->n, m = g->m;
   const int L = g->row_len;
 
@@ -134,6 +142,14 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     b_dev = w.sino;
   }
   VRPS_TRY(gather_rows(b_dev, w.b_perm, order, g->n_angles, L, s));
+  // BF16 storage: iterations k < kc read b and the estimator table as bfloat16
+  const int K = o.max_iters;
+  int kc = 0;
+  if (bf_run) {
+    const long long corr = (long long)o.correction_epochs * N;
+    kc = corr >= K ? 0 : (int)(K - corr);
+    VRPS_TRY(to_bf16(w.b_perm, w.b16, m, s));
+  }
 
   // step size (Section 3)
   vrps_report r;
@@ -164,7 +180,6 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   VRPS_CUDA(cudaMemcpyAsync(w.xprox, x, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s));
 
   // draws
-  const int K = o.max_iters;
   if (w.sched_cap < K) {
     if (w.sched_dev) cudaFree(w.sched_dev);
     if (w.sched_host) cudaFreeHost(w.sched_host);
@@ -186,6 +201,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     std::memset(&ua, 0, sizeof(ua));
     ua.out = w.gbar;
     VRPS_TRY(proj_adjoint(g, w.tab, order, g->n_angles, ua, s));
+    if (kc > 0) VRPS_TRY(to_bf16(w.tab, w.tab16, m, s));
     r.passes += 1.0;
   }
   VRPS_CUDA(cudaStreamSynchronize(s));
@@ -207,8 +223,28 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     const int coin = w.sched_host[3 * k + 2];
     const int* ids_i = order + (*off)[i];
     const int rows_i = (*off)[i + 1] - (*off)[i];
-    float* b_i = w.b_perm + (size_t)(*off)[i] * L;
-    float* tab_i = w.tab + (size_t)(*off)[i] * L;
+    const int bf = k < kc ? 1 : 0;
+    const size_t es = bf ? sizeof(__nv_bfloat16) : sizeof(float);
+    char* const b_all = bf ? (char*)w.b16 : (char*)w.b_perm;
+    char* const tab_all = bf ? (char*)w.tab16 : (char*)w.tab;
+    char* b_i = b_all + es * (size_t)(*off)[i] * L;
+    char* tab_i = tab_all + es * (size_t)(*off)[i] * L;
+    bool force_refresh = false;
+    if (bf_run && k == kc && kc > 0) {
+      // switch to float32 storage from an exact float32 full gradient
+      if (est == VRPS_EST_SAGA) {
+        // rho = A x - b unscaled (the table), gbar = A^T rho
+        FwdOut fo{w.tab, w.b_perm, nullptr};
+        VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_RESID, fo, s));
+        UpdateArgs ga;
+        std::memset(&ga, 0, sizeof(ga));
+        ga.out = w.gbar;
+        VRPS_TRY(proj_adjoint(g, w.tab, order, g->n_angles, ga, s));
+        r.passes += 1.0;
+      } else {
+        force_refresh = true;
+      }
+    }
 
     UpdateArgs ua;
     std::memset(&ua, 0, sizeof(ua));
@@ -225,19 +261,19 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     ua.v = w.v;
 
     if (est == EST_FULL) {
-      FwdOut fo{w.res, w.b_perm, nullptr, pre};
+      FwdOut fo{w.res, b_all, nullptr, pre, bf};
       VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_RESID, fo, s));
       ua.cN = 1.f;
       VRPS_TRY(proj_adjoint(g, w.res, order, g->n_angles, ua, s));
       r.passes += 1.0;
     } else if (est == VRPS_EST_SGD) {
-      FwdOut fo{w.res, b_i, nullptr, pre};
+      FwdOut fo{w.res, b_i, nullptr, pre, bf};
       VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_RESID, fo, s));
       ua.cN = (float)N;
       VRPS_TRY(proj_adjoint(g, w.res, ids_i, rows_i, ua, s));
       r.passes += 1.0 / N;
     } else if (est == VRPS_EST_SAGA) {
-      FwdOut fo{w.res, b_i, tab_i, pre};
+      FwdOut fo{w.res, b_i, tab_i, pre, bf};
       VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_SAGA, fo, s));
       ua.cN = (float)N;
       ua.gbar = w.gbar;
@@ -245,10 +281,10 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
       VRPS_TRY(proj_adjoint(g, w.res, ids_i, rows_i, ua, s));
       r.passes += 1.0 / N;
     } else {  // SVRG / LSVRG
-      const bool refresh = est == VRPS_EST_SVRG ? (k % N == 0) : (k == 0 || coin != 0);
+      const bool refresh = force_refresh || (est == VRPS_EST_SVRG ? (k % N == 0) : (k == 0 || coin != 0));
       if (refresh) {
         // snapshot x~ = x_k: store A x~ (subset-major), gbar = A^T (A x~ - b); then G = gbar
-        FwdOut fo{w.res, w.b_perm, w.tab, pre};
+        FwdOut fo{w.res, b_all, tab_all, pre, bf};
         VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_SNAP, fo, s));
         UpdateArgs pa;
         std::memset(&pa, 0, sizeof(pa));
@@ -261,7 +297,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
         r.snapshots += 1;
         r.passes += 1.0;
       } else {
-        FwdOut fo{w.res, nullptr, tab_i, pre};
+        FwdOut fo{w.res, nullptr, tab_i, pre, bf};
         VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_SVRG, fo, s));
         ua.cN = (float)N;
         ua.gbar = w.gbar;

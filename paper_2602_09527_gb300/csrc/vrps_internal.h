@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the CUDA library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -153,6 +154,7 @@ struct Workspace {
   float *x = nullptr, *xf = nullptr, *xfT = nullptr, *h = nullptr, *xhat = nullptr, *v = nullptr,
         *gbar = nullptr, *xprox = nullptr, *dual = nullptr;
   float *b_perm = nullptr, *tab = nullptr, *res = nullptr;
+  float *b16 = nullptr, *tab16 = nullptr;   // bfloat16 storage of b_perm / tab (m halves each)
   int32_t* sched_dev = nullptr;
   int sched_cap = 0;
   int32_t* sched_host = nullptr;   // pinned
@@ -205,11 +207,22 @@ int ensure_d(double** p, size_t count);
 // ---- 2D projector (joseph2d.cu)
 enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_SVRG = 2, FWD_SAGA = 3, FWD_SNAP = 4 };
 struct FwdOut {
-  float* y;           // output rows
-  const float* b;     // data rows (RESID, SAGA, SNAP)
-  float* tab;         // table rows (SVRG read, SAGA read/write, SNAP write)
+  float* y;           // output rows (float32 always)
+  const void* b;      // data rows (RESID, SAGA, SNAP): float32, or bfloat16 when bf16
+  void* tab;          // table rows (SVRG read, SAGA read/write, SNAP write): likewise
   int prescale = 0;   // 3D: write y times the ray's length factor (input of a prescaled adjoint)
+  int bf16 = 0;       // b and tab are stored as bfloat16 (arithmetic stays float32)
 };
+
+// Stored sinogram values (data and estimator tables): float32 or bfloat16 storage, float32
+// arithmetic; bfloat16 stores round to nearest even.
+__device__ __forceinline__ float ld_store(const void* p, size_t i, int bf16) {
+  return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]) : static_cast<const float*>(p)[i];
+}
+__device__ __forceinline__ void st_store(void* p, size_t i, float v, int bf16) {
+  if (bf16) static_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(v);
+  else static_cast<float*>(p)[i] = v;
+}
 int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
           FwdOut o, cudaStream_t s);
 int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s, int slices = 1);
@@ -247,14 +260,14 @@ inline double update_bytes(const UpdateArgs& u, size_t n) {
 }
 
 // Algorithmic bytes of a forward launch's sinogram epilogue over m_i rays (FwdMode).
-inline double fwd_mode_bytes(int mode, size_t mi) {
-  const double f = 4.0 * (double)mi;
+inline double fwd_mode_bytes(int mode, size_t mi, int bf16 = 0) {
+  const double f = 4.0 * (double)mi, t = (bf16 ? 2.0 : 4.0) * (double)mi;   // y, stored rows
   switch (mode) {
-    case FWD_PLAIN: return f;          // write y
-    case FWD_RESID: return 2 * f;      // read b, write y
-    case FWD_SVRG: return 2 * f;       // read A x~, write y
-    case FWD_SAGA: return 4 * f;       // read b, table; write y, table
-    default: return 3 * f;             // snapshot: read b; write table, y
+    case FWD_PLAIN: return f;              // write y
+    case FWD_RESID: return f + t;          // read b, write y
+    case FWD_SVRG: return f + t;           // read A x~, write y
+    case FWD_SAGA: return f + 3 * t;       // read b, table; write y, table
+    default: return f + 2 * t;             // snapshot: read b; write table, y
   }
 }
 
@@ -304,6 +317,7 @@ int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_
 int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s);
 int fill(float* p, float v, int64_t n, cudaStream_t s);
 int copy_or_zero(float* dst, const float* src, int64_t n, cudaStream_t s);
+int to_bf16(const float* src, void* dst, int64_t n, cudaStream_t s);
 
 // projector dispatch (2D or 3D) used by the solver and the API
 int proj_forward(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows,
