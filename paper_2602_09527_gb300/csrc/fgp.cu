@@ -47,6 +47,30 @@ struct MomBlock {
   float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
 };
 
+// One blocked launch: nsteps (<= FB_T) iterations from (w, z) to (wn, zn).
+struct FgpBlockArgs {
+  const float* v;
+  const float* w;
+  const float* z;
+  float* wn;
+  float* zn;
+  int nx, ny;
+  float tau, step;
+  MomBlock mom;
+  int nsteps, nonneg;
+};
+
+// x+ and the fused tail over a whole image.
+struct FgpOutArgs {
+  const float* v;
+  const float* w;
+  float* wdst;   // copy of w (may be null)
+  int nx, ny;
+  float tau;
+  int nonneg;
+  ProxTail t;
+};
+
 // Projection onto the unit ball: g / max(1, |g|) through the hardware reciprocal square
 // root (relative error a few ulp, far below the float32 tolerances of the prox).
 __device__ __forceinline__ void ball2(float g1, float g2, float& n1, float& n2) {
@@ -125,13 +149,18 @@ __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, flo
   }
 }
 
+// One output tile (bx, by) of a blocked launch; smf: dynamic shared memory (TL::SMEM bytes).
 template <class TL>
-__global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ v, const float* __restrict__ w_g,
-                                                      const float* __restrict__ z_g, float* __restrict__ wn_g,
-                                                      float* __restrict__ zn_g, int nx, int ny, float tau, float step,
-                                                      MomBlock mom, int nsteps, int nonneg) {
+__device__ __forceinline__ void fgp2d_block_item(const FgpBlockArgs& A, int bx, int by, float* smf) {
   constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT;
-  extern __shared__ float smf[];
+  const float* __restrict__ v = A.v;
+  const float* __restrict__ w_g = A.w;
+  const float* __restrict__ z_g = A.z;
+  float* __restrict__ wn_g = A.wn;
+  float* __restrict__ zn_g = A.zn;
+  const int nx = A.nx, ny = A.ny, nsteps = A.nsteps;
+  const float tau = A.tau, step = A.step;
+  const MomBlock& mom = A.mom;
   float* sv = smf;
   float* w1 = sv + NE;
   float* w2 = w1 + NE;
@@ -139,7 +168,7 @@ __global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ 
   float* z2 = z1 + NE;
   float* sx = z2 + NE;
   const int tid = threadIdx.x;
-  const int ox = blockIdx.x * TL::TX - FB_T, oy = blockIdx.y * TL::TY - FB_T;
+  const int ox = bx * TL::TX - FB_T, oy = by * TL::TY - FB_T;
   const size_t n = (size_t)nx * ny;
   for (int i = tid; i < NE; i += NT) {
     const int gx = ox + i % EX, gy = oy + i / EX;
@@ -160,7 +189,7 @@ __global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ 
   }
   __syncthreads();
   const bool interior = ox >= 1 && oy >= 1 && ox + EX <= nx - 1 && oy + EY <= ny - 1;
-  if (nonneg) {
+  if (A.nonneg) {
     if (interior)
       fgp2d_steps<TL, true, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
     else
@@ -185,12 +214,21 @@ __global__ void __launch_bounds__(TL::NT) fgp2d_block(const float* __restrict__ 
   }
 }
 
+template <class TL>
+__global__ void __launch_bounds__(TL::NT) fgp2d_block(FgpBlockArgs A) {
+  extern __shared__ float smf[];
+  fgp2d_block_item<TL>(A, blockIdx.x, blockIdx.y, smf);
+}
+
 // x+ = P_+(v + tau div w) and the fused tail.  32x32 tile, block 32x8 (4 rows per thread).
-__global__ void __launch_bounds__(256) fgp2d_out(const float* __restrict__ v, const float* __restrict__ w,
-                                                 float* wdst, int nx, int ny, float tau, int nonneg,
-                                                 ProxTail t) {
-  __shared__ float tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+__device__ __forceinline__ void fgp2d_out_item(const FgpOutArgs& A, int tbx, int tby, float (*tile)[33]) {
+  const float* __restrict__ v = A.v;
+  const float* __restrict__ w = A.w;
+  float* wdst = A.wdst;
+  const int nx = A.nx, ny = A.ny, nonneg = A.nonneg;
+  const float tau = A.tau;
+  const ProxTail& t = A.t;
+  const int bx = tbx * 32, by = tby * 32;
   const size_t n = (size_t)nx * ny;
   const bool transposed = (t.mode == 1) && (t.xT || t.yT);
   for (int k = threadIdx.y; k < 32; k += 8) {
@@ -234,6 +272,11 @@ __global__ void __launch_bounds__(256) fgp2d_out(const float* __restrict__ v, co
     const int gy = by + threadIdx.x, gx = bx + k;
     if (gx < nx && gy < ny && dstT) dstT[(size_t)gx * ny + gy] = tile[threadIdx.x][k];
   }
+}
+
+__global__ void __launch_bounds__(256) fgp2d_out(FgpOutArgs A) {
+  __shared__ float tile[32][33];
+  fgp2d_out_item(A, blockIdx.x, blockIdx.y, tile);
 }
 
 // ---------------------------------------------------------------- 3D
@@ -434,8 +477,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
         // read v, w and z (one array when z = w), write w and z
         LaunchScope _ls("fgp2d_block", s, 4.0 * g->n * (rz == rw ? 7 : 9));
         dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
-        VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, g->nx, g->ny, tau,
-                                                                           step, mb, ns, nonneg));
+        const FgpBlockArgs A{v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg};
+        VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, A));
       }
       VRPS_LAUNCHED("fgp2d_block");
       rw = wn;
@@ -476,7 +519,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32), block(32, 8);
     {
       LaunchScope _ls("fgp2d_out", s, 4.0 * g->n * (wdst ? 5 : 3) + tail_bytes(tail, (size_t)g->n));
-      VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail));
+      const FgpOutArgs A{v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail};
+      VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, A));
     }
   } else {
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
@@ -581,8 +625,8 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
     {
       LaunchScope _ls("fgp2d_block", s, 4.0 * nx * ny * (rz == rw ? 7 : 9));
       dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
-      VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, v, rw, rz, wn, zn, nx, ny, tau, step, mb,
-                                                                         ns, nonneg ? 1 : 0));
+      const FgpBlockArgs A{v, rw, rz, wn, zn, nx, ny, tau, step, mb, ns, nonneg ? 1 : 0};
+      VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, A));
     }
     VRPS_LAUNCHED("fgp2d_block");
     rw = wn;
@@ -597,7 +641,8 @@ extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, 
   {
     dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
     LaunchScope _ls("fgp2d_out", s, 4.0 * nx * ny * (wdst ? 5 : 3) + tail_bytes(t, (size_t)nx * ny));
-    VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t));
+    const FgpOutArgs A{v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t};
+    VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, A));
   }
   VRPS_LAUNCHED("fgp2d_out");
   return VRPS_OK;

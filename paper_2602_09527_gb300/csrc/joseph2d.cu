@@ -82,14 +82,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // runs the epilogue.
 constexpr int FWD_PAD = 4;   // zero floats left and right of each staged line (16 bytes)
 
+struct FwdShared {
+  unsigned long long bar;   // mbarrier of the band copies (initialised once per CTA)
+  unsigned last;            // this CTA completed the angle row
+};
+
+// One (band c, angle row) item of the forward.  With BULK the band arrives by bulk copies that
+// complete phase `parity` of S.bar; returns 1 when it used the barrier (the caller flips its
+// parity for the next item).
 template <int MODE, bool BULK>
-__global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
-  extern __shared__ __align__(128) float band[];
-  __shared__ __align__(8) unsigned long long bar;
-  __shared__ unsigned s_last;
+__device__ __forceinline__ int fwd2d_item(const Fwd2DParams& P, int c, int row, float* band, FwdShared& S,
+                                          unsigned parity) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c = blockIdx.x, row = blockIdx.y;
   const AngleInfo2D in = P.ang[P.ids[row]];
+  int used = 0;
   const bool tr = in.T != 0;
   const float* __restrict__ img = tr ? P.xT : P.x;
   const int ncols = tr ? P.ny : P.nx;
@@ -105,25 +111,23 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
       band[L * stride + (q < FWD_PAD ? q : ncols + q)] = 0.f;
     }
     if (BULK) {
+      used = 1;
       if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+        // order earlier generic accesses of the band before the async-proxy writes
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      }
-      __syncthreads();
-      if (tid == 0) {
         const unsigned row_bytes = (unsigned)(ncols * sizeof(float));
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&S.bar)),
                      "r"(row_bytes * (unsigned)nl)
                      : "memory");
         for (int L = 0; L < nl; ++L)
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                   smem_addr(band + L * stride + FWD_PAD)),
-              "l"(global_addr(src + (size_t)L * ncols)), "r"(row_bytes), "r"(smem_addr(&bar))
+              "l"(global_addr(src + (size_t)L * ncols)), "r"(row_bytes), "r"(smem_addr(&S.bar))
               : "memory");
       }
       unsigned it = 0;
-      while (!mbar_try_wait(&bar, 0) && ++it < WAIT_LIMIT) {
+      while (!mbar_try_wait(&S.bar, parity) && ++it < WAIT_LIMIT) {
       }
       ok = it < WAIT_LIMIT;
       if (!ok) {
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
         // shared memory before this CTA retires, and compute nothing from the band
         if (tid == 0) atomicOr(P.err, 1u);
         unsigned it2 = 0;
-        while (!mbar_try_wait(&bar, 0) && ++it2 < WAIT_LIMIT) {
+        while (!mbar_try_wait(&S.bar, parity) && ++it2 < WAIT_LIMIT) {
         }
       }
       __syncthreads();   // the zero margins written above
@@ -209,11 +213,11 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
   __syncthreads();
   if (tid == 0) {
     const unsigned prev = atomicAdd(P.count + row, 1u);
-    s_last = prev == (unsigned)(P.bands - 1) ? 1u : 0u;
-    if (s_last) P.count[row] = 0u;
+    S.last = prev == (unsigned)(P.bands - 1) ? 1u : 0u;
+    if (S.last) P.count[row] = 0u;
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!S.last) return used;
   __threadfence();
   const size_t rbase = (size_t)row * P.bands * P.nb;
   for (int j = tid; j < P.nb; j += FWD_THREADS) {
@@ -237,6 +241,23 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
       P.o.y[idx] = r - ld_store(P.o.b, idx, bf);
     }
   }
+  return used;
+}
+
+__device__ __forceinline__ void fwd2d_init_barrier(FwdShared& S) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+template <int MODE, bool BULK>
+__global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
+  extern __shared__ __align__(128) float band[];
+  __shared__ FwdShared S;
+  if (BULK) fwd2d_init_barrier(S);
+  fwd2d_item<MODE, BULK>(P, blockIdx.x, blockIdx.y, band, S, 0u);
 }
 
 struct Adj2DParams {
@@ -254,7 +275,10 @@ struct Adj2DParams {
 // theta = 1: keep x_hat and write the prox input v = x_hat - (gamma/p) h.
 __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, float g) {
   float G = u.cN * g;
-  if (u.gbar) {
+  if (u.snap) {            // SVRG snapshot: g is the full gradient; gbar <- g, G = g
+    u.gbar[p] = g;
+    G = g;
+  } else if (u.gbar) {
     const float gb = u.gbar[p];
     G += gb;
     if (u.saga) u.gbar[p] = gb + g;
@@ -287,18 +311,26 @@ __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, flo
 // small float) and receives max(0, 1 - |j - t|/hw) r_j from the bins within hw of t.
 // NC = 2 covers hw <= 1 (bins not finer than pixels): two candidates, unrolled; NC = 0 is
 // the general loop over P.nc candidates.
+struct AdjShared {
+  float4 par[ADJ_CHUNK];   // Bx, By, (F0 - hw), 1/hw
+  float c0[ADJ_CHUNK];     // 1 - hw
+  int off[ADJ_CHUNK];      // J0 - jlo
+  int jlo[ADJ_CHUNK];
+  float wgt[ADJ_CHUNK];
+  float tile[32][ADJ_TX + 1];
+};
+
+// One pixel tile (bx, by) of the transpose; sm: dynamic shared [chunk][fp].
 template <int NC, int PPT>
-__global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
+__device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by, float* sm, AdjShared& S) {
   constexpr int TY = (ADJ_THREADS / ADJ_TX) * PPT;   // tile rows: 16 (one pixel per thread) or 32
-  extern __shared__ float sm[];                  // [chunk][fp]
-  __shared__ float4 s_par[ADJ_CHUNK];            // Bx, By, (F0 - hw), 1/hw
-  __shared__ float s_c0[ADJ_CHUNK];              // 1 - hw
-  __shared__ int s_off[ADJ_CHUNK];               // J0 - jlo
-  __shared__ int s_jlo[ADJ_CHUNK];
-  __shared__ float s_wgt[ADJ_CHUNK];
-  __shared__ float s_tile[TY][ADJ_TX + 1];
+  float4* s_par = S.par;
+  float* s_c0 = S.c0;
+  int* s_off = S.off;
+  int* s_jlo = S.jlo;
+  float* s_wgt = S.wgt;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_TX + tx;
-  const int ix0 = blockIdx.x * ADJ_TX, iy0 = blockIdx.y * TY;
+  const int ix0 = bx * ADJ_TX, iy0 = by * TY;
   const float ftx = (float)tx, fty = (float)ty;
   const float half_rows = (float)(TY / 2);
   float acc0 = 0.f, acc1 = 0.f;                  // pixels (tx, ty) and, with PPT = 2, (tx, ty + TY/2)
@@ -376,15 +408,22 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
   const float x0 = in0 ? update_pixel(u, p0, acc0) : 0.f;
   const float x1 = in1 ? update_pixel(u, p1, acc1) : 0.f;
   if (!u.theta && u.xT) {
-    s_tile[ty][tx] = x0;
-    if (PPT == 2) s_tile[ty + TY / 2][tx] = x1;
+    S.tile[ty][tx] = x0;
+    if (PPT == 2) S.tile[ty + TY / 2][tx] = x1;
     __syncthreads();
     for (int e = tid; e < ADJ_TX * TY; e += ADJ_THREADS) {
       const int c = e / TY, r = e - c * TY;
       const int ox = ix0 + c, oy = iy0 + r;
-      if (ox < P.nx && oy < P.ny) u.xT[(size_t)ox * P.ny + oy] = s_tile[r][c];
+      if (ox < P.nx && oy < P.ny) u.xT[(size_t)ox * P.ny + oy] = S.tile[r][c];
     }
   }
+}
+
+template <int NC, int PPT>
+__global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
+  extern __shared__ float sm[];
+  __shared__ AdjShared S;
+  adj2d_item<NC, PPT>(P, blockIdx.x, blockIdx.y, sm, S);
 }
 
 __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx) {

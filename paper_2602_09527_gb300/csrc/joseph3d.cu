@@ -224,7 +224,10 @@ __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
       continue;
     }
     float G = u.cN * g;
-    if (u.gbar) {
+    if (u.snap) {            // SVRG snapshot: g is the full gradient; gbar <- g, G = g
+      u.gbar[p] = g;
+      G = g;
+    } else if (u.gbar) {
       const float gb = u.gbar[p];
       G += gb;
       if (u.saga) u.gbar[p] = gb + g;

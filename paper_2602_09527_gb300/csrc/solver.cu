@@ -283,17 +283,14 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     } else {  // SVRG / LSVRG
       const bool refresh = force_refresh || (est == VRPS_EST_SVRG ? (k % N == 0) : (k == 0 || coin != 0));
       if (refresh) {
-        // snapshot x~ = x_k: store A x~ (subset-major), gbar = A^T (A x~ - b); then G = gbar
+        // snapshot x~ = x_k: store A x~ (subset-major), gbar = A^T (A x~ - b) and G = gbar,
+        // the full adjoint's epilogue writing gbar and taking the step in one pass
         FwdOut fo{w.res, b_all, tab_all, pre, bf};
         VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_SNAP, fo, s));
-        UpdateArgs pa;
-        std::memset(&pa, 0, sizeof(pa));
-        pa.out = w.gbar;
-        pa.prescaled = pre;
-        VRPS_TRY(proj_adjoint(g, w.res, order, g->n_angles, pa, s));
         ua.cN = 0.f;
         ua.gbar = w.gbar;
-        VRPS_TRY(proj_adjoint(g, w.res, ids_i, 0, ua, s));
+        ua.snap = 1;
+        VRPS_TRY(proj_adjoint(g, w.res, order, g->n_angles, ua, s));
         r.snapshots += 1;
         r.passes += 1.0;
       } else {

@@ -243,6 +243,7 @@ struct UpdateArgs {
   float* xhat;            // theta = 1 and h in use: keep x_hat
   float* v;               // theta = 1: prox input
   int prescaled;          // 3D: r already carries the ray length factors (see FwdOut::prescale)
+  int snap;               // SVRG snapshot: g is the full gradient; gbar <- g and G = g
 };
 int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
           cudaStream_t s);
