@@ -240,6 +240,67 @@ int vrps_solve(const float* b, const vrps_geom* g, double alpha, int algo, doubl
                uint64_t seed, const vrps_solve_opts* opts, float* x_out, vrps_report* report,
                vrps_stream_t stream);
 
+/* ---------------------------------------------------------------- batched / served jobs
+ * Many independent 2D VR-ProxSkip reconstructions (Algorithm 1 with a variance-reduced
+ * estimator, x0 = 0) advancing together; no counterpart in the paper, which runs one problem.
+ * One tick performs one iteration of every running job, each phase of the tick being one
+ * persistent launch over all jobs' tiles (optionally replayed from a CUDA graph).  A job's
+ * result is bit-identical to vrps_solve(b, geom, alpha, VRPS_ALGO_VR_PROXSKIP, p, gamma,
+ * seed, {estimator, fgp_iters, max_iters, nonneg, n_subsets, job, storage,
+ * correction_epochs}) whatever other jobs share its ticks.
+ * The batch owns one CUDA stream; device inputs must be ready when vrps_batch_submit is
+ * called (it synchronises that stream once to read the draws).  A geometry handle serves one
+ * running job at a time (its workspace holds the job's state) and may be reused once the job
+ * has finished. */
+typedef struct vrps_batch vrps_batch;
+
+typedef struct vrps_job {
+  const vrps_geom* geom;  /* 2D geometry (caller-owned, kept alive until the job finished) */
+  const float* b;         /* device [m] sinogram in natural angle order (read during submit) */
+  float* x_out;           /* device [n]: the final iterate, written when the job finishes */
+  double alpha;           /* TV weight >= 0 */
+  double p;               /* skip probability in (0, 1] */
+  double gamma;           /* step > 0 */
+  uint64_t seed;          /* Philox key */
+  uint32_t job;           /* Philox counter word 2 */
+  int estimator;          /* vrps_estimator */
+  int fgp_iters;          /* 0 .. 128 */
+  int max_iters;          /* iterations of this job (> 0) */
+  int n_subsets;          /* 0: the geometry's N */
+  int nonneg;
+  int storage;            /* vrps_storage */
+  int correction_epochs;  /* see vrps_solve_opts */
+} vrps_job;
+
+/* Creates an empty batch on the current device.  Errors: CUDA, OUT_OF_MEMORY. */
+int vrps_batch_create(vrps_batch** out);
+/* Waits for the batch's work, releases its buffers, graphs and events. */
+int vrps_batch_free(vrps_batch* batch);
+/* on = 0: launch each tick's kernels directly instead of replaying captured graphs. */
+int vrps_batch_set_graphs(vrps_batch* batch, int on);
+/* Admits a job before the next tick: allocates its state in the geometry's workspace,
+ * reorders b subset-major, draws its Philox schedule and (SAGA) builds its table.  *id is
+ * the job's handle.  Errors: INVALID_ARG (bad field, geometry busy), UNSUPPORTED (3D
+ * geometry, more than 256 running jobs), OUT_OF_MEMORY, CUDA. */
+int vrps_batch_submit(vrps_batch* batch, const vrps_job* job, int* id);
+/* Enqueues up to `ticks` ticks (fewer when every job finishes); *active = jobs still
+ * running.  Returns once the work is enqueued (the host may block on a work-list slot that
+ * the device still reads). */
+int vrps_batch_step(vrps_batch* batch, int ticks, int* active);
+/* *done = 1 once job `id` has finished on the device, with its report (seconds = device
+ * time from admission to completion).  Errors: INVALID_ARG, TIMEOUT (a bounded device wait
+ * of the job expired), CUDA. */
+int vrps_batch_poll(vrps_batch* batch, int id, int* done, vrps_report* report);
+/* Runs ticks until job `id` finished, waits for it and reports it. */
+int vrps_batch_wait(vrps_batch* batch, int id, vrps_report* report);
+/* Waits until every enqueued tick has completed. */
+int vrps_batch_sync(vrps_batch* batch);
+/* Ticks enqueued so far and running jobs. */
+int vrps_batch_ticks(const vrps_batch* batch, long long* ticks, int* active);
+/* Device bytes a job's state occupies on top of its geometry's tables (for admission by
+ * HBM footprint). */
+int vrps_job_footprint(const vrps_geom* g, const vrps_job* job, size_t* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,16 @@ class Report(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class JobDesc(ctypes.Structure):
+    _fields_ = [
+        ("geom", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x_out", ctypes.c_void_p),
+        ("alpha", ctypes.c_double), ("p", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("job", ctypes.c_uint32), ("estimator", ctypes.c_int),
+        ("fgp_iters", ctypes.c_int), ("max_iters", ctypes.c_int), ("n_subsets", ctypes.c_int),
+        ("nonneg", ctypes.c_int), ("storage", ctypes.c_int), ("correction_epochs", ctypes.c_int),
+    ]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -85,6 +95,16 @@ def _load():
         "vrps_kernel_launches": (u64, []),
         "vrps_profile_enable": (i, [i]),
         "vrps_profile_read": (i, [P(KernelStat), i, P(i)]),
+        "vrps_batch_create": (i, [P(vp)]),
+        "vrps_batch_free": (i, [vp]),
+        "vrps_batch_set_graphs": (i, [vp, i]),
+        "vrps_batch_submit": (i, [vp, P(JobDesc), P(i)]),
+        "vrps_batch_step": (i, [vp, i, P(i)]),
+        "vrps_batch_poll": (i, [vp, i, P(i), P(Report)]),
+        "vrps_batch_wait": (i, [vp, i, P(Report)]),
+        "vrps_batch_sync": (i, [vp]),
+        "vrps_batch_ticks": (i, [vp, P(ctypes.c_longlong), P(i)]),
+        "vrps_job_footprint": (i, [vp, P(JobDesc), P(ctypes.c_size_t)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -340,3 +360,99 @@ def profile_read() -> dict:
     _check(lib.vrps_profile_read(arr, cap, ctypes.byref(cnt)))
     return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms), float(arr[k].bytes))
             for k in range(min(cnt.value, cap))}
+
+
+def _job_desc(g: Geometry, b: torch.Tensor, x_out: torch.Tensor, alpha: float, p: float, gamma: float, seed: int,
+              job: int, estimator: str, fgp_iters: int, max_iters: int, n_subsets: int, nonneg: bool,
+              storage: str, correction_epochs: int) -> JobDesc:
+    d = JobDesc()
+    d.geom = g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle
+    d.b = _dev_ptr(b, "b", g.m).value
+    d.x_out = _dev_ptr(x_out, "x_out", g.n).value
+    d.alpha, d.p, d.gamma = float(alpha), float(p), float(gamma)
+    d.seed, d.job = int(seed), int(job)
+    d.estimator = ESTIMATORS[estimator.upper()]
+    d.fgp_iters, d.max_iters, d.n_subsets = int(fgp_iters), int(max_iters), int(n_subsets)
+    d.nonneg = 1 if nonneg else 0
+    d.storage = {"FP32": 0, "BF16": 1}[storage.upper()]
+    d.correction_epochs = int(correction_epochs)
+    return d
+
+
+class Batch:
+    """vrps_batch_*: many 2D VR-ProxSkip jobs advancing together, one iteration per job per
+    tick, each tick's phases one persistent launch over all jobs (continuous batching)."""
+
+    def __init__(self, graphs: bool = True):
+        h = ctypes.c_void_p()
+        _check(lib.vrps_batch_create(ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+        if not graphs:
+            _check(lib.vrps_batch_set_graphs(self.handle, 0))
+
+    def submit(self, g: Geometry, b: torch.Tensor, *, alpha: float, p: float, gamma: float, seed: int = 0,
+               job: int = 0, estimator: str = "SVRG", fgp_iters: int = 50, max_iters: int = 100,
+               n_subsets: int = 0, nonneg: bool = True, storage: str = "FP32", correction_epochs: int = 0,
+               x_out: torch.Tensor | None = None) -> int:
+        if x_out is None:
+            x_out = torch.empty(g.n, device=b.device, dtype=torch.float32)
+        d = _job_desc(g, b, x_out, alpha, p, gamma, seed, job, estimator, fgp_iters, max_iters, n_subsets, nonneg,
+                      storage, correction_epochs)
+        torch.cuda.current_stream().synchronize()   # b must be ready: the batch runs on its own stream
+        jid = ctypes.c_int()
+        _check(lib.vrps_batch_submit(self.handle, ctypes.byref(d), ctypes.byref(jid)))
+        self._keep[jid.value] = (g, b, x_out)
+        return jid.value
+
+    def step(self, ticks: int = 1) -> int:
+        act = ctypes.c_int()
+        _check(lib.vrps_batch_step(self.handle, int(ticks), ctypes.byref(act)))
+        return act.value
+
+    def poll(self, jid: int):
+        done, rep = ctypes.c_int(), Report()
+        _check(lib.vrps_batch_poll(self.handle, int(jid), ctypes.byref(done), ctypes.byref(rep)))
+        return bool(done.value), (rep.as_dict() if done.value else None)
+
+    def wait(self, jid: int) -> dict:
+        rep = Report()
+        _check(lib.vrps_batch_wait(self.handle, int(jid), ctypes.byref(rep)))
+        return rep.as_dict()
+
+    def result(self, jid: int) -> torch.Tensor:
+        return self._keep[jid][2]
+
+    def release(self, jid: int):
+        self._keep.pop(jid, None)
+
+    def sync(self):
+        _check(lib.vrps_batch_sync(self.handle))
+
+    def ticks(self):
+        t, a = ctypes.c_longlong(), ctypes.c_int()
+        _check(lib.vrps_batch_ticks(self.handle, ctypes.byref(t), ctypes.byref(a)))
+        return t.value, a.value
+
+    def close(self):
+        if self.handle:
+            _check(lib.vrps_batch_free(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def job_footprint(g: Geometry, *, max_iters: int, storage: str = "FP32") -> int:
+    """vrps_job_footprint: device bytes of one job's state (admission by HBM footprint)."""
+    d = JobDesc()
+    d.geom = g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle
+    d.max_iters = int(max_iters)
+    d.storage = {"FP32": 0, "BF16": 1}[storage.upper()]
+    out = ctypes.c_size_t()
+    _check(lib.vrps_job_footprint(g.handle, ctypes.byref(d), ctypes.byref(out)))
+    return out.value

@@ -696,6 +696,10 @@ void launch_end(cudaStream_t s) {
   t_open.name = nullptr;
 }
 
+void launch_count_add(long long n) { prof().launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+bool profiling_on() { return prof().on.load(std::memory_order_relaxed); }
+
 }  // namespace vrps
 
 extern "C" {

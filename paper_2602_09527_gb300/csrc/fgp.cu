@@ -29,7 +29,6 @@ namespace {
 // w' = P_B(z + step D x) and the next extrapolation z' = w' + mom' (w' - w), both in place
 // (each only reads its own pixel's w and z).  Reads and writes go to different buffer
 // pairs, so neighbouring CTAs never see a half-updated dual.
-constexpr int FB_T = 8;   // iterations per launch (= halo width)
 
 // Tile: TX x TY outputs per CTA of NT threads; the grown tile (EX x EY elements) is walked
 // in NS linear slots per thread (slot e = tid + k NT).  Each slot carries the depth at which
@@ -43,33 +42,6 @@ struct FgpTile {
 };
 using TileLarge = FgpTile<32, 32, 512>;
 
-struct MomBlock {
-  float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
-};
-
-// One blocked launch: nsteps (<= FB_T) iterations from (w, z) to (wn, zn).
-struct FgpBlockArgs {
-  const float* v;
-  const float* w;
-  const float* z;
-  float* wn;
-  float* zn;
-  int nx, ny;
-  float tau, step;
-  MomBlock mom;
-  int nsteps, nonneg;
-};
-
-// x+ and the fused tail over a whole image.
-struct FgpOutArgs {
-  const float* v;
-  const float* w;
-  float* wdst;   // copy of w (may be null)
-  int nx, ny;
-  float tau;
-  int nonneg;
-  ProxTail t;
-};
 
 // Projection onto the unit ball: g / max(1, |g|) through the hardware reciprocal square
 // root (relative error a few ulp, far below the float32 tolerances of the prox).
@@ -434,19 +406,44 @@ __global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, co
 
 }  // namespace
 
+std::vector<MomBlock> fgp_momentum(int iters) {
+  // t_0 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 in float64; the z formed after iteration k
+  // extrapolates with (t_k - 1) / t_{k+1}; none after the call's last iteration
+  std::vector<MomBlock> out;
+  double t_cur = 1.0;
+  for (int k0 = 0; k0 < iters; k0 += FB_T) {
+    const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
+    MomBlock mb;
+    for (int q = 0; q <= FB_T; ++q) {
+      mb.c[q] = 0.f;
+      if (q < ns) {
+        const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
+        if (k0 + q + 1 < iters) mb.c[q] = (float)((t_cur - 1.0) / t_next);
+        t_cur = t_next;
+      }
+    }
+    out.push_back(mb);
+  }
+  return out;
+}
+
+int fgp_prepare(vrps_geom* g) {
+  Workspace& ws = g->ws;
+  const size_t dn = (size_t)g->dims * (size_t)g->n;
+  VRPS_TRY(ensure(&ws.dual_s1, dn));
+  VRPS_TRY(ensure(&ws.dual_s2, dn));
+  if (g->dims == 2) {
+    VRPS_TRY(ensure(&ws.dual_s3, dn));
+    VRPS_TRY(ensure(&ws.dual_s4, dn));
+  }
+  return VRPS_OK;
+}
+
 int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
             const ProxTail& tail, cudaStream_t s) {
   vrps_geom* gm = const_cast<vrps_geom*>(g);
   Workspace& ws = gm->ws;
-  const size_t dn = (size_t)g->dims * (size_t)g->n;
-  if (iters > 0) {
-    VRPS_TRY(ensure(&ws.dual_s1, dn));
-    VRPS_TRY(ensure(&ws.dual_s2, dn));
-    if (g->dims == 2) {
-      VRPS_TRY(ensure(&ws.dual_s3, dn));
-      VRPS_TRY(ensure(&ws.dual_s4, dn));
-    }
-  }
+  if (iters > 0) VRPS_TRY(fgp_prepare(gm));
   // momentum in float64: t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2; the z formed after
   // iteration k extrapolates with (t_k - 1)/t_{k+1} (iteration 0 itself uses z = w)
   double t_cur = 1.0;
@@ -460,17 +457,10 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
     int which = 0;
     VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLarge>, TileLarge::SMEM));
+    const std::vector<MomBlock> moms = fgp_momentum(iters);
     for (int k0 = 0; k0 < iters; k0 += FB_T) {
       const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
-      MomBlock mb;
-      for (int q = 0; q <= FB_T; ++q) {
-        mb.c[q] = 0.f;
-        if (q < ns) {
-          const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
-          if (k0 + q + 1 < iters) mb.c[q] = (float)((t_cur - 1.0) / t_next);
-          t_cur = t_next;
-        }
-      }
+      const MomBlock& mb = moms[k0 / FB_T];
       float* wn = pairs[which][0];
       float* zn = pairs[which][1];
       {
@@ -531,6 +521,95 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     }
   }
   VRPS_LAUNCHED("fgp_out");
+  return VRPS_OK;
+}
+
+}  // namespace vrps
+
+// ---------------------------------------------------------------- batched 2D prox
+namespace vrps {
+namespace {
+
+__device__ __forceinline__ int fgp_batch_job(const int* pre, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Launch b of every prox call of the tick: the tiles of all jobs with more than b blocks.
+__global__ void __launch_bounds__(TileLarge::NT) fgp2d_block_batched_kernel(const char* __restrict__ slot, int b) {
+  extern __shared__ float smf[];
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
+  const int n = H.n_prox;
+  if (n <= 0) return;
+  const BatchFgp* jobs = reinterpret_cast<const BatchFgp*>(slot + H.off_fgp);
+  const int* src = reinterpret_cast<const int*>(slot + H.off_pfgp) + (size_t)b * (n + 1);
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) pre[i] = src[i];
+  __syncthreads();
+  const int total = pre[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = fgp_batch_job(pre, n, item);
+    const BatchFgp& J = jobs[j];
+    const int local = item - pre[j];
+    fgp2d_block_item<TileLarge>(J.A[b], local % J.tiles_x, local / J.tiles_x, smf);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) fgp2d_out_batched_kernel(const char* __restrict__ slot) {
+  __shared__ float tile[32][33];
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
+  const int n = H.n_prox;
+  if (n <= 0) return;
+  const BatchOut* jobs = reinterpret_cast<const BatchOut*>(slot + H.off_out);
+  const int* src = reinterpret_cast<const int*>(slot + H.off_pout);
+  for (int i = threadIdx.y * blockDim.x + threadIdx.x; i <= n; i += blockDim.x * blockDim.y) pre[i] = src[i];
+  __syncthreads();
+  const int total = pre[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = fgp_batch_job(pre, n, item);
+    const BatchOut& J = jobs[j];
+    const int local = item - pre[j];
+    fgp2d_out_item(J.A, local % J.tiles_x, local / J.tiles_x, tile);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int fgp2d_block_batched(const char* slot, int b, int grid, cudaStream_t s) {
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM));
+  LaunchScope _ls("fgp2d_block_batched", s);
+  VRPS_CUDA(launch_kernel(fgp2d_block_batched_kernel, dim3(grid), dim3(TileLarge::NT), (size_t)TileLarge::SMEM, s,
+                          slot, b));
+  return VRPS_OK;
+}
+
+int fgp2d_out_batched(const char* slot, int grid, cudaStream_t s) {
+  LaunchScope _ls("fgp2d_out_batched", s);
+  VRPS_CUDA(launch_kernel(fgp2d_out_batched_kernel, dim3(grid), dim3(32, 8), (size_t)0, s, slot));
+  return VRPS_OK;
+}
+
+int batched_grid(int which, size_t smem, int* grid) {
+  if (which <= 1) return batched_grid_2d(which, smem, grid);
+  int dev = 0, sms = 0, per = 0;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (which == 2) {
+    VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM));
+    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_block_batched_kernel, TileLarge::NT,
+                                                             TileLarge::SMEM));
+  } else {
+    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_out_batched_kernel, 256, 0));
+  }
+  *grid = (per < 1 ? 1 : per) * sms;
   return VRPS_OK;
 }
 

@@ -27,20 +27,6 @@ constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_CHUNK = 64;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // bounded mbarrier polls before giving up
 
-struct Fwd2DParams {
-  const float* x;
-  const float* xT;
-  const AngleInfo2D* ang;
-  const int* ids;
-  int nx, ny, nb;
-  float jc;
-  int band;                   // lines per band
-  int bands;                  // gridDim.x
-  float* part;                // [rows][bands][nb] partial sums
-  unsigned* count;            // [rows] arrival counters, zero between launches
-  unsigned* err;              // device error word
-  FwdOut o;
-};
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -260,15 +246,6 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
   fwd2d_item<MODE, BULK>(P, blockIdx.x, blockIdx.y, band, S, 0u);
 }
 
-struct Adj2DParams {
-  const float* r;
-  const AngleInfo2D* ang;
-  const int* ids;
-  int rows;
-  int nx, ny, nb;
-  int fp, nc, chunk;
-  UpdateArgs u;
-};
 
 // Algorithm 1, estimator and x_hat lines for one pixel: G = cN g + gbar,
 // x_hat = base - gamma (G - h); theta = 0: x <- x_hat (returned for the transposed copy);
@@ -453,10 +430,9 @@ int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s, int
   return VRPS_OK;
 }
 
-int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
-          FwdOut o, cudaStream_t s) {
-  if (rows <= 0) return VRPS_OK;
-  Fwd2DParams P;
+int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, FwdOut o,
+                Fwd2DParams* out, size_t* smem, bool* bulk) {
+  Fwd2DParams& P = *out;
   P.x = x;
   P.xT = xT;
   P.ang = g->ang2d;
@@ -493,8 +469,19 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.count = ws.fwd_count;
   P.err = ws.dev_error;
   // the bulk copy needs 16-byte aligned rows: line lengths that are multiples of 4 floats
-  const bool bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
-  const size_t smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD);
+  *bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
+  *smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD);
+  (void)rows;
+  return VRPS_OK;
+}
+
+int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
+          FwdOut o, cudaStream_t s) {
+  if (rows <= 0) return VRPS_OK;
+  Fwd2DParams P;
+  size_t smem = 0;
+  bool bulk = false;
+  VRPS_TRY(fwd2d_setup(g, x, xT, ids, rows, o, &P, &smem, &bulk));
   dim3 grid(P.bands, rows), block(FWD_THREADS);
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
@@ -514,9 +501,9 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   return VRPS_OK;
 }
 
-int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
-          cudaStream_t s) {
-  Adj2DParams P;
+int adj2d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+                Adj2DParams* out, size_t* smem, int* variant, int* tiles_x, int* tiles_y) {
+  Adj2DParams& P = *out;
   P.r = r;
   P.ang = g->ang2d;
   P.ids = ids;
@@ -529,23 +516,148 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   int chunk = (int)(96 * 1024 / (sizeof(float) * (size_t)g->adj_fp));
   P.chunk = chunk < ADJ_CHUNK ? (chunk < 1 ? 1 : chunk) : ADJ_CHUNK;
   P.u = u;
-  const size_t smem = sizeof(float) * (size_t)P.chunk * P.fp;
+  *smem = sizeof(float) * (size_t)P.chunk * P.fp;
   // two pixels per thread (shared per-angle parameters) unless the image is very small
   const bool two = (long long)g->nx * g->ny > 512LL * g->sms;
   const int ty = (ADJ_THREADS / ADJ_TX) * (two ? 2 : 1);
-  dim3 grid((g->nx + ADJ_TX - 1) / ADJ_TX, (g->ny + ty - 1) / ty), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
+  *variant = (g->adj_nc == 2 ? 2 : 0) + (two ? 1 : 0);
+  *tiles_x = (g->nx + ADJ_TX - 1) / ADJ_TX;
+  *tiles_y = (g->ny + ty - 1) / ty;
+  return VRPS_OK;
+}
+
+int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+          cudaStream_t s) {
+  Adj2DParams P;
+  size_t smem = 0;
+  int variant = 0, tx = 0, ty = 0;
+  VRPS_TRY(adj2d_setup(g, r, ids, rows, u, &P, &smem, &variant, &tx, &ty));
+  dim3 grid(tx, ty), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("adj2d_kernel", s, 4.0 * rows * g->n_bins + update_bytes(u, (size_t)g->n));
     VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };
-  if (g->adj_nc == 2) {
-    VRPS_TRY(two ? launch(adj2d_kernel<2, 2>) : launch(adj2d_kernel<2, 1>));
-  } else {
-    VRPS_TRY(two ? launch(adj2d_kernel<0, 2>) : launch(adj2d_kernel<0, 1>));
+  switch (variant) {
+    case 3: VRPS_TRY(launch(adj2d_kernel<2, 2>)); break;
+    case 2: VRPS_TRY(launch(adj2d_kernel<2, 1>)); break;
+    case 1: VRPS_TRY(launch(adj2d_kernel<0, 2>)); break;
+    default: VRPS_TRY(launch(adj2d_kernel<0, 1>)); break;
   }
   VRPS_LAUNCHED("adj2d");
+  return VRPS_OK;
+}
+
+// ------------------------------------------------------------------ batched launches
+namespace {
+
+// Job j of item `item` from the prefix array cached in shared memory (pre[j] <= item < pre[j+1]).
+__device__ __forceinline__ int batch_job(const int* pre, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void batch_load_prefix(int* dst, const int* src, int n) {
+  for (int i = threadIdx.y * blockDim.x + threadIdx.x; i <= n; i += blockDim.x * blockDim.y) dst[i] = src[i];
+  __syncthreads();
+}
+
+template <bool BULK>
+__device__ __forceinline__ int fwd2d_item_mode(const BatchFwd& J, int c, int row, float* band, FwdShared& S,
+                                               unsigned parity) {
+  switch (J.mode) {
+    case FWD_PLAIN: return fwd2d_item<FWD_PLAIN, BULK>(J.P, c, row, band, S, parity);
+    case FWD_RESID: return fwd2d_item<FWD_RESID, BULK>(J.P, c, row, band, S, parity);
+    case FWD_SVRG: return fwd2d_item<FWD_SVRG, BULK>(J.P, c, row, band, S, parity);
+    case FWD_SAGA: return fwd2d_item<FWD_SAGA, BULK>(J.P, c, row, band, S, parity);
+    default: return fwd2d_item<FWD_SNAP, BULK>(J.P, c, row, band, S, parity);
+  }
+}
+
+__global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(const char* __restrict__ slot) {
+  extern __shared__ __align__(128) float band[];
+  __shared__ FwdShared S;
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
+  const int n = H.n_fwd;
+  if (n <= 0) return;
+  const BatchFwd* jobs = reinterpret_cast<const BatchFwd*>(slot + H.off_fwd);
+  batch_load_prefix(pre, reinterpret_cast<const int*>(slot + H.off_pfwd), n);
+  fwd2d_init_barrier(S);
+  unsigned parity = 0;
+  const int total = pre[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = batch_job(pre, n, item);
+    const BatchFwd& J = jobs[j];
+    const int local = item - pre[j];
+    const int bands = J.P.bands;
+    const int c = local % bands, row = local / bands;
+    const int used = J.bulk ? fwd2d_item_mode<true>(J, c, row, band, S, parity)
+                            : fwd2d_item_mode<false>(J, c, row, band, S, parity);
+    parity ^= (unsigned)used;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(ADJ_THREADS) adj2d_batched_kernel(const char* __restrict__ slot) {
+  extern __shared__ float sm[];
+  __shared__ AdjShared S;
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
+  const int n = H.n_adj;
+  if (n <= 0) return;
+  const BatchAdj* jobs = reinterpret_cast<const BatchAdj*>(slot + H.off_adj);
+  batch_load_prefix(pre, reinterpret_cast<const int*>(slot + H.off_padj), n);
+  const int total = pre[n];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int j = batch_job(pre, n, item);
+    const BatchAdj& J = jobs[j];
+    const int local = item - pre[j];
+    const int bx = local % J.tiles_x, by = local / J.tiles_x;
+    switch (J.variant) {
+      case 3: adj2d_item<2, 2>(J.P, bx, by, sm, S); break;
+      case 2: adj2d_item<2, 1>(J.P, bx, by, sm, S); break;
+      case 1: adj2d_item<0, 2>(J.P, bx, by, sm, S); break;
+      default: adj2d_item<0, 1>(J.P, bx, by, sm, S); break;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int fwd2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s) {
+  VRPS_TRY(smem_opt_in((const void*)fwd2d_batched_kernel, smem));
+  LaunchScope _ls("fwd2d_batched", s);
+  VRPS_CUDA(launch_kernel(fwd2d_batched_kernel, dim3(grid), dim3(FWD_THREADS), smem, s, slot));
+  return VRPS_OK;
+}
+
+int adj2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s) {
+  VRPS_TRY(smem_opt_in((const void*)adj2d_batched_kernel, smem));
+  LaunchScope _ls("adj2d_batched", s);
+  VRPS_CUDA(launch_kernel(adj2d_batched_kernel, dim3(grid), dim3(ADJ_TX, ADJ_THREADS / ADJ_TX), smem, s, slot));
+  return VRPS_OK;
+}
+
+int batched_grid_2d(int which, size_t smem, int* grid) {
+  int dev = 0, sms = 0, per = 0;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (which == 0) {
+    VRPS_TRY(smem_opt_in((const void*)fwd2d_batched_kernel, smem));
+    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fwd2d_batched_kernel, FWD_THREADS, smem));
+  } else {
+    VRPS_TRY(smem_opt_in((const void*)adj2d_batched_kernel, smem));
+    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj2d_batched_kernel, ADJ_THREADS, smem));
+  }
+  *grid = (per < 1 ? 1 : per) * sms;
   return VRPS_OK;
 }
 

@@ -30,7 +30,16 @@ struct State {
   float *x, *xf, *xfT, *h, *xhat, *v, *gbar, *xprox, *dual, *b_perm, *tab, *res;
 };
 
-int alloc_solver(vrps_geom* g, bool fista, bool bf16) {
+double step_factor(int algo, int est) {
+  if (algo == VRPS_ALGO_ISTA || algo == VRPS_ALGO_PROXSKIP) return 1.99;
+  if (algo == VRPS_ALGO_SAGA) return 1.0 / 3.0;
+  if (algo == VRPS_ALGO_VR_PROXSKIP && est == VRPS_EST_SAGA) return 1.0 / 3.0;
+  return 1.0;
+}
+
+}  // namespace
+
+int solver_alloc(vrps_geom* g, bool fista, bool bf16) {
   Workspace& w = g->ws;
   const size_t n = (size_t)g->n, m = (size_t)g->m;
   VRPS_TRY(ensure(&w.x, n));
@@ -53,14 +62,6 @@ int alloc_solver(vrps_geom* g, bool fista, bool bf16) {
   return VRPS_OK;
 }
 
-double step_factor(int algo, int est) {
-  if (algo == VRPS_ALGO_ISTA || algo == VRPS_ALGO_PROXSKIP) return 1.99;
-  if (algo == VRPS_ALGO_SAGA) return 1.0 / 3.0;
-  if (algo == VRPS_ALGO_VR_PROXSKIP && est == VRPS_EST_SAGA) return 1.0 / 3.0;
-  return 1.0;
-}
-
-}  // namespace
 }  // namespace vrps
 
 using namespace vrps;
@@ -117,7 +118,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   cudaStream_t s = (cudaStream_t)stream;
   Workspace& w = g->ws;
   const bool bf_run = o.storage == VRPS_STORAGE_BF16;
-  VRPS_TRY(alloc_solver(g, fista, bf_run));
+  VRPS_TRY(solver_alloc(g, fista, bf_run));
   const int64_t n = g->n, m = g->m;
   const int L = g->row_len;
 

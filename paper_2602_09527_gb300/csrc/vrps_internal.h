@@ -245,8 +245,39 @@ struct UpdateArgs {
   int prescaled;          // 3D: r already carries the ray length factors (see FwdOut::prescale)
   int snap;               // SVRG snapshot: g is the full gradient; gbar <- g and G = g
 };
+// ---- 2D projector launch parameters (joseph2d.cu)
+struct Fwd2DParams {
+  const float* x;
+  const float* xT;
+  const AngleInfo2D* ang;
+  const int* ids;
+  int nx, ny, nb;
+  float jc;
+  int band;                   // lines per band
+  int bands;                  // gridDim.x
+  float* part;                // [rows][bands][nb] partial sums
+  unsigned* count;            // [rows] arrival counters, zero between launches
+  unsigned* err;              // device error word
+  FwdOut o;
+};
+
+struct Adj2DParams {
+  const float* r;
+  const AngleInfo2D* ang;
+  const int* ids;
+  int rows;
+  int nx, ny, nb;
+  int fp, nc, chunk;
+  UpdateArgs u;
+};
+
 int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
           cudaStream_t s);
+// Launch constants of one forward / adjoint (allocating the geometry's scratch on first use).
+int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, FwdOut o,
+                Fwd2DParams* P, size_t* smem, bool* bulk);
+int adj2d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+                Adj2DParams* P, size_t* smem, int* variant, int* tiles_x, int* tiles_y);
 
 // Algorithmic bytes of the image-side epilogue of an adjoint launch over n pixels.
 inline double update_bytes(const UpdateArgs& u, size_t n) {
@@ -292,8 +323,83 @@ struct ProxTail {
   float* yT;
   float mom;
 };
+// ---- 2D FGP launch arguments (fgp.cu)
+constexpr int FB_T = 8;   // iterations per launch (= halo width)
+
+struct MomBlock {
+  float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
+};
+
+// One blocked launch: nsteps (<= FB_T) iterations from (w, z) to (wn, zn).
+struct FgpBlockArgs {
+  const float* v;
+  const float* w;
+  const float* z;
+  float* wn;
+  float* zn;
+  int nx, ny;
+  float tau, step;
+  MomBlock mom;
+  int nsteps, nonneg;
+};
+
+// x+ and the fused tail over a whole image.
+struct FgpOutArgs {
+  const float* v;
+  const float* w;
+  float* wdst;   // copy of w (may be null)
+  int nx, ny;
+  float tau;
+  int nonneg;
+  ProxTail t;
+};
+
 int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
             const ProxTail& tail, cudaStream_t s);
+// Momentum coefficients of the blocked 2D FGP launches of one prox call (t restarts at 1).
+std::vector<MomBlock> fgp_momentum(int iters);
+// Allocates the dual rotation buffers of the geometry's prox.
+int fgp_prepare(vrps_geom* g);
+
+// ---- batched persistent launches (a CTA walks items blockIdx.x, blockIdx.x + gridDim.x, ...
+// over the items of many problems; the same item functions as the single-problem kernels)
+constexpr int BATCH_MAX_JOBS = 256;
+constexpr int BATCH_MAX_BLOCKS = 16;   // FGP blocks per prox call: at most 128 inner iterations
+constexpr int FGP_TILE = 32;           // 2D FGP output tile (TileLarge)
+struct BatchFwd {
+  Fwd2DParams P;
+  int mode;   // FwdMode
+  int bulk;   // band staged by bulk copies
+};
+struct BatchAdj {
+  Adj2DParams P;
+  int variant;   // 2 (nc == 2) + 1 (two pixels per thread)
+  int tiles_x;
+};
+struct BatchFgp {
+  FgpBlockArgs A[BATCH_MAX_BLOCKS];   // launch b of the call
+  int nblocks;
+  int tiles_x;
+};
+struct BatchOut {
+  FgpOutArgs A;
+  int tiles_x;
+};
+// One tick's work list, packed in one buffer: the header, then the arrays at its offsets.
+// Prefix arrays hold each job's first item (n + 1 entries); the FGP prefix is
+// [BATCH_MAX_BLOCKS][n_prox + 1].
+struct TickHeader {
+  int n_fwd, n_adj, n_prox, pad;
+  unsigned off_fwd, off_pfwd, off_adj, off_padj, off_fgp, off_pfgp, off_out, off_pout;
+};
+int fwd2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s);
+int adj2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s);
+int fgp2d_block_batched(const char* slot, int b, int grid, cudaStream_t s);
+int fgp2d_out_batched(const char* slot, int grid, cudaStream_t s);
+// Persistent grid (CTAs resident on all SMs) of batched kernel `which` (0 fwd, 1 adj, 2 FGP
+// block, 3 FGP out) at `smem` bytes of dynamic shared memory.
+int batched_grid(int which, size_t smem, int* grid);
+int batched_grid_2d(int which, size_t smem, int* grid);
 
 // Algorithmic bytes of the prox output launch's tail over n pixels (beyond reading v, w).
 inline double tail_bytes(const ProxTail& t, size_t n) {
@@ -319,6 +425,12 @@ int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row
 int fill(float* p, float v, int64_t n, cudaStream_t s);
 int copy_or_zero(float* dst, const float* src, int64_t n, cudaStream_t s);
 int to_bf16(const float* src, void* dst, int64_t n, cudaStream_t s);
+// Solver state in the geometry's workspace (solver.cu).
+int solver_alloc(vrps_geom* g, bool fista, bool bf16);
+// Adds to the library's launch counter (kernels launched through a CUDA graph).
+void launch_count_add(long long n);
+// Whether per-launch event profiling is on (graphs are bypassed then).
+bool profiling_on();
 
 // projector dispatch (2D or 3D) used by the solver and the API
 int proj_forward(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows,

@@ -1,0 +1,161 @@
+"""Batched / served jobs (vrps_batch_*): every job's result is bit-identical to vrps_solve with
+the same arguments, alone and in any mix, with jobs admitted between ticks, with and
+without CUDA-graph replay; one batched job also against the float64 oracle (1e-4)."""
+import math
+
+import numpy as np
+import pytest
+
+from tests._gpu import dev, host, need_gpu, rel, torch
+
+import synthetic
+from oracle import joseph2d, solvers
+
+pytestmark = pytest.mark.gpu
+
+
+def _vr():
+    need_gpu()
+    import paper_2602_09527_gb300 as vr
+    return vr
+
+
+# (side_x, side_y, angles, bins, N, estimator, p, fgp_iters, iters, storage, correction epochs)
+MIX = [
+    (64, 64, 90, 96, 10, "SVRG", 0.1, 50, 60, "FP32", 0),
+    (48, 80, 72, 120, 8, "SAGA", 0.3, 20, 50, "FP32", 0),
+    (96, 96, 144, 144, 12, "SAGA", 0.2, 16, 70, "BF16", 2),
+    (30, 30, 45, 45, 5, "LSVRG", 0.5, 12, 40, "FP32", 0),     # sides not multiples of 4
+    (128, 128, 192, 192, 16, "SVRG", 0.1, 100, 48, "BF16", 1),
+    (40, 56, 60, 84, 6, "SGD", 0.25, 0, 30, "FP32", 0),       # no inner FGP iteration
+]
+
+
+def _problem(vr, i, spec):
+    sx, sy, na, nb, N = spec[:5]
+    rng = np.random.default_rng(100 + i)
+    ells = synthetic.random_ellipses(6, min(sx, sy) / 2.0, rng)
+    ps = synthetic.Par2DSpec(nx=sx, ny=sy, pixel=1.0, angles=synthetic.uniform_angles(na, math.pi), n_bins=nb,
+                             bin_spacing=1.0, n_subsets=N)
+    b = synthetic.gaussian_noise(synthetic.ellipse_sinogram(ells, ps.angles, ps.bin_centers()), 0.01, rng)
+    g = vr.Geometry.from_spec(ps)
+    L = vr.power_iteration(g, 60, seed=7)
+    return ps, g, b, L
+
+
+def _kw(spec, L, i):
+    est, p, fgp, K, storage, corr = spec[5:]
+    fac = 1 / 3 if est == "SAGA" else 1.0
+    return dict(alpha=0.02, p=p, gamma=fac / L, seed=900 + i, job=i, estimator=est, fgp_iters=fgp,
+                max_iters=K, storage=storage, correction_epochs=corr)
+
+
+def _solo(vr, g, b, kw):
+    kw = dict(kw)
+    x, rep, _ = vr.solve(dev(b), g, kw.pop("alpha"), "VR_PROXSKIP", p=kw.pop("p"), gamma=kw.pop("gamma"),
+                         seed=kw.pop("seed"), **kw)
+    torch.cuda.synchronize()
+    return x.clone(), rep
+
+
+@pytest.fixture(scope="module")
+def mix():
+    vr = _vr()
+    probs = [_problem(vr, i, s) for i, s in enumerate(MIX)]
+    solo = []
+    for i, (ps, g, b, L) in enumerate(probs):
+        solo.append(_solo(vr, g, b, _kw(MIX[i], L, i)))
+    return vr, probs, solo
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_mix_bit_identical_to_solo(mix, graphs):
+    vr, probs, solo = mix
+    B = vr.Batch(graphs=graphs)
+    ids = []
+    for i, (ps, g, b, L) in enumerate(probs):
+        ids.append(B.submit(g, dev(b), **_kw(MIX[i], L, i)))
+    while B.step(4):
+        pass
+    for i, jid in enumerate(ids):
+        rep = B.wait(jid)
+        x = B.result(jid)
+        assert torch.equal(x, solo[i][0]), (i, rel(host(x), host(solo[i][0])))
+        assert rep["iterations"] == solo[i][1]["iterations"]
+        assert rep["prox_calls"] == solo[i][1]["prox_calls"]
+        assert rep["snapshots"] == solo[i][1]["snapshots"]
+        assert abs(rep["passes"] - solo[i][1]["passes"]) < 1e-9
+    B.close()
+
+
+def test_staggered_admission_and_alone(mix):
+    """Jobs joining while others run, and a job running alone, give the same bits."""
+    vr, probs, solo = mix
+    B = vr.Batch()
+    first = [B.submit(probs[i][1], dev(probs[i][2]), **_kw(MIX[i], probs[i][3], i)) for i in (0, 3)]
+    B.step(7)
+    later = [B.submit(probs[i][1], dev(probs[i][2]), **_kw(MIX[i], probs[i][3], i)) for i in (1, 4)]
+    B.step(3)
+    last = [B.submit(probs[i][1], dev(probs[i][2]), **_kw(MIX[i], probs[i][3], i)) for i in (2, 5)]
+    order = {first[0]: 0, first[1]: 3, later[0]: 1, later[1]: 4, last[0]: 2, last[1]: 5}
+    for jid, i in order.items():
+        B.wait(jid)
+        assert torch.equal(B.result(jid), solo[i][0]), i
+    B.close()
+    A = vr.Batch()
+    jid = A.submit(probs[2][1], dev(probs[2][2]), **_kw(MIX[2], probs[2][3], 2))
+    A.wait(jid)
+    assert torch.equal(A.result(jid), solo[2][0])
+    A.close()
+
+
+def test_batched_job_matches_oracle():
+    vr = _vr()
+    P = synthetic.make_problem_2d(32, 40, 48, 5, seed=21, noise="gauss", alpha=0.02)
+    g = vr.Geometry.from_spec(P.spec)
+    op = solvers.Operator(joseph2d.Geometry2D.from_spec(P.spec))
+    L = solvers.power_iteration(op, 200, seed=3)
+    B = vr.Batch()
+    jid = B.submit(g, dev(P.b), alpha=P.alpha, p=0.3, gamma=1 / (3 * L), seed=77, estimator="SAGA", fgp_iters=20,
+                   max_iters=30)
+    B.wait(jid)
+    ref = solvers.run(op, P.b, P.alpha, "VR_PROXSKIP", 1 / (3 * L), 30, 20, p=0.3, seed=77, estimator="SAGA")
+    assert rel(host(B.result(jid)), ref.x) < 1e-4
+    B.close()
+
+
+def test_busy_geometry_and_bad_jobs_rejected(mix):
+    vr, probs, _ = mix
+    ps, g, b, L = probs[0]
+    B = vr.Batch()
+    B.submit(g, dev(b), **_kw(MIX[0], L, 0))
+    with pytest.raises(vr.VrpsError):
+        B.submit(g, dev(b), **_kw(MIX[0], L, 0))          # geometry in use
+    g2 = vr.Geometry.from_spec(ps)
+    bad = _kw(MIX[0], L, 0)
+    bad["gamma"] = 0.0
+    with pytest.raises(vr.VrpsError):
+        B.submit(g2, dev(b), **bad)
+    bad = _kw(MIX[0], L, 0)
+    bad["fgp_iters"] = 200
+    with pytest.raises(vr.VrpsError):
+        B.submit(g2, dev(b), **bad)
+    B.close()
+    assert vr.job_footprint(g2, max_iters=100) > 4 * g2.n * 10
+    g2.close()
+
+
+def test_launch_count_per_tick(mix):
+    """A tick is 3 + (FGP blocks) launches however many jobs run."""
+    vr, probs, _ = mix
+    B = vr.Batch()
+    for i in (0, 1, 3):
+        B.submit(probs[i][1], dev(probs[i][2]), **_kw(MIX[i], probs[i][3], i))
+    B.step(1)
+    B.sync()
+    n0 = vr.kernel_launches()
+    B.step(5)
+    B.sync()
+    per_tick = (vr.kernel_launches() - n0) / 5
+    assert per_tick == 3 + math.ceil(50 / 8)
+    B.close()
