@@ -87,7 +87,7 @@ int batch_grids(vrps_batch* B) {
 }
 
 // The tick's kernels on stream s, reading the work list at slot.
-int launch_tick(vrps_batch* B, const char* slot, cudaStream_t s) {
+int launch_tick(vrps_batch* B, char* slot, cudaStream_t s) {
   VRPS_TRY(fwd2d_batched(slot, B->grid_fwd, B->fwd_smem, s));
   VRPS_TRY(adj2d_batched(slot, B->grid_adj, B->adj_smem, s));
   for (int b = 0; b < B->max_blocks; ++b) VRPS_TRY(fgp2d_block_batched(slot, b, B->grid_fgp, s));

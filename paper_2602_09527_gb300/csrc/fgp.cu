@@ -541,49 +541,58 @@ __device__ __forceinline__ int fgp_batch_job(const int* pre, int n, int item) {
 }
 
 // Launch b of every prox call of the tick: the tiles of all jobs with more than b blocks.
-__global__ void __launch_bounds__(TileLarge::NT) fgp2d_block_batched_kernel(const char* __restrict__ slot, int b) {
+__device__ __forceinline__ int fgp_batch_next(unsigned* counter, int* s_item) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) *s_item = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  return *s_item;
+}
+
+__global__ void __launch_bounds__(TileLarge::NT) fgp2d_block_batched_kernel(char* __restrict__ slot, int b) {
   extern __shared__ float smf[];
   __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
   const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
   const int n = H.n_prox;
   if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader*>(slot)->cnt + 3 + b;
   const BatchFgp* jobs = reinterpret_cast<const BatchFgp*>(slot + H.off_fgp);
   const int* src = reinterpret_cast<const int*>(slot + H.off_pfgp) + (size_t)b * (n + 1);
   for (int i = threadIdx.x; i <= n; i += blockDim.x) pre[i] = src[i];
   __syncthreads();
   const int total = pre[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  for (int item = fgp_batch_next(counter, &s_item); item < total; item = fgp_batch_next(counter, &s_item)) {
     const int j = fgp_batch_job(pre, n, item);
     const BatchFgp& J = jobs[j];
     const int local = item - pre[j];
     fgp2d_block_item<TileLarge>(J.A[b], local % J.tiles_x, local / J.tiles_x, smf);
-    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(256) fgp2d_out_batched_kernel(const char* __restrict__ slot) {
+__global__ void __launch_bounds__(256) fgp2d_out_batched_kernel(char* __restrict__ slot) {
   __shared__ float tile[32][33];
   __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
   const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
   const int n = H.n_prox;
   if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader*>(slot)->cnt + 2;
   const BatchOut* jobs = reinterpret_cast<const BatchOut*>(slot + H.off_out);
   const int* src = reinterpret_cast<const int*>(slot + H.off_pout);
   for (int i = threadIdx.y * blockDim.x + threadIdx.x; i <= n; i += blockDim.x * blockDim.y) pre[i] = src[i];
   __syncthreads();
   const int total = pre[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  for (int item = fgp_batch_next(counter, &s_item); item < total; item = fgp_batch_next(counter, &s_item)) {
     const int j = fgp_batch_job(pre, n, item);
     const BatchOut& J = jobs[j];
     const int local = item - pre[j];
     fgp2d_out_item(J.A, local % J.tiles_x, local / J.tiles_x, tile);
-    __syncthreads();
   }
 }
 
 }  // namespace
 
-int fgp2d_block_batched(const char* slot, int b, int grid, cudaStream_t s) {
+int fgp2d_block_batched(char* slot, int b, int grid, cudaStream_t s) {
   VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM));
   LaunchScope _ls("fgp2d_block_batched", s);
   VRPS_CUDA(launch_kernel(fgp2d_block_batched_kernel, dim3(grid), dim3(TileLarge::NT), (size_t)TileLarge::SMEM, s,
@@ -591,7 +600,7 @@ int fgp2d_block_batched(const char* slot, int b, int grid, cudaStream_t s) {
   return VRPS_OK;
 }
 
-int fgp2d_out_batched(const char* slot, int grid, cudaStream_t s) {
+int fgp2d_out_batched(char* slot, int grid, cudaStream_t s) {
   LaunchScope _ls("fgp2d_out_batched", s);
   VRPS_CUDA(launch_kernel(fgp2d_out_batched_kernel, dim3(grid), dim3(32, 8), (size_t)0, s, slot));
   return VRPS_OK;

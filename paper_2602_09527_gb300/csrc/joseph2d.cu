@@ -68,6 +68,26 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // runs the epilogue.
 constexpr int FWD_PAD = 4;   // zero floats left and right of each staged line (16 bytes)
 
+// Estimator epilogue of one ray with value r = (A_i x)_ray (FwdMode).
+template <int MODE>
+__device__ __forceinline__ void fwd2d_epilogue(const FwdOut& o, size_t idx, float r) {
+  const int bf = o.bf16;
+  if (MODE == FWD_PLAIN) {
+    o.y[idx] = r;
+  } else if (MODE == FWD_RESID) {
+    o.y[idx] = r - ld_store(o.b, idx, bf);
+  } else if (MODE == FWD_SVRG) {
+    o.y[idx] = r - ld_store(o.tab, idx, bf);
+  } else if (MODE == FWD_SAGA) {
+    const float res = r - ld_store(o.b, idx, bf);
+    o.y[idx] = res - ld_store(o.tab, idx, bf);
+    st_store(o.tab, idx, res, bf);
+  } else {  // FWD_SNAP
+    st_store(o.tab, idx, r, bf);
+    o.y[idx] = r - ld_store(o.b, idx, bf);
+  }
+}
+
 struct FwdShared {
   unsigned long long bar;   // mbarrier of the band copies (initialised once per CTA)
   unsigned last;            // this CTA completed the angle row
@@ -205,26 +225,33 @@ __device__ __forceinline__ int fwd2d_item(const Fwd2DParams& P, int c, int row, 
   __syncthreads();
   if (!S.last) return used;
   __threadfence();
-  const size_t rbase = (size_t)row * P.bands * P.nb;
-  for (int j = tid; j < P.nb; j += FWD_THREADS) {
-    float s = 0.f;
-    for (int q = 0; q < P.bands; ++q) s += __ldcg(P.part + rbase + (size_t)q * P.nb + j);
-    const float r = s * in.wgt;
-    const size_t idx = (size_t)row * P.nb + j;
-    const int bf = P.o.bf16;
-    if (MODE == FWD_PLAIN) {
-      P.o.y[idx] = r;
-    } else if (MODE == FWD_RESID) {
-      P.o.y[idx] = r - ld_store(P.o.b, idx, bf);
-    } else if (MODE == FWD_SVRG) {
-      P.o.y[idx] = r - ld_store(P.o.tab, idx, bf);
-    } else if (MODE == FWD_SAGA) {
-      const float res = r - ld_store(P.o.b, idx, bf);
-      P.o.y[idx] = res - ld_store(P.o.tab, idx, bf);
-      st_store(P.o.tab, idx, res, bf);
-    } else {  // FWD_SNAP
-      st_store(P.o.tab, idx, r, bf);
-      P.o.y[idx] = r - ld_store(P.o.b, idx, bf);
+  const int bands = P.bands, nb = P.nb;
+  const float* __restrict__ part = P.part + (size_t)row * bands * nb;
+  const size_t obase = (size_t)row * nb;
+  if ((nb & 3) == 0) {
+    // four rays per thread with 16-byte loads; each ray still adds its bands in order
+    const int nb4 = nb >> 2;
+    const float4* __restrict__ p4 = reinterpret_cast<const float4*>(part);
+    for (int j4 = tid; j4 < nb4; j4 += FWD_THREADS) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+      for (int q = 0; q < bands; ++q) {
+        const float4 v = __ldcg(p4 + (size_t)q * nb4 + j4);
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+      }
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 0, s.x * in.wgt);
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 1, s.y * in.wgt);
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 2, s.z * in.wgt);
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 3, s.w * in.wgt);
+    }
+  } else {
+    for (int j = tid; j < nb; j += FWD_THREADS) {
+      float s = 0.f;
+      for (int q = 0; q < bands; ++q) s += __ldcg(part + (size_t)q * nb + j);
+      fwd2d_epilogue<MODE>(P.o, obase + j, s * in.wgt);
     }
   }
   return used;
@@ -580,19 +607,30 @@ __device__ __forceinline__ int fwd2d_item_mode(const BatchFwd& J, int c, int row
   }
 }
 
-__global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(const char* __restrict__ slot) {
+// Next item of the launch for the whole CTA: one atomic on the tick's counter (items are
+// handed out in order, so the CTAs in flight work on neighbouring tiles of one job).
+__device__ __forceinline__ int batch_next(unsigned* counter, int* s_item) {
+  __syncthreads();   // everyone has read the previous item
+  if (threadIdx.x == 0 && threadIdx.y == 0) *s_item = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  return *s_item;
+}
+
+__global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(char* __restrict__ slot) {
   extern __shared__ __align__(128) float band[];
   __shared__ FwdShared S;
   __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
   const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
   const int n = H.n_fwd;
   if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader*>(slot)->cnt + 0;
   const BatchFwd* jobs = reinterpret_cast<const BatchFwd*>(slot + H.off_fwd);
   batch_load_prefix(pre, reinterpret_cast<const int*>(slot + H.off_pfwd), n);
   fwd2d_init_barrier(S);
   unsigned parity = 0;
   const int total = pre[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  for (int item = batch_next(counter, &s_item); item < total; item = batch_next(counter, &s_item)) {
     const int j = batch_job(pre, n, item);
     const BatchFwd& J = jobs[j];
     const int local = item - pre[j];
@@ -601,21 +639,22 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(const char* 
     const int used = J.bulk ? fwd2d_item_mode<true>(J, c, row, band, S, parity)
                             : fwd2d_item_mode<false>(J, c, row, band, S, parity);
     parity ^= (unsigned)used;
-    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(ADJ_THREADS) adj2d_batched_kernel(const char* __restrict__ slot) {
+__global__ void __launch_bounds__(ADJ_THREADS) adj2d_batched_kernel(char* __restrict__ slot) {
   extern __shared__ float sm[];
   __shared__ AdjShared S;
   __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
   const TickHeader& H = *reinterpret_cast<const TickHeader*>(slot);
   const int n = H.n_adj;
   if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader*>(slot)->cnt + 1;
   const BatchAdj* jobs = reinterpret_cast<const BatchAdj*>(slot + H.off_adj);
   batch_load_prefix(pre, reinterpret_cast<const int*>(slot + H.off_padj), n);
   const int total = pre[n];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  for (int item = batch_next(counter, &s_item); item < total; item = batch_next(counter, &s_item)) {
     const int j = batch_job(pre, n, item);
     const BatchAdj& J = jobs[j];
     const int local = item - pre[j];
@@ -626,20 +665,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_batched_kernel(const char* 
       case 1: adj2d_item<0, 2>(J.P, bx, by, sm, S); break;
       default: adj2d_item<0, 1>(J.P, bx, by, sm, S); break;
     }
-    __syncthreads();
   }
 }
 
 }  // namespace
 
-int fwd2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s) {
+int fwd2d_batched(char* slot, int grid, size_t smem, cudaStream_t s) {
   VRPS_TRY(smem_opt_in((const void*)fwd2d_batched_kernel, smem));
   LaunchScope _ls("fwd2d_batched", s);
   VRPS_CUDA(launch_kernel(fwd2d_batched_kernel, dim3(grid), dim3(FWD_THREADS), smem, s, slot));
   return VRPS_OK;
 }
 
-int adj2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s) {
+int adj2d_batched(char* slot, int grid, size_t smem, cudaStream_t s) {
   VRPS_TRY(smem_opt_in((const void*)adj2d_batched_kernel, smem));
   LaunchScope _ls("adj2d_batched", s);
   VRPS_CUDA(launch_kernel(adj2d_batched_kernel, dim3(grid), dim3(ADJ_TX, ADJ_THREADS / ADJ_TX), smem, s, slot));

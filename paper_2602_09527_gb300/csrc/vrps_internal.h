@@ -388,14 +388,17 @@ struct BatchOut {
 // One tick's work list, packed in one buffer: the header, then the arrays at its offsets.
 // Prefix arrays hold each job's first item (n + 1 entries); the FGP prefix is
 // [BATCH_MAX_BLOCKS][n_prox + 1].
+// cnt: item counters the launches hand out work from (0 forward, 1 adjoint, 2 prox output,
+// 3 + b FGP block b); uploaded as zeros with the tick.
 struct TickHeader {
   int n_fwd, n_adj, n_prox, pad;
   unsigned off_fwd, off_pfwd, off_adj, off_padj, off_fgp, off_pfgp, off_out, off_pout;
+  unsigned cnt[3 + BATCH_MAX_BLOCKS];
 };
-int fwd2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s);
-int adj2d_batched(const char* slot, int grid, size_t smem, cudaStream_t s);
-int fgp2d_block_batched(const char* slot, int b, int grid, cudaStream_t s);
-int fgp2d_out_batched(const char* slot, int grid, cudaStream_t s);
+int fwd2d_batched(char* slot, int grid, size_t smem, cudaStream_t s);
+int adj2d_batched(char* slot, int grid, size_t smem, cudaStream_t s);
+int fgp2d_block_batched(char* slot, int b, int grid, cudaStream_t s);
+int fgp2d_out_batched(char* slot, int grid, cudaStream_t s);
 // Persistent grid (CTAs resident on all SMs) of batched kernel `which` (0 fwd, 1 adj, 2 FGP
 // block, 3 FGP out) at `smem` bytes of dynamic shared memory.
 int batched_grid(int which, size_t smem, int* grid);
