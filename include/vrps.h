@@ -208,7 +208,11 @@ typedef struct vrps_solve_opts {
 } vrps_solve_opts;
 
 /* Storage of sinogram-sized solver state (not in the paper: a precision/footprint choice). */
-typedef enum vrps_storage { VRPS_STORAGE_FP32 = 0, VRPS_STORAGE_BF16 = 1 } vrps_storage;
+typedef enum vrps_storage {
+  VRPS_STORAGE_FP32 = 0,
+  VRPS_STORAGE_BF16 = 1,
+  VRPS_STORAGE_FP16 = 2   /* holds value * 2^s, s chosen from the data's RMS (|stored| <= 65504) */
+} vrps_storage;
 
 typedef struct vrps_report {
   int iterations;     /* outer iterations performed */

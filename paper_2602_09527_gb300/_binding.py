@@ -19,6 +19,7 @@ _LIB_PATH = _build.LIB
 
 ALGOS = {"ISTA": 0, "FISTA": 1, "SVRG": 2, "SAGA": 3, "PROXSKIP": 4, "VR_PROXSKIP": 5}
 ESTIMATORS = {"SVRG": 0, "SAGA": 1, "LSVRG": 2, "SGD": 3}
+STORAGE = {"FP32": 0, "BF16": 1, "FP16": 2}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "CUDA", -4: "TIMEOUT",
           -5: "DIVERGED", -6: "UNSUPPORTED"}
 
@@ -309,7 +310,7 @@ def solve(b: torch.Tensor, g: Geometry, alpha: float, algo: str = "VR_PROXSKIP",
     o.power_iters, o.eval_every = int(power_iters), int(eval_every)
     o.f_star, o.target_gap = float(f_star), float(target_gap)
     o.host_io, o.n_subsets, o.job = 1 if host_io else 0, int(n_subsets), int(job)
-    o.storage = {"FP32": 0, "BF16": 1}[storage.upper()]
+    o.storage = STORAGE[storage.upper()]
     o.correction_epochs = int(correction_epochs)
     if host_io:
         bp = _host_ptr(b, "b", g.m)
@@ -374,7 +375,7 @@ def _job_desc(g: Geometry, b: torch.Tensor, x_out: torch.Tensor, alpha: float, p
     d.estimator = ESTIMATORS[estimator.upper()]
     d.fgp_iters, d.max_iters, d.n_subsets = int(fgp_iters), int(max_iters), int(n_subsets)
     d.nonneg = 1 if nonneg else 0
-    d.storage = {"FP32": 0, "BF16": 1}[storage.upper()]
+    d.storage = STORAGE[storage.upper()]
     d.correction_epochs = int(correction_epochs)
     return d
 
@@ -452,7 +453,7 @@ def job_footprint(g: Geometry, *, max_iters: int, storage: str = "FP32") -> int:
     d = JobDesc()
     d.geom = g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle
     d.max_iters = int(max_iters)
-    d.storage = {"FP32": 0, "BF16": 1}[storage.upper()]
+    d.storage = STORAGE[storage.upper()]
     out = ctypes.c_size_t()
     _check(lib.vrps_job_footprint(g.handle, ctypes.byref(d), ctypes.byref(out)))
     return out.value

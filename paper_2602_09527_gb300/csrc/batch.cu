@@ -30,7 +30,9 @@ struct Job {
   float* x_out = nullptr;
   double alpha = 0, p = 1, gamma = 0;
   int est = VRPS_EST_SVRG, fgp_iters = 0, K = 0, N = 1, nonneg = 1;
-  bool bf_run = false;
+  bool bf_run = false;   // reduced-precision storage
+  int store = 0;         // its StoreKind
+  float sc = 1.f, isc = 1.f;
   int kc = 0;   // first iteration with float32 storage
   int k = 0;
   int state = 0;   // 0 running, 1 finished (kernels enqueued), 2 released
@@ -148,7 +150,9 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   if (J->bf_run) {
     const long long corr = (long long)d->correction_epochs * J->N;
     J->kc = corr >= J->K ? 0 : (int)(J->K - corr);
-    VRPS_TRY(to_bf16(w.b_perm, w.b16, m, s));
+    VRPS_TRY(storage_scale(g, J->store, &J->sc, s));
+    J->isc = 1.f / J->sc;
+    VRPS_TRY(to_store(w.b_perm, w.b16, m, J->store, J->sc, s));
   }
   VRPS_TRY(copy_or_zero(w.x, nullptr, n, s));
   VRPS_TRY(transpose2d(w.x, w.xfT, g->ny, g->nx, s));
@@ -176,7 +180,7 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
     std::memset(&ua, 0, sizeof(ua));
     ua.out = w.gbar;
     VRPS_TRY(proj_adjoint(g, w.tab, J->order, g->n_angles, ua, s));
-    if (J->kc > 0) VRPS_TRY(to_bf16(w.tab, w.tab16, m, s));
+    if (J->kc > 0) VRPS_TRY(to_store(w.tab, w.tab16, m, J->store, J->sc, s));
     J->rep.passes += 1.0;
   }
   VRPS_CUDA(cudaStreamSynchronize(s));
@@ -235,7 +239,7 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
   const int coin = J->sched[3 * (size_t)k + 2];
   const int* ids_i = J->order + J->off[i];
   const int rows_i = J->off[i + 1] - J->off[i];
-  const int bf = k < J->kc ? 1 : 0;
+  const int bf = k < J->kc ? J->store : STORE_F32;
   const size_t es = bf ? sizeof(__nv_bfloat16) : sizeof(float);
   char* const b_all = bf ? (char*)w.b16 : (char*)w.b_perm;
   char* const tab_all = bf ? (char*)w.tab16 : (char*)w.tab;
@@ -271,7 +275,7 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
   int mode;
   const int* ids = ids_i;
   int rows = rows_i;
-  FwdOut fo{w.res, nullptr, nullptr, 0, bf};
+  FwdOut fo{w.res, nullptr, nullptr, 0, bf, J->sc, J->isc};
   if (J->est == VRPS_EST_SGD) {
     mode = FWD_RESID;
     fo.b = b_i;
@@ -563,7 +567,7 @@ int vrps_batch_submit(vrps_batch* B, const vrps_job* d, int* id) {
     return fail(VRPS_ERR_INVALID_ARG, "fgp_iters must be in [0, %d]", FB_T * BATCH_MAX_BLOCKS);
   if (d->estimator < VRPS_EST_SVRG || d->estimator > VRPS_EST_SGD)
     return fail(VRPS_ERR_INVALID_ARG, "bad estimator %d", d->estimator);
-  if (d->storage != VRPS_STORAGE_FP32 && d->storage != VRPS_STORAGE_BF16)
+  if (d->storage < VRPS_STORAGE_FP32 || d->storage > VRPS_STORAGE_FP16)
     return fail(VRPS_ERR_INVALID_ARG, "bad storage %d", d->storage);
   if (d->correction_epochs < 0) return fail(VRPS_ERR_INVALID_ARG, "correction_epochs must be >= 0");
   const int N = d->n_subsets > 0 ? d->n_subsets : g->n_subsets;
@@ -584,7 +588,8 @@ int vrps_batch_submit(vrps_batch* B, const vrps_job* d, int* id) {
   J->K = d->max_iters;
   J->N = N;
   J->nonneg = d->nonneg ? 1 : 0;
-  J->bf_run = d->storage == VRPS_STORAGE_BF16;
+  J->bf_run = d->storage != VRPS_STORAGE_FP32;
+  J->store = d->storage;
   J->tau = (float)(d->gamma * d->alpha / d->p);
   J->step = (float)(1.0 / (4.0 * 2 * (double)J->tau));
   J->fgamma = (float)d->gamma;
@@ -656,7 +661,7 @@ int vrps_job_footprint(const vrps_geom* g, const vrps_job* d, size_t* bytes) {
   f += 4 * n * 8;                   // x, h, x_hat, v, gbar, prox copy, x^T, transposed scratch
   f += 4 * 2 * n * 5;               // dual and four rotation buffers
   f += 4 * m * 4;                   // b (subset-major), table, residual, scratch sinogram
-  if (d->storage == VRPS_STORAGE_BF16) f += 2 * m * 2;
+  if (d->storage != VRPS_STORAGE_FP32) f += 2 * m * 2;
   f += 4 * (size_t)g->n_angles * bands * g->n_bins;   // forward band partial sums
   f += 12 * (size_t)d->max_iters + 64 * (size_t)g->n_angles;   // draws, angle tables
   *bytes = f;

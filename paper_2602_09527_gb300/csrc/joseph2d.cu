@@ -69,22 +69,23 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 constexpr int FWD_PAD = 4;   // zero floats left and right of each staged line (16 bytes)
 
 // Estimator epilogue of one ray with value r = (A_i x)_ray (FwdMode).
+// Tables keep the stored (rounded) values and the residual handed to the adjoint is formed
+// from them, so that the running sums built from the table (SVRG's gbar, SAGA's v-bar) stay
+// equal to the sums of the stored rows (no drift from rounding).
 template <int MODE>
 __device__ __forceinline__ void fwd2d_epilogue(const FwdOut& o, size_t idx, float r) {
-  const int bf = o.bf16;
   if (MODE == FWD_PLAIN) {
     o.y[idx] = r;
   } else if (MODE == FWD_RESID) {
-    o.y[idx] = r - ld_store(o.b, idx, bf);
+    o.y[idx] = r - ld_store(o, o.b, idx);
   } else if (MODE == FWD_SVRG) {
-    o.y[idx] = r - ld_store(o.tab, idx, bf);
+    o.y[idx] = r - ld_store(o, o.tab, idx);
   } else if (MODE == FWD_SAGA) {
-    const float res = r - ld_store(o.b, idx, bf);
-    o.y[idx] = res - ld_store(o.tab, idx, bf);
-    st_store(o.tab, idx, res, bf);
+    const float res = r - ld_store(o, o.b, idx);
+    const float old = ld_store(o, o.tab, idx);
+    o.y[idx] = st_store(o, o.tab, idx, res) - old;
   } else {  // FWD_SNAP
-    st_store(o.tab, idx, r, bf);
-    o.y[idx] = r - ld_store(o.b, idx, bf);
+    o.y[idx] = st_store(o, o.tab, idx, r) - ld_store(o, o.b, idx);
   }
 }
 
@@ -512,7 +513,7 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   dim3 grid(P.bands, rows), block(FWD_THREADS);
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
-    LaunchScope _ls("fwd2d_kernel", s, 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->n_bins, o.bf16));
+    LaunchScope _ls("fwd2d_kernel", s, 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->n_bins, o.store));
     VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };

@@ -92,20 +92,20 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
   const float r = acc * wgt;
   const float ys = P.o.prescale ? wgt : 1.f;   // ray factor carried into the adjoint's input
   const size_t idx = (size_t)row * P.nu * P.nv + (size_t)iv * P.nu + iu;
-  const int bf = P.o.bf16;
+  const FwdOut& o = P.o;
   if (MODE == FWD_PLAIN) {
-    P.o.y[idx] = r * ys;
+    o.y[idx] = r * ys;
   } else if (MODE == FWD_RESID) {
-    P.o.y[idx] = (r - ld_store(P.o.b, idx, bf)) * ys;
+    o.y[idx] = (r - ld_store(o, o.b, idx)) * ys;
   } else if (MODE == FWD_SVRG) {
-    P.o.y[idx] = (r - ld_store(P.o.tab, idx, bf)) * ys;
+    o.y[idx] = (r - ld_store(o, o.tab, idx)) * ys;
   } else if (MODE == FWD_SAGA) {
-    const float res = r - ld_store(P.o.b, idx, bf);
-    P.o.y[idx] = (res - ld_store(P.o.tab, idx, bf)) * ys;
-    st_store(P.o.tab, idx, res, bf);
+    // stored (rounded) table values on both sides, as in the 2D epilogue
+    const float res = r - ld_store(o, o.b, idx);
+    const float old = ld_store(o, o.tab, idx);
+    o.y[idx] = (st_store(o, o.tab, idx, res) - old) * ys;
   } else {
-    st_store(P.o.tab, idx, r, bf);
-    P.o.y[idx] = (r - ld_store(P.o.b, idx, bf)) * ys;
+    o.y[idx] = (st_store(o, o.tab, idx, r) - ld_store(o, o.b, idx)) * ys;
   }
 }
 
@@ -272,7 +272,7 @@ int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.vox = (float)g->pixel;
   P.o = o;
   dim3 grid((g->nu + 31) / 32, (g->nv + 7) / 8, rows), block(32, 8);
-  const double fb = 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->nu * g->nv, o.bf16);
+  const double fb = 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->nu * g->nv, o.store);
   switch (mode) {
     case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_PLAIN>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;
     case FWD_RESID: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_RESID>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;

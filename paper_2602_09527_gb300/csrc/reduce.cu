@@ -126,9 +126,9 @@ __global__ void scatter_rows_kernel(const float* __restrict__ src, float* __rest
     dst[d0 + j] = src[so + j];
 }
 
-__global__ void bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
+__global__ void store_kernel(const float* __restrict__ src, void* __restrict__ dst, int64_t n, FwdOut f) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = __float2bfloat16_rn(src[i]);
+    st_store(f, dst, (size_t)i, src[i]);
 }
 
 __global__ void fill_kernel(float* p, float v, int64_t n) {
@@ -212,11 +212,15 @@ int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row
   return VRPS_OK;
 }
 
-int to_bf16(const float* src, void* dst, int64_t n, cudaStream_t s) {
-  { LaunchScope _ls("bf16_kernel", s, 6.0 * n);
-  VRPS_CUDA(launch_kernel(bf16_kernel, dim3(NPART), dim3(256), (size_t)(0), s, src, (__nv_bfloat16*)dst, n));
+int to_store(const float* src, void* dst, int64_t n, int kind, float scale, cudaStream_t s) {
+  FwdOut f{};
+  f.store = kind;
+  f.scale = scale;
+  f.inv = 1.f / scale;
+  { LaunchScope _ls("store_kernel", s, (kind ? 6.0 : 8.0) * n);
+  VRPS_CUDA(launch_kernel(store_kernel, dim3(NPART), dim3(256), (size_t)(0), s, src, dst, n, f));
   }
-  VRPS_LAUNCHED("to_bf16");
+  VRPS_LAUNCHED("to_store");
   return VRPS_OK;
 }
 

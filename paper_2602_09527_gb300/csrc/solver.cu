@@ -39,6 +39,24 @@ double step_factor(int algo, int est) {
 
 }  // namespace
 
+// FP16 storage scale: a power of two bringing the data's RMS into [512, 1024) (reads b_perm).
+int storage_scale(vrps_geom* g, int kind, float* scale, cudaStream_t s) {
+  *scale = 1.f;
+  if (kind != STORE_F16) return VRPS_OK;
+  Workspace& w = g->ws;
+  VRPS_TRY(dot64(w.b_perm, w.b_perm, g->m, w.scalars + 7, w, s));
+  double ss = 0.0;
+  VRPS_CUDA(cudaMemcpyAsync(&ss, w.scalars + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
+  VRPS_CUDA(cudaStreamSynchronize(s));
+  const double rms = std::sqrt(ss / (double)g->m);
+  if (!(rms > 0.0) || !std::isfinite(rms)) return VRPS_OK;
+  int e = (int)std::floor(std::log2(1024.0 / rms));
+  if (e > 60) e = 60;
+  if (e < -60) e = -60;
+  *scale = (float)std::ldexp(1.0, e);
+  return VRPS_OK;
+}
+
 int solver_alloc(vrps_geom* g, bool fista, bool bf16) {
   Workspace& w = g->ws;
   const size_t n = (size_t)g->n, m = (size_t)g->m;
@@ -98,7 +116,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   if (!skip) p = 1.0;
   if (!std::isfinite(gamma)) return fail(VRPS_ERR_INVALID_ARG, "gamma is not finite");
   if (o.history && o.history_cap <= 0) return fail(VRPS_ERR_INVALID_ARG, "history_cap must be > 0");
-  if (o.storage != VRPS_STORAGE_FP32 && o.storage != VRPS_STORAGE_BF16)
+  if (o.storage < VRPS_STORAGE_FP32 || o.storage > VRPS_STORAGE_FP16)
     return fail(VRPS_ERR_INVALID_ARG, "bad storage %d", o.storage);
   if (o.correction_epochs < 0) return fail(VRPS_ERR_INVALID_ARG, "correction_epochs must be >= 0");
   vrps_geom* g = const_cast<vrps_geom*>(gc);
@@ -117,7 +135,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   const bool fista = algo == VRPS_ALGO_FISTA;
   cudaStream_t s = (cudaStream_t)stream;
   Workspace& w = g->ws;
-  const bool bf_run = o.storage == VRPS_STORAGE_BF16;
+  const bool bf_run = o.storage != VRPS_STORAGE_FP32;   // reduced-precision storage
   VRPS_TRY(solver_alloc(g, fista, bf_run));
   const int64_t n = g->n, m = g->m;
   const int L = g->row_len;
@@ -143,14 +161,17 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     b_dev = w.sino;
   }
   VRPS_TRY(gather_rows(b_dev, w.b_perm, order, g->n_angles, L, s));
-  // BF16 storage: iterations k < kc read b and the estimator table as bfloat16
+  // reduced storage: iterations k < kc read b and the estimator table as bfloat16 / float16
   const int K = o.max_iters;
   int kc = 0;
+  float sc = 1.f;
   if (bf_run) {
     const long long corr = (long long)o.correction_epochs * N;
     kc = corr >= K ? 0 : (int)(K - corr);
-    VRPS_TRY(to_bf16(w.b_perm, w.b16, m, s));
+    VRPS_TRY(storage_scale(g, o.storage, &sc, s));
+    VRPS_TRY(to_store(w.b_perm, w.b16, m, o.storage, sc, s));
   }
+  const float isc = 1.f / sc;
 
   // step size (Section 3)
   vrps_report r;
@@ -202,7 +223,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     std::memset(&ua, 0, sizeof(ua));
     ua.out = w.gbar;
     VRPS_TRY(proj_adjoint(g, w.tab, order, g->n_angles, ua, s));
-    if (kc > 0) VRPS_TRY(to_bf16(w.tab, w.tab16, m, s));
+    if (kc > 0) VRPS_TRY(to_store(w.tab, w.tab16, m, o.storage, sc, s));
     r.passes += 1.0;
   }
   VRPS_CUDA(cudaStreamSynchronize(s));
@@ -224,7 +245,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     const int coin = w.sched_host[3 * k + 2];
     const int* ids_i = order + (*off)[i];
     const int rows_i = (*off)[i + 1] - (*off)[i];
-    const int bf = k < kc ? 1 : 0;
+    const int bf = k < kc ? o.storage : STORE_F32;
     const size_t es = bf ? sizeof(__nv_bfloat16) : sizeof(float);
     char* const b_all = bf ? (char*)w.b16 : (char*)w.b_perm;
     char* const tab_all = bf ? (char*)w.tab16 : (char*)w.tab;
@@ -262,19 +283,19 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     ua.v = w.v;
 
     if (est == EST_FULL) {
-      FwdOut fo{w.res, b_all, nullptr, pre, bf};
+      FwdOut fo{w.res, b_all, nullptr, pre, bf, sc, isc};
       VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_RESID, fo, s));
       ua.cN = 1.f;
       VRPS_TRY(proj_adjoint(g, w.res, order, g->n_angles, ua, s));
       r.passes += 1.0;
     } else if (est == VRPS_EST_SGD) {
-      FwdOut fo{w.res, b_i, nullptr, pre, bf};
+      FwdOut fo{w.res, b_i, nullptr, pre, bf, sc, isc};
       VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_RESID, fo, s));
       ua.cN = (float)N;
       VRPS_TRY(proj_adjoint(g, w.res, ids_i, rows_i, ua, s));
       r.passes += 1.0 / N;
     } else if (est == VRPS_EST_SAGA) {
-      FwdOut fo{w.res, b_i, tab_i, pre, bf};
+      FwdOut fo{w.res, b_i, tab_i, pre, bf, sc, isc};
       VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_SAGA, fo, s));
       ua.cN = (float)N;
       ua.gbar = w.gbar;
@@ -286,7 +307,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
       if (refresh) {
         // snapshot x~ = x_k: store A x~ (subset-major), gbar = A^T (A x~ - b) and G = gbar,
         // the full adjoint's epilogue writing gbar and taking the step in one pass
-        FwdOut fo{w.res, b_all, tab_all, pre, bf};
+        FwdOut fo{w.res, b_all, tab_all, pre, bf, sc, isc};
         VRPS_TRY(proj_forward(g, xf, xfT, order, g->n_angles, FWD_SNAP, fo, s));
         ua.cN = 0.f;
         ua.gbar = w.gbar;
@@ -295,7 +316,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
         r.snapshots += 1;
         r.passes += 1.0;
       } else {
-        FwdOut fo{w.res, nullptr, tab_i, pre, bf};
+        FwdOut fo{w.res, nullptr, tab_i, pre, bf, sc, isc};
         VRPS_TRY(proj_forward(g, xf, xfT, ids_i, rows_i, FWD_SVRG, fo, s));
         ua.cN = (float)N;
         ua.gbar = w.gbar;

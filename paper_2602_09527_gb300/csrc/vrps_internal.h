@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -206,22 +207,39 @@ int ensure_d(double** p, size_t count);
 
 // ---- 2D projector (joseph2d.cu)
 enum FwdMode { FWD_PLAIN = 0, FWD_RESID = 1, FWD_SVRG = 2, FWD_SAGA = 3, FWD_SNAP = 4 };
+// Storage of the solver's sinogram-sized rows (data b and the SVRG / SAGA table): float32,
+// bfloat16, or float16 holding value * scale (scale a power of two); arithmetic is float32.
+enum StoreKind { STORE_F32 = 0, STORE_BF16 = 1, STORE_F16 = 2 };
 struct FwdOut {
-  float* y;           // output rows (float32 always)
-  const void* b;      // data rows (RESID, SAGA, SNAP): float32, or bfloat16 when bf16
-  void* tab;          // table rows (SVRG read, SAGA read/write, SNAP write): likewise
-  int prescale = 0;   // 3D: write y times the ray's length factor (input of a prescaled adjoint)
-  int bf16 = 0;       // b and tab are stored as bfloat16 (arithmetic stays float32)
+  float* y;            // output rows (float32 always)
+  const void* b;       // data rows (RESID, SAGA, SNAP), stored as `store`
+  void* tab;           // table rows (SVRG read, SAGA read/write, SNAP write), likewise
+  int prescale = 0;    // 3D: write y times the ray's length factor (input of a prescaled adjoint)
+  int store = 0;       // StoreKind of b and tab
+  float scale = 1.f;   // float16: stored = value * scale
+  float inv = 1.f;     // 1 / scale (exact)
 };
 
-// Stored sinogram values (data and estimator tables): float32 or bfloat16 storage, float32
-// arithmetic; bfloat16 stores round to nearest even.
-__device__ __forceinline__ float ld_store(const void* p, size_t i, int bf16) {
-  return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]) : static_cast<const float*>(p)[i];
+__device__ __forceinline__ float ld_store(const FwdOut& o, const void* p, size_t i) {
+  if (o.store == STORE_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+  if (o.store == STORE_F16) return __half2float(static_cast<const __half*>(p)[i]) * o.inv;
+  return static_cast<const float*>(p)[i];
 }
-__device__ __forceinline__ void st_store(void* p, size_t i, float v, int bf16) {
-  if (bf16) static_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(v);
-  else static_cast<float*>(p)[i] = v;
+// Stores v (rounded to nearest) and returns the value the stored entry decodes to, so that a
+// table and the sums built from it use the same numbers.  float16 saturates at +-65504.
+__device__ __forceinline__ float st_store(const FwdOut& o, void* p, size_t i, float v) {
+  if (o.store == STORE_BF16) {
+    const __nv_bfloat16 e = __float2bfloat16_rn(v);
+    static_cast<__nv_bfloat16*>(p)[i] = e;
+    return __bfloat162float(e);
+  }
+  if (o.store == STORE_F16) {
+    const __half e = __float2half_rn(fminf(fmaxf(v * o.scale, -65504.f), 65504.f));
+    static_cast<__half*>(p)[i] = e;
+    return __half2float(e) * o.inv;
+  }
+  static_cast<float*>(p)[i] = v;
+  return v;
 }
 int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
           FwdOut o, cudaStream_t s);
@@ -292,8 +310,8 @@ inline double update_bytes(const UpdateArgs& u, size_t n) {
 }
 
 // Algorithmic bytes of a forward launch's sinogram epilogue over m_i rays (FwdMode).
-inline double fwd_mode_bytes(int mode, size_t mi, int bf16 = 0) {
-  const double f = 4.0 * (double)mi, t = (bf16 ? 2.0 : 4.0) * (double)mi;   // y, stored rows
+inline double fwd_mode_bytes(int mode, size_t mi, int store = 0) {
+  const double f = 4.0 * (double)mi, t = (store ? 2.0 : 4.0) * (double)mi;   // y, stored rows
   switch (mode) {
     case FWD_PLAIN: return f;              // write y
     case FWD_RESID: return f + t;          // read b, write y
@@ -427,9 +445,11 @@ int gather_rows(const float* src, float* dst, const int* ids, int rows, int row_
 int scatter_rows(const float* src, float* dst, const int* ids, int rows, int row_len, cudaStream_t s);
 int fill(float* p, float v, int64_t n, cudaStream_t s);
 int copy_or_zero(float* dst, const float* src, int64_t n, cudaStream_t s);
-int to_bf16(const float* src, void* dst, int64_t n, cudaStream_t s);
+// float32 rows -> storage `kind` (StoreKind; float16 multiplied by scale).
+int to_store(const float* src, void* dst, int64_t n, int kind, float scale, cudaStream_t s);
 // Solver state in the geometry's workspace (solver.cu).
 int solver_alloc(vrps_geom* g, bool fista, bool bf16);
+int storage_scale(vrps_geom* g, int kind, float* scale, cudaStream_t s);
 // Adds to the library's launch counter (kernels launched through a CUDA graph).
 void launch_count_add(long long n);
 // Whether per-launch event profiling is on (graphs are bypassed then).

@@ -28,6 +28,7 @@ MIX = [
     (30, 30, 45, 45, 5, "LSVRG", 0.5, 12, 40, "FP32", 0),     # sides not multiples of 4
     (128, 128, 192, 192, 16, "SVRG", 0.1, 100, 48, "BF16", 1),
     (40, 56, 60, 84, 6, "SGD", 0.25, 0, 30, "FP32", 0),       # no inner FGP iteration
+    (72, 72, 108, 108, 9, "SAGA", 0.2, 24, 45, "FP16", 2),
 ]
 
 

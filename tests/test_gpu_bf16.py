@@ -1,7 +1,7 @@
-"""BF16 storage of the solver's sinogram-sized state (b and the SVRG / SAGA table) with
-float32 arithmetic, finished by float32 correction epochs, against the float64 oracle on the
-same Philox trajectory.  Tolerance: the objective of the final iterate within 1e-3 relative
-of the oracle's."""
+"""Reduced-precision storage (bfloat16, or float16 with a power-of-two scale) of the solver's
+sinogram-sized state (b and the SVRG / SAGA table) with float32 arithmetic, finished by float32
+correction epochs, against the float64 oracle on the same Philox trajectory.  Tolerance: the
+objective of the final iterate within 1e-3 relative of the oracle's."""
 import numpy as np
 import pytest
 
@@ -32,12 +32,13 @@ def c1():
     return vr, P, g, op, L
 
 
+@pytest.mark.parametrize("storage", ["BF16", "FP16"])
 @pytest.mark.parametrize("est,fac", [("SVRG", 1.0), ("SAGA", 1 / 3)])
-def test_bf16_storage_objective_within_1e3(c1, est, fac):
+def test_reduced_storage_objective_within_1e3(c1, est, fac, storage):
     vr, P, g, op, L = c1
     K, seed = 300, 20260209
     x, rep, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", p=0.1, gamma=fac / L, seed=seed, estimator=est,
-                         fgp_iters=50, max_iters=K, storage="BF16", correction_epochs=2)
+                         fgp_iters=50, max_iters=K, storage=storage, correction_epochs=2)
     ref = solvers.run(op, P.b, P.alpha, "VR_PROXSKIP", fac / L, K, 50, p=0.1, seed=seed, estimator=est)
     F = solvers.objective(op, P.b, host(x), P.alpha)
     Fr = solvers.objective(op, P.b, ref.x, P.alpha)
@@ -56,6 +57,17 @@ def test_bf16_without_correction_differs_from_fp32(c1):
     b, _, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", storage="BF16", **kw)
     d = rel(host(b), host(a))
     assert 1e-4 < d < 5e-2
+
+
+def test_fp16_closer_than_bf16(c1):
+    """float16 keeps 3 more mantissa bits than bfloat16: without correction its run stays
+    closer to the float32 run."""
+    vr, P, g, op, L = c1
+    kw = dict(p=0.1, gamma=1 / (3 * L), seed=6, estimator="SAGA", fgp_iters=20, max_iters=80)
+    a, _, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", **kw)
+    b, _, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", storage="BF16", **kw)
+    h, _, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", storage="FP16", **kw)
+    assert rel(host(h), host(a)) < 0.5 * rel(host(b), host(a))
 
 
 def test_correction_covering_whole_run_equals_fp32(c1):
