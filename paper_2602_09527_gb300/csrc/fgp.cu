@@ -46,7 +46,7 @@ using TileLarge = FgpTile<32, 32, 512>;
 // Projection onto the unit ball: g / max(1, |g|) through the hardware reciprocal square
 // root (relative error a few ulp, far below the float32 tolerances of the prox).
 __device__ __forceinline__ void ball2(float g1, float g2, float& n1, float& n2) {
-  const float q = g1 * g1 + g2 * g2;
+  const float q = fmaf(g1, g1, __fmul_rn(g2, g2));
   if (q > 1.f) {
     const float r = rsqrtf(q);
     n1 = g1 * r;
@@ -224,10 +224,10 @@ __device__ __forceinline__ void fgp2d_out_item(const FgpOutArgs& A, int tbx, int
       } else {
         const float xold = t.x[p];
         t.x[p] = xp;
-        if (t.h) t.h[p] += t.p_over_gamma * (xp - t.xhat[p]);
+        if (t.h) t.h[p] = fmaf(t.p_over_gamma, __fsub_rn(xp, t.xhat[p]), t.h[p]);
         if (t.xprox) t.xprox[p] = xp;
         if (t.y) {
-          const float yv = xp + t.mom * (xp - xold);
+          const float yv = fmaf(t.mom, __fsub_rn(xp, xold), xp);
           t.y[p] = yv;
           tv_out = yv;
         } else {
@@ -399,9 +399,9 @@ __global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, co
   }
   const float xold = t.x[p];
   t.x[p] = xp;
-  if (t.h) t.h[p] += t.p_over_gamma * (xp - t.xhat[p]);
+  if (t.h) t.h[p] = fmaf(t.p_over_gamma, __fsub_rn(xp, t.xhat[p]), t.h[p]);
   if (t.xprox) t.xprox[p] = xp;
-  if (t.y) t.y[p] = xp + t.mom * (xp - xold);
+  if (t.y) t.y[p] = fmaf(t.mom, __fsub_rn(xp, xold), xp);
 }
 
 }  // namespace

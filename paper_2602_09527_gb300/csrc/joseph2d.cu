@@ -71,21 +71,22 @@ constexpr int FWD_PAD = 4;   // zero floats left and right of each staged line (
 // Estimator epilogue of one ray with value r = (A_i x)_ray (FwdMode).
 // Tables keep the stored (rounded) values and the residual handed to the adjoint is formed
 // from them, so that the running sums built from the table (SVRG's gbar, SAGA's v-bar) stay
-// equal to the sums of the stored rows (no drift from rounding).
+// equal to the sums of the stored rows (no drift from rounding).  Explicitly rounded
+// operations: the result does not depend on how the compiler contracts the caller's code.
 template <int MODE>
 __device__ __forceinline__ void fwd2d_epilogue(const FwdOut& o, size_t idx, float r) {
   if (MODE == FWD_PLAIN) {
     o.y[idx] = r;
   } else if (MODE == FWD_RESID) {
-    o.y[idx] = r - ld_store(o, o.b, idx);
+    o.y[idx] = __fsub_rn(r, ld_store(o, o.b, idx));
   } else if (MODE == FWD_SVRG) {
-    o.y[idx] = r - ld_store(o, o.tab, idx);
+    o.y[idx] = __fsub_rn(r, ld_store(o, o.tab, idx));
   } else if (MODE == FWD_SAGA) {
-    const float res = r - ld_store(o, o.b, idx);
+    const float res = __fsub_rn(r, ld_store(o, o.b, idx));
     const float old = ld_store(o, o.tab, idx);
-    o.y[idx] = st_store(o, o.tab, idx, res) - old;
+    o.y[idx] = __fsub_rn(st_store(o, o.tab, idx, res), old);
   } else {  // FWD_SNAP
-    o.y[idx] = st_store(o, o.tab, idx, r) - ld_store(o, o.b, idx);
+    o.y[idx] = __fsub_rn(st_store(o, o.tab, idx, r), ld_store(o, o.b, idx));
   }
 }
 
@@ -243,16 +244,16 @@ __device__ __forceinline__ int fwd2d_item(const Fwd2DParams& P, int c, int row, 
         s.z += v.z;
         s.w += v.w;
       }
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 0, s.x * in.wgt);
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 1, s.y * in.wgt);
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 2, s.z * in.wgt);
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 3, s.w * in.wgt);
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 0, __fmul_rn(s.x, in.wgt));
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 1, __fmul_rn(s.y, in.wgt));
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 2, __fmul_rn(s.z, in.wgt));
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 3, __fmul_rn(s.w, in.wgt));
     }
   } else {
     for (int j = tid; j < nb; j += FWD_THREADS) {
       float s = 0.f;
       for (int q = 0; q < bands; ++q) s += __ldcg(part + (size_t)q * nb + j);
-      fwd2d_epilogue<MODE>(P.o, obase + j, s * in.wgt);
+      fwd2d_epilogue<MODE>(P.o, obase + j, __fmul_rn(s, in.wgt));
     }
   }
   return used;
@@ -278,29 +279,32 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
 // Algorithm 1, estimator and x_hat lines for one pixel: G = cN g + gbar,
 // x_hat = base - gamma (G - h); theta = 0: x <- x_hat (returned for the transposed copy);
 // theta = 1: keep x_hat and write the prox input v = x_hat - (gamma/p) h.
+// (Explicit roundings and fused multiply-adds: identical bits in every kernel that inlines it.)
 __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, float g) {
-  float G = u.cN * g;
+  float G;
   if (u.snap) {            // SVRG snapshot: g is the full gradient; gbar <- g, G = g
     u.gbar[p] = g;
     G = g;
   } else if (u.gbar) {
     const float gb = u.gbar[p];
-    G += gb;
-    if (u.saga) u.gbar[p] = gb + g;
+    G = fmaf(u.cN, g, gb);
+    if (u.saga) u.gbar[p] = __fadd_rn(gb, g);
+  } else {
+    G = __fmul_rn(u.cN, g);
   }
   const float base = u.base[p];
   if (u.h) {
     const float hp = u.h[p];
-    const float xh = base - u.gamma * (G - hp);
+    const float xh = fmaf(-u.gamma, __fsub_rn(G, hp), base);
     if (u.theta) {
       u.xhat[p] = xh;
-      u.v[p] = xh - u.gamma_over_p * hp;
+      u.v[p] = fmaf(-u.gamma_over_p, hp, xh);
       return 0.f;
     }
     u.x[p] = xh;
     return xh;
   }
-  const float xh = base - u.gamma * G;
+  const float xh = fmaf(-u.gamma, G, base);
   if (u.theta) {
     u.v[p] = xh;
     return 0.f;
