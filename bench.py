@@ -66,6 +66,17 @@ WORKLOADS_BATCH = {
                     alpha=0.02, epochs=20, estimator="SAGA", storage="FP16", correction_epochs=1, seed=20260209),
 }
 
+# Served stream (optional): Poisson arrivals at `rate` per second for `seconds`; each request a
+# 2D parallel-beam job with side drawn from the batched workload's sizes (angles = bins =
+# 1.5 x side), N uniform in [10, 30], alpha ~ U[0.005, 0.05], ProxSAGASkip p = 0.1 with 50
+# FGP iterations and a fixed budget of 20 epochs.  Phantoms come from a pool of 4 per size;
+# every request has its own seed and weight.  Latency = completion - arrival (wall clock).
+WORKLOADS_SERVE = {
+    "serve": dict(rate=50.0, seconds=60.0, sides=(128, 256, 384, 512, 1024), n_min=10, n_max=30,
+                  alpha=(0.005, 0.05), p=0.1, fgp_iters=50, epochs=20, pool=4, handles=24,
+                  budget_gb=120.0, seed=20260209),
+}
+
 # Iteration counts of the replayed trajectory (same seed and draws on any machine), used only
 # by the CPU oracle legs to scale a bounded sample up to a whole reconstruction.  Recorded from
 # the GPU replay of this workload; the GPU arm recomputes them every run.
@@ -518,6 +529,112 @@ def bench_batch(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------- served stream
+def bench_serve(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2602_09527_gb300 as vr
+    from paper_2602_09527_gb300 import serve
+    w = WORKLOADS_SERVE[args.workload]
+    seconds = args.serve_seconds if args.serve_seconds else w["seconds"]
+    rng = np.random.default_rng(w["seed"] + rank)
+    pools, data, lips = {}, {}, {}
+    for side in w["sides"]:
+        na = nb = int(1.5 * side)
+        spec = synthetic.Par2DSpec(nx=side, ny=side, pixel=1.0, angles=synthetic.uniform_angles(na, math.pi),
+                                   n_bins=nb, bin_spacing=1.0, n_subsets=20)
+        pools[side] = [vr.Geometry.from_spec(spec) for _ in range(w["handles"])]
+        lips[side] = vr.power_iteration(pools[side][0], 50, seed=w["seed"])
+        data[side] = []
+        for _ in range(w["pool"]):
+            ells = synthetic.random_ellipses(10, side / 2.0, rng)
+            b = synthetic.gaussian_noise(synthetic.ellipse_sinogram(ells, spec.angles, spec.bin_centers()), 0.01, rng)
+            data[side].append(torch.tensor(b.astype(np.float32).ravel(), device="cuda"))
+    # one arrival sequence for every variant
+    t, arrivals = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / w["rate"])
+        if t > seconds:
+            break
+        side = int(rng.choice(w["sides"]))
+        arrivals.append(dict(arrival=t, side=side, k=int(rng.integers(w["pool"])),
+                             alpha=float(rng.uniform(*w["alpha"])), N=int(rng.integers(w["n_min"], w["n_max"] + 1)),
+                             seed=int(rng.integers(1 << 40))))
+
+    def requests(storage, corr):
+        return [serve.Request(key=a["side"], b=data[a["side"]][a["k"]], arrival=a["arrival"], alpha=a["alpha"],
+                              gamma=1.0 / (3.0 * lips[a["side"]]), seed=a["seed"], p=w["p"], estimator="SAGA",
+                              fgp_iters=w["fgp_iters"], max_iters=w["epochs"] * a["N"], n_subsets=a["N"],
+                              storage=storage, correction_epochs=corr) for a in arrivals]
+
+    def summary(st, reqs):
+        lat = st.latencies
+        return {"p50_s": round(serve.percentile(lat, 50), 4), "p99_s": round(serve.percentile(lat, 99), 4),
+                "mean_s": round(float(np.mean(lat)), 4), "completed": st.completed,
+                "reconstructions_per_s": round(st.completed / st.wall, 3), "wall_s": round(st.wall, 3),
+                "queue_wait_p99_s": round(serve.percentile(st.queue_waits, 99), 4),
+                "peak_running_jobs": st.peak_jobs, "peak_state_gb": round(st.peak_bytes / 1e9, 3)}
+
+    budget = int(w["budget_gb"] * 1e9)
+    # warm-up: a short stream through the batched server (graph capture, allocations)
+    warm = requests("FP16", 1)[: min(len(arrivals), 40)]
+    for r in warm:
+        r.arrival = 0.0
+    srv = serve.BatchServer(pools, budget)
+    srv.run(warm)
+    results = {}
+    launches0 = vr.kernel_launches()
+    with ClockSampler(local) as clk:
+        reqs16 = requests("FP16", 1)
+        st16 = srv.run(reqs16)
+    launches = vr.kernel_launches() - launches0
+    results["batched_fp16"] = summary(st16, reqs16)
+    reqs32 = requests("FP32", 0)
+    results["batched_fp32"] = summary(srv.run(reqs32), reqs32)
+    srv.close()
+    seq = serve.SequentialServer(pools)
+    reqsq = requests("FP32", 0)
+    results["per_job_fp32"] = summary(seq.run(reqsq), reqsq)
+    # same job alone and in the mix: the served results equal vrps_solve's bit for bit
+    same = all(torch.equal(a.x, b.x) for a, b in zip(reqs32[:50], reqsq[:50]))
+    head = results["batched_fp16"]
+    out = {
+        "metric": "served p99 latency",
+        "value": head["p99_s"],
+        "unit": "s",
+        "n_gpus": world,
+        "steps": 1,
+        "warmup": 1,
+        "ms_per_step": round(st16.wall * 1e3, 1),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (fp16 storage)",
+        "data": "synthetic (pooled ellipse phantoms, analytic sinograms, Gaussian 1%)",
+        "config": {"workload": args.workload, "rate_per_s": w["rate"], "seconds": seconds, "requests": len(arrivals),
+                   "sides": list(w["sides"]), "subsets": f"U[{w['n_min']}, {w['n_max']}]",
+                   "alpha": f"U{list(w['alpha'])}", "algo": "ProxSAGASkip", "p": w["p"], "fgp_iters": w["fgp_iters"],
+                   "epochs": w["epochs"], "budget_gb": w["budget_gb"], "handles_per_size": w["handles"],
+                   "ticks_per_step": 2, "timing": "host wall clock per request (arrival to completion)",
+                   "scope": "2D requests only"},
+        "p50_s": head["p50_s"],
+        "reconstructions_per_s": head["reconstructions_per_s"],
+        "variants": results,
+        "batched_equals_per_job_bits": bool(same),
+        "e2e": {"value": head["p99_s"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "requests' data resident on the device; latency is measured end to end per request"},
+        "gpu_launches": int(launches),
+        "roofline": None,
+        "clocks": clk.summary(),
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    for v in pools.values():
+        for g in v:
+            g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -525,7 +642,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default="par2d_512",
-                    choices=list(WORKLOADS) + list(WORKLOADS_3D) + list(WORKLOADS_BATCH))
+                    choices=list(WORKLOADS) + list(WORKLOADS_3D) + list(WORKLOADS_BATCH) + list(WORKLOADS_SERVE))
+    ap.add_argument("--serve-seconds", type=float, default=0.0, help="served stream: arrival window (s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--alpha", type=float, default=None, help="override the workload's TV weight")
     ap.add_argument("--profile-once", type=int, default=0, metavar="K",
@@ -536,7 +654,7 @@ def main():
         args.warmup = 3
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     wl = args.workload
-    w = WORKLOADS.get(wl) or WORKLOADS_3D.get(wl) or WORKLOADS_BATCH[wl]
+    w = WORKLOADS.get(wl) or WORKLOADS_3D.get(wl) or WORKLOADS_BATCH.get(wl) or WORKLOADS_SERVE[wl]
     if args.alpha is not None:
         w["alpha"] = args.alpha
 
@@ -546,6 +664,8 @@ def main():
         return bench_3d(args, rank, world, local)
     if wl in WORKLOADS_BATCH:
         return bench_batch(args, rank, world, local)
+    if wl in WORKLOADS_SERVE:
+        return bench_serve(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -724,9 +844,9 @@ def reference_arm(args, rank, world):
     wl = args.workload
     if wl in WORKLOADS_3D:
         return reference_arm_3d(args, wl)
-    if wl in WORKLOADS_BATCH:
-        print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle arm; "
-                          "its baseline is the per-job float32 solver timed inside the own arm"}))
+    if wl in WORKLOADS_BATCH or wl in WORKLOADS_SERVE:
+        print(json.dumps({"impl": "reference", "unavailable": "the batched and served workloads have no oracle "
+                          "arm; their baseline is the per-job float32 solver timed inside the own arm"}))
         return
     w = WORKLOADS[wl]
     counts = TRAJECTORY[wl]

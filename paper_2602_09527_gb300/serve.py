@@ -1,0 +1,164 @@
+"""Request loop over the batched engine (vrps_batch_*): continuous batching of reconstruction
+jobs with admission by device-memory footprint.
+
+Requests wait in arrival order.  Before every group of ticks the loop admits waiting
+requests while a geometry handle of their size is free and the admitted jobs' state fits the
+memory budget; admitted jobs join the running batch at the next tick, and a job's handle and
+memory are released as soon as its last iteration has finished on the device.  All device
+work (job setup, every tick, the result copy) happens in the library; this module only
+schedules.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _binding as vb
+
+
+@dataclass
+class Request:
+    """One reconstruction request: a geometry class, its data and the solver settings."""
+    key: object                  # geometry class (requests of one class share handles)
+    b: torch.Tensor              # device sinogram, natural angle order
+    arrival: float               # seconds since the start of the run
+    alpha: float
+    gamma: float
+    seed: int
+    p: float = 0.1
+    estimator: str = "SAGA"
+    fgp_iters: int = 50
+    max_iters: int = 100
+    n_subsets: int = 0           # 0: the geometry's N
+    storage: str = "FP32"
+    correction_epochs: int = 0
+    admitted: float | None = None
+    finished: float | None = None
+    report: dict | None = None
+    x: torch.Tensor | None = None
+
+
+@dataclass
+class ServerStats:
+    latencies: list = field(default_factory=list)
+    queue_waits: list = field(default_factory=list)
+    completed: int = 0
+    ticks: int = 0
+    peak_jobs: int = 0
+    peak_bytes: int = 0
+    wall: float = 0.0
+
+
+class BatchServer:
+    """Continuous batching of jobs on one GPU.
+
+    pools: {key: [Geometry, ...]} handles per geometry class (each running job holds one);
+    budget_bytes: upper bound on the summed footprint (vrps_job_footprint) of running jobs;
+    ticks_per_step: ticks enqueued between two admission / completion checks."""
+
+    def __init__(self, pools: dict, budget_bytes: int, ticks_per_step: int = 2, graphs: bool = True):
+        self.free = {k: list(v) for k, v in pools.items()}
+        self.budget = int(budget_bytes)
+        self.ticks_per_step = int(ticks_per_step)
+        self.batch = vb.Batch(graphs=graphs)
+        self.running = {}            # job id -> (request, geometry, bytes)
+        self.used = 0
+
+    def _try_admit(self, r: Request, now: float) -> bool:
+        pool = self.free.get(r.key)
+        if not pool:
+            return False
+        g = pool[-1]
+        need = vb.job_footprint(g, max_iters=r.max_iters, storage=r.storage)
+        if self.running and self.used + need > self.budget:
+            return False
+        pool.pop()
+        r.x = torch.empty(g.n, device=r.b.device, dtype=torch.float32)
+        jid = self.batch.submit(g, r.b, alpha=r.alpha, p=r.p, gamma=r.gamma, seed=r.seed, estimator=r.estimator,
+                                fgp_iters=r.fgp_iters, max_iters=r.max_iters, n_subsets=r.n_subsets,
+                                storage=r.storage, correction_epochs=r.correction_epochs, x_out=r.x)
+        r.admitted = now
+        self.running[jid] = (r, g, need)
+        self.used += need
+        return True
+
+    def run(self, requests: list, clock=time.perf_counter) -> ServerStats:
+        """Serves `requests` (sorted by arrival) in real time; returns latency statistics."""
+        st = ServerStats()
+        waiting = deque()
+        i = 0
+        t0 = clock()
+        while i < len(requests) or waiting or self.running:
+            now = clock() - t0
+            while i < len(requests) and requests[i].arrival <= now:
+                waiting.append(requests[i])
+                i += 1
+            while waiting and self._try_admit(waiting[0], now):
+                waiting.popleft()
+            st.peak_jobs = max(st.peak_jobs, len(self.running))
+            st.peak_bytes = max(st.peak_bytes, self.used)
+            if self.running:
+                self.batch.step(self.ticks_per_step)
+                st.ticks += self.ticks_per_step
+            elif i < len(requests):
+                time.sleep(max(0.0, min(requests[i].arrival - now, 0.002)))
+            now = clock() - t0
+            for jid in list(self.running):
+                done, rep = self.batch.poll(jid)
+                if not done:
+                    continue
+                r, g, need = self.running.pop(jid)
+                r.finished = now
+                r.report = rep
+                self.batch.release(jid)
+                self.free[r.key].append(g)
+                self.used -= need
+                st.completed += 1
+                st.latencies.append(r.finished - r.arrival)
+                st.queue_waits.append(r.admitted - r.arrival)
+        st.wall = clock() - t0
+        return st
+
+    def close(self):
+        self.batch.close()
+
+
+class SequentialServer:
+    """The per-job baseline: requests in arrival order, one vrps_solve at a time."""
+
+    def __init__(self, pools: dict):
+        self.geom = {k: v[0] for k, v in pools.items()}
+
+    def run(self, requests: list, clock=time.perf_counter) -> ServerStats:
+        st = ServerStats()
+        t0 = clock()
+        for r in requests:
+            now = clock() - t0
+            if r.arrival > now:
+                time.sleep(r.arrival - now)
+            r.admitted = clock() - t0
+            g = self.geom[r.key]
+            x, rep, _ = vb.solve(r.b, g, r.alpha, "VR_PROXSKIP", p=r.p, gamma=r.gamma, seed=r.seed,
+                                 estimator=r.estimator, fgp_iters=r.fgp_iters, max_iters=r.max_iters,
+                                 n_subsets=r.n_subsets, storage=r.storage, correction_epochs=r.correction_epochs)
+            r.finished = clock() - t0
+            r.report, r.x = rep, x
+            st.completed += 1
+            st.latencies.append(r.finished - r.arrival)
+            st.queue_waits.append(r.admitted - r.arrival)
+        st.wall = clock() - t0
+        return st
+
+
+def percentile(values, q):
+    """q-th percentile (0..100) by linear interpolation between order statistics."""
+    v = sorted(values)
+    if not v:
+        return float("nan")
+    pos = (len(v) - 1) * q / 100.0
+    lo = int(pos)
+    hi = min(lo + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (pos - lo)

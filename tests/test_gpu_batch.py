@@ -160,3 +160,33 @@ def test_launch_count_per_tick(mix):
     per_tick = (vr.kernel_launches() - n0) / 5
     assert per_tick == 3 + math.ceil(50 / 8)
     B.close()
+
+
+def test_served_stream_results_equal_solo(mix):
+    """Requests arriving over time through the request loop (admission by footprint with a
+    budget that holds only some jobs at once) finish, and each result equals vrps_solve's."""
+    vr, probs, solo = mix
+    from paper_2602_09527_gb300 import serve
+    pools = {i: [probs[i][1]] for i in range(len(MIX))}
+    reqs = []
+    for t, i in enumerate([3, 0, 5, 1, 2, 4, 6]):
+        kw = _kw(MIX[i], probs[i][3], i)
+        reqs.append(serve.Request(key=i, b=dev(probs[i][2]), arrival=0.01 * t, alpha=kw["alpha"], gamma=kw["gamma"],
+                                  seed=kw["seed"], p=kw["p"], estimator=kw["estimator"], fgp_iters=kw["fgp_iters"],
+                                  max_iters=kw["max_iters"], storage=kw["storage"],
+                                  correction_epochs=kw["correction_epochs"]))
+        reqs[-1].job = i
+    budget = 3 * max(vr.job_footprint(probs[i][1], max_iters=100) for i in range(len(MIX)))
+    srv = serve.BatchServer(pools, budget)
+    st = srv.run(reqs)
+    srv.close()
+    assert st.completed == len(reqs)
+    assert all(l > 0 for l in st.latencies)
+    assert st.peak_bytes <= budget
+    for r, i in zip(reqs, [3, 0, 5, 1, 2, 4, 6]):
+        assert r.finished >= r.admitted >= r.arrival
+        # the request loop passes job word 0; compare with the solo run of the same settings
+        kw = _kw(MIX[i], probs[i][3], i)
+        kw["job"] = 0
+        x, _ = _solo(vr, probs[i][1], probs[i][2], kw)
+        assert torch.equal(r.x, x), i
