@@ -175,7 +175,6 @@ def test_served_stream_results_equal_solo(mix):
                                   seed=kw["seed"], p=kw["p"], estimator=kw["estimator"], fgp_iters=kw["fgp_iters"],
                                   max_iters=kw["max_iters"], storage=kw["storage"],
                                   correction_epochs=kw["correction_epochs"]))
-        reqs[-1].job = i
     budget = 3 * max(vr.job_footprint(probs[i][1], max_iters=100) for i in range(len(MIX)))
     srv = serve.BatchServer(pools, budget)
     st = srv.run(reqs)
