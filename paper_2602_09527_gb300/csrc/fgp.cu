@@ -288,9 +288,20 @@ constexpr int F3_TX = 32, F3_TY = 16, F3_ZC = 64;
 constexpr int F3_HX = F3_TX + 2, F3_HY = F3_TY + 2;   // z tile with a one-voxel halo
 constexpr int F3_XX = F3_TX + 1, F3_XY = F3_TY + 1;   // x tile with the + halo
 
-__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
-                                                             const float* __restrict__ wp, float* __restrict__ wn,
-                                                             Dims3 D, float tau, float step, float mom, int nonneg) {
+constexpr int F3_NT = F3_TX * F3_TY;
+constexpr int F3_ZSL = (F3_HX * F3_HY + F3_NT - 1) / F3_NT;   // z-tile elements per thread
+constexpr int F3_XSL = (F3_XX * F3_XY + F3_NT - 1) / F3_NT;   // x-tile elements per thread
+
+// Registers holding one plane's raw inputs while they are in flight (issued one plane ahead).
+struct F3Pre {
+  float c[F3_ZSL][3];   // w_k
+  float p[F3_ZSL][3];   // w_{k-1}
+  float v[F3_XSL];
+};
+
+__global__ void __launch_bounds__(F3_NT) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
+                                                      const float* __restrict__ wp, float* __restrict__ wn,
+                                                      Dims3 D, float tau, float step, float mom, int nonneg) {
   __shared__ float zs[3][F3_HY][F3_HX];   // extrapolated dual of the current plane (+ halo)
   __shared__ float z3p[F3_HY][F3_HX];     // z-component of the previous plane
   __shared__ float xs[2][F3_XY][F3_XX];   // x of two consecutive planes
@@ -298,24 +309,53 @@ __global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __rest
   const int ix0 = blockIdx.x * F3_TX, iy0 = blockIdx.y * F3_TY;
   const int zb = blockIdx.z * F3_ZC, ze = min(zb + F3_ZC, D.nz);
   const size_t nxy = (size_t)D.nx * D.ny;
-  auto load_z = [&](int g) {
-    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) {
+  const bool extra = mom != 0.f;
+  F3Pre pre;
+  // issue the loads of plane g (nothing is waited for until the registers are used)
+  auto prefetch = [&](int g) {
+#pragma unroll
+    for (int q = 0; q < F3_ZSL; ++q) {
+      const int e = tid + q * F3_NT;
       const int ly = e / F3_HX, lx = e - ly * F3_HX;
       const int gx = ix0 + lx - 1, gy = iy0 + ly - 1;
-      float a = 0.f, b = 0.f, c = 0.f;
-      if (gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny) {
-        const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
-        a = zval(wc, wp, p, mom);
-        b = zval(wc, wp, D.n + p, mom);
-        c = zval(wc, wp, 2 * D.n + p, mom);
+      const bool in = e < F3_HX * F3_HY && gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny;
+      const size_t pp = (size_t)g * nxy + (size_t)gy * D.nx + gx;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        pre.c[q][k] = in ? wc[k * D.n + pp] : 0.f;
+        pre.p[q][k] = (in && extra) ? wp[k * D.n + pp] : 0.f;
       }
-      zs[0][ly][lx] = a;
-      zs[1][ly][lx] = b;
-      zs[2][ly][lx] = c;
+    }
+#pragma unroll
+    for (int q = 0; q < F3_XSL; ++q) {
+      const int e = tid + q * F3_NT;
+      const int ly = e / F3_XX, lx = e - ly * F3_XX;
+      const int gx = ix0 + lx, gy = iy0 + ly;
+      const bool in = e < F3_XX * F3_XY && gx < D.nx && gy < D.ny;
+      pre.v[q] = in ? v[(size_t)g * nxy + (size_t)gy * D.nx + gx] : 0.f;
     }
   };
+  // z = w_k + mom (w_k - w_{k-1}) of the prefetched plane into shared memory; keeps its v
+  float vv[F3_XSL];
+  auto commit = [&]() {
+#pragma unroll
+    for (int q = 0; q < F3_ZSL; ++q) {
+      const int e = tid + q * F3_NT;
+      if (e < F3_HX * F3_HY) {
+        const int ly = e / F3_HX, lx = e - ly * F3_HX;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          zs[k][ly][lx] = extra ? fmaf(mom, __fsub_rn(pre.c[q][k], pre.p[q][k]), pre.c[q][k]) : pre.c[q][k];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < F3_XSL; ++q) vv[q] = pre.v[q];
+  };
   auto comp_x = [&](int g, float (*xb)[F3_XX]) {
-    for (int e = tid; e < F3_XX * F3_XY; e += F3_TX * F3_TY) {
+#pragma unroll
+    for (int q = 0; q < F3_XSL; ++q) {
+      const int e = tid + q * F3_NT;
+      if (e >= F3_XX * F3_XY) continue;
       const int ly = e / F3_XX, lx = e - ly * F3_XX;
       const int gx = ix0 + lx, gy = iy0 + ly;
       float xv = 0.f;
@@ -328,22 +368,28 @@ __global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __rest
         if (gy > 0) d -= zs[1][hy - 1][hx];
         if (g < D.nz - 1) d += zs[2][hy][hx];
         if (g > 0) d -= z3p[hy][hx];
-        xv = fmaf(tau, d, v[(size_t)g * nxy + (size_t)gy * D.nx + gx]);
+        xv = fmaf(tau, d, vv[q]);
         if (nonneg) xv = fmaxf(xv, 0.f);
       }
       xb[ly][lx] = xv;
     }
   };
+  auto copy_z3 = [&]() {
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_NT) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
+  };
   // prologue: z3 of the plane below the chunk, then plane zb and its x
   if (zb > 0) {
-    load_z(zb - 1);
+    prefetch(zb - 1);
+    commit();
     __syncthreads();
-    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
+    copy_z3();
   } else {
-    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = 0.f;
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_NT) z3p[e / F3_HX][e % F3_HX] = 0.f;
   }
+  prefetch(zb);
   __syncthreads();
-  load_z(zb);
+  commit();
+  if (zb + 1 < D.nz) prefetch(zb + 1);
   __syncthreads();
   comp_x(zb, xs[0]);
   __syncthreads();
@@ -353,9 +399,10 @@ __global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __rest
   for (int g = zb; g < ze; ++g) {
     const int cur = (g - zb) & 1, nxt = cur ^ 1;
     if (g + 1 < D.nz) {
-      for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
+      copy_z3();
       __syncthreads();
-      load_z(g + 1);
+      commit();                                  // plane g+1, loaded during the last plane
+      if (g + 2 < D.nz && g + 1 < ze) prefetch(g + 2);
       __syncthreads();
       comp_x(g + 1, xs[nxt]);
       __syncthreads();
@@ -366,11 +413,11 @@ __global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __rest
       const float d2 = gy < D.ny - 1 ? xs[cur][ty + 1][tx] - xc : 0.f;
       const float d3 = g < D.nz - 1 ? xs[nxt][ty][tx] - xc : 0.f;
       const float q1 = fmaf(step, d1, zo0), q2 = fmaf(step, d2, zo1), q3 = fmaf(step, d3, zo2);
-      const float den = fmaxf(1.f, sqrtf(q1 * q1 + q2 * q2 + q3 * q3));
-      const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
-      wn[p] = q1 / den;
-      wn[D.n + p] = q2 / den;
-      wn[2 * D.n + p] = q3 / den;
+      const float den = fmaxf(1.f, sqrtf(fmaf(q1, q1, fmaf(q2, q2, __fmul_rn(q3, q3)))));
+      const size_t pp = (size_t)g * nxy + (size_t)gy * D.nx + gx;
+      wn[pp] = q1 / den;
+      wn[D.n + pp] = q2 / den;
+      wn[2 * D.n + pp] = q3 / den;
     }
     if (g + 1 < D.nz) {
       zo0 = zs[0][ty + 1][tx + 1];
