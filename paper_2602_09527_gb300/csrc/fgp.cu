@@ -288,28 +288,9 @@ constexpr int F3_TX = 32, F3_TY = 16, F3_ZC = 64;
 constexpr int F3_HX = F3_TX + 2, F3_HY = F3_TY + 2;   // z tile with a one-voxel halo
 constexpr int F3_XX = F3_TX + 1, F3_XY = F3_TY + 1;   // x tile with the + halo
 
-constexpr int F3_NT = F3_TX * F3_TY;
-constexpr int F3_ZE = F3_HX * F3_HY;                 // z-tile elements
-constexpr int F3_XE = F3_XX * F3_XY;                 // x-tile elements
-constexpr int F3_STAGE = 6 * F3_ZE + F3_XE;          // raw w_k, w_{k-1} (3 each) and v of one plane
-constexpr size_t F3_SMEM = sizeof(float) * 2 * F3_STAGE;   // two planes in flight
-
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(valid ? 4 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// The inputs of each plane are copied asynchronously into a shared stage (cp.async, zero-filled
-// outside the volume) one plane ahead of their use, so the loads overlap the stencil work of
-// the plane before.
-__global__ void __launch_bounds__(F3_NT) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
-                                                      const float* __restrict__ wp, float* __restrict__ wn,
-                                                      Dims3 D, float tau, float step, float mom, int nonneg) {
-  extern __shared__ float stage[];          // [2][F3_STAGE]
+__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
+                                                             const float* __restrict__ wp, float* __restrict__ wn,
+                                                             Dims3 D, float tau, float step, float mom, int nonneg) {
   __shared__ float zs[3][F3_HY][F3_HX];   // extrapolated dual of the current plane (+ halo)
   __shared__ float z3p[F3_HY][F3_HX];     // z-component of the previous plane
   __shared__ float xs[2][F3_XY][F3_XX];   // x of two consecutive planes
@@ -317,43 +298,24 @@ __global__ void __launch_bounds__(F3_NT) fgp3d_stream(const float* __restrict__ 
   const int ix0 = blockIdx.x * F3_TX, iy0 = blockIdx.y * F3_TY;
   const int zb = blockIdx.z * F3_ZC, ze = min(zb + F3_ZC, D.nz);
   const size_t nxy = (size_t)D.nx * D.ny;
-  const bool extra = mom != 0.f;
-  auto issue = [&](int g) {
-    float* st = stage + (g & 1) * F3_STAGE;
-    for (int e = tid; e < F3_ZE; e += F3_NT) {
+  auto load_z = [&](int g) {
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) {
       const int ly = e / F3_HX, lx = e - ly * F3_HX;
       const int gx = ix0 + lx - 1, gy = iy0 + ly - 1;
-      const bool in = gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny;
-      const size_t pp = in ? (size_t)g * nxy + (size_t)gy * D.nx + gx : 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        cp_async4(st + k * F3_ZE + e, wc + k * D.n + pp, in);
-        if (extra) cp_async4(st + (3 + k) * F3_ZE + e, wp + k * D.n + pp, in);
+      float a = 0.f, b = 0.f, c = 0.f;
+      if (gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny) {
+        const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
+        a = zval(wc, wp, p, mom);
+        b = zval(wc, wp, D.n + p, mom);
+        c = zval(wc, wp, 2 * D.n + p, mom);
       }
-    }
-    for (int e = tid; e < F3_XE; e += F3_NT) {
-      const int ly = e / F3_XX, lx = e - ly * F3_XX;
-      const int gx = ix0 + lx, gy = iy0 + ly;
-      const bool in = gx < D.nx && gy < D.ny;
-      cp_async4(st + 6 * F3_ZE + e, v + (in ? (size_t)g * nxy + (size_t)gy * D.nx + gx : 0), in);
-    }
-    cp_async_commit();
-  };
-  // z = w_k + mom (w_k - w_{k-1}) of plane g (landed in its stage) into zs
-  auto commit = [&](int g) {
-    const float* st = stage + (g & 1) * F3_STAGE;
-    for (int e = tid; e < F3_ZE; e += F3_NT) {
-      const int ly = e / F3_HX, lx = e - ly * F3_HX;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float c = st[k * F3_ZE + e];
-        zs[k][ly][lx] = extra ? fmaf(mom, __fsub_rn(c, st[(3 + k) * F3_ZE + e]), c) : c;
-      }
+      zs[0][ly][lx] = a;
+      zs[1][ly][lx] = b;
+      zs[2][ly][lx] = c;
     }
   };
   auto comp_x = [&](int g, float (*xb)[F3_XX]) {
-    const float* sv = stage + (g & 1) * F3_STAGE + 6 * F3_ZE;
-    for (int e = tid; e < F3_XE; e += F3_NT) {
+    for (int e = tid; e < F3_XX * F3_XY; e += F3_TX * F3_TY) {
       const int ly = e / F3_XX, lx = e - ly * F3_XX;
       const int gx = ix0 + lx, gy = iy0 + ly;
       float xv = 0.f;
@@ -366,36 +328,22 @@ __global__ void __launch_bounds__(F3_NT) fgp3d_stream(const float* __restrict__ 
         if (gy > 0) d -= zs[1][hy - 1][hx];
         if (g < D.nz - 1) d += zs[2][hy][hx];
         if (g > 0) d -= z3p[hy][hx];
-        xv = fmaf(tau, d, sv[e]);
+        xv = fmaf(tau, d, v[(size_t)g * nxy + (size_t)gy * D.nx + gx]);
         if (nonneg) xv = fmaxf(xv, 0.f);
       }
       xb[ly][lx] = xv;
     }
   };
-  auto copy_z3 = [&]() {
-    for (int e = tid; e < F3_ZE; e += F3_NT) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
-  };
-  // prologue: z3 of the plane below the chunk, then plane zb and its x; plane zb + 1 in flight
+  // prologue: z3 of the plane below the chunk, then plane zb and its x
   if (zb > 0) {
-    issue(zb - 1);
-    cp_async_wait<0>();
+    load_z(zb - 1);
     __syncthreads();
-    commit(zb - 1);
-    __syncthreads();
-    copy_z3();
-    __syncthreads();   // stage (zb - 1) & 1 = (zb + 1) & 1 is reused below
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
   } else {
-    for (int e = tid; e < F3_ZE; e += F3_NT) z3p[e / F3_HX][e % F3_HX] = 0.f;
-  }
-  issue(zb);
-  if (zb + 1 < D.nz) {
-    issue(zb + 1);
-    cp_async_wait<1>();
-  } else {
-    cp_async_wait<0>();
+    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = 0.f;
   }
   __syncthreads();
-  commit(zb);
+  load_z(zb);
   __syncthreads();
   comp_x(zb, xs[0]);
   __syncthreads();
@@ -405,14 +353,9 @@ __global__ void __launch_bounds__(F3_NT) fgp3d_stream(const float* __restrict__ 
   for (int g = zb; g < ze; ++g) {
     const int cur = (g - zb) & 1, nxt = cur ^ 1;
     if (g + 1 < D.nz) {
-      // plane g's stage is free (committed and used last round): start plane g + 2 into it
-      const bool ahead = g + 2 < D.nz && g + 1 < ze;
-      if (ahead) issue(g + 2);
-      copy_z3();
-      if (ahead) cp_async_wait<1>();
-      else cp_async_wait<0>();
+      for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
       __syncthreads();
-      commit(g + 1);
+      load_z(g + 1);
       __syncthreads();
       comp_x(g + 1, xs[nxt]);
       __syncthreads();
@@ -423,11 +366,11 @@ __global__ void __launch_bounds__(F3_NT) fgp3d_stream(const float* __restrict__ 
       const float d2 = gy < D.ny - 1 ? xs[cur][ty + 1][tx] - xc : 0.f;
       const float d3 = g < D.nz - 1 ? xs[nxt][ty][tx] - xc : 0.f;
       const float q1 = fmaf(step, d1, zo0), q2 = fmaf(step, d2, zo1), q3 = fmaf(step, d3, zo2);
-      const float den = fmaxf(1.f, sqrtf(fmaf(q1, q1, fmaf(q2, q2, __fmul_rn(q3, q3)))));
-      const size_t pp = (size_t)g * nxy + (size_t)gy * D.nx + gx;
-      wn[pp] = q1 / den;
-      wn[D.n + pp] = q2 / den;
-      wn[2 * D.n + pp] = q3 / den;
+      const float den = fmaxf(1.f, sqrtf(q1 * q1 + q2 * q2 + q3 * q3));
+      const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
+      wn[p] = q1 / den;
+      wn[D.n + p] = q2 / den;
+      wn[2 * D.n + p] = q3 / den;
     }
     if (g + 1 < D.nz) {
       zo0 = zs[0][ty + 1][tx + 1];
@@ -535,7 +478,6 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     const float* rc = rw;
     w_final = rc;
   } else {
-    VRPS_TRY(smem_opt_in((const void*)fgp3d_stream, F3_SMEM));
     float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};
     int cur = 0, prev = 0;
     double t_prev = 1.0;
@@ -553,7 +495,7 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       {
         // read v, w_k (and w_{k-1} when extrapolating), write w_{k+1}
         LaunchScope _ls("fgp3d_stream", s, 4.0 * g->n * (mk != 0.f ? 10 : 7));
-        VRPS_CUDA(launch_kernel(fgp3d_stream, grid, dim3(F3_TX, F3_TY), F3_SMEM, s, v, (const float*)buf[cur],
+        VRPS_CUDA(launch_kernel(fgp3d_stream, grid, dim3(F3_TX, F3_TY), (size_t)0, s, v, (const float*)buf[cur],
                                 (const float*)buf[prev], buf[nxt], D, tau, step, mk, nonneg));
       }
       VRPS_LAUNCHED("fgp_iter");
