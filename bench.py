@@ -411,6 +411,9 @@ def bench_batch(args, rank, world, local):
     w = WORKLOADS_BATCH[wl]
     jobs = make_batch_jobs(w, rank)
     geoms = [vr.Geometry.from_spec(j["spec"]) for j in jobs]
+    if not args.no_autotune:
+        for g in geoms:
+            vr.autotune(g, reps=3)
     bs = [torch.tensor(j["b"].astype(np.float32).ravel(), device="cuda") for j in jobs]
     kws = []
     for j, (J, g) in enumerate(zip(jobs, geoms)):
@@ -544,6 +547,9 @@ def bench_serve(args, rank, world, local):
         spec = synthetic.Par2DSpec(nx=side, ny=side, pixel=1.0, angles=synthetic.uniform_angles(na, math.pi),
                                    n_bins=nb, bin_spacing=1.0, n_subsets=20)
         pools[side] = [vr.Geometry.from_spec(spec) for _ in range(w["handles"])]
+        if not args.no_autotune:
+            for g in pools[side]:
+                vr.autotune(g, reps=2)
         lips[side] = vr.power_iteration(pools[side][0], 50, seed=w["seed"])
         data[side] = []
         for _ in range(w["pool"]):
@@ -644,6 +650,7 @@ def main():
     ap.add_argument("--workload", default="par2d_512",
                     choices=list(WORKLOADS) + list(WORKLOADS_3D) + list(WORKLOADS_BATCH) + list(WORKLOADS_SERVE))
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="served stream: arrival window (s)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in 2D launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--alpha", type=float, default=None, help="override the workload's TV weight")
     ap.add_argument("--profile-once", type=int, default=0, metavar="K",
@@ -689,6 +696,7 @@ def main():
 
     P = make_problem(wl, rank)
     g = vr.Geometry.from_spec(P.spec)
+    tuned = None if args.no_autotune else vr.autotune(g)
     N = w["n_subsets"]
     b_dev = torch.tensor(P.b.astype(np.float32).ravel(), device="cuda")
     b_host = torch.tensor(P.b.astype(np.float32).ravel()).pin_memory()
@@ -815,7 +823,8 @@ def main():
                    "alpha": w["alpha"], "gamma": "1/L", "k_star": k_star, "target_reached": reached,
                    "f_star": f_star, "gap_at_k_star": (gap_check - f_star) / abs(f_star),
                    "prox_calls": rep["prox_calls"], "snapshots": rep["snapshots"], "passes": rep["passes"],
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
+                   "launch_shapes": tuned if tuned else "built-in"},
         "e2e": {"value": round(statistics.mean(e2e), 6), "unit": "s", "h2d_bytes_per_step": 4 * g.m,
                 "d2h_bytes_per_step": 4 * g.n},
         "gpu_launches": int(launches),

@@ -103,6 +103,16 @@ int vrps_geom_sizes(const vrps_geom* g, int subset, int64_t* n, int64_t* m, int*
  * the host in float64.  One sample is one "ray-voxel" of the projector throughput metric. */
 int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
 
+/* Launch-shape autotuner (no counterpart in the paper).  For a 2D geometry, times subset 0's
+ * forward for shared-memory bands of 16, 24, 32, 48, 64 and 96 KB and its adjoint with one
+ * and two pixels per thread (CUDA events, best of `reps` after one warm-up) and keeps the
+ * fastest of each in the handle; later projections, solves and batched jobs on the handle
+ * use them.  Results change only the grouping of floating-point sums (outputs agree to
+ * rounding).  out3 (HOST, nullable): chosen band bytes, chosen pixels per thread, and the
+ * tuned forward + adjoint time in microseconds.  3D geometries: no-op.  Errors: INVALID_ARG,
+ * OUT_OF_MEMORY, CUDA. */
+int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream);
+
 /* ---------------------------------------------------------------- operators
  * y = A_i x  (Section 1.2: the forward operator of subset i; i = -1 for A).
  * x: [n] image.  y: [rows(i) * row_len] sinogram rows of subset i, overwritten.

@@ -84,6 +84,7 @@ def _load():
         "vrps_geom_free": (i, [vp]),
         "vrps_geom_sizes": (i, [vp, i, P(i64), P(i64), P(i), P(i), P(i)]),
         "vrps_geom_samples": (i, [vp, i, P(i64)]),
+        "vrps_autotune": (i, [vp, i, P(d), vp]),
         "vrps_proj_fwd": (i, [vp, i, vp, vp, vp]),
         "vrps_proj_adj": (i, [vp, i, vp, vp, vp]),
         "vrps_prox_tv": (i, [vp, vp, vp, ctypes.c_float, i, i, vp, vp]),
@@ -231,6 +232,13 @@ def vrps_geom_par2d(*a, **k):
 
 def vrps_geom_cone3d(*a, **k):
     return Geometry.cone3d(*a, **k)
+
+
+def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
+    """vrps_autotune: choose the 2D forward band and adjoint pixels per thread by timing."""
+    out = (ctypes.c_double * 3)()
+    _check(lib.vrps_autotune(g.handle, int(reps), out, _stream(stream)))
+    return {"fwd_band_bytes": int(out[0]), "adj_pixels_per_thread": int(out[1]), "fwd_adj_us": float(out[2])}
 
 
 def proj_fwd(g: Geometry, subset: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):

@@ -521,6 +521,84 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples) {
   return VRPS_OK;
 }
 
+int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
+  VRPS_TRY(check_geom(g));
+  if (reps < 1) return fail(VRPS_ERR_INVALID_ARG, "reps must be >= 1");
+  if (g->dims != 2) return VRPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int* ids = nullptr;
+  int rows = 0;
+  VRPS_TRY(subset_rows(g, 0, &ids, &rows));
+  Workspace& w = g->ws;
+  VRPS_TRY(ensure(&w.img, (size_t)g->n));
+  VRPS_TRY(ensure(&w.img2, (size_t)g->n));
+  VRPS_TRY(ensure(&w.sino, (size_t)g->m));
+  VRPS_TRY(fill(w.img, 1.f, g->n, s));
+  VRPS_TRY(transpose2d(w.img, w.img2, g->ny, g->nx, s));
+  cudaEvent_t e0, e1;
+  VRPS_CUDA(cudaEventCreate(&e0));
+  VRPS_CUDA(cudaEventCreate(&e1));
+  auto timed = [&](auto&& launch, float* best) -> int {
+    VRPS_TRY(launch());   // warm-up
+    *best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      VRPS_CUDA(cudaEventRecord(e0, s));
+      VRPS_TRY(launch());
+      VRPS_CUDA(cudaEventRecord(e1, s));
+      VRPS_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      VRPS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < *best) *best = ms;
+    }
+    return VRPS_OK;
+  };
+  FwdOut fo{w.sino, nullptr, nullptr};
+  const int cand[] = {16 << 10, 24 << 10, 32 << 10, 48 << 10, 64 << 10, 96 << 10};
+  int best_bytes = 0;
+  float best_f = 1e30f;
+  for (int c : cand) {
+    g->tune_fwd_bytes = c;
+    float t = 0.f;
+    const int rc = timed([&]() { return fwd2d(g, w.img, w.img2, ids, rows, FWD_PLAIN, fo, s); }, &t);
+    if (rc != VRPS_OK) {
+      g->tune_fwd_bytes = 0;
+      return rc;
+    }
+    if (t < best_f) {
+      best_f = t;
+      best_bytes = c;
+    }
+  }
+  g->tune_fwd_bytes = best_bytes;
+  UpdateArgs ua;
+  std::memset(&ua, 0, sizeof(ua));
+  ua.out = w.img;
+  int best_two = 0;
+  float best_a = 1e30f;
+  for (int two = 0; two < 2; ++two) {
+    g->tune_adj_two = two;
+    float t = 0.f;
+    const int rc = timed([&]() { return adj2d(g, w.sino, ids, rows, ua, s); }, &t);
+    if (rc != VRPS_OK) {
+      g->tune_adj_two = -1;
+      return rc;
+    }
+    if (t < best_a) {
+      best_a = t;
+      best_two = two;
+    }
+  }
+  g->tune_adj_two = best_two;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out3) {
+    out3[0] = best_bytes;
+    out3[1] = best_two ? 2 : 1;
+    out3[2] = 1e3 * (double)(best_f + best_a);
+  }
+  return VRPS_OK;
+}
+
 int vrps_proj_fwd(const vrps_geom* g, int subset, const float* x, float* y, vrps_stream_t stream) {
   VRPS_TRY(check_geom(g));
   if (!x || !y) return fail(VRPS_ERR_INVALID_ARG, "x or y is NULL");

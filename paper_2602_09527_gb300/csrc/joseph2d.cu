@@ -476,7 +476,8 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   P.o = o;
   const int maxw = g->nx > g->ny ? g->nx : g->ny;   // widest line (row of x or of x^T)
   const int maxl = maxw;
-  int band = FWD_BAND_BYTES / (int)(sizeof(float) * (maxw + 2 * FWD_PAD));
+  const int band_bytes = g->tune_fwd_bytes > 0 ? g->tune_fwd_bytes : FWD_BAND_BYTES;
+  int band = band_bytes / (int)(sizeof(float) * (maxw + 2 * FWD_PAD));
   if (band < 1) band = 1;
   if (band > maxl) band = maxl;
   P.band = band;
@@ -550,7 +551,7 @@ int adj2d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, co
   P.u = u;
   *smem = sizeof(float) * (size_t)P.chunk * P.fp;
   // two pixels per thread (shared per-angle parameters) unless the image is very small
-  const bool two = (long long)g->nx * g->ny > 512LL * g->sms;
+  const bool two = g->tune_adj_two >= 0 ? g->tune_adj_two != 0 : (long long)g->nx * g->ny > 512LL * g->sms;
   const int ty = (ADJ_THREADS / ADJ_TX) * (two ? 2 : 1);
   *variant = (g->adj_nc == 2 ? 2 : 0) + (two ? 1 : 0);
   *tiles_x = (g->nx + ADJ_TX - 1) / ADJ_TX;

@@ -185,6 +185,9 @@ struct vrps_geom {
   vrps::AngleInfo2D* ang2d = nullptr;
   int adj_fp = 0;        // footprint slots per angle of the 2D adjoint tile
   int adj_nc = 0;        // candidate bins per pixel and angle
+  // launch shapes chosen by vrps_autotune (0 / -1: built-in defaults)
+  int tune_fwd_bytes = 0;   // shared-memory band of the 2D forward (bytes)
+  int tune_adj_two = -1;    // 2D adjoint: two pixels per thread (1) or one (0)
   // 3D tables
   vrps::RayInfo3D* ray3d = nullptr;     // [n_views][nu]
   vrps::ViewInfo3D* view3d = nullptr;   // [n_views]

@@ -139,3 +139,22 @@ def test_full_size_512_sampled_angles():
     # subset forward equals the matching rows of the full forward (same kernels, same rays)
     ys = host(vr.proj_fwd(g, 7, dev(x))).reshape(-1, 768)
     assert np.array_equal(ys, y[og.subset(7)])
+
+
+def test_autotuned_shapes_keep_parity():
+    """vrps_autotune picks a forward band and adjoint shape by timing; the tuned projector
+    still matches the oracle at every candidate's tolerance."""
+    vr = _vr()
+    spec = synthetic.Par2DSpec(256, 192, 1.0, synthetic.uniform_angles(120, math.pi), 300, 1.0, 6)
+    g = vr.Geometry.from_spec(spec)
+    og = J.Geometry2D.from_spec(spec)
+    t = vr.autotune(g, reps=2)
+    assert t["fwd_band_bytes"] in (16 << 10, 24 << 10, 32 << 10, 48 << 10, 64 << 10, 96 << 10)
+    assert t["adj_pixels_per_thread"] in (1, 2) and t["fwd_adj_us"] > 0
+    rng = np.random.default_rng(31)
+    x = rng.uniform(0, 1, size=(192, 256))
+    rows = list(range(2, 120, 6))
+    y = host(vr.proj_fwd(g, 2, dev(x))).reshape(len(rows), 300)
+    assert rel(y, J.forward(og, x, rows)) < TOL
+    r = rng.standard_normal((len(rows), 300))
+    assert rel(host(vr.proj_adj(g, 2, dev(r))), J.adjoint(og, r, rows)) < TOL
