@@ -77,6 +77,11 @@ WORKLOADS_SERVE = {
                   budget_gb=120.0, seed=20260209),
 }
 
+# Operator costs (optional), the structure of the paper's cost figure on the 512^2 / 720-angle
+# geometry: one TV prox at K = 10 and K = 100 FGP iterations, one full gradient, and one
+# subset gradient for N = 10 ... 720 subsets.
+WORKLOADS_OPS = {"ops": dict(base="par2d_512", ks=(10, 100), ns=(10, 20, 50, 100, 200, 400, 720), reps=20)}
+
 # Iteration counts of the replayed trajectory (same seed and draws on any machine), used only
 # by the CPU oracle legs to scale a bounded sample up to a whole reconstruction.  Recorded from
 # the GPU replay of this workload; the GPU arm recomputes them every run.
@@ -641,6 +646,62 @@ def bench_serve(args, rank, world, local):
             g.close()
 
 
+# --------------------------------------------------------------------------- operator costs
+def bench_ops(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2602_09527_gb300 as vr
+    w = WORKLOADS_OPS[args.workload]
+    base = WORKLOADS[w["base"]]
+    P = make_problem(w["base"], rank)
+    b = torch.tensor(P.b.astype(np.float32).ravel(), device="cuda")
+    x = torch.rand(P.spec.nx * P.spec.ny, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def time_it(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(w["reps"]):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / w["reps"] * 1e3   # microseconds
+
+    out_rows = {}
+    for N in w["ns"]:
+        spec = synthetic.Par2DSpec(P.spec.nx, P.spec.ny, P.spec.pixel, P.spec.angles, P.spec.n_bins, P.spec.bin_spacing, N)
+        g = vr.Geometry.from_spec(spec)
+        if not args.no_autotune:
+            vr.autotune(g, reps=3)
+        y = torch.empty(g.m, device="cuda")
+        xa = torch.empty(g.n, device="cuda")
+        rows = g.sizes(0).rows
+        ysub = torch.empty(rows * spec.n_bins, device="cuda")
+        t_sub = time_it(lambda: (vr.proj_fwd(g, 0, x, ysub), vr.proj_adj(g, 0, ysub, xa)))
+        if N == w["ns"][0]:
+            out_rows["full_gradient_us"] = round(time_it(lambda: (vr.proj_fwd(g, -1, x, y), vr.proj_adj(g, -1, y, xa))), 2)
+            for K in w["ks"]:
+                dual = torch.zeros(2 * g.n, device="cuda")
+                out_rows[f"prox_K{K}_us"] = round(time_it(lambda: vr.prox_tv(g, x, 0.01, K, dual=dual, x=xa)), 2)
+        out_rows[f"subset_gradient_N{N}_us"] = round(t_sub, 2)
+        g.close()
+    full = out_rows["full_gradient_us"]
+    out = {
+        "metric": "operator costs (us)", "value": full, "unit": "us", "n_gpus": 1, "steps": w["reps"], "warmup": 3,
+        "ms_per_step": round(full / 1e3, 4), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded ellipse phantom)",
+        "config": {"workload": args.workload, "geometry": "512x512, 720 angles, 768 bins",
+                   "gradient": "forward (plain) + adjoint (plain) launches of the CUDA path, CUDA events"},
+        "operators": out_rows,
+        "subset_over_full": {f"N{N}": round(out_rows[f"subset_gradient_N{N}_us"] / full, 4) for N in w["ns"]},
+        "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,7 +709,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default="par2d_512",
-                    choices=list(WORKLOADS) + list(WORKLOADS_3D) + list(WORKLOADS_BATCH) + list(WORKLOADS_SERVE))
+                    choices=list(WORKLOADS) + list(WORKLOADS_3D) + list(WORKLOADS_BATCH) + list(WORKLOADS_SERVE)
+                    + list(WORKLOADS_OPS))
     ap.add_argument("--serve-seconds", type=float, default=0.0, help="served stream: arrival window (s)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in 2D launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -661,7 +723,8 @@ def main():
         args.warmup = 3
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     wl = args.workload
-    w = WORKLOADS.get(wl) or WORKLOADS_3D.get(wl) or WORKLOADS_BATCH.get(wl) or WORKLOADS_SERVE[wl]
+    w = (WORKLOADS.get(wl) or WORKLOADS_3D.get(wl) or WORKLOADS_BATCH.get(wl) or WORKLOADS_SERVE.get(wl)
+         or WORKLOADS_OPS[wl])
     if args.alpha is not None:
         w["alpha"] = args.alpha
 
@@ -673,6 +736,8 @@ def main():
         return bench_batch(args, rank, world, local)
     if wl in WORKLOADS_SERVE:
         return bench_serve(args, rank, world, local)
+    if wl in WORKLOADS_OPS:
+        return bench_ops(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -853,7 +918,7 @@ def reference_arm(args, rank, world):
     wl = args.workload
     if wl in WORKLOADS_3D:
         return reference_arm_3d(args, wl)
-    if wl in WORKLOADS_BATCH or wl in WORKLOADS_SERVE:
+    if wl in WORKLOADS_BATCH or wl in WORKLOADS_SERVE or wl in WORKLOADS_OPS:
         print(json.dumps({"impl": "reference", "unavailable": "the batched and served workloads have no oracle "
                           "arm; their baseline is the per-job float32 solver timed inside the own arm"}))
         return
