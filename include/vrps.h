@@ -254,6 +254,18 @@ int vrps_solve(const float* b, const vrps_geom* g, double alpha, int algo, doubl
                uint64_t seed, const vrps_solve_opts* opts, float* x_out, vrps_report* report,
                vrps_stream_t stream);
 
+/* Reference minimiser of Eq. (tomography_problem) by preconditioned PDHG (the paper's long-run
+ * solver for x* and F*, Section 2.1 and Section 3): Chambolle-Pock on K = [A; D] with the
+ * diagonal steps of Pock and Chambolle (2011): tau_j = 1 / (column sum of A + column sum of
+ * |D|), sigma = 1 / ray sum of A for the data rows and 1/2 for the difference rows; x0 = 0.
+ * b: [m] device sinogram in natural angle order.  nonneg: include I_{x>=0}.  Every
+ * eval_every iterations (0: never) F(x) is evaluated into the HOST array history
+ * [history_cap][2] (iteration, F).  x_out: [n] device.  The call allocates its own
+ * 3n + (dims) n + 3m floats and frees them before returning (synchronous).  Errors:
+ * INVALID_ARG, OUT_OF_MEMORY, CUDA, DIVERGED. */
+int vrps_pdhg(const float* b, const vrps_geom* g, double alpha, int iters, int nonneg, int eval_every,
+              double* history, int history_cap, float* x_out, vrps_report* report, vrps_stream_t stream);
+
 /* ---------------------------------------------------------------- batched / served jobs
  * Many independent 2D VR-ProxSkip reconstructions (Algorithm 1 with a variance-reduced
  * estimator, x0 = 0) advancing together; no counterpart in the paper, which runs one problem.

@@ -7,9 +7,9 @@ this package is its thin ctypes binding.  Entry points keep the C names without 
 (``vrps_batch_*``).
 """
 from ._binding import (ALGOS, ESTIMATORS, Batch, autotune, Geometry, Report, SolveOpts, VrpsError, job_footprint,
-                       kernel_launches, lib, objective, philox_schedule, power_iteration, profile_enable,
+                       kernel_launches, lib, objective, pdhg, philox_schedule, power_iteration, profile_enable,
                        profile_read, prox_tv, prox_tv2d_noalloc, proj_adj, proj_fwd, solve)
 
 __all__ = ["ALGOS", "ESTIMATORS", "Batch", "autotune", "Geometry", "job_footprint", "Report", "SolveOpts", "VrpsError", "kernel_launches", "lib",
-           "objective", "philox_schedule", "power_iteration", "profile_enable", "profile_read", "prox_tv",
+           "objective", "pdhg", "philox_schedule", "power_iteration", "profile_enable", "profile_read", "prox_tv",
            "prox_tv2d_noalloc", "proj_adj", "proj_fwd", "solve"]

@@ -97,6 +97,7 @@ def _load():
         "vrps_kernel_launches": (u64, []),
         "vrps_profile_enable": (i, [i]),
         "vrps_profile_read": (i, [P(KernelStat), i, P(i)]),
+        "vrps_pdhg": (i, [vp, vp, d, i, i, i, P(d), i, vp, P(Report), vp]),
         "vrps_batch_create": (i, [P(vp)]),
         "vrps_batch_free": (i, [vp]),
         "vrps_batch_set_graphs": (i, [vp, i]),
@@ -349,6 +350,20 @@ def solve(b: torch.Tensor, g: Geometry, alpha: float, algo: str = "VR_PROXSKIP",
         for e in range(min(rep.evaluations, history_cap)):
             h.append([hist[4 * e + q] for q in range(4)])
     return x_out, rd, h
+
+
+def pdhg(b: torch.Tensor, g: Geometry, alpha: float, iters: int, *, nonneg: bool = True, eval_every: int = 0,
+         history_cap: int = 0, x_out: torch.Tensor | None = None, stream=None):
+    """vrps_pdhg: preconditioned PDHG reference run.  Returns (x, report dict, history)."""
+    if x_out is None:
+        x_out = torch.empty(g.n, device=b.device, dtype=torch.float32)
+    hist = (ctypes.c_double * (2 * history_cap))() if history_cap > 0 else None
+    rep = Report()
+    _check(lib.vrps_pdhg(_dev_ptr(b, "b", g.m), g.handle, float(alpha), int(iters), 1 if nonneg else 0,
+                         int(eval_every), hist, int(history_cap), _dev_ptr(x_out, "x_out", g.n), ctypes.byref(rep),
+                         _stream(stream)))
+    h = [(hist[2 * e], hist[2 * e + 1]) for e in range(min(rep.evaluations, history_cap))] if hist else []
+    return x_out, rep.as_dict(), h
 
 
 def kernel_launches() -> int:
