@@ -268,6 +268,7 @@ def bench_3d(args, rank, world, local):
     w = WORKLOADS_3D[wl]
     P = make_problem3(wl, rank)
     g = vr.Geometry.from_spec(P.spec)
+    tuned = None if args.no_autotune else vr.autotune(g, reps=2)
     N = w["n_subsets"]
     iters = w["epochs"] * N
     b_dev = torch.tensor(P.b.astype(np.float32).ravel(), device="cuda")
@@ -367,7 +368,8 @@ def bench_3d(args, rank, world, local):
                    "algo": "ProxSVRGSkip", "p": w["p"], "fgp_iters": w["fgp_iters"], "alpha": w["alpha"],
                    "gamma": "1/L (30 power iterations)", "epochs_per_step": w["epochs"],
                    "prox_calls": rep["prox_calls"], "snapshots": rep["snapshots"],
-                   "l2": "flushed between steps (256 MB write); working set > L2", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between steps (256 MB write); working set > L2", "parallelism": f"replicas x{world}",
+                   "launch_shapes": tuned if tuned else "built-in"},
         "e2e": {"value": round(statistics.mean(e2e) / w["epochs"], 6), "unit": "s",
                 "h2d_bytes_per_step": 4 * g.m, "d2h_bytes_per_step": 4 * g.n},
         "gpu_launches": int(launches),

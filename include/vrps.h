@@ -109,8 +109,9 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
  * fastest of each in the handle; later projections, solves and batched jobs on the handle
  * use them.  Results change only the grouping of floating-point sums (outputs agree to
  * rounding).  out3 (HOST, nullable): chosen band bytes, chosen pixels per thread, and the
- * tuned forward + adjoint time in microseconds.  3D geometries: no-op.  Errors: INVALID_ARG,
- * OUT_OF_MEMORY, CUDA. */
+ * tuned forward + adjoint time in microseconds.  3D geometries: times three iterations of the
+ * streaming FGP prox for chunks of 16, 32, 64 and 128 z planes and keeps the fastest (out3:
+ * chunk, 0, time in microseconds).  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
 int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream);
 
 /* ---------------------------------------------------------------- operators

@@ -236,9 +236,11 @@ def vrps_geom_cone3d(*a, **k):
 
 
 def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
-    """vrps_autotune: choose the 2D forward band and adjoint pixels per thread by timing."""
+    """vrps_autotune: 2D forward band and adjoint pixels per thread, or the 3D FGP chunk, by timing."""
     out = (ctypes.c_double * 3)()
     _check(lib.vrps_autotune(g.handle, int(reps), out, _stream(stream)))
+    if g.dims == 3:
+        return {"fgp3d_chunk_planes": int(out[0]), "fgp3_iterations_us": float(out[2])}
     return {"fwd_band_bytes": int(out[0]), "adj_pixels_per_thread": int(out[1]), "fwd_adj_us": float(out[2])}
 
 

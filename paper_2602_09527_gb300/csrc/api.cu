@@ -524,8 +524,49 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples) {
 int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
   VRPS_TRY(check_geom(g));
   if (reps < 1) return fail(VRPS_ERR_INVALID_ARG, "reps must be >= 1");
-  if (g->dims != 2) return VRPS_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if (g->dims == 3) {
+    // 3D: z planes per chunk of the streaming FGP iteration, timed on 3 iterations
+    Workspace& w = g->ws;
+    VRPS_TRY(ensure(&w.img, (size_t)g->n));
+    VRPS_TRY(ensure(&w.img2, (size_t)g->n));
+    VRPS_TRY(ensure(&w.dual, 3 * (size_t)g->n));
+    VRPS_TRY(fill(w.img, 0.5f, g->n, s));
+    ProxTail t;
+    std::memset(&t, 0, sizeof(t));
+    t.out = w.img2;
+    cudaEvent_t e0, e1;
+    VRPS_CUDA(cudaEventCreate(&e0));
+    VRPS_CUDA(cudaEventCreate(&e1));
+    const int cand[] = {16, 32, 64, 128};
+    int best_zc = 0;
+    float best = 1e30f;
+    for (int zc : cand) {
+      g->tune_f3_zc = zc;
+      for (int r = 0; r <= reps; ++r) {
+        VRPS_CUDA(cudaMemsetAsync(w.dual, 0, sizeof(float) * 3 * (size_t)g->n, s));
+        VRPS_CUDA(cudaEventRecord(e0, s));
+        VRPS_TRY(fgp_run(g, w.img, 0.01f, 3, 1, w.dual, t, s));
+        VRPS_CUDA(cudaEventRecord(e1, s));
+        VRPS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VRPS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0 && ms < best) {
+          best = ms;
+          best_zc = zc;
+        }
+      }
+    }
+    g->tune_f3_zc = best_zc;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out3) {
+      out3[0] = best_zc;
+      out3[1] = 0;
+      out3[2] = 1e3 * (double)best;
+    }
+    return VRPS_OK;
+  }
   const int* ids = nullptr;
   int rows = 0;
   VRPS_TRY(subset_rows(g, 0, &ids, &rows));

@@ -279,7 +279,7 @@ __device__ __forceinline__ float x3(const float* __restrict__ v, const float* wc
 }
 
 // One FGP iteration in 3D as a 2.5-D streaming stencil.  A CTA owns a F3_TX x F3_TY tile of
-// z columns and walks a chunk of F3_ZC planes.  Per plane it builds the extrapolated dual
+// z columns and walks a chunk of zc planes (default F3_ZC, tunable).  Per plane it builds the extrapolated dual
 // z = w_k + mom (w_k - w_{k-1}) on the tile grown by one voxel, then x = P_+(v + tau div z)
 // on the tile grown by one voxel on the + sides; the new dual of plane g is finished once x of
 // plane g+1 exists.  Each voxel's v, w_k, w_{k-1} are read about once (plus the tile halo)
@@ -290,13 +290,14 @@ constexpr int F3_XX = F3_TX + 1, F3_XY = F3_TY + 1;   // x tile with the + halo
 
 __global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
                                                              const float* __restrict__ wp, float* __restrict__ wn,
-                                                             Dims3 D, float tau, float step, float mom, int nonneg) {
+                                                             Dims3 D, float tau, float step, float mom, int nonneg,
+                                                             int zc) {
   __shared__ float zs[3][F3_HY][F3_HX];   // extrapolated dual of the current plane (+ halo)
   __shared__ float z3p[F3_HY][F3_HX];     // z-component of the previous plane
   __shared__ float xs[2][F3_XY][F3_XX];   // x of two consecutive planes
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * F3_TX + tx;
   const int ix0 = blockIdx.x * F3_TX, iy0 = blockIdx.y * F3_TY;
-  const int zb = blockIdx.z * F3_ZC, ze = min(zb + F3_ZC, D.nz);
+  const int zb = blockIdx.z * zc, ze = min(zb + zc, D.nz);
   const size_t nxy = (size_t)D.nx * D.ny;
   auto load_z = [&](int g) {
     for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) {
@@ -491,12 +492,13 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       t_prev = t_cur;
       t_cur = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
       Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
-      dim3 grid((g->nx + F3_TX - 1) / F3_TX, (g->ny + F3_TY - 1) / F3_TY, (g->nz + F3_ZC - 1) / F3_ZC);
+      const int zc = g->tune_f3_zc > 0 ? g->tune_f3_zc : F3_ZC;
+      dim3 grid((g->nx + F3_TX - 1) / F3_TX, (g->ny + F3_TY - 1) / F3_TY, (g->nz + zc - 1) / zc);
       {
         // read v, w_k (and w_{k-1} when extrapolating), write w_{k+1}
         LaunchScope _ls("fgp3d_stream", s, 4.0 * g->n * (mk != 0.f ? 10 : 7));
         VRPS_CUDA(launch_kernel(fgp3d_stream, grid, dim3(F3_TX, F3_TY), (size_t)0, s, v, (const float*)buf[cur],
-                                (const float*)buf[prev], buf[nxt], D, tau, step, mk, nonneg));
+                                (const float*)buf[prev], buf[nxt], D, tau, step, mk, nonneg, zc));
       }
       VRPS_LAUNCHED("fgp_iter");
       prev = cur;

@@ -49,9 +49,11 @@ constexpr float TWO_M32 = 2.3283064365386963e-10f;   // 2^-32
 
 template <int MODE>
 __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
+  // grid (column tiles, views, row bands): CTAs issued together cover every view of the same
+  // detector rows, whose rays cross the same z slab of the volume (kept in L2)
   const int iu = blockIdx.x * 32 + threadIdx.x;
-  const int iv = blockIdx.y * 8 + threadIdx.y;
-  const int row = blockIdx.z;
+  const int iv = blockIdx.z * 8 + threadIdx.y;
+  const int row = blockIdx.y;
   if (iu >= P.nu || iv >= P.nv) return;
   const int view = P.ids[row];
   const RayInfo3D ri = P.rays[(size_t)view * P.nu + iu];
@@ -271,7 +273,7 @@ int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.cv = 0.5f * (float)(g->nv - 1);
   P.vox = (float)g->pixel;
   P.o = o;
-  dim3 grid((g->nu + 31) / 32, (g->nv + 7) / 8, rows), block(32, 8);
+  dim3 grid((g->nu + 31) / 32, rows, (g->nv + 7) / 8), block(32, 8);
   const double fb = 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->nu * g->nv, o.store);
   switch (mode) {
     case FWD_PLAIN: { LaunchScope _ls("fwd3d_kernel", s, fb); VRPS_CUDA(launch_kernel(fwd3d_kernel<FWD_PLAIN>, dim3(grid), dim3(block), (size_t)(0), s, P)); } break;

@@ -188,6 +188,7 @@ struct vrps_geom {
   // launch shapes chosen by vrps_autotune (0 / -1: built-in defaults)
   int tune_fwd_bytes = 0;   // shared-memory band of the 2D forward (bytes)
   int tune_adj_two = -1;    // 2D adjoint: two pixels per thread (1) or one (0)
+  int tune_f3_zc = 0;       // 3D FGP: z planes per streaming chunk
   // 3D tables
   vrps::RayInfo3D* ray3d = nullptr;     // [n_views][nu]
   vrps::ViewInfo3D* view3d = nullptr;   // [n_views]

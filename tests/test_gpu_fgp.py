@@ -89,3 +89,16 @@ def test_prox_rejects_bad_args():
         vr.prox_tv(g, v, 0.1, -1)
     with pytest.raises(vr.VrpsError):
         vr.prox_tv(g, v, 0.1, 3, x=v)
+
+
+def test_fgp3d_after_autotune():
+    """The 3D autotuner picks the streaming chunk; the prox still matches the oracle, also with
+    chunks that do not divide the volume."""
+    vr, g = _geom3(40, 24, 75)
+    t = vr.autotune(g, reps=1)
+    assert t["fgp3d_chunk_planes"] in (16, 32, 64, 128)
+    rng = np.random.default_rng(17)
+    v = rng.uniform(-0.2, 1.0, size=(75, 24, 40))
+    x = vr.prox_tv(g, dev(v), 0.05, 12)
+    ref, _ = tv.fgp(v, 0.05, 12)
+    assert rel(host(x), ref) < TOL
