@@ -104,15 +104,22 @@ int vrps_geom_sizes(const vrps_geom* g, int subset, int64_t* n, int64_t* m, int*
 int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
 
 /* Launch-shape autotuner (no counterpart in the paper).  For a 2D geometry, times subset 0's
- * forward for shared-memory bands of 16, 24, 32, 48, 64 and 96 KB and its adjoint with one
- * and two pixels per thread (CUDA events, best of `reps` after one warm-up) and keeps the
- * fastest of each in the handle; later projections, solves and batched jobs on the handle
- * use them.  Results change only the grouping of floating-point sums (outputs agree to
- * rounding).  out3 (HOST, nullable): chosen band bytes, chosen pixels per thread, and the
- * tuned forward + adjoint time in microseconds.  3D geometries: times three iterations of the
- * streaming FGP prox for chunks of 16, 32, 64 and 128 z planes and keeps the fastest (out3:
- * chunk, 0, time in microseconds).  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
-int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream);
+ * forward for shared-memory bands of 16 ... 96 KB walked one or 2, 4, 8 bands per CTA
+ * (double-buffered copies), and its adjoint with one and two pixels per thread (CUDA events,
+ * best of `reps` after one warm-up), and keeps the fastest of each in the handle; later
+ * projections, solves and batched jobs on the handle use them.  Results change only the
+ * grouping of floating-point sums (outputs agree to rounding).  out4 (HOST, nullable, 4
+ * doubles): chosen band bytes, pixels per thread, tuned forward + adjoint time in
+ * microseconds, bands per CTA.  3D geometries: times three iterations of the streaming FGP
+ * prox for chunks of 16, 32, 64 and 128 z planes and keeps the fastest (out4: chunk, 0,
+ * time in microseconds, 0).  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+int vrps_autotune(vrps_geom* g, int reps, double* out4, vrps_stream_t stream);
+
+/* Sets the launch shapes by hand (0 = built-in default for each): forward band bytes, forward
+ * bands per CTA, adjoint pixels per thread (1 or 2), 3D FGP planes per chunk.  Errors:
+ * INVALID_ARG. */
+int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread,
+                          int fgp3_chunk);
 
 /* ---------------------------------------------------------------- operators
  * y = A_i x  (Section 1.2: the forward operator of subset i; i = -1 for A).

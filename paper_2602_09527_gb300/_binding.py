@@ -85,6 +85,7 @@ def _load():
         "vrps_geom_sizes": (i, [vp, i, P(i64), P(i64), P(i), P(i), P(i)]),
         "vrps_geom_samples": (i, [vp, i, P(i64)]),
         "vrps_autotune": (i, [vp, i, P(d), vp]),
+        "vrps_set_launch_shape": (i, [vp, i, i, i, i]),
         "vrps_proj_fwd": (i, [vp, i, vp, vp, vp]),
         "vrps_proj_adj": (i, [vp, i, vp, vp, vp]),
         "vrps_prox_tv": (i, [vp, vp, vp, ctypes.c_float, i, i, vp, vp]),
@@ -237,11 +238,19 @@ def vrps_geom_cone3d(*a, **k):
 
 def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
     """vrps_autotune: 2D forward band and adjoint pixels per thread, or the 3D FGP chunk, by timing."""
-    out = (ctypes.c_double * 3)()
+    out = (ctypes.c_double * 4)()
     _check(lib.vrps_autotune(g.handle, int(reps), out, _stream(stream)))
     if g.dims == 3:
         return {"fgp3d_chunk_planes": int(out[0]), "fgp3_iterations_us": float(out[2])}
-    return {"fwd_band_bytes": int(out[0]), "adj_pixels_per_thread": int(out[1]), "fwd_adj_us": float(out[2])}
+    return {"fwd_band_bytes": int(out[0]), "fwd_bands_per_cta": int(out[3]), "adj_pixels_per_thread": int(out[1]),
+            "fwd_adj_us": float(out[2])}
+
+
+def set_launch_shape(g: Geometry, fwd_band_bytes: int = 0, fwd_group: int = 0, adj_pixels_per_thread: int = 0,
+                     fgp3_chunk: int = 0):
+    """vrps_set_launch_shape (0 = built-in default for each)."""
+    _check(lib.vrps_set_launch_shape(g.handle, int(fwd_band_bytes), int(fwd_group), int(adj_pixels_per_thread),
+                                     int(fgp3_chunk)))
 
 
 def proj_fwd(g: Geometry, subset: int, x: torch.Tensor, y: torch.Tensor | None = None, stream=None):

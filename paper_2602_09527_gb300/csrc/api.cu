@@ -564,6 +564,7 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
       out3[0] = best_zc;
       out3[1] = 0;
       out3[2] = 1e3 * (double)best;
+      out3[3] = 0;
     }
     return VRPS_OK;
   }
@@ -595,22 +596,30 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
   };
   FwdOut fo{w.sino, nullptr, nullptr};
   const int cand[] = {16 << 10, 24 << 10, 32 << 10, 48 << 10, 64 << 10, 96 << 10};
-  int best_bytes = 0;
+  const int groups[] = {1, 2, 4, 8};
+  int best_bytes = 0, best_group = 1;
   float best_f = 1e30f;
   for (int c : cand) {
-    g->tune_fwd_bytes = c;
-    float t = 0.f;
-    const int rc = timed([&]() { return fwd2d(g, w.img, w.img2, ids, rows, FWD_PLAIN, fo, s); }, &t);
-    if (rc != VRPS_OK) {
-      g->tune_fwd_bytes = 0;
-      return rc;
-    }
-    if (t < best_f) {
-      best_f = t;
-      best_bytes = c;
+    for (int grp : groups) {
+      if (grp > 1 && (c > (64 << 10) || g->n_bins > 1536)) continue;   // two buffers; rays held in registers
+      g->tune_fwd_bytes = c;
+      g->tune_fwd_group = grp;
+      float t = 0.f;
+      const int rc = timed([&]() { return fwd2d(g, w.img, w.img2, ids, rows, FWD_PLAIN, fo, s); }, &t);
+      if (rc != VRPS_OK) {
+        g->tune_fwd_bytes = 0;
+        g->tune_fwd_group = 0;
+        return rc;
+      }
+      if (t < best_f) {
+        best_f = t;
+        best_bytes = c;
+        best_group = grp;
+      }
     }
   }
   g->tune_fwd_bytes = best_bytes;
+  g->tune_fwd_group = best_group;
   UpdateArgs ua;
   std::memset(&ua, 0, sizeof(ua));
   ua.out = w.img;
@@ -636,7 +645,20 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
     out3[0] = best_bytes;
     out3[1] = best_two ? 2 : 1;
     out3[2] = 1e3 * (double)(best_f + best_a);
+    out3[3] = best_group;
   }
+  return VRPS_OK;
+}
+
+int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread, int fgp3_chunk) {
+  VRPS_TRY(check_geom(g));
+  if (fwd_band_bytes < 0 || fwd_band_bytes > (200 << 10) || fwd_group < 0 || fwd_group > 64 ||
+      adj_pixels_per_thread < 0 || adj_pixels_per_thread > 2 || fgp3_chunk < 0)
+    return fail(VRPS_ERR_INVALID_ARG, "launch shape out of range");
+  g->tune_fwd_bytes = fwd_band_bytes;
+  g->tune_fwd_group = fwd_group;
+  g->tune_adj_two = adj_pixels_per_thread == 0 ? -1 : (adj_pixels_per_thread == 2 ? 1 : 0);
+  g->tune_f3_zc = fgp3_chunk;
   return VRPS_OK;
 }
 

@@ -53,6 +53,7 @@ struct Slot {
   cudaGraphExec_t graph = nullptr;
   int graph_blocks = -1;
   size_t graph_fwd_smem = 0, graph_adj_smem = 0;
+  bool graph_grouped = false;
 };
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -72,6 +73,7 @@ struct vrps_batch {
   int slot_i = 0;
   int grid_fwd = 0, grid_adj = 0, grid_fgp = 0, grid_out = 0;
   size_t fwd_smem = 0, adj_smem = 0;
+  bool fwd_grouped = false;   // some job's forward walks band groups
   int max_blocks = 0;
   bool graphs = true;
   long long ticks = 0;
@@ -81,7 +83,7 @@ struct vrps_batch {
 namespace {
 
 int batch_grids(vrps_batch* B) {
-  VRPS_TRY(batched_grid(0, B->fwd_smem, &B->grid_fwd));
+  VRPS_TRY(batched_grid(B->fwd_grouped ? 4 : 0, B->fwd_smem, &B->grid_fwd));
   VRPS_TRY(batched_grid(1, B->adj_smem, &B->grid_adj));
   VRPS_TRY(batched_grid(2, 0, &B->grid_fgp));
   VRPS_TRY(batched_grid(3, 0, &B->grid_out));
@@ -90,7 +92,7 @@ int batch_grids(vrps_batch* B) {
 
 // The tick's kernels on stream s, reading the work list at slot.
 int launch_tick(vrps_batch* B, char* slot, cudaStream_t s) {
-  VRPS_TRY(fwd2d_batched(slot, B->grid_fwd, B->fwd_smem, s));
+  VRPS_TRY(fwd2d_batched(slot, B->grid_fwd, B->fwd_smem, B->fwd_grouped, s));
   VRPS_TRY(adj2d_batched(slot, B->grid_adj, B->adj_smem, s));
   for (int b = 0; b < B->max_blocks; ++b) VRPS_TRY(fgp2d_block_batched(slot, b, B->grid_fgp, s));
   VRPS_TRY(fgp2d_out_batched(slot, B->grid_out, s));
@@ -102,7 +104,7 @@ int tick_kernels(const vrps_batch* B) { return 3 + B->max_blocks; }
 // Graph of the tick's kernels for one slot, captured on the batch's capture stream.
 int ensure_graph(vrps_batch* B, Slot& S) {
   if (S.graph && S.graph_blocks == B->max_blocks && S.graph_fwd_smem == B->fwd_smem &&
-      S.graph_adj_smem == B->adj_smem)
+      S.graph_adj_smem == B->adj_smem && S.graph_grouped == B->fwd_grouped)
     return VRPS_OK;
   if (S.graph) {
     cudaGraphExecDestroy(S.graph);
@@ -124,6 +126,7 @@ int ensure_graph(vrps_batch* B, Slot& S) {
   S.graph_blocks = B->max_blocks;
   S.graph_fwd_smem = B->fwd_smem;
   S.graph_adj_smem = B->adj_smem;
+  S.graph_grouped = B->fwd_grouped;
   return VRPS_OK;
 }
 
@@ -200,6 +203,10 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   bool regrid = false;
   if (fs > B->fwd_smem) {
     B->fwd_smem = fs;
+    regrid = true;
+  }
+  if (fp.group > 1 && bulk && !B->fwd_grouped) {
+    B->fwd_grouped = true;
     regrid = true;
   }
   if (as > B->adj_smem) {

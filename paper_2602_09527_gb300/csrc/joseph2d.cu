@@ -91,132 +91,201 @@ __device__ __forceinline__ void fwd2d_epilogue(const FwdOut& o, size_t idx, floa
 }
 
 struct FwdShared {
-  unsigned long long bar;   // mbarrier of the band copies (initialised once per CTA)
-  unsigned last;            // this CTA completed the angle row
+  unsigned long long bar[2];   // mbarriers of the two band buffers (initialised once per CTA)
+  unsigned last;               // this CTA completed the angle row
 };
 
-// One (band c, angle row) item of the forward.  With BULK the band arrives by bulk copies that
-// complete phase `parity` of S.bar; returns 1 when it used the barrier (the caller flips its
-// parity for the next item).
-template <int MODE, bool BULK>
-__device__ __forceinline__ int fwd2d_item(const Fwd2DParams& P, int c, int row, float* band, FwdShared& S,
-                                          unsigned parity) {
+constexpr int FWD_RPT = 6;   // rays per thread held in registers across a band group (nb <= 1536)
+
+// Stages band lines [l0, l0 + nl) of img into buf (zero margins; BULK: bulk copies on bar, the
+// caller waits; otherwise plain loads, visible after the caller's barrier).
+template <bool BULK>
+__device__ __forceinline__ void fwd2d_stage(const float* img, int ncols, int stride, int l0, int nl, float* buf,
+                                            unsigned long long* bar) {
+  const int tid = threadIdx.x;
+  const float* src = img + (size_t)l0 * ncols;
+  for (int e = tid; e < nl * 2 * FWD_PAD; e += FWD_THREADS) {
+    const int L = e / (2 * FWD_PAD), q = e - L * 2 * FWD_PAD;
+    buf[L * stride + (q < FWD_PAD ? q : ncols + q)] = 0.f;
+  }
+  if (BULK) {
+    if (tid == 0) {
+      // order earlier generic accesses of the buffer before the async-proxy writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const unsigned row_bytes = (unsigned)(ncols * sizeof(float));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                   "r"(row_bytes * (unsigned)nl)
+                   : "memory");
+      for (int L = 0; L < nl; ++L)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(buf + L * stride + FWD_PAD)),
+            "l"(global_addr(src + (size_t)L * ncols)), "r"(row_bytes), "r"(smem_addr(bar))
+            : "memory");
+    }
+  } else {
+    for (int e = tid; e < nl * ncols; e += FWD_THREADS) {
+      const int L = e / ncols;
+      buf[L * stride + FWD_PAD + (e - L * ncols)] = __ldg(src + e);
+    }
+  }
+}
+
+// Bounded wait for phase `ph` of bar; false (and the error word set) when it gave up.
+__device__ __forceinline__ bool fwd2d_wait(unsigned long long* bar, unsigned ph, unsigned* err) {
+  unsigned it = 0;
+  while (!mbar_try_wait(bar, ph) && ++it < WAIT_LIMIT) {
+  }
+  if (it < WAIT_LIMIT) return true;
+  // record the failure and give the copies in flight a second bounded chance to land in shared
+  // memory before the buffer is reused; nothing is computed from it
+  if (threadIdx.x == 0) atomicOr(err, 1u);
+  unsigned it2 = 0;
+  while (!mbar_try_wait(bar, ph) && ++it2 < WAIT_LIMIT) {
+  }
+  return false;
+}
+
+// Ray j's samples on lines [l0, l0 + nl) of the staged band buf (acc0: even lines of each
+// trip of four, acc1: odd ones).  Positions: every trip of four lines re-anchors exactly from
+// the 64-bit fixed-point walk (u = I + F); the four samples of the trip add A2 k to F in float.
+__device__ __forceinline__ void fwd2d_ray(const Fwd2DParams& P, const AngleInfo2D& in, const float* buf, int j,
+                                          int l0, int nl, int ncols, int nlines, int stride, float& acc0,
+                                          float& acc1) {
+  const float uc = 0.5f * (float)(ncols - 1);
+  const float lc = 0.5f * (float)(nlines - 1);
+  const float u0 = fmaf(in.A1, (float)j - P.jc, uc);   // line-range clipping only
+  int lo = l0, hi = l0 + nl - 1;
+  if (in.A2 != 0.f) {
+    float la = fmaf(-1.f - u0, in.inv_A2, lc);
+    float lb = fmaf((float)ncols - u0, in.inv_A2, lc);
+    if (la > lb) {
+      const float q = la;
+      la = lb;
+      lb = q;
+    }
+    la = fminf(fmaxf(la, -2.f), (float)nlines + 1.f);
+    lb = fminf(fmaxf(lb, -2.f), (float)nlines + 1.f);
+    lo = max(lo, (int)floorf(la) - 1);
+    hi = min(hi, (int)ceilf(lb) + 1);
+  } else if (!(u0 > -1.f && u0 < (float)ncols)) {
+    hi = -1;
+  }
+  if (lo > hi) return;
+  // exact fixed-point walk along the ray: U = u * 2^32; FWD_PAD shifts into the padded row
+  long long U = (long long)(ncols - 1 + 2 * FWD_PAD) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
+                in.A2H * (long long)(2 * lo - (nlines - 1));
+  const long long dU4 = 8 * in.A2H;   // four lines
+  const float A2 = in.A2;
+  int rb = (lo - l0) * stride;          // shared-memory offset of the current line
+  int l = lo;
+  for (; l + 3 <= hi; l += 4) {
+    const int I = fix_floor(U) + rb;
+    const float F = fix_frac(U);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float ur = fmaf(A2, (float)q, F);
+      const float fl = floorf(ur);
+      const float f = ur - fl;
+      const float* t = buf + (I + q * stride + (int)fl);
+      const float a = t[0], b = t[1];
+      if (q & 1) acc1 += fmaf(f, b - a, a);
+      else acc0 += fmaf(f, b - a, a);
+    }
+    U += dU4;
+    rb += 4 * stride;
+  }
+  const int I = fix_floor(U) + rb;
+  const float F = fix_frac(U);
+  for (int q = 0; l <= hi; ++l, ++q) {
+    const float ur = fmaf(A2, (float)q, F);
+    const float fl = floorf(ur);
+    const float f = ur - fl;
+    const float* t = buf + (I + q * stride + (int)fl);
+    acc0 += fmaf(f, t[1] - t[0], t[0]);
+  }
+}
+
+// Forward projector, one CTA item per (angle row, group of P.group consecutive bands of
+// P.band dominant-axis lines).  A band -- lines of x (rows-marched angles) or of x^T
+// (columns-marched angles) -- is copied row by row into shared memory by bulk copies, with
+// FWD_PAD zero columns on both sides of every row so that the taps of any sample whose point
+// lies in (-1, ncols) are read without bounds tests; with groups of several bands the next
+// band is copied into the second buffer while the current one is walked, and each thread
+// keeps its rays' sums in registers across the group.  Each ray's group sum goes to a partial
+// buffer; the CTA that completes a row last adds the groups in order (deterministic) and runs
+// the epilogue.  ph[2]: the phases of the CTA's two barriers (flipped on every use).
+template <int MODE, bool BULK, bool GROUPED>
+__device__ __forceinline__ void fwd2d_item(const Fwd2DParams& P, int cg, int row, float* smem, FwdShared& S,
+                                           unsigned* ph) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const AngleInfo2D in = P.ang[P.ids[row]];
-  int used = 0;
   const bool tr = in.T != 0;
   const float* __restrict__ img = tr ? P.xT : P.x;
   const int ncols = tr ? P.ny : P.nx;
   const int nlines = tr ? P.nx : P.ny;
   const int stride = ncols + 2 * FWD_PAD;
-  const int l0 = c * P.band;
-  const int nl = min(P.band, nlines - l0);   // lines of this band (may be <= 0)
+  const int c0 = cg * P.group;
+  const int c1 = min(c0 + P.group, P.nbands);
+  const size_t pbase = (size_t)row * P.bands * P.nb + (size_t)cg * P.nb;
   bool ok = true;
-  if (nl > 0) {
-    const float* src = img + (size_t)l0 * ncols;
-    for (int e = tid; e < nl * 2 * FWD_PAD; e += FWD_THREADS) {   // zero margins
-      const int L = e / (2 * FWD_PAD), q = e - L * 2 * FWD_PAD;
-      band[L * stride + (q < FWD_PAD ? q : ncols + q)] = 0.f;
-    }
-    if (BULK) {
-      used = 1;
-      if (tid == 0) {
-        // order earlier generic accesses of the band before the async-proxy writes
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const unsigned row_bytes = (unsigned)(ncols * sizeof(float));
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&S.bar)),
-                     "r"(row_bytes * (unsigned)nl)
-                     : "memory");
-        for (int L = 0; L < nl; ++L)
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                  smem_addr(band + L * stride + FWD_PAD)),
-              "l"(global_addr(src + (size_t)L * ncols)), "r"(row_bytes), "r"(smem_addr(&S.bar))
-              : "memory");
-      }
-      unsigned it = 0;
-      while (!mbar_try_wait(&S.bar, parity) && ++it < WAIT_LIMIT) {
-      }
-      ok = it < WAIT_LIMIT;
-      if (!ok) {
-        // record the failure, give the copies in flight a second bounded chance to land in
-        // shared memory before this CTA retires, and compute nothing from the band
-        if (tid == 0) atomicOr(P.err, 1u);
-        unsigned it2 = 0;
-        while (!mbar_try_wait(&S.bar, parity) && ++it2 < WAIT_LIMIT) {
-        }
-      }
-      __syncthreads();   // the zero margins written above
-    } else {
-      for (int e = tid; e < nl * ncols; e += FWD_THREADS) {
-        const int L = e / ncols;
-        band[L * stride + FWD_PAD + (e - L * ncols)] = __ldg(src + e);
+  if (!GROUPED || P.group == 1 || P.nb > FWD_RPT * FWD_THREADS) {
+    // one band per item: rays written as they finish
+    const int l0 = c0 * P.band;
+    const int nl = min(P.band, nlines - l0);
+    if (nl > 0) {
+      fwd2d_stage<BULK>(img, ncols, stride, l0, nl, smem, &S.bar[0]);
+      if (BULK) {
+        ok = fwd2d_wait(&S.bar[0], ph[0], P.err);
+        ph[0] ^= 1u;
       }
       __syncthreads();
     }
-  }
-  const float uc = 0.5f * (float)(ncols - 1);
-  const float lc = 0.5f * (float)(nlines - 1);
-  const size_t pbase = (size_t)row * P.bands * P.nb + (size_t)c * P.nb;
-  for (int j0 = warp * FWD_LANES; j0 < P.nb; j0 += FWD_THREADS) {
-    const int j = j0 + lane;
-    float acc0 = 0.f, acc1 = 0.f;
-    if (j < P.nb && nl > 0 && ok) {
-      const float u0 = fmaf(in.A1, (float)j - P.jc, uc);   // line-range clipping only
-      int lo = l0, hi = l0 + nl - 1;
-      if (in.A2 != 0.f) {
-        float la = fmaf(-1.f - u0, in.inv_A2, lc);
-        float lb = fmaf((float)ncols - u0, in.inv_A2, lc);
-        if (la > lb) {
-          const float q = la;
-          la = lb;
-          lb = q;
-        }
-        la = fminf(fmaxf(la, -2.f), (float)nlines + 1.f);
-        lb = fminf(fmaxf(lb, -2.f), (float)nlines + 1.f);
-        lo = max(lo, (int)floorf(la) - 1);
-        hi = min(hi, (int)ceilf(lb) + 1);
-      } else if (!(u0 > -1.f && u0 < (float)ncols)) {
-        hi = -1;
-      }
-      // exact fixed-point walk along the ray: U = u * 2^32; FWD_PAD shifts into the padded row
-      long long U = (long long)(ncols - 1 + 2 * FWD_PAD) * 2147483648LL +
-                    in.A1H * (long long)(2 * j - (P.nb - 1)) + in.A2H * (long long)(2 * lo - (nlines - 1));
-      const long long dU4 = 8 * in.A2H;   // four lines
-      const float A2 = in.A2;
-      int rb = (lo - l0) * stride;          // shared-memory offset of the current line
-      int l = lo;
-      for (; l + 3 <= hi; l += 4) {
-        const int I = fix_floor(U) + rb;
-        const float F = fix_frac(U);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float ur = fmaf(A2, (float)q, F);
-          const float fl = floorf(ur);
-          const float f = ur - fl;
-          const float* t = band + (I + q * stride + (int)fl);
-          const float a = t[0], b = t[1];
-          if (q & 1) acc1 += fmaf(f, b - a, a);
-          else acc0 += fmaf(f, b - a, a);
-        }
-        U += dU4;
-        rb += 4 * stride;
-      }
-      {
-        const int I = fix_floor(U) + rb;
-        const float F = fix_frac(U);
-        for (int q = 0; l <= hi; ++l, ++q) {
-          const float ur = fmaf(A2, (float)q, F);
-          const float fl = floorf(ur);
-          const float f = ur - fl;
-          const float* t = band + (I + q * stride + (int)fl);
-          acc0 += fmaf(f, t[1] - t[0], t[0]);
-        }
-      }
+    for (int j0 = warp * FWD_LANES; j0 < P.nb; j0 += FWD_THREADS) {
+      const int j = j0 + lane;
+      float acc0 = 0.f, acc1 = 0.f;
+      if (j < P.nb && nl > 0 && ok) fwd2d_ray(P, in, smem, j, l0, nl, ncols, nlines, stride, acc0, acc1);
+      if (j < P.nb) P.part[pbase + j] = acc0 + acc1;
     }
-    if (j < P.nb) P.part[pbase + j] = acc0 + acc1;
+  } else {
+    const int band_floats = P.band * stride;
+    float acc[FWD_RPT][2];
+#pragma unroll
+    for (int k = 0; k < FWD_RPT; ++k) acc[k][0] = acc[k][1] = 0.f;
+    {
+      const int nl0 = min(P.band, nlines - c0 * P.band);
+      if (nl0 > 0) fwd2d_stage<BULK>(img, ncols, stride, c0 * P.band, nl0, smem, &S.bar[0]);
+    }
+    for (int c = c0; c < c1; ++c) {
+      const int b = (c - c0) & 1;
+      const int l0 = c * P.band;
+      const int nl = min(P.band, nlines - l0);
+      if (nl <= 0) break;   // bands grow along the lines: the rest lie beyond this orientation's image
+      const int nl1 = c + 1 < c1 ? min(P.band, nlines - l0 - P.band) : 0;
+      if (nl1 > 0) fwd2d_stage<BULK>(img, ncols, stride, l0 + P.band, nl1, smem + (b ^ 1) * band_floats, &S.bar[b ^ 1]);
+      if (BULK) {
+        ok = fwd2d_wait(&S.bar[b], ph[b], P.err) && ok;
+        ph[b] ^= 1u;
+      }
+      __syncthreads();   // margins, plain loads and bulk data of band c visible
+      if (ok) {
+        const float* buf = smem + b * band_floats;
+#pragma unroll
+        for (int k = 0; k < FWD_RPT; ++k) {
+          const int j = warp * FWD_LANES + k * FWD_THREADS + lane;
+          if (warp * FWD_LANES + k * FWD_THREADS < P.nb && j < P.nb)
+            fwd2d_ray(P, in, buf, j, l0, nl, ncols, nlines, stride, acc[k][0], acc[k][1]);
+        }
+      }
+      __syncthreads();   // band c's buffer is free for band c + 2
+    }
+#pragma unroll
+    for (int k = 0; k < FWD_RPT; ++k) {
+      const int j = warp * FWD_LANES + k * FWD_THREADS + lane;
+      if (j < P.nb) P.part[pbase + j] = acc[k][0] + acc[k][1];
+    }
   }
-  // the last CTA of this row adds the bands in order and applies the epilogue
+  // the last CTA of this row adds the groups in order and applies the epilogue
   __threadfence();
   __syncthreads();
   if (tid == 0) {
@@ -225,54 +294,55 @@ __device__ __forceinline__ int fwd2d_item(const Fwd2DParams& P, int c, int row, 
     if (S.last) P.count[row] = 0u;
   }
   __syncthreads();
-  if (!S.last) return used;
+  if (!S.last) return;
   __threadfence();
   const int bands = P.bands, nb = P.nb;
   const float* __restrict__ part = P.part + (size_t)row * bands * nb;
   const size_t obase = (size_t)row * nb;
   if ((nb & 3) == 0) {
-    // four rays per thread with 16-byte loads; each ray still adds its bands in order
+    // four rays per thread with 16-byte loads; each ray still adds its groups in order
     const int nb4 = nb >> 2;
     const float4* __restrict__ p4 = reinterpret_cast<const float4*>(part);
     for (int j4 = tid; j4 < nb4; j4 += FWD_THREADS) {
-      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 8
       for (int q = 0; q < bands; ++q) {
         const float4 v = __ldcg(p4 + (size_t)q * nb4 + j4);
-        s.x += v.x;
-        s.y += v.y;
-        s.z += v.z;
-        s.w += v.w;
+        sum.x += v.x;
+        sum.y += v.y;
+        sum.z += v.z;
+        sum.w += v.w;
       }
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 0, __fmul_rn(s.x, in.wgt));
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 1, __fmul_rn(s.y, in.wgt));
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 2, __fmul_rn(s.z, in.wgt));
-      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 3, __fmul_rn(s.w, in.wgt));
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 0, __fmul_rn(sum.x, in.wgt));
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 1, __fmul_rn(sum.y, in.wgt));
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 2, __fmul_rn(sum.z, in.wgt));
+      fwd2d_epilogue<MODE>(P.o, obase + 4 * j4 + 3, __fmul_rn(sum.w, in.wgt));
     }
   } else {
     for (int j = tid; j < nb; j += FWD_THREADS) {
-      float s = 0.f;
-      for (int q = 0; q < bands; ++q) s += __ldcg(part + (size_t)q * nb + j);
-      fwd2d_epilogue<MODE>(P.o, obase + j, __fmul_rn(s, in.wgt));
+      float sum = 0.f;
+      for (int q = 0; q < bands; ++q) sum += __ldcg(part + (size_t)q * nb + j);
+      fwd2d_epilogue<MODE>(P.o, obase + j, __fmul_rn(sum, in.wgt));
     }
   }
-  return used;
 }
 
 __device__ __forceinline__ void fwd2d_init_barrier(FwdShared& S) {
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar[1])) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
 }
 
-template <int MODE, bool BULK>
+template <int MODE, bool BULK, bool GROUPED>
 __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
   extern __shared__ __align__(128) float band[];
   __shared__ FwdShared S;
   if (BULK) fwd2d_init_barrier(S);
-  fwd2d_item<MODE, BULK>(P, blockIdx.x, blockIdx.y, band, S, 0u);
+  unsigned ph[2] = {0u, 0u};
+  fwd2d_item<MODE, BULK, GROUPED>(P, blockIdx.x, blockIdx.y, band, S, ph);
 }
 
 
@@ -481,7 +551,10 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   if (band < 1) band = 1;
   if (band > maxl) band = maxl;
   P.band = band;
-  P.bands = (maxl + band - 1) / band;
+  P.nbands = (maxl + band - 1) / band;
+  P.group = g->tune_fwd_group > 1 && g->n_bins <= FWD_RPT * FWD_THREADS ? g->tune_fwd_group : 1;
+  if (P.group > P.nbands) P.group = P.nbands;
+  P.bands = (P.nbands + P.group - 1) / P.group;
   vrps_geom* gm = const_cast<vrps_geom*>(g);
   Workspace& ws = gm->ws;
   if (!ws.fwd_part || ws.fwd_bands != P.bands) {
@@ -503,7 +576,7 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   P.err = ws.dev_error;
   // the bulk copy needs 16-byte aligned rows: line lengths that are multiples of 4 floats
   *bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
-  *smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD);
+  *smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD) * (P.group > 1 ? 2 : 1);
   (void)rows;
   return VRPS_OK;
 }
@@ -522,12 +595,19 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
     VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
     return VRPS_OK;
   };
+  const bool grouped = bulk && P.group > 1;
   switch (mode) {
-    case FWD_PLAIN: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_PLAIN, true>) : launch(fwd2d_kernel<FWD_PLAIN, false>)); break;
-    case FWD_RESID: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_RESID, true>) : launch(fwd2d_kernel<FWD_RESID, false>)); break;
-    case FWD_SVRG: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_SVRG, true>) : launch(fwd2d_kernel<FWD_SVRG, false>)); break;
-    case FWD_SAGA: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_SAGA, true>) : launch(fwd2d_kernel<FWD_SAGA, false>)); break;
-    case FWD_SNAP: VRPS_TRY(bulk ? launch(fwd2d_kernel<FWD_SNAP, true>) : launch(fwd2d_kernel<FWD_SNAP, false>)); break;
+#define VRPS_FWD_CASE(M)                                                                          \
+  case M:                                                                                         \
+    VRPS_TRY(grouped ? launch(fwd2d_kernel<M, true, true>)                                        \
+                     : (bulk ? launch(fwd2d_kernel<M, true, false>) : launch(fwd2d_kernel<M, false, false>))); \
+    break;
+    VRPS_FWD_CASE(FWD_PLAIN)
+    VRPS_FWD_CASE(FWD_RESID)
+    VRPS_FWD_CASE(FWD_SVRG)
+    VRPS_FWD_CASE(FWD_SAGA)
+    VRPS_FWD_CASE(FWD_SNAP)
+#undef VRPS_FWD_CASE
     default: return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
   }
   VRPS_LAUNCHED("fwd2d");
@@ -601,15 +681,15 @@ __device__ __forceinline__ void batch_load_prefix(int* dst, const int* src, int 
   __syncthreads();
 }
 
-template <bool BULK>
-__device__ __forceinline__ int fwd2d_item_mode(const BatchFwd& J, int c, int row, float* band, FwdShared& S,
-                                               unsigned parity) {
+template <bool BULK, bool GROUPED>
+__device__ __forceinline__ void fwd2d_item_mode(const BatchFwd& J, int c, int row, float* band, FwdShared& S,
+                                                unsigned* ph) {
   switch (J.mode) {
-    case FWD_PLAIN: return fwd2d_item<FWD_PLAIN, BULK>(J.P, c, row, band, S, parity);
-    case FWD_RESID: return fwd2d_item<FWD_RESID, BULK>(J.P, c, row, band, S, parity);
-    case FWD_SVRG: return fwd2d_item<FWD_SVRG, BULK>(J.P, c, row, band, S, parity);
-    case FWD_SAGA: return fwd2d_item<FWD_SAGA, BULK>(J.P, c, row, band, S, parity);
-    default: return fwd2d_item<FWD_SNAP, BULK>(J.P, c, row, band, S, parity);
+    case FWD_PLAIN: fwd2d_item<FWD_PLAIN, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
+    case FWD_RESID: fwd2d_item<FWD_RESID, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
+    case FWD_SVRG: fwd2d_item<FWD_SVRG, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
+    case FWD_SAGA: fwd2d_item<FWD_SAGA, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
+    default: fwd2d_item<FWD_SNAP, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
   }
 }
 
@@ -622,6 +702,7 @@ __device__ __forceinline__ int batch_next(unsigned* counter, int* s_item) {
   return *s_item;
 }
 
+template <bool GROUPED>
 __global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(char* __restrict__ slot) {
   extern __shared__ __align__(128) float band[];
   __shared__ FwdShared S;
@@ -634,7 +715,7 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(char* __rest
   const BatchFwd* jobs = reinterpret_cast<const BatchFwd*>(slot + H.off_fwd);
   batch_load_prefix(pre, reinterpret_cast<const int*>(slot + H.off_pfwd), n);
   fwd2d_init_barrier(S);
-  unsigned parity = 0;
+  unsigned ph[2] = {0u, 0u};
   const int total = pre[n];
   for (int item = batch_next(counter, &s_item); item < total; item = batch_next(counter, &s_item)) {
     const int j = batch_job(pre, n, item);
@@ -642,9 +723,8 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(char* __rest
     const int local = item - pre[j];
     const int bands = J.P.bands;
     const int c = local % bands, row = local / bands;
-    const int used = J.bulk ? fwd2d_item_mode<true>(J, c, row, band, S, parity)
-                            : fwd2d_item_mode<false>(J, c, row, band, S, parity);
-    parity ^= (unsigned)used;
+    if (J.bulk) fwd2d_item_mode<true, GROUPED>(J, c, row, band, S, ph);
+    else fwd2d_item_mode<false, false>(J, c, row, band, S, ph);
   }
 }
 
@@ -676,10 +756,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_batched_kernel(char* __rest
 
 }  // namespace
 
-int fwd2d_batched(char* slot, int grid, size_t smem, cudaStream_t s) {
-  VRPS_TRY(smem_opt_in((const void*)fwd2d_batched_kernel, smem));
+int fwd2d_batched(char* slot, int grid, size_t smem, bool grouped, cudaStream_t s) {
+  auto kern = grouped ? fwd2d_batched_kernel<true> : fwd2d_batched_kernel<false>;
+  VRPS_TRY(smem_opt_in((const void*)kern, smem));
   LaunchScope _ls("fwd2d_batched", s);
-  VRPS_CUDA(launch_kernel(fwd2d_batched_kernel, dim3(grid), dim3(FWD_THREADS), smem, s, slot));
+  VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(FWD_THREADS), smem, s, slot));
   return VRPS_OK;
 }
 
@@ -694,9 +775,10 @@ int batched_grid_2d(int which, size_t smem, int* grid) {
   int dev = 0, sms = 0, per = 0;
   VRPS_CUDA(cudaGetDevice(&dev));
   VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (which == 0) {
-    VRPS_TRY(smem_opt_in((const void*)fwd2d_batched_kernel, smem));
-    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fwd2d_batched_kernel, FWD_THREADS, smem));
+  if (which == 0 || which == 4) {
+    auto kern = which == 4 ? fwd2d_batched_kernel<true> : fwd2d_batched_kernel<false>;
+    VRPS_TRY(smem_opt_in((const void*)kern, smem));
+    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FWD_THREADS, smem));
   } else {
     VRPS_TRY(smem_opt_in((const void*)adj2d_batched_kernel, smem));
     VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj2d_batched_kernel, ADJ_THREADS, smem));

@@ -187,6 +187,7 @@ struct vrps_geom {
   int adj_nc = 0;        // candidate bins per pixel and angle
   // launch shapes chosen by vrps_autotune (0 / -1: built-in defaults)
   int tune_fwd_bytes = 0;   // shared-memory band of the 2D forward (bytes)
+  int tune_fwd_group = 0;   // bands per forward CTA item (0: one)
   int tune_adj_two = -1;    // 2D adjoint: two pixels per thread (1) or one (0)
   int tune_f3_zc = 0;       // 3D FGP: z planes per streaming chunk
   // 3D tables
@@ -276,8 +277,10 @@ struct Fwd2DParams {
   int nx, ny, nb;
   float jc;
   int band;                   // lines per band
-  int bands;                  // gridDim.x
-  float* part;                // [rows][bands][nb] partial sums
+  int nbands;                 // bands covering the longest line count
+  int group;                  // bands per CTA item (walked with double-buffered copies)
+  int bands;                  // band groups per row = items per row (gridDim.x)
+  float* part;                // [rows][bands][nb] partial sums (one per group)
   unsigned* count;            // [rows] arrival counters, zero between launches
   unsigned* err;              // device error word
   FwdOut o;
@@ -417,12 +420,12 @@ struct TickHeader {
   unsigned off_fwd, off_pfwd, off_adj, off_padj, off_fgp, off_pfgp, off_out, off_pout;
   unsigned cnt[3 + BATCH_MAX_BLOCKS];
 };
-int fwd2d_batched(char* slot, int grid, size_t smem, cudaStream_t s);
+int fwd2d_batched(char* slot, int grid, size_t smem, bool grouped, cudaStream_t s);
 int adj2d_batched(char* slot, int grid, size_t smem, cudaStream_t s);
 int fgp2d_block_batched(char* slot, int b, int grid, cudaStream_t s);
 int fgp2d_out_batched(char* slot, int grid, cudaStream_t s);
 // Persistent grid (CTAs resident on all SMs) of batched kernel `which` (0 fwd, 1 adj, 2 FGP
-// block, 3 FGP out) at `smem` bytes of dynamic shared memory.
+// block, 3 FGP out, 4 fwd with band groups) at `smem` bytes of dynamic shared memory.
 int batched_grid(int which, size_t smem, int* grid);
 int batched_grid_2d(int which, size_t smem, int* grid);
 

@@ -110,6 +110,25 @@ def test_staggered_admission_and_alone(mix):
     A.close()
 
 
+def test_grouped_forward_shapes_in_the_mix(mix):
+    """Jobs whose geometries walk several forward bands per CTA (and others that do not) stay
+    bit-identical to their solo runs."""
+    vr, probs, solo = mix
+    for i in (0, 2, 4):
+        vr.set_launch_shape(probs[i][1], fwd_band_bytes=16 << 10, fwd_group=3)
+    try:
+        ref = [_solo(vr, probs[i][1], probs[i][2], _kw(MIX[i], probs[i][3], i))[0] for i in range(len(MIX))]
+        B = vr.Batch()
+        ids = [B.submit(probs[i][1], dev(probs[i][2]), **_kw(MIX[i], probs[i][3], i)) for i in range(len(MIX))]
+        for i, jid in enumerate(ids):
+            B.wait(jid)
+            assert torch.equal(B.result(jid), ref[i]), i
+        B.close()
+    finally:
+        for i in (0, 2, 4):
+            vr.set_launch_shape(probs[i][1])
+
+
 def test_batched_job_matches_oracle():
     vr = _vr()
     P = synthetic.make_problem_2d(32, 40, 48, 5, seed=21, noise="gauss", alpha=0.02)
