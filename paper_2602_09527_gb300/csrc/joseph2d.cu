@@ -552,7 +552,10 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   if (band > maxl) band = maxl;
   P.band = band;
   P.nbands = (maxl + band - 1) / band;
-  P.group = g->tune_fwd_group > 1 && g->n_bins <= FWD_RPT * FWD_THREADS ? g->tune_fwd_group : 1;
+  // the bulk copy needs 16-byte aligned rows: line lengths that are multiples of 4 floats
+  *bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
+  // band groups: bulk copies only (the plain-load path walks one band per item)
+  P.group = *bulk && g->tune_fwd_group > 1 && g->n_bins <= FWD_RPT * FWD_THREADS ? g->tune_fwd_group : 1;
   if (P.group > P.nbands) P.group = P.nbands;
   P.bands = (P.nbands + P.group - 1) / P.group;
   vrps_geom* gm = const_cast<vrps_geom*>(g);
@@ -574,8 +577,6 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   P.part = ws.fwd_part;
   P.count = ws.fwd_count;
   P.err = ws.dev_error;
-  // the bulk copy needs 16-byte aligned rows: line lengths that are multiples of 4 floats
-  *bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
   *smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD) * (P.group > 1 ? 2 : 1);
   (void)rows;
   return VRPS_OK;
