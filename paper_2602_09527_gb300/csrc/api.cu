@@ -639,6 +639,32 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
     }
   }
   g->tune_adj_two = best_two;
+  // 2D FGP output tile, timed on one 16-iteration prox call
+  {
+    VRPS_TRY(ensure(&w.dual, 2 * (size_t)g->n));
+    ProxTail t;
+    std::memset(&t, 0, sizeof(t));
+    t.out = w.img2;
+    int best_tile = 0;
+    float best_p = 1e30f;
+    for (int tile = 0; tile < 3; ++tile) {
+      g->tune_fgp_tile = tile;
+      float tp = 0.f;
+      const int rc = timed([&]() -> int {
+        VRPS_CUDA(cudaMemsetAsync(w.dual, 0, sizeof(float) * 2 * (size_t)g->n, s));
+        return fgp_run(g, w.img, 0.01f, 16, 1, w.dual, t, s);
+      }, &tp);
+      if (rc != VRPS_OK) {
+        g->tune_fgp_tile = 0;
+        return rc;
+      }
+      if (tp < best_p) {
+        best_p = tp;
+        best_tile = tile;
+      }
+    }
+    g->tune_fgp_tile = best_tile;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (out3) {
@@ -650,11 +676,24 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
   return VRPS_OK;
 }
 
-int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread, int fgp3_chunk) {
+int vrps_launch_shape(const vrps_geom* g, int* out5) {
+  VRPS_TRY(check_geom(g));
+  if (!out5) return fail(VRPS_ERR_INVALID_ARG, "out5 is NULL");
+  out5[0] = g->tune_fwd_bytes;
+  out5[1] = g->tune_fwd_group;
+  out5[2] = g->tune_adj_two < 0 ? 0 : (g->tune_adj_two ? 2 : 1);
+  out5[3] = g->tune_f3_zc;
+  out5[4] = g->tune_fgp_tile;
+  return VRPS_OK;
+}
+
+int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread, int fgp3_chunk,
+                          int fgp_tile) {
   VRPS_TRY(check_geom(g));
   if (fwd_band_bytes < 0 || fwd_band_bytes > (200 << 10) || fwd_group < 0 || fwd_group > 64 ||
-      adj_pixels_per_thread < 0 || adj_pixels_per_thread > 2 || fgp3_chunk < 0)
+      adj_pixels_per_thread < 0 || adj_pixels_per_thread > 2 || fgp3_chunk < 0 || fgp_tile < 0 || fgp_tile > 2)
     return fail(VRPS_ERR_INVALID_ARG, "launch shape out of range");
+  g->tune_fgp_tile = fgp_tile;
   g->tune_fwd_bytes = fwd_band_bytes;
   g->tune_fwd_group = fwd_group;
   g->tune_adj_two = adj_pixels_per_thread == 0 ? -1 : (adj_pixels_per_thread == 2 ? 1 : 0);

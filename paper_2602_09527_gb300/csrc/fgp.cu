@@ -40,7 +40,9 @@ struct FgpTile {
   static constexpr int NS = (NE + NT - 1) / NT;
   static constexpr size_t SMEM = sizeof(float) * 6 * NE;
 };
-using TileLarge = FgpTile<32, 32, 512>;
+using TileLarge = FgpTile<32, 32, 512>;   // 48 x 48 grown tile, 55 KB
+using TileWide = FgpTile<32, 16, 256>;    // 48 x 32, 36 KB: twice the tiles of TileLarge
+using TileSmall = FgpTile<16, 16, 256>;   // 32 x 32, 24 KB: four times the tiles
 
 
 // Projection onto the unit ball: g / max(1, |g|) through the hardware reciprocal square
@@ -457,7 +459,10 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     const float* rz = dual;
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
     int which = 0;
+    const int tile = g->tune_fgp_tile;   // 0 large, 1 wide, 2 small
     VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLarge>, TileLarge::SMEM));
+    VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileWide>, TileWide::SMEM));
+    VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileSmall>, TileSmall::SMEM));
     const std::vector<MomBlock> moms = fgp_momentum(iters);
     for (int k0 = 0; k0 < iters; k0 += FB_T) {
       const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
@@ -467,9 +472,15 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
       {
         // read v, w and z (one array when z = w), write w and z
         LaunchScope _ls("fgp2d_block", s, 4.0 * g->n * (rz == rw ? 7 : 9));
-        dim3 grid((g->nx + TileLarge::TX - 1) / TileLarge::TX, (g->ny + TileLarge::TY - 1) / TileLarge::TY);
         const FgpBlockArgs A{v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg};
-        VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, A));
+        auto launch = [&](auto kern, auto tl) -> cudaError_t {
+          using TL = decltype(tl);
+          dim3 grid((g->nx + TL::TX - 1) / TL::TX, (g->ny + TL::TY - 1) / TL::TY);
+          return launch_kernel(kern, grid, dim3(TL::NT), (size_t)TL::SMEM, s, A);
+        };
+        if (tile == 1) VRPS_CUDA(launch(fgp2d_block<TileWide>, TileWide{}));
+        else if (tile == 2) VRPS_CUDA(launch(fgp2d_block<TileSmall>, TileSmall{}));
+        else VRPS_CUDA(launch(fgp2d_block<TileLarge>, TileLarge{}));
       }
       VRPS_LAUNCHED("fgp2d_block");
       rw = wn;

@@ -190,6 +190,7 @@ struct vrps_geom {
   int tune_fwd_group = 0;   // bands per forward CTA item (0: one)
   int tune_adj_two = -1;    // 2D adjoint: two pixels per thread (1) or one (0)
   int tune_f3_zc = 0;       // 3D FGP: z planes per streaming chunk
+  int tune_fgp_tile = 0;    // 2D FGP output tile: 0 32x32, 1 32x16, 2 16x16
   // 3D tables
   vrps::RayInfo3D* ray3d = nullptr;     // [n_views][nu]
   vrps::ViewInfo3D* view3d = nullptr;   // [n_views]

@@ -102,3 +102,20 @@ def test_fgp3d_after_autotune():
     x = vr.prox_tv(g, dev(v), 0.05, 12)
     ref, _ = tv.fgp(v, 0.05, 12)
     assert rel(host(x), ref) < TOL
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(70, 45), (16, 130)])
+def test_fgp2d_tiles(tile, shape):
+    """The three 2D output tiles the autotuner chooses from give the oracle's K-step FGP."""
+    vr, g = _geom2(shape[1], shape[0])
+    vr.set_launch_shape(g, fgp_tile=tile)
+    rng = np.random.default_rng(tile + shape[0])
+    v = rng.uniform(-0.2, 1.0, size=shape)
+    w0 = rng.standard_normal(2 * v.size) * 0.3
+    w0 = (w0.reshape(2, -1) / np.maximum(1.0, np.sqrt((w0.reshape(2, -1) ** 2).sum(0)))).ravel()
+    d = dev(w0)
+    x = vr.prox_tv(g, dev(v), 0.05, 21, dual=d)
+    ref, wref = tv.fgp(v, 0.05, 21, w0=w0)
+    assert rel(host(x), ref) < TOL
+    assert rel(host(d), wref) < TOL
