@@ -74,7 +74,10 @@ WORKLOADS_BATCH = {
 WORKLOADS_SERVE = {
     "serve": dict(rate=50.0, seconds=60.0, sides=(128, 256, 384, 512, 1024), n_min=10, n_max=30,
                   alpha=(0.005, 0.05), p=0.1, fgp_iters=50, epochs=20, pool=4, handles=24,
-                  budget_gb=120.0, seed=20260209),
+                  budget_gb=120.0, seed=20260209,
+                  # 3D requests: the 256^3 cone geometry scaled to side s (same field of view, views
+                  # 1.4 s, detector 1.5 s), N = 30, served by a worker on a second stream
+                  share3d=0.05, sides3d=(64, 128), pool3d=2, handles3d=2),
 }
 
 # Operator costs (optional), the structure of the paper's cost figure on the 512^2 / 720-angle
@@ -570,26 +573,53 @@ def bench_serve(args, rank, world, local):
             ells = synthetic.random_ellipses(10, side / 2.0, rng)
             b = synthetic.gaussian_noise(synthetic.ellipse_sinogram(ells, spec.angles, spec.bin_centers()), 0.01, rng)
             data[side].append(torch.tensor(b.astype(np.float32).ravel(), device="cuda"))
+    pools3, data3, lips3 = {}, {}, {}
+    for side in w["sides3d"]:
+        views, det = int(round(1.4 * side)), int(round(1.5 * side))
+        key = ("3d", side)
+        data3[key] = []
+        for q in range(w["pool3d"]):
+            P3 = synthetic.make_problem_3d(side, 0.5 * 256 / side, views, det, 384.0 / det, 500.0, 1000.0, 30,
+                                           seed=w["seed"] + 97 * q + side)
+            data3[key].append(torch.tensor(P3.b.astype(np.float32).ravel(), device="cuda"))
+        pools3[key] = [vr.Geometry.from_spec(P3.spec) for _ in range(w["handles3d"])]
+        lips3[key] = vr.power_iteration(pools3[key][0], 30, seed=w["seed"])
     # one arrival sequence for every variant
     t, arrivals = 0.0, []
     while True:
         t += rng.exponential(1.0 / w["rate"])
         if t > seconds:
             break
+        if rng.uniform() < w["share3d"]:
+            key = ("3d", int(rng.choice(w["sides3d"])))
+            arrivals.append(dict(arrival=t, key=key, k=int(rng.integers(w["pool3d"])),
+                                 alpha=float(rng.uniform(*w["alpha"])), N=30, seed=int(rng.integers(1 << 40))))
+            continue
         side = int(rng.choice(w["sides"]))
-        arrivals.append(dict(arrival=t, side=side, k=int(rng.integers(w["pool"])),
+        arrivals.append(dict(arrival=t, key=side, k=int(rng.integers(w["pool"])),
                              alpha=float(rng.uniform(*w["alpha"])), N=int(rng.integers(w["n_min"], w["n_max"] + 1)),
                              seed=int(rng.integers(1 << 40))))
 
     def requests(storage, corr):
-        return [serve.Request(key=a["side"], b=data[a["side"]][a["k"]], arrival=a["arrival"], alpha=a["alpha"],
-                              gamma=1.0 / (3.0 * lips[a["side"]]), seed=a["seed"], p=w["p"], estimator="SAGA",
-                              fgp_iters=w["fgp_iters"], max_iters=w["epochs"] * a["N"], n_subsets=a["N"],
-                              storage=storage, correction_epochs=corr) for a in arrivals]
+        out = []
+        for a in arrivals:
+            is3 = isinstance(a["key"], tuple)
+            b = (data3 if is3 else data)[a["key"]][a["k"]]
+            lip = (lips3 if is3 else lips)[a["key"]]
+            out.append(serve.Request(key=a["key"], b=b, arrival=a["arrival"], alpha=a["alpha"], gamma=1.0 / (3.0 * lip),
+                                     seed=a["seed"], p=w["p"], estimator="SAGA", fgp_iters=w["fgp_iters"],
+                                     max_iters=w["epochs"] * a["N"], n_subsets=a["N"],
+                                     storage=storage if not is3 else "FP32", correction_epochs=corr if not is3 else 0))
+        return out
 
     def summary(st, reqs):
         lat = st.latencies
+        l2 = [r.finished - r.arrival for r in reqs if not isinstance(r.key, tuple) and r.finished is not None]
+        l3 = [r.finished - r.arrival for r in reqs if isinstance(r.key, tuple) and r.finished is not None]
         return {"p50_s": round(serve.percentile(lat, 50), 4), "p99_s": round(serve.percentile(lat, 99), 4),
+                "p50_2d_s": round(serve.percentile(l2, 50), 4), "p99_2d_s": round(serve.percentile(l2, 99), 4),
+                "p50_3d_s": round(serve.percentile(l3, 50), 4), "p99_3d_s": round(serve.percentile(l3, 99), 4),
+                "requests_3d": len(l3),
                 "mean_s": round(float(np.mean(lat)), 4), "completed": st.completed,
                 "reconstructions_per_s": round(st.completed / st.wall, 3), "wall_s": round(st.wall, 3),
                 "queue_wait_p99_s": round(serve.percentile(st.queue_waits, 99), 4),
@@ -600,7 +630,7 @@ def bench_serve(args, rank, world, local):
     warm = requests("FP16", 1)[: min(len(arrivals), 40)]
     for r in warm:
         r.arrival = 0.0
-    srv = serve.BatchServer(pools, budget)
+    srv = serve.MixedServer(pools, pools3, budget)
     srv.run(warm)
     results = {}
     launches0 = vr.kernel_launches()
@@ -612,11 +642,11 @@ def bench_serve(args, rank, world, local):
     reqs32 = requests("FP32", 0)
     results["batched_fp32"] = summary(srv.run(reqs32), reqs32)
     srv.close()
-    seq = serve.SequentialServer(pools)
+    seq = serve.SequentialServer({**pools, **pools3})
     reqsq = requests("FP32", 0)
     results["per_job_fp32"] = summary(seq.run(reqsq), reqsq)
     # same job alone and in the mix: the served results equal vrps_solve's bit for bit
-    same = all(torch.equal(a.x, b.x) for a, b in zip(reqs32[:50], reqsq[:50]))
+    same = all(torch.equal(a.x, b.x) for a, b in zip(reqs32[:50], reqsq[:50]) if a.x is not None)
     head = results["batched_fp16"]
     out = {
         "metric": "served p99 latency",
@@ -636,7 +666,8 @@ def bench_serve(args, rank, world, local):
                    "alpha": f"U{list(w['alpha'])}", "algo": "ProxSAGASkip", "p": w["p"], "fgp_iters": w["fgp_iters"],
                    "epochs": w["epochs"], "budget_gb": w["budget_gb"], "handles_per_size": w["handles"],
                    "ticks_per_step": 2, "timing": "host wall clock per request (arrival to completion)",
-                   "scope": "2D requests only"},
+                   "share_3d": w["share3d"], "sides_3d": list(w["sides3d"]),
+                   "scope": "2D requests continuously batched; 3D requests by a worker on a second stream"},
         "p50_s": head["p50_s"],
         "reconstructions_per_s": head["reconstructions_per_s"],
         "variants": results,
