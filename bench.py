@@ -77,7 +77,7 @@ WORKLOADS_SERVE = {
                   budget_gb=120.0, seed=20260209,
                   # 3D requests: the 256^3 cone geometry scaled to side s (same field of view, views
                   # 1.4 s, detector 1.5 s), N = 30, served by a worker on a second stream
-                  share3d=0.05, sides3d=(64, 128), pool3d=2, handles3d=2),
+                  share3d=0.02, sides3d=(64, 96), pool3d=2, handles3d=2),
 }
 
 # Operator costs (optional), the structure of the paper's cost figure on the 512^2 / 720-angle
