@@ -1,14 +1,15 @@
 // 2D parallel-beam Joseph projector: ray-driven forward (gather) with fused residual /
 // estimator epilogues, and pixel-driven exact transpose with the fused ProxSkip update.
 //
-// Forward (Section 1.2, A_i x): one CTA row of 32 bins x 8 line phases marches the rays
-// of one angle; each thread accumulates every 8th dominant-axis line, the 8 partial sums
-// are reduced in shared memory in a fixed order.  Rays of angles marched along columns
-// read the transposed image so that the 32 lanes always read along a row (coalesced).
+// Forward (Section 1.2, A_i x): a CTA item is (angle, group of bands of dominant-axis lines);
+// the band is copied into shared memory by bulk copies (rows of x, or of x^T for angles
+// marched along columns, so that adjacent rays read along a row) and every ray of the angle
+// is walked through it with exact fixed-point positions; per-group partial ray sums are added
+// in a fixed order by the CTA that completes the angle, which runs the estimator epilogue.
 //
-// Adjoint (A_i^T r): one thread per pixel of a 16x16 tile.  For every angle of the launch
-// the tile's footprint on the detector (at most fp bins) is staged in shared memory, then
-// each pixel sums w_j r_j over the <= nc bins whose ray passes within one interpolation
+// Adjoint (A_i^T r): a CTA owns a 16 x 16 or 16 x 32 pixel tile.  For every angle of the
+// launch the tile's footprint on the detector (at most fp bins) is staged in shared memory,
+// then each pixel sums w_j r_j over the <= nc bins whose ray passes within one interpolation
 // cell of its centre, with the Joseph weight of that (ray, pixel) pair.  No atomics.
 #include <cstdint>
 #include <cstring>
@@ -21,8 +22,7 @@ namespace {
 constexpr int FWD_LANES = 32;
 constexpr int FWD_THREADS = 256;
 constexpr int FWD_BAND_BYTES = 64 * 1024;   // shared-memory band of image lines per CTA
-constexpr int ADJ_TX = ADJ2D_TILE_X;        // pixel tile: 16 columns x 32 rows
-constexpr int ADJ_TY = ADJ2D_TILE_Y;
+constexpr int ADJ_TX = ADJ2D_TILE_X;        // pixel tile: 16 columns (x 16 or 32 rows)
 constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_CHUNK = 64;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // bounded mbarrier polls before giving up
@@ -36,15 +36,6 @@ __device__ __forceinline__ unsigned long long global_addr(const void* p) {
   return g;
 }
 
-// TMA bulk copy global -> shared completing on an mbarrier (transaction bytes).
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(global_addr(src)), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
   unsigned ok;
