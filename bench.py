@@ -106,6 +106,28 @@ def _env_int(name, default):
         return default
 
 
+def max_over_ranks(value, dist):
+    """The largest of every rank's value (the replicas' timed region ends with the slowest)."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, world, seconds):
+    """Whole-job throughput of N independent replicas: every rank's units over the slowest time."""
+    return units_per_rank * world / seconds
+
+
+def emit(out, rank):
+    """Only rank 0 prints the JSON line."""
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def make_problem(wl, rank):
     w = WORKLOADS[wl]
     return synthetic.make_problem_2d(w["n"], w["n_angles"], w["n_bins"], w["n_subsets"], seed=w["seed"] + rank,
@@ -313,10 +335,7 @@ def bench_3d(args, rank, world, local):
             dist.barrier()
     launches = (vr.kernel_launches() - launches0) // args.steps
     total = sum(times)
-    if dist is not None:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, dist)
     sec_epoch = total / args.steps / w["epochs"]
     e2e = []
     for _ in range(2):
@@ -495,10 +514,7 @@ def bench_batch(args, rank, world, local):
     dF16 = max(abs(a - b) / abs(b) for a, b in zip(F_b16, F_seq))
     dFo = max(abs(a - b) / abs(b) for a, b in zip(F_oth, F_seq))
     total = sum(times)
-    if dist is not None:
-        tt = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
+    total = max_over_ranks(total, dist)
     sec = total / args.steps
     ticks, _ = B.ticks()
     # per-kernel shares of one batched run (CUDA events; graphs are bypassed while profiling)
@@ -863,10 +879,7 @@ def main():
             dist.barrier()
     launches = (vr.kernel_launches() - launches0) // args.steps
     total = sum(times)
-    if dist is not None:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, dist)
     sec_per = total / args.steps
 
     # end to end through the public API with host buffers (H2D of b, D2H of x inside)
@@ -947,7 +960,7 @@ def main():
         "projector": {"metric": "G ray-voxel/s", "value": round(gvox, 3), "samples_per_subset": samples_sub,
                       "fwd_us": round(t_fwd * 1e6, 3), "adj_us": round(t_adj * 1e6, 3),
                       "what": "subset 0 (36 angles x 768 bins): 2 x Joseph samples / (forward + adjoint kernel time)"},
-        "reconstructions_per_s": round(world / sec_per, 4),
+        "reconstructions_per_s": round(replica_value(1, world, sec_per), 4),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
