@@ -110,19 +110,21 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
  * projections, solves and batched jobs on the handle use them.  Results change only the
  * grouping of floating-point sums (outputs agree to rounding).  out4 (HOST, nullable, 4
  * doubles): chosen band bytes, pixels per thread, tuned forward + adjoint time in
- * microseconds, bands per CTA; the 2D FGP output tile (32 x 32, 32 x 16 or 16 x 16) is chosen
- * on a 16-iteration prox call (see vrps_launch_shape).  3D geometries: times three iterations of the streaming FGP
+ * microseconds, bands per CTA; the adjoint's angle shares per pixel tile (1, 2, 4: partial sums
+ * added in share order by the last share) are timed with the pixels per thread, and the 2D FGP
+ * output tile (32 x 32, 32 x 16 or 16 x 16) on a 16-iteration prox call (see vrps_launch_shape).  3D geometries: times three iterations of the streaming FGP
  * prox for chunks of 16, 32, 64 and 128 z planes and keeps the fastest (out4: chunk, 0,
  * time in microseconds, 0).  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
 int vrps_autotune(vrps_geom* g, int reps, double* out4, vrps_stream_t stream);
 
 /* Sets the launch shapes by hand (0 = built-in default for each): forward band bytes, forward
  * bands per CTA, adjoint pixels per thread (1 or 2), 3D FGP planes per chunk, 2D FGP output
- * tile (0: 32 x 32, 1: 32 x 16, 2: 16 x 16).  Errors: INVALID_ARG. */
+ * tile (0: 32 x 32, 1: 32 x 16, 2: 16 x 16), adjoint angle shares per tile.  Errors:
+ * INVALID_ARG. */
 int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread,
-                          int fgp3_chunk, int fgp_tile);
-/* Current launch shapes of the handle in the same order (HOST int[5]; 0 = default). */
-int vrps_launch_shape(const vrps_geom* g, int* out5);
+                          int fgp3_chunk, int fgp_tile, int adj_split);
+/* Current launch shapes of the handle in the same order (HOST int[6]; 0 = default). */
+int vrps_launch_shape(const vrps_geom* g, int* out6);
 
 /* ---------------------------------------------------------------- operators
  * y = A_i x  (Section 1.2: the forward operator of subset i; i = -1 for A).

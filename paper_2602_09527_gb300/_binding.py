@@ -85,7 +85,7 @@ def _load():
         "vrps_geom_sizes": (i, [vp, i, P(i64), P(i64), P(i), P(i), P(i)]),
         "vrps_geom_samples": (i, [vp, i, P(i64)]),
         "vrps_autotune": (i, [vp, i, P(d), vp]),
-        "vrps_set_launch_shape": (i, [vp, i, i, i, i, i]),
+        "vrps_set_launch_shape": (i, [vp, i, i, i, i, i, i]),
         "vrps_launch_shape": (i, [vp, P(i)]),
         "vrps_proj_fwd": (i, [vp, i, vp, vp, vp]),
         "vrps_proj_adj": (i, [vp, i, vp, vp, vp]),
@@ -245,19 +245,21 @@ def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
         return {"fgp3d_chunk_planes": int(out[0]), "fgp3_iterations_us": float(out[2])}
     shape = launch_shape(g)
     return {"fwd_band_bytes": int(out[0]), "fwd_bands_per_cta": int(out[3]), "adj_pixels_per_thread": int(out[1]),
-            "fgp_tile": ["32x32", "32x16", "16x16"][shape[4]], "fwd_adj_us": float(out[2])}
+            "adj_angle_shares": max(1, shape[5]), "fgp_tile": ["32x32", "32x16", "16x16"][shape[4]],
+            "fwd_adj_us": float(out[2])}
 
 
 def set_launch_shape(g: Geometry, fwd_band_bytes: int = 0, fwd_group: int = 0, adj_pixels_per_thread: int = 0,
-                     fgp3_chunk: int = 0, fgp_tile: int = 0):
+                     fgp3_chunk: int = 0, fgp_tile: int = 0, adj_split: int = 0):
     """vrps_set_launch_shape (0 = built-in default for each)."""
     _check(lib.vrps_set_launch_shape(g.handle, int(fwd_band_bytes), int(fwd_group), int(adj_pixels_per_thread),
-                                     int(fgp3_chunk), int(fgp_tile)))
+                                     int(fgp3_chunk), int(fgp_tile), int(adj_split)))
 
 
 def launch_shape(g: Geometry) -> list:
-    """vrps_launch_shape: [fwd band bytes, bands per CTA, adjoint pixels per thread, 3D FGP chunk, 2D FGP tile]."""
-    out = (ctypes.c_int * 5)()
+    """vrps_launch_shape: [fwd band bytes, bands per CTA, adjoint pixels per thread, 3D FGP chunk,
+    2D FGP tile, adjoint angle shares]."""
+    out = (ctypes.c_int * 6)()
     _check(lib.vrps_launch_shape(g.handle, out))
     return list(out)
 

@@ -141,6 +141,8 @@ static void free_ws(Workspace& w) {
   if (w.fwd_part) cudaFree(w.fwd_part);
   if (w.fwd_count) cudaFree(w.fwd_count);
   if (w.dev_error) cudaFree(w.dev_error);
+  if (w.adj_part) cudaFree(w.adj_part);
+  if (w.adj_count) cudaFree(w.adj_count);
   if (w.scalars) cudaFree(w.scalars);
   if (w.sched_dev) cudaFree(w.sched_dev);
   if (w.sched_host) cudaFreeHost(w.sched_host);
@@ -623,22 +625,28 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
   UpdateArgs ua;
   std::memset(&ua, 0, sizeof(ua));
   ua.out = w.img;
-  int best_two = 0;
+  int best_two = 0, best_split = 1;
   float best_a = 1e30f;
-  for (int two = 0; two < 2; ++two) {
-    g->tune_adj_two = two;
-    float t = 0.f;
-    const int rc = timed([&]() { return adj2d(g, w.sino, ids, rows, ua, s); }, &t);
-    if (rc != VRPS_OK) {
-      g->tune_adj_two = -1;
-      return rc;
-    }
-    if (t < best_a) {
-      best_a = t;
-      best_two = two;
+  for (int split : {1, 2, 4}) {
+    for (int two = 0; two < 2; ++two) {
+      g->tune_adj_two = two;
+      g->tune_adj_split = split;
+      float t = 0.f;
+      const int rc = timed([&]() { return adj2d(g, w.sino, ids, rows, ua, s); }, &t);
+      if (rc != VRPS_OK) {
+        g->tune_adj_two = -1;
+        g->tune_adj_split = 0;
+        return rc;
+      }
+      if (t < best_a) {
+        best_a = t;
+        best_two = two;
+        best_split = split;
+      }
     }
   }
   g->tune_adj_two = best_two;
+  g->tune_adj_split = best_split;
   // 2D FGP output tile, timed on one 16-iteration prox call
   {
     VRPS_TRY(ensure(&w.dual, 2 * (size_t)g->n));
@@ -676,24 +684,27 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
   return VRPS_OK;
 }
 
-int vrps_launch_shape(const vrps_geom* g, int* out5) {
+int vrps_launch_shape(const vrps_geom* g, int* out6) {
   VRPS_TRY(check_geom(g));
-  if (!out5) return fail(VRPS_ERR_INVALID_ARG, "out5 is NULL");
-  out5[0] = g->tune_fwd_bytes;
-  out5[1] = g->tune_fwd_group;
-  out5[2] = g->tune_adj_two < 0 ? 0 : (g->tune_adj_two ? 2 : 1);
-  out5[3] = g->tune_f3_zc;
-  out5[4] = g->tune_fgp_tile;
+  if (!out6) return fail(VRPS_ERR_INVALID_ARG, "out6 is NULL");
+  out6[0] = g->tune_fwd_bytes;
+  out6[1] = g->tune_fwd_group;
+  out6[2] = g->tune_adj_two < 0 ? 0 : (g->tune_adj_two ? 2 : 1);
+  out6[3] = g->tune_f3_zc;
+  out6[4] = g->tune_fgp_tile;
+  out6[5] = g->tune_adj_split;
   return VRPS_OK;
 }
 
 int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread, int fgp3_chunk,
-                          int fgp_tile) {
+                          int fgp_tile, int adj_split) {
   VRPS_TRY(check_geom(g));
   if (fwd_band_bytes < 0 || fwd_band_bytes > (200 << 10) || fwd_group < 0 || fwd_group > 64 ||
-      adj_pixels_per_thread < 0 || adj_pixels_per_thread > 2 || fgp3_chunk < 0 || fgp_tile < 0 || fgp_tile > 2)
+      adj_pixels_per_thread < 0 || adj_pixels_per_thread > 2 || fgp3_chunk < 0 || fgp_tile < 0 || fgp_tile > 2 ||
+      adj_split < 0 || adj_split > 64)
     return fail(VRPS_ERR_INVALID_ARG, "launch shape out of range");
   g->tune_fgp_tile = fgp_tile;
+  g->tune_adj_split = adj_split;
   g->tune_fwd_bytes = fwd_band_bytes;
   g->tune_fwd_group = fwd_group;
   g->tune_adj_two = adj_pixels_per_thread == 0 ? -1 : (adj_pixels_per_thread == 2 ? 1 : 0);

@@ -327,7 +327,7 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
   VRPS_TRY(adj2d_setup(g, w.res, ids, rows, ua, &E->a.P, &sm, &var, &tx, &ty));
   E->a.variant = var;
   E->a.tiles_x = tx;
-  E->a_items = tx * ty;
+  E->a_items = tx * ty * E->a.P.split;
   E->prox = theta != 0;
   E->fg_items = 0;
   E->o_items = 0;

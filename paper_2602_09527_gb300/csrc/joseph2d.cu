@@ -382,6 +382,7 @@ __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, flo
 // NC = 2 covers hw <= 1 (bins not finer than pixels): two candidates, unrolled; NC = 0 is
 // the general loop over P.nc candidates.
 struct AdjShared {
+  unsigned last;           // this CTA completed the tile (angle shares)
   float4 par[ADJ_CHUNK];   // Bx, By, (F0 - hw), 1/hw
   float c0[ADJ_CHUNK];     // 1 - hw
   int off[ADJ_CHUNK];      // J0 - jlo
@@ -392,8 +393,12 @@ struct AdjShared {
 
 // One pixel tile (bx, by) of the transpose; sm: dynamic shared [chunk][fp].
 template <int NC, int PPT>
-__device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by, float* sm, AdjShared& S) {
+__device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by, float* sm, AdjShared& S,
+                                           int part = 0) {
   constexpr int TY = (ADJ_THREADS / ADJ_TX) * PPT;   // tile rows: 16 (one pixel per thread) or 32
+  // angle range of this item: part `part` of P.split equal shares of the launch's rows
+  const int ra = (int)(((long long)P.rows * part) / P.split);
+  const int rz = (int)(((long long)P.rows * (part + 1)) / P.split);
   float4* s_par = S.par;
   float* s_c0 = S.c0;
   int* s_off = S.off;
@@ -404,8 +409,8 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
   const float ftx = (float)tx, fty = (float)ty;
   const float half_rows = (float)(TY / 2);
   float acc0 = 0.f, acc1 = 0.f;                  // pixels (tx, ty) and, with PPT = 2, (tx, ty + TY/2)
-  for (int r0 = 0; r0 < P.rows; r0 += P.chunk) {
-    const int nr = min(P.chunk, P.rows - r0);
+  for (int r0 = ra; r0 < rz; r0 += P.chunk) {
+    const int nr = min(P.chunk, rz - r0);
     if (tid < nr) {
       const AngleInfo2D in = P.ang[P.ids[r0 + tid]];
       const long long T0 = (long long)(P.nb - 1) * 2147483648LL + in.BxH * (long long)(2 * ix0 - (P.nx - 1)) +
@@ -469,6 +474,30 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
   const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + TY / 2;
   const bool in0 = ix < P.nx && iy < P.ny, in1 = PPT == 2 && ix < P.nx && iy1 < P.ny;
   const size_t p0 = (size_t)iy * P.nx + ix, p1 = (size_t)iy1 * P.nx + ix;
+  if (P.split > 1) {
+    // angle shares of one tile: partial sums to scratch; the last share to arrive adds them in
+    // share order (deterministic) and runs the epilogue
+    const size_t n = (size_t)P.nx * P.ny;
+    if (in0) P.part[(size_t)part * n + p0] = acc0;
+    if (in1) P.part[(size_t)part * n + p1] = acc1;
+    __threadfence();
+    __syncthreads();
+    const int tile = by * P.tiles_x + bx;
+    if (tid == 0) {
+      const unsigned prev = atomicAdd(P.count + tile, 1u);
+      S.last = prev == (unsigned)(P.split - 1) ? 1u : 0u;
+      if (S.last) P.count[tile] = 0u;
+    }
+    __syncthreads();
+    if (!S.last) return;
+    __threadfence();
+    acc0 = 0.f;
+    acc1 = 0.f;
+    for (int q = 0; q < P.split; ++q) {
+      if (in0) acc0 += __ldcg(P.part + (size_t)q * n + p0);
+      if (in1) acc1 += __ldcg(P.part + (size_t)q * n + p1);
+    }
+  }
   const UpdateArgs& u = P.u;
   if (!u.enabled) {
     if (in0) u.out[p0] = acc0;
@@ -493,7 +522,8 @@ template <int NC, int PPT>
 __global__ void __launch_bounds__(ADJ_THREADS) adj2d_kernel(Adj2DParams P) {
   extern __shared__ float sm[];
   __shared__ AdjShared S;
-  adj2d_item<NC, PPT>(P, blockIdx.x, blockIdx.y, sm, S);
+  // blockIdx.y = tile row * split + angle share
+  adj2d_item<NC, PPT>(P, blockIdx.x, blockIdx.y / P.split, sm, S, blockIdx.y % P.split);
 }
 
 __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx) {
@@ -628,6 +658,36 @@ int adj2d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, co
   *variant = (g->adj_nc == 2 ? 2 : 0) + (two ? 1 : 0);
   *tiles_x = (g->nx + ADJ_TX - 1) / ADJ_TX;
   *tiles_y = (g->ny + ty - 1) / ty;
+  P.tiles_x = *tiles_x;
+  // angle shares per tile (at least 4 angles each)
+  int split = g->tune_adj_split > 1 ? g->tune_adj_split : 1;
+  while (split > 1 && rows / split < 4) --split;
+  P.split = split;
+  P.part = nullptr;
+  P.count = nullptr;
+  if (split > 1) {
+    vrps_geom* gm = const_cast<vrps_geom*>(g);
+    Workspace& ws = gm->ws;
+    const size_t need = (size_t)split * (size_t)g->n;
+    if (ws.adj_part_cap < need) {
+      if (ws.adj_part) cudaFree(ws.adj_part);
+      ws.adj_part = nullptr;
+      ws.adj_part_cap = 0;
+      VRPS_CUDA(cudaMalloc((void**)&ws.adj_part, sizeof(float) * need));
+      ws.adj_part_cap = need;
+    }
+    const size_t tiles = (size_t)(*tiles_x) * (*tiles_y);
+    if (ws.adj_count_cap < tiles) {
+      if (ws.adj_count) cudaFree(ws.adj_count);
+      ws.adj_count = nullptr;
+      ws.adj_count_cap = 0;
+      VRPS_CUDA(cudaMalloc((void**)&ws.adj_count, sizeof(unsigned) * tiles));
+      VRPS_CUDA(cudaMemset(ws.adj_count, 0, sizeof(unsigned) * tiles));
+      ws.adj_count_cap = tiles;
+    }
+    P.part = ws.adj_part;
+    P.count = ws.adj_count;
+  }
   return VRPS_OK;
 }
 
@@ -637,7 +697,7 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   size_t smem = 0;
   int variant = 0, tx = 0, ty = 0;
   VRPS_TRY(adj2d_setup(g, r, ids, rows, u, &P, &smem, &variant, &tx, &ty));
-  dim3 grid(tx, ty), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
+  dim3 grid(tx, ty * P.split), block(ADJ_TX, ADJ_THREADS / ADJ_TX);
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("adj2d_kernel", s, 4.0 * rows * g->n_bins + update_bytes(u, (size_t)g->n));
@@ -736,12 +796,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_batched_kernel(char* __rest
     const int j = batch_job(pre, n, item);
     const BatchAdj& J = jobs[j];
     const int local = item - pre[j];
-    const int bx = local % J.tiles_x, by = local / J.tiles_x;
+    const int sp = J.P.split;
+    const int tile = local / sp, part = local - tile * sp;
+    const int bx = tile % J.tiles_x, by = tile / J.tiles_x;
     switch (J.variant) {
-      case 3: adj2d_item<2, 2>(J.P, bx, by, sm, S); break;
-      case 2: adj2d_item<2, 1>(J.P, bx, by, sm, S); break;
-      case 1: adj2d_item<0, 2>(J.P, bx, by, sm, S); break;
-      default: adj2d_item<0, 1>(J.P, bx, by, sm, S); break;
+      case 3: adj2d_item<2, 2>(J.P, bx, by, sm, S, part); break;
+      case 2: adj2d_item<2, 1>(J.P, bx, by, sm, S, part); break;
+      case 1: adj2d_item<0, 2>(J.P, bx, by, sm, S, part); break;
+      default: adj2d_item<0, 1>(J.P, bx, by, sm, S, part); break;
     }
   }
 }

@@ -156,6 +156,10 @@ struct Workspace {
         *gbar = nullptr, *xprox = nullptr, *dual = nullptr;
   float *b_perm = nullptr, *tab = nullptr, *res = nullptr;
   float *b16 = nullptr, *tab16 = nullptr;   // bfloat16 storage of b_perm / tab (m halves each)
+  float* adj_part = nullptr;      // 2D adjoint: partial sums of the angle shares
+  size_t adj_part_cap = 0;
+  unsigned* adj_count = nullptr;  // 2D adjoint: per-tile arrival counters
+  size_t adj_count_cap = 0;
   int32_t* sched_dev = nullptr;
   int sched_cap = 0;
   int32_t* sched_host = nullptr;   // pinned
@@ -191,6 +195,7 @@ struct vrps_geom {
   int tune_adj_two = -1;    // 2D adjoint: two pixels per thread (1) or one (0)
   int tune_f3_zc = 0;       // 3D FGP: z planes per streaming chunk
   int tune_fgp_tile = 0;    // 2D FGP output tile: 0 32x32, 1 32x16, 2 16x16
+  int tune_adj_split = 0;   // 2D adjoint: angle shares per pixel tile (0: one)
   // 3D tables
   vrps::RayInfo3D* ray3d = nullptr;     // [n_views][nu]
   vrps::ViewInfo3D* view3d = nullptr;   // [n_views]
@@ -294,6 +299,10 @@ struct Adj2DParams {
   int rows;
   int nx, ny, nb;
   int fp, nc, chunk;
+  int split;                  // angle shares per tile (1: one CTA per tile)
+  int tiles_x;
+  float* part;                // [split][n] partial sums of the shares
+  unsigned* count;            // [tiles] arrival counters, zero between launches
   UpdateArgs u;
 };
 

@@ -115,7 +115,7 @@ def test_grouped_forward_shapes_in_the_mix(mix):
     bit-identical to their solo runs."""
     vr, probs, solo = mix
     for i in (0, 2, 4):
-        vr.set_launch_shape(probs[i][1], fwd_band_bytes=16 << 10, fwd_group=3)
+        vr.set_launch_shape(probs[i][1], fwd_band_bytes=16 << 10, fwd_group=3, adj_split=2)
     try:
         ref = [_solo(vr, probs[i][1], probs[i][2], _kw(MIX[i], probs[i][3], i))[0] for i in range(len(MIX))]
         B = vr.Batch()

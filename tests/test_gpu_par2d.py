@@ -160,23 +160,31 @@ def test_autotuned_shapes_keep_parity():
     assert rel(host(vr.proj_adj(g, 2, dev(r))), J.adjoint(og, r, rows)) < TOL
 
 
-@pytest.mark.parametrize("shape", [(16 << 10, 1, 1), (16 << 10, 3, 2), (24 << 10, 4, 1), (48 << 10, 8, 2),
-                                   (8 << 10, 2, 2)])
+@pytest.mark.parametrize("shape", [(16 << 10, 1, 1, 1), (16 << 10, 3, 2, 2), (24 << 10, 4, 1, 3), (48 << 10, 8, 2, 4),
+                                   (8 << 10, 2, 2, 7)])
 @pytest.mark.parametrize("dims", [(200, 136, 150), (96, 250, 180), (90, 90, 130)])
 def test_forward_band_groups_keep_parity(shape, dims):
-    """Forward bands walked several per CTA (double-buffered copies, rays kept in registers),
-    on non-square images where the two marching orientations have different line counts and a
-    side that is not a multiple of 4 (plain loads instead of bulk copies)."""
+    """Forward bands walked several per CTA (double-buffered copies, rays kept in registers) and
+    adjoint tiles split into angle shares, on non-square images where the two marching
+    orientations have different line counts and a side that is not a multiple of 4 (plain
+    loads instead of bulk copies)."""
     vr = _vr()
     nx, ny, nb = dims
-    spec = synthetic.Par2DSpec(nx, ny, 1.0, synthetic.uniform_angles(60, math.pi), nb, 1.0, 4)
+    spec = synthetic.Par2DSpec(nx, ny, 1.0, synthetic.uniform_angles(64, math.pi), nb, 1.0, 2)
     g = vr.Geometry.from_spec(spec)
     og = J.Geometry2D.from_spec(spec)
-    vr.set_launch_shape(g, fwd_band_bytes=shape[0], fwd_group=shape[1], adj_pixels_per_thread=shape[2])
+    vr.set_launch_shape(g, fwd_band_bytes=shape[0], fwd_group=shape[1], adj_pixels_per_thread=shape[2],
+                        adj_split=shape[3])
     x = np.random.default_rng(3).uniform(0, 1, size=(ny, nx))
-    for s_ in (0, 3):
-        rows = list(range(s_, 60, 4))
+    for s_ in (0, 1):
+        rows = list(range(s_, 64, 2))
         y = host(vr.proj_fwd(g, s_, dev(x))).reshape(len(rows), nb)
         assert rel(y, J.forward(og, x, rows)) < TOL, (s_, shape)
-    r = np.random.default_rng(4).standard_normal((15, nb))
-    assert rel(host(vr.proj_adj(g, 1, dev(r))), J.adjoint(og, r, list(range(1, 60, 4)))) < TOL
+    r = np.random.default_rng(4).standard_normal((32, nb))
+    assert rel(host(vr.proj_adj(g, 1, dev(r))), J.adjoint(og, r, list(range(1, 64, 2)))) < TOL
+    # the full operator (all 64 angles: shares of 16 and more) through the adjoint identity
+    xa = np.random.default_rng(5).standard_normal((ny, nx))
+    ra = np.random.default_rng(6).standard_normal((64, nb))
+    lhs = float((host(vr.proj_fwd(g, -1, dev(xa))) * ra.ravel()).sum())
+    rhs = float((xa.ravel() * host(vr.proj_adj(g, -1, dev(ra)))).sum())
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
