@@ -254,10 +254,6 @@ __global__ void __launch_bounds__(256) fgp2d_out(FgpOutArgs A) {
 }
 
 // ---------------------------------------------------------------- 3D
-struct Dims3 {
-  int nx, ny, nz;
-  size_t n;
-};
 
 __device__ __forceinline__ float zval(const float* wc, const float* wp, size_t idx, float mom) {
   const float c = wc[idx];
@@ -286,20 +282,20 @@ __device__ __forceinline__ float x3(const float* __restrict__ v, const float* wc
 // on the tile grown by one voxel on the + sides; the new dual of plane g is finished once x of
 // plane g+1 exists.  Each voxel's v, w_k, w_{k-1} are read about once (plus the tile halo)
 // and w_{k+1} written once: 10 floats per voxel per iteration.
-constexpr int F3_TX = 32, F3_TY = 16, F3_ZC = 64;
+constexpr int F3_TX = FGP3_TX, F3_TY = FGP3_TY, F3_ZC = FGP3_ZC;
 constexpr int F3_HX = F3_TX + 2, F3_HY = F3_TY + 2;   // z tile with a one-voxel halo
 constexpr int F3_XX = F3_TX + 1, F3_XY = F3_TY + 1;   // x tile with the + halo
 
-__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
-                                                             const float* __restrict__ wp, float* __restrict__ wn,
-                                                             Dims3 D, float tau, float step, float mom, int nonneg,
-                                                             int zc) {
+__device__ __forceinline__ void fgp3d_stream_item(const float* __restrict__ v, const float* __restrict__ wc,
+                                                  const float* __restrict__ wp, float* __restrict__ wn, Dims3 D,
+                                                  float tau, float step, float mom, int nonneg, int zc, int bx, int by,
+                                                  int bz) {
   __shared__ float zs[3][F3_HY][F3_HX];   // extrapolated dual of the current plane (+ halo)
   __shared__ float z3p[F3_HY][F3_HX];     // z-component of the previous plane
   __shared__ float xs[2][F3_XY][F3_XX];   // x of two consecutive planes
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * F3_TX + tx;
-  const int ix0 = blockIdx.x * F3_TX, iy0 = blockIdx.y * F3_TY;
-  const int zb = blockIdx.z * zc, ze = min(zb + zc, D.nz);
+  const int ix0 = bx * F3_TX, iy0 = by * F3_TY;
+  const int zb = bz * zc, ze = min(zb + zc, D.nz);
   const size_t nxy = (size_t)D.nx * D.ny;
   auto load_z = [&](int g) {
     for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) {
@@ -383,11 +379,18 @@ __global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __rest
   }
 }
 
-__global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, const float* __restrict__ w,
-                                                 float* wdst, Dims3 D, float tau, int nonneg, ProxTail t) {
-  const int gx = blockIdx.x * 32 + threadIdx.x;
-  const int gy = blockIdx.y * 8 + threadIdx.y;
-  const int gz = blockIdx.z;
+__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
+                                                             const float* __restrict__ wp, float* __restrict__ wn,
+                                                             Dims3 D, float tau, float step, float mom, int nonneg,
+                                                             int zc) {
+  fgp3d_stream_item(v, wc, wp, wn, D, tau, step, mom, nonneg, zc, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__device__ __forceinline__ void fgp3d_out_item(const float* __restrict__ v, const float* __restrict__ w, float* wdst,
+                                               Dims3 D, float tau, int nonneg, const ProxTail& t, int bx, int by,
+                                               int gz) {
+  const int gx = bx * 32 + threadIdx.x;
+  const int gy = by * 8 + threadIdx.y;
   if (gx >= D.nx || gy >= D.ny) return;
   const size_t p = ((size_t)gz * D.ny + gy) * D.nx + gx;
   const float xp = x3(v, w, w, D, gx, gy, gz, tau, 0.f, nonneg);
@@ -405,6 +408,11 @@ __global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, co
   if (t.h) t.h[p] = fmaf(t.p_over_gamma, __fsub_rn(xp, t.xhat[p]), t.h[p]);
   if (t.xprox) t.xprox[p] = xp;
   if (t.y) t.y[p] = fmaf(t.mom, __fsub_rn(xp, xold), xp);
+}
+
+__global__ void __launch_bounds__(256) fgp3d_out(const float* __restrict__ v, const float* __restrict__ w,
+                                                 float* wdst, Dims3 D, float tau, int nonneg, ProxTail t) {
+  fgp3d_out_item(v, w, wdst, D, tau, nonneg, t, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace
@@ -430,6 +438,29 @@ std::vector<MomBlock> fgp_momentum(int iters) {
   return out;
 }
 
+Fgp3Schedule fgp3_schedule(int iters) {
+  // iteration k extrapolates with (t_{k-1} - 1) / t_k (0 for k = 0, 1), t_0 = 1,
+  // t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 in float64; three buffers rotate, buffer 0 holding
+  // the warm-started dual
+  Fgp3Schedule S;
+  int cur = 0, prev = 0;
+  double t_prev = 1.0, t_cur = 1.0;
+  for (int k = 0; k < iters; ++k) {
+    const int nxt = (k == 0) ? 1 : 3 - cur - prev;
+    const float mk = k >= 1 ? (float)((t_prev - 1.0) / t_cur) : 0.f;
+    t_prev = t_cur;
+    t_cur = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
+    S.cur.push_back(cur);
+    S.prev.push_back(prev);
+    S.nxt.push_back(nxt);
+    S.mom.push_back(mk);
+    prev = cur;
+    cur = nxt;
+  }
+  S.final_buf = cur;
+  return S;
+}
+
 int fgp_prepare(vrps_geom* g) {
   Workspace& ws = g->ws;
   const size_t dn = (size_t)g->dims * (size_t)g->n;
@@ -447,9 +478,7 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   vrps_geom* gm = const_cast<vrps_geom*>(g);
   Workspace& ws = gm->ws;
   if (iters > 0) VRPS_TRY(fgp_prepare(gm));
-  // momentum in float64: t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2; the z formed after
-  // iteration k extrapolates with (t_k - 1)/t_{k+1} (iteration 0 itself uses z = w)
-  double t_cur = 1.0;
+  // momentum: fgp_momentum (2D blocks) and fgp3_schedule (3D iterations)
   const float step = (float)(1.0 / (4.0 * g->dims * (double)tau));
   const float* w_final = dual;
   if (g->dims == 2) {
@@ -491,31 +520,21 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     w_final = rc;
   } else {
     float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};
-    int cur = 0, prev = 0;
-    double t_prev = 1.0;
+    const Fgp3Schedule sch = fgp3_schedule(iters);
+    Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
+    const int zc = g->tune_f3_zc > 0 ? g->tune_f3_zc : F3_ZC;
+    dim3 grid((g->nx + F3_TX - 1) / F3_TX, (g->ny + F3_TY - 1) / F3_TY, (g->nz + zc - 1) / zc);
     for (int k = 0; k < iters; ++k) {
-      const int nxt = (k == 0) ? 1 : 3 - cur - prev;
-      // iteration k extrapolates with (t_{k-1} - 1)/t_k (0 for k = 0, 1)
-      float mk = 0.f;
-      if (k >= 1) {
-        mk = (float)((t_prev - 1.0) / t_cur);
-      }
-      t_prev = t_cur;
-      t_cur = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
-      Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
-      const int zc = g->tune_f3_zc > 0 ? g->tune_f3_zc : F3_ZC;
-      dim3 grid((g->nx + F3_TX - 1) / F3_TX, (g->ny + F3_TY - 1) / F3_TY, (g->nz + zc - 1) / zc);
+      const float mk = sch.mom[k];
       {
         // read v, w_k (and w_{k-1} when extrapolating), write w_{k+1}
         LaunchScope _ls("fgp3d_stream", s, 4.0 * g->n * (mk != 0.f ? 10 : 7));
-        VRPS_CUDA(launch_kernel(fgp3d_stream, grid, dim3(F3_TX, F3_TY), (size_t)0, s, v, (const float*)buf[cur],
-                                (const float*)buf[prev], buf[nxt], D, tau, step, mk, nonneg, zc));
+        VRPS_CUDA(launch_kernel(fgp3d_stream, grid, dim3(F3_TX, F3_TY), (size_t)0, s, v, (const float*)buf[sch.cur[k]],
+                                (const float*)buf[sch.prev[k]], buf[sch.nxt[k]], D, tau, step, mk, nonneg, zc));
       }
       VRPS_LAUNCHED("fgp_iter");
-      prev = cur;
-      cur = nxt;
     }
-    w_final = buf[cur];
+    w_final = buf[sch.final_buf];
   }
   float* wdst = (w_final != dual) ? dual : nullptr;
   if (g->dims == 2) {

@@ -15,15 +15,6 @@
 namespace vrps {
 namespace {
 
-struct Fwd3DParams {
-  const float* x;    // [nz][ny][nx]
-  const float* xT;   // [nz][nx][ny]
-  const RayInfo3D* rays;
-  const int* ids;
-  int nx, ny, nz, nu, nv;
-  float cx, cy, cz, cv, vox;
-  FwdOut o;
-};
 
 // Plane indices l in [0, nl) where intercept + slope (l - lc) lies in (-1, n); widened by 1.
 __device__ __forceinline__ void clip_range(float intercept, float slope, float lc, int n, int nl, int& lo,
@@ -48,12 +39,9 @@ __device__ __forceinline__ void clip_range(float intercept, float slope, float l
 constexpr float TWO_M32 = 2.3283064365386963e-10f;   // 2^-32
 
 template <int MODE>
-__global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
-  // grid (column tiles, views, row bands): CTAs issued together cover every view of the same
-  // detector rows, whose rays cross the same z slab of the volume (kept in L2)
-  const int iu = blockIdx.x * 32 + threadIdx.x;
-  const int iv = blockIdx.z * 8 + threadIdx.y;
-  const int row = blockIdx.y;
+__device__ __forceinline__ void fwd3d_item(const Fwd3DParams& P, int bx, int row, int bz) {
+  const int iu = bx * 32 + threadIdx.x;
+  const int iv = bz * 8 + threadIdx.y;
   if (iu >= P.nu || iv >= P.nv) return;
   const int view = P.ids[row];
   const RayInfo3D ri = P.rays[(size_t)view * P.nu + iu];
@@ -111,16 +99,13 @@ __global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
   }
 }
 
-struct Adj3DParams {
-  const float* r;
-  const RayInfo3D* rays;
-  const ViewInfo3D* views;
-  const int* ids;
-  int rows;
-  int nx, ny, nz, nu, nv;
-  float cx, cy, cz, cv, vox;
-  UpdateArgs u;
-};
+// grid (column tiles, views, row bands): CTAs issued together cover every view of the same
+// detector rows, whose rays cross the same z slab of the volume (kept in L2)
+template <int MODE>
+__global__ void __launch_bounds__(256) fwd3d_kernel(Fwd3DParams P) {
+  fwd3d_item<MODE>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 
 // Fractional detector column of the ray from the source through the point (qx, qy, *).
 __device__ __forceinline__ float column_of(const ViewInfo3D& vi, float qx, float qy) {
@@ -153,10 +138,10 @@ __global__ void __launch_bounds__(256) prescale3d_kernel(const float* __restrict
 // column) it adds, voxel by voxel, wt * wz * r over the detector rows iv whose ray passes
 // within one voxel in z.  r arrives pre-multiplied by the ray length factors.
 template <int NCV>
-__global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
-  const int gx = blockIdx.x * 32 + threadIdx.x;
-  const int gy = blockIdx.y * 8 + threadIdx.y;
-  const int z0 = blockIdx.z * ADJ3_ZC;
+__device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by, int bz) {
+  const int gx = bx * 32 + threadIdx.x;
+  const int gy = by * 8 + threadIdx.y;
+  const int z0 = bz * ADJ3_ZC;
   if (gx >= P.nx || gy >= P.ny) return;
   const float X = ((float)gx - P.cx) * P.vox, Y = ((float)gy - P.cy) * P.vox;
   float acc[ADJ3_ZC];
@@ -252,12 +237,17 @@ __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
   }
 }
 
+template <int NCV>
+__global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
+  adj3d_item<NCV>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 }  // namespace
 
-int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode, FwdOut o,
-          cudaStream_t s) {
-  if (rows <= 0) return VRPS_OK;
-  Fwd3DParams P;
+int fwd3d_setup(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, FwdOut o,
+                Fwd3DParams* out) {
+  Fwd3DParams& P = *out;
+  (void)rows;
   P.x = x;
   P.xT = xT;
   P.rays = g->ray3d;
@@ -273,6 +263,14 @@ int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   P.cv = 0.5f * (float)(g->nv - 1);
   P.vox = (float)g->pixel;
   P.o = o;
+  return VRPS_OK;
+}
+
+int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode, FwdOut o,
+          cudaStream_t s) {
+  if (rows <= 0) return VRPS_OK;
+  Fwd3DParams P;
+  VRPS_TRY(fwd3d_setup(g, x, xT, ids, rows, o, &P));
   dim3 grid((g->nu + 31) / 32, rows, (g->nv + 7) / 8), block(32, 8);
   const double fb = 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->nu * g->nv, o.store);
   switch (mode) {
@@ -287,8 +285,9 @@ int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   return VRPS_OK;
 }
 
-int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u, cudaStream_t s) {
-  Adj3DParams P;
+int adj3d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+                Adj3DParams* out) {
+  Adj3DParams& P = *out;
   P.rays = g->ray3d;
   P.views = g->view3d;
   P.ids = ids;
@@ -305,6 +304,15 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   P.vox = (float)g->pixel;
   P.u = u;
   P.r = r;
+  if (g->adj3_ncv > g->nv)
+    return fail(VRPS_ERR_UNSUPPORTED, "detector of %d rows is shorter than the %d-row adjoint window", g->nv,
+                g->adj3_ncv);
+  return VRPS_OK;
+}
+
+int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u, cudaStream_t s) {
+  Adj3DParams P;
+  VRPS_TRY(adj3d_setup(g, r, ids, rows, u, &P));
   if (!u.prescaled && rows > 0) {
     vrps_geom* gm = const_cast<vrps_geom*>(g);
     VRPS_TRY(ensure(&gm->ws.sino2, (size_t)g->m));
@@ -317,9 +325,6 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
     VRPS_LAUNCHED("prescale3d");
     P.r = gm->ws.sino2;
   }
-  if (g->adj3_ncv > g->nv)
-    return fail(VRPS_ERR_UNSUPPORTED, "detector of %d rows is shorter than the %d-row adjoint window", g->nv,
-                g->adj3_ncv);
   dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + ADJ3_ZC - 1) / ADJ3_ZC), block(32, 8);
   LaunchScope _ls("adj3d_kernel", s, 4.0 * rows * g->nu * g->nv + update_bytes(u, (size_t)g->n));
   switch (g->adj3_ncv) {

@@ -339,6 +339,32 @@ inline double fwd_mode_bytes(int mode, size_t mi, int store = 0) {
 }
 
 // ---- 3D projector (joseph3d.cu)
+struct Fwd3DParams {
+  const float* x;    // [nz][ny][nx]
+  const float* xT;   // [nz][nx][ny]
+  const RayInfo3D* rays;
+  const int* ids;
+  int nx, ny, nz, nu, nv;
+  float cx, cy, cz, cv, vox;
+  FwdOut o;
+};
+
+struct Adj3DParams {
+  const float* r;
+  const RayInfo3D* rays;
+  const ViewInfo3D* views;
+  const int* ids;
+  int rows;
+  int nx, ny, nz, nu, nv;
+  float cx, cy, cz, cv, vox;
+  UpdateArgs u;
+};
+
+// Launch constants of one 3D forward / adjoint.
+int fwd3d_setup(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, FwdOut o,
+                Fwd3DParams* P);
+int adj3d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u, Adj3DParams* P);
+
 int fwd3d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode, FwdOut o,
           cudaStream_t s);
 int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
@@ -359,6 +385,21 @@ struct ProxTail {
   float mom;
 };
 // ---- 2D FGP launch arguments (fgp.cu)
+struct Dims3 {
+  int nx, ny, nz;
+  size_t n;
+};
+
+// The 3D FGP of one prox call: buffer rotation (0 = the warm-started dual) and extrapolation
+// of every iteration, and the buffer that holds w_K.
+struct Fgp3Schedule {
+  std::vector<int> cur, prev, nxt;
+  std::vector<float> mom;
+  int final_buf = 0;
+};
+Fgp3Schedule fgp3_schedule(int iters);
+constexpr int FGP3_TX = 32, FGP3_TY = 16, FGP3_ZC = 64;   // streaming tile and default chunk
+
 constexpr int FB_T = 8;   // iterations per launch (= halo width)
 
 struct MomBlock {
