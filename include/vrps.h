@@ -280,10 +280,12 @@ int vrps_pdhg(const float* b, const vrps_geom* g, double alpha, int iters, int n
               double* history, int history_cap, float* x_out, vrps_report* report, vrps_stream_t stream);
 
 /* ---------------------------------------------------------------- batched / served jobs
- * Many independent 2D VR-ProxSkip reconstructions (Algorithm 1 with a variance-reduced
+ * Many independent VR-ProxSkip reconstructions (Algorithm 1 with a variance-reduced
  * estimator, x0 = 0) advancing together; no counterpart in the paper, which runs one problem.
- * One tick performs one iteration of every running job, each phase of the tick being one
- * persistent launch over all jobs' tiles (optionally replayed from a CUDA graph).  A job's
+ * A batch holds 2D jobs or 3D jobs, fixed by its first job.  One tick performs one iteration
+ * of every running job, each phase of the tick being one persistent launch over all jobs'
+ * tiles (optionally replayed from a CUDA graph; a 3D tick replays its prox phase only when a
+ * job takes a prox step).  A job's
  * result is bit-identical to vrps_solve(b, geom, alpha, VRPS_ALGO_VR_PROXSKIP, p, gamma,
  * seed, {estimator, fgp_iters, max_iters, nonneg, n_subsets, job, storage,
  * correction_epochs}) whatever other jobs share its ticks.
@@ -294,7 +296,7 @@ int vrps_pdhg(const float* b, const vrps_geom* g, double alpha, int iters, int n
 typedef struct vrps_batch vrps_batch;
 
 typedef struct vrps_job {
-  const vrps_geom* geom;  /* 2D geometry (caller-owned, kept alive until the job finished) */
+  const vrps_geom* geom;  /* geometry (caller-owned, kept alive until the job finished) */
   const float* b;         /* device [m] sinogram in natural angle order (read during submit) */
   float* x_out;           /* device [n]: the final iterate, written when the job finishes */
   double alpha;           /* TV weight >= 0 */
@@ -303,7 +305,7 @@ typedef struct vrps_job {
   uint64_t seed;          /* Philox key */
   uint32_t job;           /* Philox counter word 2 */
   int estimator;          /* vrps_estimator */
-  int fgp_iters;          /* 0 .. 128 */
+  int fgp_iters;          /* 0 .. 128 (2D and 3D) */
   int max_iters;          /* iterations of this job (> 0) */
   int n_subsets;          /* 0: the geometry's N */
   int nonneg;
@@ -319,8 +321,9 @@ int vrps_batch_free(vrps_batch* batch);
 int vrps_batch_set_graphs(vrps_batch* batch, int on);
 /* Admits a job before the next tick: allocates its state in the geometry's workspace,
  * reorders b subset-major, draws its Philox schedule and (SAGA) builds its table.  *id is
- * the job's handle.  Errors: INVALID_ARG (bad field, geometry busy), UNSUPPORTED (3D
- * geometry, more than 256 running jobs), OUT_OF_MEMORY, CUDA. */
+ * the job's handle.  Errors: INVALID_ARG (bad field, geometry busy, 2D job in a 3D batch or
+ * the reverse), UNSUPPORTED (more than 256 running jobs, a 3D detector with rows much finer
+ * than the voxels), OUT_OF_MEMORY, CUDA. */
 int vrps_batch_submit(vrps_batch* batch, const vrps_job* job, int* id);
 /* Enqueues up to `ticks` ticks (fewer when every job finishes); *active = jobs still
  * running.  Returns once the work is enqueued (the host may block on a work-list slot that

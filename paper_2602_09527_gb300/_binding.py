@@ -426,8 +426,9 @@ def _job_desc(g: Geometry, b: torch.Tensor, x_out: torch.Tensor, alpha: float, p
 
 
 class Batch:
-    """vrps_batch_*: many 2D VR-ProxSkip jobs advancing together, one iteration per job per
-    tick, each tick's phases one persistent launch over all jobs (continuous batching)."""
+    """vrps_batch_*: many VR-ProxSkip jobs (all 2D or all 3D) advancing together, one
+    iteration per job per tick, each tick's phases one persistent launch over all jobs
+    (continuous batching)."""
 
     def __init__(self, graphs: bool = True):
         h = ctypes.c_void_p()

@@ -1,11 +1,14 @@
 // Batched and served reconstruction: many VR-ProxSkip jobs (Algorithm 1 with a variance-
-// reduced estimator), each on its own 2D geometry and data, advance together.  One tick
-// performs one iteration of every active job; each phase of a tick -- the subset forward
-// with its estimator epilogue, the adjoint with the fused update, every blocked FGP launch of
-// the prox calls due this tick, and the prox output -- is ONE persistent launch over the
-// tiles of all jobs, running the same per-tile device code as the single-job solver.  A
-// job's arithmetic therefore does not depend on which other jobs share its ticks: its result
-// is bit-identical alone, in any mix, and to vrps_solve with the same arguments.
+// reduced estimator), each on its own geometry and data, advance together.  A batch holds 2D
+// jobs or 3D jobs (fixed by its first job).  One tick performs one iteration of every active
+// job; each phase of a tick is ONE persistent launch over the tiles of all jobs, running the
+// same per-tile device code as the single-job solver:
+//   2D: subset forward with its estimator epilogue, adjoint with the fused update, every
+//       blocked FGP launch of the prox calls due this tick, prox output;
+//   3D: slice transpose of x, subset forward, adjoint with the fused update, every FGP
+//       iteration of the prox calls due this tick, prox output.
+// A job's arithmetic therefore does not depend on which other jobs share its ticks: its
+// result is bit-identical alone, in any mix, and to vrps_solve with the same arguments.
 //
 // The host builds each tick's work list (per-job launch parameters and item prefix sums)
 // from the jobs' precomputed Philox draws, packs it into a pinned buffer and copies it to a
@@ -54,6 +57,8 @@ struct Slot {
   int graph_blocks = -1;
   size_t graph_fwd_smem = 0, graph_adj_smem = 0;
   bool graph_grouped = false;
+  cudaGraphExec_t graph_prox = nullptr;   // 3D: the prox launches, replayed on ticks with a prox call
+  int graph_prox_iters = -1;
 };
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -77,6 +82,9 @@ struct vrps_batch {
   int max_blocks = 0;
   bool graphs = true;
   long long ticks = 0;
+  int dims = 0;                  // 2 or 3, set by the first job
+  int grid3[5] = {0, 0, 0, 0, 0};   // 3D persistent grids: transpose, forward, adjoint, FGP, output
+  int max_f3 = 0;                // 3D: most FGP iterations of any job (rows of the FGP prefix table)
   std::vector<char> pack;
 };
 
@@ -130,6 +138,54 @@ int ensure_graph(vrps_batch* B, Slot& S) {
   return VRPS_OK;
 }
 
+// 3D ticks: the projection phase (every tick) and the prox phase (ticks with a prox call,
+// `iters` FGP iteration launches then the output launch).
+int launch_tick3_proj(vrps_batch* B, char* slot, cudaStream_t s) {
+  VRPS_TRY(tr3_batched(slot, B->grid3[0], s));
+  VRPS_TRY(fwd3d_batched(slot, B->grid3[1], s));
+  VRPS_TRY(adj3d_batched(slot, B->grid3[2], s));
+  return VRPS_OK;
+}
+
+int launch_tick3_prox(vrps_batch* B, char* slot, int iters, cudaStream_t s) {
+  for (int it = 0; it < iters; ++it) VRPS_TRY(fgp3d_iter_batched(slot, it, B->grid3[3], s));
+  VRPS_TRY(fgp3d_out_batched(slot, B->grid3[4], s));
+  return VRPS_OK;
+}
+
+template <class F>
+int capture(vrps_batch* B, cudaGraphExec_t* exec, int kernels, F&& body) {
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  VRPS_CUDA(cudaStreamBeginCapture(B->capture, cudaStreamCaptureModeRelaxed));
+  const int rc = body(B->capture);
+  const cudaError_t ec = cudaStreamEndCapture(B->capture, &graph);
+  if (rc != VRPS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  VRPS_CUDA(ec);
+  launch_count_add(-(long long)kernels);   // counted per replay instead
+  const cudaError_t ei = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  VRPS_CUDA(ei);
+  return VRPS_OK;
+}
+
+int ensure_graph3(vrps_batch* B, Slot& S, bool prox) {
+  if (!S.graph)
+    VRPS_TRY(capture(B, &S.graph, 3, [&](cudaStream_t c) { return launch_tick3_proj(B, S.dev, c); }));
+  if (prox && S.graph_prox_iters != B->max_f3) {
+    VRPS_TRY(capture(B, &S.graph_prox, B->max_f3 + 1,
+                     [&](cudaStream_t c) { return launch_tick3_prox(B, S.dev, B->max_f3, c); }));
+    S.graph_prox_iters = B->max_f3;
+  }
+  return VRPS_OK;
+}
+
 // Job initialisation, identical to vrps_solve's for VR-ProxSkip (x0 = 0, h = 0, dual = 0).
 int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   vrps_geom* g = J->g;
@@ -137,8 +193,10 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   Workspace& w = g->ws;
   const int64_t n = g->n, m = g->m;
   const int L = g->row_len;
+  const bool three = g->dims == 3;
   VRPS_TRY(solver_alloc(g, false, J->bf_run));
   VRPS_TRY(fgp_prepare(g));
+  if (three) VRPS_TRY(ensure(&w.xT, (size_t)n));
   J->order = g->order_subset;
   J->off = g->subset_off;
   if (J->N != g->n_subsets) {
@@ -158,9 +216,9 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
     VRPS_TRY(to_store(w.b_perm, w.b16, m, J->store, J->sc, s));
   }
   VRPS_TRY(copy_or_zero(w.x, nullptr, n, s));
-  VRPS_TRY(transpose2d(w.x, w.xfT, g->ny, g->nx, s));
+  if (!three) VRPS_TRY(transpose2d(w.x, w.xfT, g->ny, g->nx, s));
   VRPS_CUDA(cudaMemsetAsync(w.h, 0, sizeof(float) * (size_t)n, s));
-  VRPS_CUDA(cudaMemsetAsync(w.dual, 0, sizeof(float) * 2 * (size_t)n, s));
+  VRPS_CUDA(cudaMemsetAsync(w.dual, 0, sizeof(float) * g->dims * (size_t)n, s));
   VRPS_CUDA(cudaMemcpyAsync(w.xprox, w.x, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s));
   // draws, copied to the host once
   if (w.sched_cap < J->K) {
@@ -178,7 +236,7 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
                             s));
   if (J->est == VRPS_EST_SAGA) {
     FwdOut fo{w.tab, w.b_perm, nullptr};
-    VRPS_TRY(proj_forward(g, w.x, w.xfT, J->order, g->n_angles, FWD_RESID, fo, s));
+    VRPS_TRY(proj_forward(g, w.x, three ? nullptr : w.xfT, J->order, g->n_angles, FWD_RESID, fo, s));
     UpdateArgs ua;
     std::memset(&ua, 0, sizeof(ua));
     ua.out = w.gbar;
@@ -188,6 +246,15 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   }
   VRPS_CUDA(cudaStreamSynchronize(s));
   J->sched.assign(w.sched_host, w.sched_host + 3 * (size_t)J->K);
+  if (three) {
+    if (J->fgp_iters > B->max_f3) B->max_f3 = J->fgp_iters;
+    if (B->grid3[0] == 0)
+      for (int q = 0; q < 5; ++q) VRPS_TRY(batched_grid_3d(q, &B->grid3[q]));
+    VRPS_CUDA(cudaEventCreate(&J->ev_start));
+    VRPS_CUDA(cudaEventCreate(&J->ev_done));
+    VRPS_CUDA(cudaEventRecord(J->ev_start, s));
+    return VRPS_OK;
+  }
   // launch constants for the batch's shared-memory maxima
   Fwd2DParams fp;
   size_t fs = 0;
@@ -222,22 +289,24 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   return VRPS_OK;
 }
 
-// Work-list entries of job J for its iteration J->k (Algorithm 1, as in vrps_solve).
-struct Entries {
-  BatchFwd f;
-  int f_items;
-  BatchAdj a;
-  int a_items;
-  bool prox;
-  BatchFgp fg;
-  int fg_items;
-  BatchOut o;
-  int o_items;
+// Iteration J->k of job J (Algorithm 1, as in vrps_solve): which forward, on which rows,
+// with which estimator epilogue and update; the SAGA switch to float32 storage is enqueued
+// here, before the tick's kernels.
+struct Plan {
+  int mode;
+  const int* ids;
+  int rows;
+  FwdOut fo;
+  UpdateArgs ua;
+  int theta;
 };
 
-int job_tick(vrps_batch* B, Job* J, Entries* E) {
+int job_plan(vrps_batch* B, Job* J, Plan* P) {
   vrps_geom* g = J->g;
   Workspace& w = g->ws;
+  const bool three = g->dims == 3;
+  const int pre = three ? 1 : 0;   // 3D forwards leave the ray length factor on the residual
+  float* const xT = three ? nullptr : w.xfT;
   const int k = J->k;
   const int N = J->N;
   const int L = g->row_len;
@@ -257,7 +326,7 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
     if (J->est == VRPS_EST_SAGA) {
       // switch to float32 storage: rho = A x - b, gbar = A^T rho (before this tick's kernels)
       FwdOut fo{w.tab, w.b_perm, nullptr};
-      VRPS_TRY(proj_forward(g, w.x, w.xfT, J->order, g->n_angles, FWD_RESID, fo, B->stream));
+      VRPS_TRY(proj_forward(g, w.x, xT, J->order, g->n_angles, FWD_RESID, fo, B->stream));
       UpdateArgs ga;
       std::memset(&ga, 0, sizeof(ga));
       ga.out = w.gbar;
@@ -267,31 +336,32 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
       force_refresh = true;
     }
   }
-  UpdateArgs ua;
+  UpdateArgs& ua = P->ua;
   std::memset(&ua, 0, sizeof(ua));
   ua.enabled = 1;
+  ua.prescaled = pre;
   ua.base = w.x;
   ua.h = w.h;
   ua.gamma = J->fgamma;
   ua.gamma_over_p = J->fgp;
   ua.theta = theta;
   ua.x = w.x;
-  ua.xT = w.xfT;
+  ua.xT = xT;
   ua.xhat = w.xhat;
   ua.v = w.v;
-  int mode;
-  const int* ids = ids_i;
-  int rows = rows_i;
-  FwdOut fo{w.res, nullptr, nullptr, 0, bf, J->sc, J->isc};
+  P->ids = ids_i;
+  P->rows = rows_i;
+  P->theta = theta;
+  P->fo = FwdOut{w.res, nullptr, nullptr, pre, bf, J->sc, J->isc};
   if (J->est == VRPS_EST_SGD) {
-    mode = FWD_RESID;
-    fo.b = b_i;
+    P->mode = FWD_RESID;
+    P->fo.b = b_i;
     ua.cN = (float)N;
     J->rep.passes += 1.0 / N;
   } else if (J->est == VRPS_EST_SAGA) {
-    mode = FWD_SAGA;
-    fo.b = b_i;
-    fo.tab = tab_i;
+    P->mode = FWD_SAGA;
+    P->fo.b = b_i;
+    P->fo.tab = tab_i;
     ua.cN = (float)N;
     ua.gbar = w.gbar;
     ua.saga = 1;
@@ -299,36 +369,77 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
   } else {
     const bool refresh = force_refresh || (J->est == VRPS_EST_SVRG ? (k % N == 0) : (k == 0 || coin != 0));
     if (refresh) {
-      mode = FWD_SNAP;
-      fo.b = b_all;
-      fo.tab = tab_all;
-      ids = J->order;
-      rows = g->n_angles;
+      P->mode = FWD_SNAP;
+      P->fo.b = b_all;
+      P->fo.tab = tab_all;
+      P->ids = J->order;
+      P->rows = g->n_angles;
       ua.cN = 0.f;
       ua.gbar = w.gbar;
       ua.snap = 1;
       J->rep.snapshots += 1;
       J->rep.passes += 1.0;
     } else {
-      mode = FWD_SVRG;
-      fo.tab = tab_i;
+      P->mode = FWD_SVRG;
+      P->fo.tab = tab_i;
       ua.cN = (float)N;
       ua.gbar = w.gbar;
       J->rep.passes += 1.0 / N;
     }
   }
+  return VRPS_OK;
+}
+
+ProxTail prox_tail(Job* J) {
+  Workspace& w = J->g->ws;
+  ProxTail t;
+  std::memset(&t, 0, sizeof(t));
+  t.mode = 1;
+  t.x = w.x;
+  t.xT = J->g->dims == 2 ? w.xfT : nullptr;
+  t.h = w.h;
+  t.xhat = w.xhat;
+  t.p_over_gamma = J->fpg;
+  t.xprox = w.xprox;
+  return t;
+}
+
+void job_advance(Job* J, bool prox) {
+  if (prox) J->rep.prox_calls += 1;
+  J->k += 1;
+  J->rep.iterations = J->k;
+}
+
+// Work-list entries of a 2D job for its iteration J->k.
+struct Entries {
+  BatchFwd f;
+  int f_items;
+  BatchAdj a;
+  int a_items;
+  bool prox;
+  BatchFgp fg;
+  int fg_items;
+  BatchOut o;
+  int o_items;
+};
+
+int job_tick(vrps_batch* B, Job* J, Entries* E) {
+  vrps_geom* g = J->g;
+  Workspace& w = g->ws;
+  Plan P;
+  VRPS_TRY(job_plan(B, J, &P));
   size_t sm = 0;
   bool bulk = false;
-  VRPS_TRY(fwd2d_setup(g, w.x, w.xfT, ids, rows, fo, &E->f.P, &sm, &bulk));
-  E->f.mode = mode;
+  VRPS_TRY(fwd2d_setup(g, w.x, w.xfT, P.ids, P.rows, P.fo, &E->f.P, &sm, &bulk));
+  E->f.mode = P.mode;
   E->f.bulk = bulk ? 1 : 0;
-  E->f_items = E->f.P.bands * rows;
+  E->f_items = E->f.P.bands * P.rows;
   int var = 0, tx = 0, ty = 0;
-  VRPS_TRY(adj2d_setup(g, w.res, ids, rows, ua, &E->a.P, &sm, &var, &tx, &ty));
+  VRPS_TRY(adj2d_setup(g, w.res, P.ids, P.rows, P.ua, &E->a.P, &sm, &var, &tx, &ty));
   E->a.variant = var;
   E->a.tiles_x = tx;
   E->a_items = tx * ty * E->a.P.split;
-  E->prox = theta != 0;
+  E->prox = P.theta != 0;
   E->fg_items = 0;
   E->o_items = 0;
   if (E->prox) {
@@ -351,23 +462,45 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
       rz = zn;
     }
     E->fg_items = ftx * fty;
-    ProxTail t;
-    std::memset(&t, 0, sizeof(t));
-    t.mode = 1;
-    t.x = w.x;
-    t.xT = w.xfT;
-    t.h = w.h;
-    t.xhat = w.xhat;
-    t.p_over_gamma = J->fpg;
-    t.xprox = w.xprox;
     float* wdst = (rw != w.dual) ? w.dual : nullptr;
-    E->o.A = FgpOutArgs{w.v, rw, wdst, g->nx, g->ny, J->tau, J->nonneg, t};
+    E->o.A = FgpOutArgs{w.v, rw, wdst, g->nx, g->ny, J->tau, J->nonneg, prox_tail(J)};
     E->o.tiles_x = ftx;
     E->o_items = ftx * fty;
-    J->rep.prox_calls += 1;
   }
-  J->k += 1;
-  J->rep.iterations = J->k;
+  job_advance(J, E->prox);
+  return VRPS_OK;
+}
+
+// Work-list entries of a 3D job for its iteration J->k.
+struct Entries3 {
+  BatchTr3 tr;
+  int tr_items;
+  BatchFwd3 f;
+  int f_items;
+  BatchAdj3 a;
+  int a_items;
+  bool prox;
+  BatchFgp3 fg;
+  int fg_items;
+  BatchOut3 o;
+  int o_items;
+};
+
+int job_tick3(vrps_batch* B, Job* J, Entries3* E) {
+  vrps_geom* g = J->g;
+  Workspace& w = g->ws;
+  Plan P;
+  VRPS_TRY(job_plan(B, J, &P));
+  VRPS_TRY(tr3_batch_entry(w.x, w.xT, g->nx, g->ny, g->nz, &E->tr, &E->tr_items));
+  VRPS_TRY(fwd3d_batch_entry(g, w.x, w.xT, P.ids, P.rows, P.mode, P.fo, &E->f, &E->f_items));
+  VRPS_TRY(adj3d_batch_entry(g, w.res, P.ids, P.rows, P.ua, &E->a, &E->a_items));
+  E->prox = P.theta != 0;
+  E->fg_items = 0;
+  E->o_items = 0;
+  if (E->prox)
+    VRPS_TRY(fgp3d_batch_entry(g, w.v, J->tau, J->fgp_iters, J->nonneg, w.dual, prox_tail(J), &E->fg, &E->fg_items,
+                               &E->o, &E->o_items));
+  job_advance(J, E->prox);
   return VRPS_OK;
 }
 
@@ -432,18 +565,106 @@ size_t pack_tick(vrps_batch* B, const std::vector<Entries>& E) {
   return off;
 }
 
+// Packs the entries of a 3D tick into B->pack; returns the packed size.  The FGP prefix
+// table has one row per iteration up to the batch's deepest prox.
+size_t pack_tick3(vrps_batch* B, const std::vector<Entries3>& E) {
+  const int n = (int)E.size();
+  int np = 0;
+  for (const Entries3& e : E) np += e.prox ? 1 : 0;
+  const int rows = B->max_f3 > 0 ? B->max_f3 : 1;
+  TickHeader3 H;
+  std::memset(&H, 0, sizeof(H));
+  H.n_jobs = n;
+  H.n_prox = np;
+  size_t off = align16(sizeof(TickHeader3));
+  H.off_tr = (unsigned)off;
+  off = align16(off + sizeof(BatchTr3) * n);
+  H.off_ptr = (unsigned)off;
+  off = align16(off + sizeof(int) * (n + 1));
+  H.off_fwd = (unsigned)off;
+  off = align16(off + sizeof(BatchFwd3) * n);
+  H.off_pfwd = (unsigned)off;
+  off = align16(off + sizeof(int) * (n + 1));
+  H.off_adj = (unsigned)off;
+  off = align16(off + sizeof(BatchAdj3) * n);
+  H.off_padj = (unsigned)off;
+  off = align16(off + sizeof(int) * (n + 1));
+  H.off_fgp = (unsigned)off;
+  off = align16(off + sizeof(BatchFgp3) * np);
+  H.off_pfgp = (unsigned)off;
+  off = align16(off + sizeof(int) * (size_t)rows * (np + 1));
+  H.off_out = (unsigned)off;
+  off = align16(off + sizeof(BatchOut3) * np);
+  H.off_pout = (unsigned)off;
+  off = align16(off + sizeof(int) * (np + 1));
+  B->pack.assign(off, 0);
+  char* base = B->pack.data();
+  std::memcpy(base, &H, sizeof(H));
+  BatchTr3* T = reinterpret_cast<BatchTr3*>(base + H.off_tr);
+  int* pt = reinterpret_cast<int*>(base + H.off_ptr);
+  BatchFwd3* F = reinterpret_cast<BatchFwd3*>(base + H.off_fwd);
+  int* pf = reinterpret_cast<int*>(base + H.off_pfwd);
+  BatchAdj3* A = reinterpret_cast<BatchAdj3*>(base + H.off_adj);
+  int* pa = reinterpret_cast<int*>(base + H.off_padj);
+  BatchFgp3* G = reinterpret_cast<BatchFgp3*>(base + H.off_fgp);
+  int* pg = reinterpret_cast<int*>(base + H.off_pfgp);
+  BatchOut3* O = reinterpret_cast<BatchOut3*>(base + H.off_out);
+  int* po = reinterpret_cast<int*>(base + H.off_pout);
+  pt[0] = pf[0] = pa[0] = po[0] = 0;
+  for (int it = 0; it < rows; ++it) pg[(size_t)it * (np + 1)] = 0;
+  int q = 0;
+  for (int j = 0; j < n; ++j) {
+    const Entries3& e = E[j];
+    T[j] = e.tr;
+    pt[j + 1] = pt[j] + e.tr_items;
+    F[j] = e.f;
+    pf[j + 1] = pf[j] + e.f_items;
+    A[j] = e.a;
+    pa[j + 1] = pa[j] + e.a_items;
+    if (e.prox) {
+      G[q] = e.fg;
+      O[q] = e.o;
+      po[q + 1] = po[q] + e.o_items;
+      for (int it = 0; it < rows; ++it) {
+        int* row = pg + (size_t)it * (np + 1);
+        row[q + 1] = row[q] + (it < e.fg.iters ? e.fg_items : 0);
+      }
+      ++q;
+    }
+  }
+  return off;
+}
+
 int run_tick(vrps_batch* B) {
   Slot& S = B->slots[B->slot_i];
   B->slot_i = (B->slot_i + 1) % SLOTS;
   if (S.used) VRPS_CUDA(cudaEventSynchronize(S.free_ev));   // its pinned and device buffers are free
-  std::vector<Entries> E(B->active.size());
+  const bool three = B->dims == 3;
   std::vector<Job*> finishing;
-  for (size_t j = 0; j < B->active.size(); ++j) {
-    Job* J = B->active[j];
-    VRPS_TRY(job_tick(B, J, &E[j]));
-    if (J->k >= J->K) finishing.push_back(J);
+  size_t bytes = 0;
+  int prox_iters = 0;   // 3D: FGP iterations of this tick's deepest prox call
+  bool any_prox = false;
+  if (three) {
+    std::vector<Entries3> E(B->active.size());
+    for (size_t j = 0; j < B->active.size(); ++j) {
+      Job* J = B->active[j];
+      VRPS_TRY(job_tick3(B, J, &E[j]));
+      if (E[j].prox) {
+        any_prox = true;
+        if (E[j].fg.iters > prox_iters) prox_iters = E[j].fg.iters;
+      }
+      if (J->k >= J->K) finishing.push_back(J);
+    }
+    bytes = pack_tick3(B, E);
+  } else {
+    std::vector<Entries> E(B->active.size());
+    for (size_t j = 0; j < B->active.size(); ++j) {
+      Job* J = B->active[j];
+      VRPS_TRY(job_tick(B, J, &E[j]));
+      if (J->k >= J->K) finishing.push_back(J);
+    }
+    bytes = pack_tick(B, E);
   }
-  const size_t bytes = pack_tick(B, E);
   if (bytes > S.cap) {
     if (S.pinned) cudaFreeHost(S.pinned);
     if (S.dev) cudaFree(S.dev);
@@ -453,6 +674,11 @@ int run_tick(vrps_batch* B) {
       cudaGraphExecDestroy(S.graph);
       S.graph = nullptr;
     }
+    if (S.graph_prox) {
+      cudaGraphExecDestroy(S.graph_prox);
+      S.graph_prox = nullptr;
+      S.graph_prox_iters = -1;
+    }
     const size_t cap = bytes * 2 > (size_t)(256 << 10) ? bytes * 2 : (size_t)(256 << 10);
     VRPS_CUDA(cudaMallocHost((void**)&S.pinned, cap));
     VRPS_CUDA(cudaMalloc((void**)&S.dev, cap));
@@ -460,7 +686,21 @@ int run_tick(vrps_batch* B) {
   }
   std::memcpy(S.pinned, B->pack.data(), bytes);
   VRPS_CUDA(cudaMemcpyAsync(S.dev, S.pinned, bytes, cudaMemcpyHostToDevice, B->stream));
-  if (B->graphs && !profiling_on()) {
+  const bool graphs = B->graphs && !profiling_on();
+  if (three) {
+    if (graphs) {
+      VRPS_TRY(ensure_graph3(B, S, any_prox));
+      VRPS_CUDA(cudaGraphLaunch(S.graph, B->stream));
+      launch_count_add(3);
+      if (any_prox) {
+        VRPS_CUDA(cudaGraphLaunch(S.graph_prox, B->stream));
+        launch_count_add(B->max_f3 + 1);
+      }
+    } else {
+      VRPS_TRY(launch_tick3_proj(B, S.dev, B->stream));
+      if (any_prox) VRPS_TRY(launch_tick3_prox(B, S.dev, prox_iters, B->stream));
+    }
+  } else if (graphs) {
     VRPS_TRY(ensure_graph(B, S));
     VRPS_CUDA(cudaGraphLaunch(S.graph, B->stream));
     launch_count_add(tick_kernels(B));
@@ -536,6 +776,7 @@ int vrps_batch_free(vrps_batch* B) {
   cudaStreamSynchronize(B->stream);
   for (Slot& S : B->slots) {
     if (S.graph) cudaGraphExecDestroy(S.graph);
+    if (S.graph_prox) cudaGraphExecDestroy(S.graph_prox);
     if (S.pinned) cudaFreeHost(S.pinned);
     if (S.dev) cudaFree(S.dev);
     if (S.free_ev) cudaEventDestroy(S.free_ev);
@@ -563,15 +804,17 @@ int vrps_batch_submit(vrps_batch* B, const vrps_job* d, int* id) {
   *id = -1;
   vrps_geom* g = const_cast<vrps_geom*>(d->geom);
   if (!g) return fail(VRPS_ERR_INVALID_ARG, "job geometry is NULL");
-  if (g->dims != 2) return fail(VRPS_ERR_UNSUPPORTED, "batched jobs are 2D");
+  if (B->dims != 0 && g->dims != B->dims)
+    return fail(VRPS_ERR_INVALID_ARG, "this batch holds %dD jobs, the job is %dD", B->dims, g->dims);
   if (g->device != B->device) return fail(VRPS_ERR_INVALID_ARG, "geometry and batch are on different devices");
   if (!d->b || !d->x_out) return fail(VRPS_ERR_INVALID_ARG, "job b or x_out is NULL");
   if (!(d->alpha >= 0) || !std::isfinite(d->alpha)) return fail(VRPS_ERR_INVALID_ARG, "alpha must be >= 0");
   if (!(d->p > 0.0 && d->p <= 1.0)) return fail(VRPS_ERR_INVALID_ARG, "p must be in (0, 1]");
   if (!(d->gamma > 0.0) || !std::isfinite(d->gamma)) return fail(VRPS_ERR_INVALID_ARG, "gamma must be > 0");
   if (d->max_iters <= 0) return fail(VRPS_ERR_INVALID_ARG, "max_iters must be > 0");
-  if (d->fgp_iters < 0 || d->fgp_iters > FB_T * BATCH_MAX_BLOCKS)
-    return fail(VRPS_ERR_INVALID_ARG, "fgp_iters must be in [0, %d]", FB_T * BATCH_MAX_BLOCKS);
+  const int max_fgp = g->dims == 3 ? BATCH3_MAX_ITERS : FB_T * BATCH_MAX_BLOCKS;
+  if (d->fgp_iters < 0 || d->fgp_iters > max_fgp)
+    return fail(VRPS_ERR_INVALID_ARG, "fgp_iters must be in [0, %d]", max_fgp);
   if (d->estimator < VRPS_EST_SVRG || d->estimator > VRPS_EST_SGD)
     return fail(VRPS_ERR_INVALID_ARG, "bad estimator %d", d->estimator);
   if (d->storage < VRPS_STORAGE_FP32 || d->storage > VRPS_STORAGE_FP16)
@@ -598,7 +841,7 @@ int vrps_batch_submit(vrps_batch* B, const vrps_job* d, int* id) {
   J->bf_run = d->storage != VRPS_STORAGE_FP32;
   J->store = d->storage;
   J->tau = (float)(d->gamma * d->alpha / d->p);
-  J->step = (float)(1.0 / (4.0 * 2 * (double)J->tau));
+  J->step = (float)(1.0 / (4.0 * g->dims * (double)J->tau));
   J->fgamma = (float)d->gamma;
   J->fgp = (float)(d->gamma / d->p);
   J->fpg = (float)(d->p / d->gamma);
@@ -610,6 +853,7 @@ int vrps_batch_submit(vrps_batch* B, const vrps_job* d, int* id) {
     delete J;
     return rc;
   }
+  B->dims = g->dims;
   B->jobs.push_back(J);
   B->active.push_back(J);
   *id = J->id;
@@ -660,6 +904,16 @@ int vrps_batch_ticks(const vrps_batch* B, long long* ticks, int* active) {
 int vrps_job_footprint(const vrps_geom* g, const vrps_job* d, size_t* bytes) {
   if (!g || !d || !bytes) return fail(VRPS_ERR_INVALID_ARG, "geometry, job or bytes is NULL");
   const size_t n = (size_t)g->n, m = (size_t)g->m;
+  if (g->dims == 3) {
+    size_t f = 0;
+    f += 4 * n * 7;                 // x, h, x_hat, v, gbar, prox copy, x^T
+    f += 4 * 3 * n * 3;             // dual and two rotation buffers
+    f += 4 * m * 5;                 // b (subset-major), table, residual, two scratch sinograms
+    if (d->storage != VRPS_STORAGE_FP32) f += 2 * m * 2;
+    f += 12 * (size_t)d->max_iters + 64 * (size_t)g->n_angles;
+    *bytes = f;
+    return VRPS_OK;
+  }
   const int maxw = g->nx > g->ny ? g->nx : g->ny;
   int band = (64 * 1024) / (int)(sizeof(float) * (maxw + 8));
   if (band < 1) band = 1;

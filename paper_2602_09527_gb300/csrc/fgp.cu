@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) fgp2d_out(FgpOutArgs A) {
 
 __device__ __forceinline__ float zval(const float* wc, const float* wp, size_t idx, float mom) {
   const float c = wc[idx];
-  return mom != 0.f ? c + mom * (c - wp[idx]) : c;
+  return mom != 0.f ? fmaf(mom, __fsub_rn(c, wp[idx]), c) : c;
 }
 
 // x at (gx,gy,gz) from the extrapolated dual; caller guarantees the point is inside.
@@ -365,7 +365,7 @@ __device__ __forceinline__ void fgp3d_stream_item(const float* __restrict__ v, c
       const float d2 = gy < D.ny - 1 ? xs[cur][ty + 1][tx] - xc : 0.f;
       const float d3 = g < D.nz - 1 ? xs[nxt][ty][tx] - xc : 0.f;
       const float q1 = fmaf(step, d1, zo0), q2 = fmaf(step, d2, zo1), q3 = fmaf(step, d3, zo2);
-      const float den = fmaxf(1.f, sqrtf(q1 * q1 + q2 * q2 + q3 * q3));
+      const float den = fmaxf(1.f, sqrtf(fmaf(q3, q3, fmaf(q2, q2, __fmul_rn(q1, q1)))));
       const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
       wn[p] = q1 / den;
       wn[D.n + p] = q2 / den;
@@ -650,6 +650,137 @@ int batched_grid(int which, size_t smem, int* grid) {
   } else {
     VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_out_batched_kernel, 256, 0));
   }
+  *grid = (per < 1 ? 1 : per) * sms;
+  return VRPS_OK;
+}
+
+}  // namespace vrps
+
+// ---------------------------------------------------------------- batched 3D prox
+namespace vrps {
+namespace {
+
+__device__ __forceinline__ int f3_next(unsigned* counter, int* s_item) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) *s_item = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  return *s_item;
+}
+
+// Iteration `it` of every 3D prox call of the tick (jobs with fewer iterations have no items).
+__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_iter_batched_kernel(char* __restrict__ slot, int it) {
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
+  const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
+  const int n = H.n_prox;
+  if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader3*>(slot)->cnt + 4 + it;
+  const BatchFgp3* jobs = reinterpret_cast<const BatchFgp3*>(slot + H.off_fgp);
+  const int* src = reinterpret_cast<const int*>(slot + H.off_pfgp) + (size_t)it * (n + 1);
+  for (int i = threadIdx.y * blockDim.x + threadIdx.x; i <= n; i += blockDim.x * blockDim.y) pre[i] = src[i];
+  __syncthreads();
+  const int total = pre[n];
+  for (int item = f3_next(counter, &s_item); item < total; item = f3_next(counter, &s_item)) {
+    const int j = fgp_batch_job(pre, n, item);
+    const BatchFgp3& J = jobs[j];
+    const int local = item - pre[j];
+    const int per = J.tiles_x * J.tiles_y;
+    const int bz = local / per, tl = local - bz * per;
+    fgp3d_stream_item(J.v, J.buf[J.cur[it]], J.buf[J.prev[it]], J.buf[J.nxt[it]], J.D, J.tau, J.step, J.mom[it],
+                      J.nonneg, J.zc, tl % J.tiles_x, tl / J.tiles_x, bz);
+  }
+}
+
+__global__ void __launch_bounds__(256) fgp3d_out_batched_kernel(char* __restrict__ slot) {
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
+  const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
+  const int n = H.n_prox;
+  if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader3*>(slot)->cnt + 3;
+  const BatchOut3* jobs = reinterpret_cast<const BatchOut3*>(slot + H.off_out);
+  const int* src = reinterpret_cast<const int*>(slot + H.off_pout);
+  for (int i = threadIdx.y * blockDim.x + threadIdx.x; i <= n; i += blockDim.x * blockDim.y) pre[i] = src[i];
+  __syncthreads();
+  const int total = pre[n];
+  for (int item = f3_next(counter, &s_item); item < total; item = f3_next(counter, &s_item)) {
+    const int j = fgp_batch_job(pre, n, item);
+    const BatchOut3& J = jobs[j];
+    const int local = item - pre[j];
+    const int per = J.tiles_x * J.tiles_y;
+    const int gz = local / per, tl = local - gz * per;
+    fgp3d_out_item(J.v, J.w, J.wdst, J.D, J.tau, J.nonneg, J.t, tl % J.tiles_x, tl / J.tiles_x, gz);
+  }
+}
+
+}  // namespace
+
+int fgp3d_iter_batched(char* slot, int it, int grid, cudaStream_t s) {
+  LaunchScope _ls("fgp3d_iter_batched", s);
+  VRPS_CUDA(launch_kernel(fgp3d_iter_batched_kernel, dim3(grid), dim3(F3_TX, F3_TY), (size_t)0, s, slot, it));
+  return VRPS_OK;
+}
+
+int fgp3d_out_batched(char* slot, int grid, cudaStream_t s) {
+  LaunchScope _ls("fgp3d_out_batched", s);
+  VRPS_CUDA(launch_kernel(fgp3d_out_batched_kernel, dim3(grid), dim3(32, 8), (size_t)0, s, slot));
+  return VRPS_OK;
+}
+
+int batched_grid_3d_proj(int which, int* grid);
+
+int fgp3d_batch_entry(vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
+                      const ProxTail& t, BatchFgp3* f, int* f_items, BatchOut3* o, int* o_items) {
+  if (iters > BATCH3_MAX_ITERS) return fail(VRPS_ERR_INVALID_ARG, "batched 3D prox takes at most %d iterations",
+                                            BATCH3_MAX_ITERS);
+  if (iters > 0) VRPS_TRY(fgp_prepare(g));
+  Workspace& ws = g->ws;
+  const Fgp3Schedule sch = fgp3_schedule(iters);
+  std::memset(f, 0, sizeof(*f));
+  f->v = v;
+  f->buf[0] = dual;
+  f->buf[1] = ws.dual_s1;
+  f->buf[2] = ws.dual_s2;
+  f->D = Dims3{g->nx, g->ny, g->nz, (size_t)g->n};
+  f->tau = tau;
+  f->step = (float)(1.0 / (4.0 * g->dims * (double)tau));
+  f->nonneg = nonneg;
+  f->zc = g->tune_f3_zc > 0 ? g->tune_f3_zc : F3_ZC;
+  f->iters = iters;
+  f->tiles_x = (g->nx + F3_TX - 1) / F3_TX;
+  f->tiles_y = (g->ny + F3_TY - 1) / F3_TY;
+  f->chunks = (g->nz + f->zc - 1) / f->zc;
+  for (int k = 0; k < iters; ++k) {
+    f->cur[k] = (unsigned char)sch.cur[k];
+    f->prev[k] = (unsigned char)sch.prev[k];
+    f->nxt[k] = (unsigned char)sch.nxt[k];
+    f->mom[k] = sch.mom[k];
+  }
+  *f_items = f->tiles_x * f->tiles_y * f->chunks;
+  const float* w_final = f->buf[sch.final_buf];
+  std::memset(o, 0, sizeof(*o));
+  o->v = v;
+  o->w = w_final;
+  o->wdst = (w_final != dual) ? dual : nullptr;
+  o->D = f->D;
+  o->tau = tau;
+  o->nonneg = nonneg;
+  o->t = t;
+  o->tiles_x = (g->nx + 31) / 32;
+  o->tiles_y = (g->ny + 7) / 8;
+  *o_items = o->tiles_x * o->tiles_y * g->nz;
+  return VRPS_OK;
+}
+
+int batched_grid_3d(int which, int* grid) {
+  if (which <= 2) return batched_grid_3d_proj(which, grid);
+  int dev = 0, sms = 0, per = 0;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (which == 3)
+    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp3d_iter_batched_kernel, F3_TX * F3_TY, 0));
+  else
+    VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp3d_out_batched_kernel, 256, 0));
   *grid = (per < 1 ? 1 : per) * sms;
   return VRPS_OK;
 }

@@ -337,43 +337,6 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
 }
 
 
-// Algorithm 1, estimator and x_hat lines for one pixel: G = cN g + gbar,
-// x_hat = base - gamma (G - h); theta = 0: x <- x_hat (returned for the transposed copy);
-// theta = 1: keep x_hat and write the prox input v = x_hat - (gamma/p) h.
-// (Explicit roundings and fused multiply-adds: identical bits in every kernel that inlines it.)
-__device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, float g) {
-  float G;
-  if (u.snap) {            // SVRG snapshot: g is the full gradient; gbar <- g, G = g
-    u.gbar[p] = g;
-    G = g;
-  } else if (u.gbar) {
-    const float gb = u.gbar[p];
-    G = fmaf(u.cN, g, gb);
-    if (u.saga) u.gbar[p] = __fadd_rn(gb, g);
-  } else {
-    G = __fmul_rn(u.cN, g);
-  }
-  const float base = u.base[p];
-  if (u.h) {
-    const float hp = u.h[p];
-    const float xh = fmaf(-u.gamma, __fsub_rn(G, hp), base);
-    if (u.theta) {
-      u.xhat[p] = xh;
-      u.v[p] = fmaf(-u.gamma_over_p, hp, xh);
-      return 0.f;
-    }
-    u.x[p] = xh;
-    return xh;
-  }
-  const float xh = fmaf(-u.gamma, G, base);
-  if (u.theta) {
-    u.v[p] = xh;
-    return 0.f;
-  }
-  u.x[p] = xh;
-  return xh;
-}
-
 // Pixel-driven transpose.  Per angle of a chunk, one thread stages the tile's detector
 // footprint: the tile origin's fractional bin t0 = J0 + F0 is exact (fixed point); the
 // footprint r[jlo .. jlo+fp) is copied to shared memory pre-multiplied by the angle's

@@ -38,6 +38,12 @@ __device__ __forceinline__ void clip_range(float intercept, float slope, float l
 
 constexpr float TWO_M32 = 2.3283064365386963e-10f;   // 2^-32
 
+// Ray length factor voxel |d| / |d_a| = voxel sqrt(1 + P1^2 + (k R)^2) with explicit roundings
+// (the same bits in every kernel that inlines it).
+__device__ __forceinline__ float ray_factor(float vox, float p1, float kr) {
+  return __fmul_rn(vox, sqrtf(fmaf(kr, kr, fmaf(p1, p1, 1.f))));
+}
+
 template <int MODE>
 __device__ __forceinline__ void fwd3d_item(const Fwd3DParams& P, int bx, int row, int bz) {
   const int iu = bx * 32 + threadIdx.x;
@@ -77,8 +83,7 @@ __device__ __forceinline__ void fwd3d_item(const Fwd3DParams& P, int bx, int row
     const float hi_z = fmaf(f, v11 - v01, v01);
     acc += fmaf(gz, hi_z - lo_z, lo_z);
   }
-  const float kr = k * ri.R;
-  const float wgt = P.vox * sqrtf(1.f + ri.P1 * ri.P1 + kr * kr);
+  const float wgt = ray_factor(P.vox, ri.P1, k * ri.R);
   const float r = acc * wgt;
   const float ys = P.o.prescale ? wgt : 1.f;   // ray factor carried into the adjoint's input
   const size_t idx = (size_t)row * P.nu * P.nv + (size_t)iv * P.nu + iu;
@@ -126,9 +131,8 @@ __global__ void __launch_bounds__(256) prescale3d_kernel(const float* __restrict
   const int row = blockIdx.z;
   if (iu >= nu || iv >= nv) return;
   const RayInfo3D ri = rays[(size_t)ids[row] * nu + iu];
-  const float kr = ((float)iv - cv) * ri.R;
   const size_t idx = (size_t)row * nu * nv + (size_t)iv * nu + iu;
-  out[idx] = r[idx] * (vox * sqrtf(1.f + ri.P1 * ri.P1 + kr * kr));
+  out[idx] = r[idx] * ray_factor(vox, ri.P1, ((float)iv - cv) * ri.R);
 }
 
 // Voxel-driven transpose of the 3D Joseph projector.  A thread owns ADJ3_ZC voxels of one z
@@ -210,30 +214,7 @@ __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by,
       u.out[p] = g;
       continue;
     }
-    float G = u.cN * g;
-    if (u.snap) {            // SVRG snapshot: g is the full gradient; gbar <- g, G = g
-      u.gbar[p] = g;
-      G = g;
-    } else if (u.gbar) {
-      const float gb = u.gbar[p];
-      G += gb;
-      if (u.saga) u.gbar[p] = gb + g;
-    }
-    const float base = u.base[p];
-    if (u.h) {
-      const float hp = u.h[p];
-      const float xh = base - u.gamma * (G - hp);
-      if (u.theta) {
-        u.xhat[p] = xh;
-        u.v[p] = xh - u.gamma_over_p * hp;
-      } else {
-        u.x[p] = xh;
-      }
-    } else {
-      const float xh = base - u.gamma * G;
-      if (u.theta) u.v[p] = xh;
-      else u.x[p] = xh;
-    }
+    update_pixel(u, p, g);
   }
 }
 
@@ -338,6 +319,191 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
     default: return fail(VRPS_ERR_UNSUPPORTED, "detector rows much finer than voxels (%d candidates)", g->adj3_ncv);
   }
   VRPS_LAUNCHED("adj3d");
+  return VRPS_OK;
+}
+
+}  // namespace vrps
+
+// ------------------------------------------------------------------ batched 3D launches
+namespace vrps {
+namespace {
+
+__device__ __forceinline__ int b3_job(const int* pre, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void b3_prefix(int* dst, const int* src, int n) {
+  for (int i = threadIdx.y * blockDim.x + threadIdx.x; i <= n; i += blockDim.x * blockDim.y) dst[i] = src[i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ int b3_next(unsigned* counter, int* s_item) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) *s_item = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  return *s_item;
+}
+
+__global__ void __launch_bounds__(256) tr3_batched_kernel(char* __restrict__ slot) {
+  __shared__ float t[32][33];
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
+  const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
+  const int n = H.n_jobs;
+  if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader3*>(slot)->cnt + 0;
+  const BatchTr3* jobs = reinterpret_cast<const BatchTr3*>(slot + H.off_tr);
+  b3_prefix(pre, reinterpret_cast<const int*>(slot + H.off_ptr), n);
+  const int total = pre[n];
+  for (int item = b3_next(counter, &s_item); item < total; item = b3_next(counter, &s_item)) {
+    const int j = b3_job(pre, n, item);
+    const BatchTr3& J = jobs[j];
+    const int local = item - pre[j];
+    const int per = J.tiles_x * J.tiles_y;
+    const int z = local / per, tl = local - z * per;
+    const int bx = (tl % J.tiles_x) * 32, by = (tl / J.tiles_x) * 32;
+    const float* in = J.in + (size_t)z * J.nx * J.ny;
+    float* out = J.out + (size_t)z * J.nx * J.ny;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+      const int x = bx + threadIdx.x, y = by + k;
+      if (x < J.nx && y < J.ny) t[k][threadIdx.x] = in[(size_t)y * J.nx + x];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+      const int y = by + threadIdx.x, x = bx + k;   // out[x][y]
+      if (x < J.nx && y < J.ny) out[(size_t)x * J.ny + y] = t[threadIdx.x][k];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) fwd3d_batched_kernel(char* __restrict__ slot) {
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
+  const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
+  const int n = H.n_jobs;
+  if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader3*>(slot)->cnt + 1;
+  const BatchFwd3* jobs = reinterpret_cast<const BatchFwd3*>(slot + H.off_fwd);
+  b3_prefix(pre, reinterpret_cast<const int*>(slot + H.off_pfwd), n);
+  const int total = pre[n];
+  for (int item = b3_next(counter, &s_item); item < total; item = b3_next(counter, &s_item)) {
+    const int j = b3_job(pre, n, item);
+    const BatchFwd3& J = jobs[j];
+    const int local = item - pre[j];
+    // same order as the single launch: column tiles fastest, then views, then row bands
+    const int bx = local % J.tiles_u, rest = local / J.tiles_u;
+    const int row = rest % J.rows, bz = rest / J.rows;
+    switch (J.mode) {
+      case FWD_PLAIN: fwd3d_item<FWD_PLAIN>(J.P, bx, row, bz); break;
+      case FWD_RESID: fwd3d_item<FWD_RESID>(J.P, bx, row, bz); break;
+      case FWD_SVRG: fwd3d_item<FWD_SVRG>(J.P, bx, row, bz); break;
+      case FWD_SAGA: fwd3d_item<FWD_SAGA>(J.P, bx, row, bz); break;
+      default: fwd3d_item<FWD_SNAP>(J.P, bx, row, bz); break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) adj3d_batched_kernel(char* __restrict__ slot) {
+  __shared__ int pre[BATCH_MAX_JOBS + 1];
+  __shared__ int s_item;
+  const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
+  const int n = H.n_jobs;
+  if (n <= 0) return;
+  unsigned* counter = reinterpret_cast<TickHeader3*>(slot)->cnt + 2;
+  const BatchAdj3* jobs = reinterpret_cast<const BatchAdj3*>(slot + H.off_adj);
+  b3_prefix(pre, reinterpret_cast<const int*>(slot + H.off_padj), n);
+  const int total = pre[n];
+  for (int item = b3_next(counter, &s_item); item < total; item = b3_next(counter, &s_item)) {
+    const int j = b3_job(pre, n, item);
+    const BatchAdj3& J = jobs[j];
+    const int local = item - pre[j];
+    const int per = J.tiles_x * J.tiles_y;
+    const int bz = local / per, tl = local - bz * per;
+    const int bx = tl % J.tiles_x, by = tl / J.tiles_x;
+    switch (J.ncv) {
+      case 2: adj3d_item<2>(J.P, bx, by, bz); break;
+      case 3: adj3d_item<3>(J.P, bx, by, bz); break;
+      case 4: adj3d_item<4>(J.P, bx, by, bz); break;
+      case 5: adj3d_item<5>(J.P, bx, by, bz); break;
+      case 6: adj3d_item<6>(J.P, bx, by, bz); break;
+      case 7: adj3d_item<7>(J.P, bx, by, bz); break;
+      default: adj3d_item<8>(J.P, bx, by, bz); break;
+    }
+  }
+}
+
+}  // namespace
+
+int tr3_batched(char* slot, int grid, cudaStream_t s) {
+  LaunchScope _ls("tr3_batched", s);
+  VRPS_CUDA(launch_kernel(tr3_batched_kernel, dim3(grid), dim3(32, 8), (size_t)0, s, slot));
+  return VRPS_OK;
+}
+
+int fwd3d_batched(char* slot, int grid, cudaStream_t s) {
+  LaunchScope _ls("fwd3d_batched", s);
+  VRPS_CUDA(launch_kernel(fwd3d_batched_kernel, dim3(grid), dim3(32, 8), (size_t)0, s, slot));
+  return VRPS_OK;
+}
+
+int adj3d_batched(char* slot, int grid, cudaStream_t s) {
+  LaunchScope _ls("adj3d_batched", s);
+  VRPS_CUDA(launch_kernel(adj3d_batched_kernel, dim3(grid), dim3(32, 8), (size_t)0, s, slot));
+  return VRPS_OK;
+}
+
+int tr3_batch_entry(const float* in, float* out, int nx, int ny, int nz, BatchTr3* e, int* items) {
+  e->in = in;
+  e->out = out;
+  e->nx = nx;
+  e->ny = ny;
+  e->nz = nz;
+  e->tiles_x = (nx + 31) / 32;
+  e->tiles_y = (ny + 31) / 32;
+  *items = e->tiles_x * e->tiles_y * nz;
+  return VRPS_OK;
+}
+
+int fwd3d_batch_entry(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
+                      FwdOut o, BatchFwd3* e, int* items) {
+  if (mode < FWD_PLAIN || mode > FWD_SNAP) return fail(VRPS_ERR_INVALID_ARG, "bad forward mode %d", mode);
+  VRPS_TRY(fwd3d_setup(g, x, xT, ids, rows, o, &e->P));
+  e->mode = mode;
+  e->tiles_u = (g->nu + 31) / 32;
+  e->rows = rows;
+  e->bands_v = (g->nv + 7) / 8;
+  *items = rows > 0 ? e->tiles_u * rows * e->bands_v : 0;
+  return VRPS_OK;
+}
+
+int adj3d_batch_entry(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+                      BatchAdj3* e, int* items) {
+  if (!u.prescaled) return fail(VRPS_ERR_UNSUPPORTED, "the batched 3D adjoint reads prescaled residuals");
+  if (g->adj3_ncv < 2 || g->adj3_ncv > 8)
+    return fail(VRPS_ERR_UNSUPPORTED, "detector rows much finer than voxels (%d candidates)", g->adj3_ncv);
+  VRPS_TRY(adj3d_setup(g, r, ids, rows, u, &e->P));
+  e->ncv = g->adj3_ncv;
+  e->tiles_x = (g->nx + 31) / 32;
+  e->tiles_y = (g->ny + 7) / 8;
+  e->chunks = (g->nz + ADJ3_ZC - 1) / ADJ3_ZC;
+  *items = e->tiles_x * e->tiles_y * e->chunks;
+  return VRPS_OK;
+}
+
+int batched_grid_3d_proj(int which, int* grid) {
+  int dev = 0, sms = 0, per = 0;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (which == 0) VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tr3_batched_kernel, 256, 0));
+  else if (which == 1) VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fwd3d_batched_kernel, 256, 0));
+  else VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj3d_batched_kernel, 256, 0));
+  *grid = (per < 1 ? 1 : per) * sms;
   return VRPS_OK;
 }
 

@@ -252,6 +252,7 @@ __device__ __forceinline__ float st_store(const FwdOut& o, void* p, size_t i, fl
   static_cast<float*>(p)[i] = v;
   return v;
 }
+
 int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
           FwdOut o, cudaStream_t s);
 int transpose2d(const float* in, float* out, int ny, int nx, cudaStream_t s, int slices = 1);
@@ -274,6 +275,43 @@ struct UpdateArgs {
   int prescaled;          // 3D: r already carries the ray length factors (see FwdOut::prescale)
   int snap;               // SVRG snapshot: g is the full gradient; gbar <- g and G = g
 };
+
+// Algorithm 1, estimator and x_hat lines for one pixel: G = cN g + gbar,
+// x_hat = base - gamma (G - h); theta = 0: x <- x_hat (returned for the transposed copy);
+// theta = 1: keep x_hat and write the prox input v = x_hat - (gamma/p) h.
+// (Explicit roundings and fused multiply-adds: identical bits in every kernel that inlines it.)
+__device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, float g) {
+  float G;
+  if (u.snap) {            // SVRG snapshot: g is the full gradient; gbar <- g, G = g
+    u.gbar[p] = g;
+    G = g;
+  } else if (u.gbar) {
+    const float gb = u.gbar[p];
+    G = fmaf(u.cN, g, gb);
+    if (u.saga) u.gbar[p] = __fadd_rn(gb, g);
+  } else {
+    G = __fmul_rn(u.cN, g);
+  }
+  const float base = u.base[p];
+  if (u.h) {
+    const float hp = u.h[p];
+    const float xh = fmaf(-u.gamma, __fsub_rn(G, hp), base);
+    if (u.theta) {
+      u.xhat[p] = xh;
+      u.v[p] = fmaf(-u.gamma_over_p, hp, xh);
+      return 0.f;
+    }
+    u.x[p] = xh;
+    return xh;
+  }
+  const float xh = fmaf(-u.gamma, G, base);
+  if (u.theta) {
+    u.v[p] = xh;
+    return 0.f;
+  }
+  u.x[p] = xh;
+  return xh;
+}
 // ---- 2D projector launch parameters (joseph2d.cu)
 struct Fwd2DParams {
   const float* x;
@@ -479,6 +517,63 @@ int fgp2d_out_batched(char* slot, int grid, cudaStream_t s);
 // block, 3 FGP out, 4 fwd with band groups) at `smem` bytes of dynamic shared memory.
 int batched_grid(int which, size_t smem, int* grid);
 int batched_grid_2d(int which, size_t smem, int* grid);
+
+// ---- batched 3D jobs (one batch holds 2D or 3D jobs): transpose, forward, adjoint, every FGP
+// iteration and the prox output are one persistent launch each over all jobs' items
+constexpr int BATCH3_MAX_ITERS = 128;
+struct BatchTr3 {            // x -> x^T slice by slice; items tiles_x * tiles_y * nz
+  const float* in;
+  float* out;
+  int nx, ny, nz, tiles_x, tiles_y;
+};
+struct BatchFwd3 {           // items tiles_u * rows * bands_v
+  Fwd3DParams P;
+  int mode, tiles_u, rows, bands_v;
+};
+struct BatchAdj3 {           // items tiles_x * tiles_y * chunks
+  Adj3DParams P;
+  int ncv, tiles_x, tiles_y, chunks;
+};
+struct BatchFgp3 {           // iteration it: items tiles_x * tiles_y * chunks when it < iters
+  const float* v;
+  float* buf[3];
+  Dims3 D;
+  float tau, step;
+  int nonneg, zc, iters, tiles_x, tiles_y, chunks;
+  unsigned char cur[BATCH3_MAX_ITERS], prev[BATCH3_MAX_ITERS], nxt[BATCH3_MAX_ITERS];
+  float mom[BATCH3_MAX_ITERS];
+};
+struct BatchOut3 {           // items tiles_x * tiles_y * nz
+  const float* v;
+  const float* w;
+  float* wdst;
+  Dims3 D;
+  float tau;
+  int nonneg;
+  ProxTail t;
+  int tiles_x, tiles_y;
+};
+// cnt: 0 transpose, 1 forward, 2 adjoint, 3 prox output, 4 + it FGP iteration it
+struct TickHeader3 {
+  int n_jobs, n_prox, pad0, pad1;
+  unsigned off_tr, off_ptr, off_fwd, off_pfwd, off_adj, off_padj, off_fgp, off_pfgp, off_out, off_pout;
+  unsigned cnt[4 + BATCH3_MAX_ITERS];
+};
+int tr3_batched(char* slot, int grid, cudaStream_t s);
+int fwd3d_batched(char* slot, int grid, cudaStream_t s);
+int adj3d_batched(char* slot, int grid, cudaStream_t s);
+int fgp3d_iter_batched(char* slot, int it, int grid, cudaStream_t s);
+int fgp3d_out_batched(char* slot, int grid, cudaStream_t s);
+// persistent grids: 0 transpose, 1 forward, 2 adjoint, 3 FGP iteration, 4 prox output
+int batched_grid_3d(int which, int* grid);
+// work-list entries with their item counts (same launch shapes as the single-job kernels)
+int tr3_batch_entry(const float* in, float* out, int nx, int ny, int nz, BatchTr3* e, int* items);
+int fwd3d_batch_entry(const vrps_geom* g, const float* x, const float* xT, const int* ids, int rows, int mode,
+                      FwdOut o, BatchFwd3* e, int* items);
+int adj3d_batch_entry(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
+                      BatchAdj3* e, int* items);
+int fgp3d_batch_entry(vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
+                      const ProxTail& t, BatchFgp3* f, int* f_items, BatchOut3* o, int* o_items);
 
 // Algorithmic bytes of the prox output launch's tail over n pixels (beyond reading v, w).
 inline double tail_bytes(const ProxTail& t, size_t n) {
