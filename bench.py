@@ -61,9 +61,19 @@ WORKLOADS_3D = {
 # job; sinograms and SAGA tables stored as float16 (power-of-two scaled) with one final
 # float32 epoch.  Metric: wall seconds from the first admission to the last result for all 64
 # jobs, against the same jobs run one after another through vrps_solve in float32.
+#
+# Batched 3D jobs (optional): 16 cone-beam problems with sides drawn uniformly from {64, 96, 128},
+# each the 256^3 geometry scaled to side s (same field of view, voxel 128 / s, 1.4 s views, a
+# 1.5 s square detector, SOD 500, SDD 1000), N = 30, ellipsoid phantoms (two per size) with
+# Gaussian 1 % noise, ProxSVRGSkip p = 0.1, 50 FGP iterations, 3 epochs per job, float32.
+# Metric: wall seconds for all 16 jobs, against the same jobs one after another through
+# vrps_solve.
 WORKLOADS_BATCH = {
     "batch64": dict(jobs=64, sides=(128, 256, 384, 512, 1024), n_min=10, n_max=30, p=0.1, fgp_iters=50,
                     alpha=0.02, epochs=20, estimator="SAGA", storage="FP16", correction_epochs=1, seed=20260209),
+    "batch3d_16": dict(dims=3, jobs=16, sides=(64, 96, 128), n_min=30, n_max=30, p=0.1, fgp_iters=50,
+                       alpha=0.01, epochs=3, estimator="SVRG", storage="FP32", correction_epochs=0, pool=2,
+                       seed=20260209),
 }
 
 # Served stream (optional): Poisson arrivals at `rate` per second for `seconds`; each request a
@@ -76,8 +86,9 @@ WORKLOADS_SERVE = {
                   alpha=(0.005, 0.05), p=0.1, fgp_iters=50, epochs=20, pool=4, handles=24,
                   budget_gb=120.0, seed=20260209,
                   # 3D requests: the 256^3 cone geometry scaled to side s (same field of view, views
-                  # 1.4 s, detector 1.5 s), N = 30, served by a worker on a second stream
-                  share3d=0.02, sides3d=(64, 96), pool3d=2, handles3d=2),
+                  # 1.4 s, detector 1.5 s), N = 30, continuously batched in a second batch (own
+                  # stream, half of the memory budget)
+                  share3d=0.02, sides3d=(64, 96), pool3d=2, handles3d=4),
 }
 
 # Operator costs (optional), the structure of the paper's cost figure on the 512^2 / 720-angle
@@ -417,6 +428,18 @@ def bench_3d(args, rank, world, local):
 def make_batch_jobs(w, rank):
     rng = np.random.default_rng(w["seed"] + rank)
     jobs = []
+    if w.get("dims", 2) == 3:
+        pool = {}
+        for j in range(w["jobs"]):
+            side = int(rng.choice(w["sides"]))
+            q = int(rng.integers(w["pool"]))
+            if (side, q) not in pool:
+                views, det = int(round(1.4 * side)), int(round(1.5 * side))
+                pool[side, q] = synthetic.make_problem_3d(side, 0.5 * 256 / side, views, det, 384.0 / det, 500.0,
+                                                          1000.0, w["n_min"], seed=w["seed"] + 97 * q + side)
+            P3 = pool[side, q]
+            jobs.append(dict(spec=P3.spec, b=P3.b, N=w["n_min"], side=side))
+        return jobs
     for j in range(w["jobs"]):
         side = int(rng.choice(w["sides"]))
         N = int(rng.integers(w["n_min"], w["n_max"] + 1))
@@ -498,7 +521,7 @@ def bench_batch(args, rank, world, local):
     t_b32 = min(t_b32, run_batched("FP32", 0)[0])
     F_b32 = objectives()
     other = "BF16" if w["storage"] == "FP16" else "FP16"
-    t_oth, _ = run_batched(other, w["correction_epochs"])
+    t_oth, _ = run_batched(other, max(w["correction_epochs"], 1))
     F_oth = objectives()
     for _ in range(args.warmup):
         run_batched(w["storage"], w["correction_epochs"])
@@ -523,8 +546,13 @@ def bench_batch(args, rank, world, local):
     prof = vr.profile_read()
     vr.profile_enable(False)
     sides = [j["side"] for j in jobs]
+    three = w.get("dims", 2) == 3
+    metric = (f"s for {w['jobs']} uneven {'3D' if three else '2D'} reconstructions ({w['epochs']} epochs each)")
+    algo = {"SAGA": "ProxSAGASkip", "SVRG": "ProxSVRGSkip"}.get(w["estimator"], w["estimator"])
+    storage = (f"{w['storage'].lower()} + {w['correction_epochs']} float32 correction epoch"
+               if w["storage"] != "FP32" else "float32")
     out = {
-        "metric": "s for 64 uneven 2D reconstructions (20 epochs each)",
+        "metric": metric,
         "value": round(sec, 6),
         "unit": "s",
         "n_gpus": world,
@@ -535,14 +563,16 @@ def bench_batch(args, rank, world, local):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": f"f32 ({w['storage'].lower()} storage)",
-        "data": "synthetic (seeded ellipse phantoms, analytic sinograms, Gaussian 1%)",
+        "data": ("synthetic (seeded ellipsoid phantoms, analytic cone projections, Gaussian 1%)" if three else
+                 "synthetic (seeded ellipse phantoms, analytic sinograms, Gaussian 1%)"),
         "config": {"workload": wl, "jobs": w["jobs"], "sides": {str(s_): sides.count(s_) for s_ in w["sides"]},
-                   "angles_bins": "1.5 x side", "subsets": f"U[{w['n_min']}, {w['n_max']}]",
-                   "algo": "ProxSAGASkip", "p": w["p"], "fgp_iters": w["fgp_iters"], "alpha": w["alpha"],
-                   "epochs": w["epochs"],
-                   "storage": f"{w['storage'].lower()} + {w['correction_epochs']} float32 correction epoch",
+                   "angles_bins": ("views 1.4 x side, detector 1.5 x side squared, 256^3 field of view" if three
+                                   else "1.5 x side"),
+                   "subsets": f"U[{w['n_min']}, {w['n_max']}]",
+                   "algo": algo, "p": w["p"], "fgp_iters": w["fgp_iters"], "alpha": w["alpha"],
+                   "epochs": w["epochs"], "storage": storage,
                    "timing": "host wall clock, device synchronised at both ends (the batch runs on its own stream)",
-                   "l2": "working set of 64 jobs > L2", "parallelism": f"replicas x{world}"},
+                   "l2": f"working set of {w['jobs']} jobs > L2", "parallelism": f"replicas x{world}"},
         "baseline_per_job_fp32_s": round(t_seq, 6),
         "batched_fp32_s": round(t_b32, 6),
         "speedup_vs_per_job_fp32": round(t_seq / sec, 3),
@@ -683,7 +713,7 @@ def bench_serve(args, rank, world, local):
                    "epochs": w["epochs"], "budget_gb": w["budget_gb"], "handles_per_size": w["handles"],
                    "ticks_per_step": 2, "timing": "host wall clock per request (arrival to completion)",
                    "share_3d": w["share3d"], "sides_3d": list(w["sides3d"]),
-                   "scope": "2D requests continuously batched; 3D requests by a worker on a second stream"},
+                   "scope": "2D and 3D requests continuously batched in two batches on two streams"},
         "p50_s": head["p50_s"],
         "reconstructions_per_s": head["reconstructions_per_s"],
         "variants": results,

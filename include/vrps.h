@@ -112,9 +112,11 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
  * doubles): chosen band bytes, pixels per thread, tuned forward + adjoint time in
  * microseconds, bands per CTA; the adjoint's angle shares per pixel tile (1, 2, 4: partial sums
  * added in share order by the last share) are timed with the pixels per thread, and the 2D FGP
- * output tile (32 x 32, 32 x 16 or 16 x 16) on a 16-iteration prox call (see vrps_launch_shape).  3D geometries: times three iterations of the streaming FGP
- * prox for chunks of 16, 32, 64 and 128 z planes and keeps the fastest (out4: chunk, 0,
- * time in microseconds, 0).  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+ * output tile (32 x 32, 32 x 16 or 16 x 16) on a 16-iteration prox call (see vrps_launch_shape).
+ * 3D geometries: times three iterations of the streaming FGP prox for chunks of 4 ... 128 z
+ * planes and keeps the fastest (out4: chunk, 0, time in microseconds, 0); untuned, the chunk
+ * is the longest of 64, 32, 16, 8 planes giving at least 8 CTAs per SM, else 4.  Chunking
+ * does not change the results.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
 int vrps_autotune(vrps_geom* g, int reps, double* out4, vrps_stream_t stream);
 
 /* Sets the launch shapes by hand (0 = built-in default for each): forward band bytes, forward
@@ -123,7 +125,8 @@ int vrps_autotune(vrps_geom* g, int reps, double* out4, vrps_stream_t stream);
  * INVALID_ARG. */
 int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread,
                           int fgp3_chunk, int fgp_tile, int adj_split);
-/* Current launch shapes of the handle in the same order (HOST int[6]; 0 = default). */
+/* Current launch shapes of the handle in the same order (HOST int[6]; 0 = default; the 3D FGP
+ * chunk is reported as the effective one for 3D geometries). */
 int vrps_launch_shape(const vrps_geom* g, int* out6);
 
 /* ---------------------------------------------------------------- operators

@@ -540,7 +540,7 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
     cudaEvent_t e0, e1;
     VRPS_CUDA(cudaEventCreate(&e0));
     VRPS_CUDA(cudaEventCreate(&e1));
-    const int cand[] = {16, 32, 64, 128};
+    const int cand[] = {4, 8, 16, 32, 64, 128};
     int best_zc = 0;
     float best = 1e30f;
     for (int zc : cand) {
@@ -690,7 +690,7 @@ int vrps_launch_shape(const vrps_geom* g, int* out6) {
   out6[0] = g->tune_fwd_bytes;
   out6[1] = g->tune_fwd_group;
   out6[2] = g->tune_adj_two < 0 ? 0 : (g->tune_adj_two ? 2 : 1);
-  out6[3] = g->tune_f3_zc;
+  out6[3] = g->dims == 3 ? fgp3_zc(g) : 0;
   out6[4] = g->tune_fgp_tile;
   out6[5] = g->tune_adj_split;
   return VRPS_OK;

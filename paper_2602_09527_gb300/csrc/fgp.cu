@@ -277,109 +277,152 @@ __device__ __forceinline__ float x3(const float* __restrict__ v, const float* wc
 }
 
 // One FGP iteration in 3D as a 2.5-D streaming stencil.  A CTA owns a F3_TX x F3_TY tile of
-// z columns and walks a chunk of zc planes (default F3_ZC, tunable).  Per plane it builds the extrapolated dual
-// z = w_k + mom (w_k - w_{k-1}) on the tile grown by one voxel, then x = P_+(v + tau div z)
-// on the tile grown by one voxel on the + sides; the new dual of plane g is finished once x of
-// plane g+1 exists.  Each voxel's v, w_k, w_{k-1} are read about once (plus the tile halo)
-// and w_{k+1} written once: 10 floats per voxel per iteration.
+// z columns and walks a chunk of zc planes (tunable; by default sized to the volume).  Per
+// plane it builds the extrapolated dual z = w_k + mom (w_k - w_{k-1}) on the tile grown by one
+// voxel, then x = P_+(v + tau div z) on the tile grown by one voxel on the + sides; the new
+// dual of plane g is finished once x of plane g+1 exists.  Each voxel's v, w_k, w_{k-1} are
+// read about once (plus the tile halo) and w_{k+1} written once: 10 floats per voxel per
+// iteration.  The z tiles of consecutive planes alternate between two shared buffers (the
+// divergence needs the previous plane's z component), so a plane costs two barriers; every
+// thread keeps fixed halo slots whose offsets are computed once per chunk, and the v loads of
+// a plane are issued together with its dual loads.
 constexpr int F3_TX = FGP3_TX, F3_TY = FGP3_TY, F3_ZC = FGP3_ZC;
 constexpr int F3_HX = F3_TX + 2, F3_HY = F3_TY + 2;   // z tile with a one-voxel halo
 constexpr int F3_XX = F3_TX + 1, F3_XY = F3_TY + 1;   // x tile with the + halo
+constexpr int F3_NT = F3_TX * F3_TY;
+constexpr int F3_NZ = F3_HX * F3_HY, F3_NX = F3_XX * F3_XY;   // halo slots of the z and x tiles
+static_assert(F3_NZ <= 2 * F3_NT && F3_NX <= 2 * F3_NT, "two halo slots per thread");
 
 __device__ __forceinline__ void fgp3d_stream_item(const float* __restrict__ v, const float* __restrict__ wc,
                                                   const float* __restrict__ wp, float* __restrict__ wn, Dims3 D,
                                                   float tau, float step, float mom, int nonneg, int zc, int bx, int by,
                                                   int bz) {
-  __shared__ float zs[3][F3_HY][F3_HX];   // extrapolated dual of the current plane (+ halo)
-  __shared__ float z3p[F3_HY][F3_HX];     // z-component of the previous plane
-  __shared__ float xs[2][F3_XY][F3_XX];   // x of two consecutive planes
+  __shared__ float zs[2][3][F3_NZ];      // extrapolated dual of two consecutive planes (+ halo)
+  __shared__ float xs[2][F3_XY][F3_XX];  // x of two consecutive planes
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * F3_TX + tx;
   const int ix0 = bx * F3_TX, iy0 = by * F3_TY;
   const int zb = bz * zc, ze = min(zb + zc, D.nz);
   const size_t nxy = (size_t)D.nx * D.ny;
-  auto load_z = [&](int g) {
-    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) {
-      const int ly = e / F3_HX, lx = e - ly * F3_HX;
-      const int gx = ix0 + lx - 1, gy = iy0 + ly - 1;
+  // z-tile slots e = tid, tid + F3_NT: in-plane offset (planes hold < 2^31 voxels), or -1
+  // outside the volume / tile
+  int zoff[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int e = tid + k * F3_NT;
+    const int ly = e / F3_HX, lx = e - ly * F3_HX;
+    const int gx = ix0 + lx - 1, gy = iy0 + ly - 1;
+    zoff[k] = (e < F3_NZ && gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny) ? gy * D.nx + gx : -1;
+  }
+  // x-tile slots: in-plane offset (or -1); z-tile index of the slot's voxel | neighbour mask << 16
+  int xoff[2], xzm[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int e = tid + k * F3_NT;
+    const int ly = e / F3_XX, lx = e - ly * F3_XX;
+    const int gx = ix0 + lx, gy = iy0 + ly;
+    const bool in = e < F3_NX && gx < D.nx && gy < D.ny;
+    xoff[k] = in ? gy * D.nx + gx : -1;
+    xzm[k] = ((ly + 1) * F3_HX + lx + 1) |
+             (((gx < D.nx - 1 ? 1 : 0) | (gx > 0 ? 2 : 0) | (gy < D.ny - 1 ? 4 : 0) | (gy > 0 ? 8 : 0)) << 16);
+  }
+  auto buf_of = [&](int g) { return (g - zb + 1) & 1; };   // plane zb - 1 in buffer 0
+  auto load_z = [&](int g, bool only_z3) {
+    float* Z = &zs[buf_of(g)][0][0];
+    const size_t base = (size_t)g * nxy;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = tid + k * F3_NT;
+      if (k == 1 && e >= F3_NZ) break;
       float a = 0.f, b = 0.f, c = 0.f;
-      if (gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny) {
-        const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
-        a = zval(wc, wp, p, mom);
-        b = zval(wc, wp, D.n + p, mom);
+      if (zoff[k] >= 0) {
+        const size_t p = base + (size_t)zoff[k];
+        if (!only_z3) {
+          a = zval(wc, wp, p, mom);
+          b = zval(wc, wp, D.n + p, mom);
+        }
         c = zval(wc, wp, 2 * D.n + p, mom);
       }
-      zs[0][ly][lx] = a;
-      zs[1][ly][lx] = b;
-      zs[2][ly][lx] = c;
+      Z[e] = a;
+      Z[F3_NZ + e] = b;
+      Z[2 * F3_NZ + e] = c;
     }
   };
-  auto comp_x = [&](int g, float (*xb)[F3_XX]) {
-    for (int e = tid; e < F3_XX * F3_XY; e += F3_TX * F3_TY) {
-      const int ly = e / F3_XX, lx = e - ly * F3_XX;
-      const int gx = ix0 + lx, gy = iy0 + ly;
+  auto load_v = [&](int g, float* vr) {
+    const size_t base = (size_t)g * nxy;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) vr[k] = xoff[k] >= 0 ? __ldg(v + base + (size_t)xoff[k]) : 0.f;
+  };
+  auto comp_x = [&](int g, const float* vr, float (*xb)[F3_XX]) {
+    const float* Z = &zs[buf_of(g)][0][0];
+    const float* Zp = &zs[buf_of(g) ^ 1][2][0];   // z component of plane g - 1
+    const bool up = g < D.nz - 1, down = g > 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = tid + k * F3_NT;
+      if (k == 1 && e >= F3_NX) break;
       float xv = 0.f;
-      if (gx < D.nx && gy < D.ny) {
-        const int hx = lx + 1, hy = ly + 1;
+      if (xoff[k] >= 0) {
+        const int q = xzm[k] & 0xffff, m = xzm[k] >> 16;
         float d = 0.f;
-        if (gx < D.nx - 1) d += zs[0][hy][hx];
-        if (gx > 0) d -= zs[0][hy][hx - 1];
-        if (gy < D.ny - 1) d += zs[1][hy][hx];
-        if (gy > 0) d -= zs[1][hy - 1][hx];
-        if (g < D.nz - 1) d += zs[2][hy][hx];
-        if (g > 0) d -= z3p[hy][hx];
-        xv = fmaf(tau, d, v[(size_t)g * nxy + (size_t)gy * D.nx + gx]);
+        if (m & 1) d += Z[q];
+        if (m & 2) d -= Z[q - 1];
+        if (m & 4) d += Z[F3_NZ + q];
+        if (m & 8) d -= Z[F3_NZ + q - F3_HX];
+        if (up) d += Z[2 * F3_NZ + q];
+        if (down) d -= Zp[q];
+        xv = fmaf(tau, d, vr[k]);
         if (nonneg) xv = fmaxf(xv, 0.f);
       }
-      xb[ly][lx] = xv;
+      (&xb[0][0])[e] = xv;
     }
   };
   // prologue: z3 of the plane below the chunk, then plane zb and its x
-  if (zb > 0) {
-    load_z(zb - 1);
-    __syncthreads();
-    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
-  } else {
-    for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = 0.f;
-  }
+  float vr[2];
+  if (zb > 0) load_z(zb - 1, true);
+  load_v(zb, vr);
+  load_z(zb, false);
   __syncthreads();
-  load_z(zb);
-  __syncthreads();
-  comp_x(zb, xs[0]);
+  comp_x(zb, vr, xs[0]);
   __syncthreads();
   const int gx = ix0 + tx, gy = iy0 + ty;
   const bool own = gx < D.nx && gy < D.ny;
-  float zo0 = zs[0][ty + 1][tx + 1], zo1 = zs[1][ty + 1][tx + 1], zo2 = zs[2][ty + 1][tx + 1];
+  const int oq = (ty + 1) * F3_HX + tx + 1;
+  const float* Z0 = &zs[buf_of(zb)][0][0];
+  float zo0 = Z0[oq], zo1 = Z0[F3_NZ + oq], zo2 = Z0[2 * F3_NZ + oq];
   for (int g = zb; g < ze; ++g) {
     const int cur = (g - zb) & 1, nxt = cur ^ 1;
-    if (g + 1 < D.nz) {
-      for (int e = tid; e < F3_HX * F3_HY; e += F3_TX * F3_TY) z3p[e / F3_HX][e % F3_HX] = zs[2][e / F3_HX][e % F3_HX];
+    const bool more = g + 1 < D.nz;
+    if (more) {
+      load_v(g + 1, vr);
+      load_z(g + 1, false);
       __syncthreads();
-      load_z(g + 1);
-      __syncthreads();
-      comp_x(g + 1, xs[nxt]);
+      comp_x(g + 1, vr, xs[nxt]);
       __syncthreads();
     }
     if (own) {
       const float xc = xs[cur][ty][tx];
       const float d1 = gx < D.nx - 1 ? xs[cur][ty][tx + 1] - xc : 0.f;
       const float d2 = gy < D.ny - 1 ? xs[cur][ty + 1][tx] - xc : 0.f;
-      const float d3 = g < D.nz - 1 ? xs[nxt][ty][tx] - xc : 0.f;
+      const float d3 = more ? xs[nxt][ty][tx] - xc : 0.f;
       const float q1 = fmaf(step, d1, zo0), q2 = fmaf(step, d2, zo1), q3 = fmaf(step, d3, zo2);
-      const float den = fmaxf(1.f, sqrtf(fmaf(q3, q3, fmaf(q2, q2, __fmul_rn(q1, q1)))));
+      // projection onto the unit ball: q / max(1, |q|)
+      const float n2 = fmaf(q3, q3, fmaf(q2, q2, __fmul_rn(q1, q1)));
+      const float inv = n2 > 1.f ? __frcp_rn(__fsqrt_rn(n2)) : 1.f;
       const size_t p = (size_t)g * nxy + (size_t)gy * D.nx + gx;
-      wn[p] = q1 / den;
-      wn[D.n + p] = q2 / den;
-      wn[2 * D.n + p] = q3 / den;
+      wn[p] = __fmul_rn(q1, inv);
+      wn[D.n + p] = __fmul_rn(q2, inv);
+      wn[2 * D.n + p] = __fmul_rn(q3, inv);
     }
-    if (g + 1 < D.nz) {
-      zo0 = zs[0][ty + 1][tx + 1];
-      zo1 = zs[1][ty + 1][tx + 1];
-      zo2 = zs[2][ty + 1][tx + 1];
+    if (more) {
+      const float* Zn = &zs[buf_of(g + 1)][0][0];
+      zo0 = Zn[oq];
+      zo1 = Zn[F3_NZ + oq];
+      zo2 = Zn[2 * F3_NZ + oq];
     }
   }
 }
 
-__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
+__global__ void __launch_bounds__(F3_TX * F3_TY, 4) fgp3d_stream(const float* __restrict__ v, const float* __restrict__ wc,
                                                              const float* __restrict__ wp, float* __restrict__ wn,
                                                              Dims3 D, float tau, float step, float mom, int nonneg,
                                                              int zc) {
@@ -461,6 +504,19 @@ Fgp3Schedule fgp3_schedule(int iters) {
   return S;
 }
 
+int fgp3_zc(const vrps_geom* g) {
+  if (g->tune_f3_zc > 0) return g->tune_f3_zc;
+  // untuned: the longest chunk that still gives about 8 CTAs per SM (the streaming iteration
+  // is latency-bound; shorter chunks add one prologue plane each)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 148;
+  const long long tiles = (long long)((g->nx + F3_TX - 1) / F3_TX) * ((g->ny + F3_TY - 1) / F3_TY);
+  for (int zc = F3_ZC; zc > 4; zc /= 2)
+    if (tiles * ((g->nz + zc - 1) / zc) >= 8LL * sms) return zc;
+  return 4;
+}
+
 int fgp_prepare(vrps_geom* g) {
   Workspace& ws = g->ws;
   const size_t dn = (size_t)g->dims * (size_t)g->n;
@@ -522,7 +578,7 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
     float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};
     const Fgp3Schedule sch = fgp3_schedule(iters);
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
-    const int zc = g->tune_f3_zc > 0 ? g->tune_f3_zc : F3_ZC;
+    const int zc = fgp3_zc(g);
     dim3 grid((g->nx + F3_TX - 1) / F3_TX, (g->ny + F3_TY - 1) / F3_TY, (g->nz + zc - 1) / zc);
     for (int k = 0; k < iters; ++k) {
       const float mk = sch.mom[k];
@@ -668,7 +724,7 @@ __device__ __forceinline__ int f3_next(unsigned* counter, int* s_item) {
 }
 
 // Iteration `it` of every 3D prox call of the tick (jobs with fewer iterations have no items).
-__global__ void __launch_bounds__(F3_TX* F3_TY) fgp3d_iter_batched_kernel(char* __restrict__ slot, int it) {
+__global__ void __launch_bounds__(F3_TX * F3_TY, 4) fgp3d_iter_batched_kernel(char* __restrict__ slot, int it) {
   __shared__ int pre[BATCH_MAX_JOBS + 1];
   __shared__ int s_item;
   const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
@@ -745,7 +801,7 @@ int fgp3d_batch_entry(vrps_geom* g, const float* v, float tau, int iters, int no
   f->tau = tau;
   f->step = (float)(1.0 / (4.0 * g->dims * (double)tau));
   f->nonneg = nonneg;
-  f->zc = g->tune_f3_zc > 0 ? g->tune_f3_zc : F3_ZC;
+  f->zc = fgp3_zc(g);
   f->iters = iters;
   f->tiles_x = (g->nx + F3_TX - 1) / F3_TX;
   f->tiles_y = (g->ny + F3_TY - 1) / F3_TY;

@@ -436,6 +436,7 @@ struct Fgp3Schedule {
   int final_buf = 0;
 };
 Fgp3Schedule fgp3_schedule(int iters);
+int fgp3_zc(const vrps_geom* g);   // z planes per chunk of the streaming 3D FGP iteration
 constexpr int FGP3_TX = 32, FGP3_TY = 16, FGP3_ZC = 64;   // streaming tile and default chunk
 
 constexpr int FB_T = 8;   // iterations per launch (= halo width)

@@ -85,12 +85,13 @@ class BatchServer:
         self.used += need
         return True
 
-    def run(self, requests: list, clock=time.perf_counter) -> ServerStats:
-        """Serves `requests` (sorted by arrival) in real time; returns latency statistics."""
+    def run(self, requests: list, clock=time.perf_counter, t0: float | None = None) -> ServerStats:
+        """Serves `requests` (sorted by arrival) in real time; returns latency statistics.
+        t0: the clock reading that arrival times count from (default: now)."""
         st = ServerStats()
         waiting = deque()
         i = 0
-        t0 = clock()
+        t0 = clock() if t0 is None else t0
         while i < len(requests) or waiting or self.running:
             now = clock() - t0
             while i < len(requests) and requests[i].arrival <= now:
@@ -164,106 +165,48 @@ def percentile(values, q):
     return v[lo] + (v[hi] - v[lo]) * (pos - lo)
 
 
-def footprint_3d(g) -> int:
-    """Device bytes a 3D solve keeps in its geometry's workspace (images, duals, sinograms)."""
-    return 4 * g.n * (12 + 3 * 5) + 4 * g.m * 5
+def merge_stats(parts: list, wall: float) -> ServerStats:
+    st = ServerStats(wall=wall)
+    for q in parts:
+        st.latencies += q.latencies
+        st.queue_waits += q.queue_waits
+        st.completed += q.completed
+        st.ticks += q.ticks
+        st.peak_jobs += q.peak_jobs
+        st.peak_bytes += q.peak_bytes
+    return st
 
 
-class MixedServer(BatchServer):
-    """BatchServer for 2D requests plus a worker thread that runs 3D requests one at a time
-    through vrps_solve on a second CUDA stream, so that their kernels overlap the batch's ticks.
-    3D requests are admitted under the same memory budget (footprint_3d)."""
+class MixedServer:
+    """2D and 3D requests: a 2D BatchServer and a 3D BatchServer, each with its own batch (and
+    CUDA stream, so that the two batches' kernels overlap) and its own share of the memory
+    budget.  The 3D server's loop runs in a worker thread; the library releases the GIL in
+    every call, so neither loop waits for the other's host blocking."""
 
-    def __init__(self, pools: dict, pools3d: dict, budget_bytes: int, ticks_per_step: int = 2):
-        super().__init__(pools, budget_bytes, ticks_per_step)
-        import queue
-        import threading
-        self.free3 = {k: list(v) for k, v in pools3d.items()}
-        self.todo3 = queue.Queue()
-        self.done3 = queue.Queue()
-        self.running3 = 0
-        self.stream3 = torch.cuda.Stream()
-        self.worker = threading.Thread(target=self._work3d, daemon=True)
-        self.worker.start()
-
-    def _work3d(self):
-        while True:
-            item = self.todo3.get()
-            if item is None:
-                return
-            r, g, t0, clock = item
-            with torch.cuda.stream(self.stream3):
-                x, rep, _ = vb.solve(r.b, g, r.alpha, "VR_PROXSKIP", p=r.p, gamma=r.gamma, seed=r.seed,
-                                     estimator=r.estimator, fgp_iters=r.fgp_iters, max_iters=r.max_iters,
-                                     n_subsets=r.n_subsets, storage=r.storage,
-                                     correction_epochs=r.correction_epochs, stream=self.stream3)
-            r.x, r.report = x, rep
-            r.finished = clock() - t0
-            self.done3.put((r, g))
-
-    def _try_admit3(self, r: Request, now: float, t0: float, clock) -> bool:
-        pool = self.free3.get(r.key)
-        if not pool:
-            return False
-        need = footprint_3d(pool[-1])
-        if (self.running or self.running3) and self.used + need > self.budget:
-            return False
-        g = pool.pop()
-        r.admitted = now
-        self.used += need
-        self.running3 += 1
-        self.todo3.put((r, g, t0, clock))
-        return True
+    def __init__(self, pools: dict, pools3d: dict, budget_bytes: int, ticks_per_step: int = 2,
+                 share3d: float = 0.5, ticks_per_step3d: int = 1):
+        self.s2 = BatchServer(pools, int(budget_bytes * (1.0 - share3d)), ticks_per_step)
+        self.s3 = BatchServer(pools3d, int(budget_bytes * share3d), ticks_per_step3d)
+        self.keys3 = set(pools3d)
 
     def run(self, requests: list, clock=time.perf_counter) -> ServerStats:
-        st = ServerStats()
-        waiting = deque()
-        i = 0
+        import threading
+        r3 = [r for r in requests if r.key in self.keys3]
+        r2 = [r for r in requests if r.key not in self.keys3]
+        out = {}
         t0 = clock()
-        while i < len(requests) or waiting or self.running or self.running3:
-            now = clock() - t0
-            while i < len(requests) and requests[i].arrival <= now:
-                waiting.append(requests[i])
-                i += 1
-            while waiting:
-                r = waiting[0]
-                ok = self._try_admit3(r, now, t0, clock) if r.key in self.free3 else self._try_admit(r, now)
-                if not ok:
-                    break
-                waiting.popleft()
-            st.peak_jobs = max(st.peak_jobs, len(self.running) + self.running3)
-            st.peak_bytes = max(st.peak_bytes, self.used)
-            if self.running:
-                self.batch.step(self.ticks_per_step)
-                st.ticks += self.ticks_per_step
-            else:
-                time.sleep(0.0005)
-            now = clock() - t0
-            for jid in list(self.running):
-                done, rep = self.batch.poll(jid)
-                if not done:
-                    continue
-                r, g, need = self.running.pop(jid)
-                r.finished = now
-                r.report = rep
-                self.batch.release(jid)
-                self.free[r.key].append(g)
-                self.used -= need
-                st.completed += 1
-                st.latencies.append(r.finished - r.arrival)
-                st.queue_waits.append(r.admitted - r.arrival)
-            while not self.done3.empty():
-                r, g = self.done3.get()
-                self.free3[r.key].append(g)
-                self.used -= footprint_3d(g)
-                self.running3 -= 1
-                st.completed += 1
-                st.latencies.append(r.finished - r.arrival)
-                st.queue_waits.append(r.admitted - r.arrival)
-        st.wall = clock() - t0
+
+        def work3():
+            out["3d"] = self.s3.run(r3, clock, t0)
+
+        th = threading.Thread(target=work3)
+        th.start()
+        st2 = self.s2.run(r2, clock, t0)
+        th.join()
+        st = merge_stats([st2, out["3d"]], clock() - t0)
+        st.ticks = st2.ticks
         return st
 
     def close(self):
-        self.todo3.put(None)
-        self.worker.join()
-        super().close()
+        self.s2.close()
+        self.s3.close()

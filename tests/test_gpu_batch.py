@@ -210,32 +210,37 @@ def test_served_stream_results_equal_solo(mix):
         assert torch.equal(r.x, x), i
 
 
-def test_mixed_server_3d_worker(mix):
-    """2D requests batched and 3D requests on the worker stream, admitted under one budget: all
-    finish, and the 3D result equals vrps_solve's on the same inputs."""
+def test_mixed_server_3d_batch(mix):
+    """2D requests in one batch and 3D requests in a second batch on its own stream, each within
+    its share of the memory budget: all finish, and each 3D result equals vrps_solve's on the
+    same inputs."""
     vr, probs, solo = mix
     from paper_2602_09527_gb300 import serve
     spec3 = synthetic.Cone3DSpec(nx=20, ny=20, nz=16, voxel=1.0, betas=synthetic.uniform_angles(24, 2 * math.pi),
                                  nu=28, nv=24, du=1.5, dv=1.5, sod=60.0, sdd=120.0, n_subsets=4)
-    g3 = vr.Geometry.from_spec(spec3)
+    g3 = [vr.Geometry.from_spec(spec3) for _ in range(2)]
     x0 = np.random.default_rng(5).uniform(0, 1, size=(16, 20, 20))
     from oracle import joseph3d
     b3 = dev(joseph3d.forward(joseph3d.GeometryCone.from_spec(spec3), x0, list(range(24))))
-    L3 = vr.power_iteration(g3, 30, seed=3)
+    L3 = vr.power_iteration(g3[0], 30, seed=3)
     reqs = []
     for t, i in enumerate([0, 1, 3]):
         kw = _kw(MIX[i], probs[i][3], i)
         reqs.append(serve.Request(key=i, b=dev(probs[i][2]), arrival=0.005 * t, alpha=kw["alpha"], gamma=kw["gamma"],
                                   seed=kw["seed"], p=kw["p"], estimator=kw["estimator"], fgp_iters=kw["fgp_iters"],
                                   max_iters=kw["max_iters"]))
-    reqs.insert(1, serve.Request(key="cone", b=b3, arrival=0.002, alpha=0.01, gamma=1 / (3 * L3), seed=44, p=0.2,
-                                 estimator="SAGA", fgp_iters=10, max_iters=40))
-    srv = serve.MixedServer({i: [probs[i][1]] for i in (0, 1, 3)}, {"cone": [g3]}, 1 << 36)
+    s3 = [dict(seed=44, estimator="SAGA", p=0.2), dict(seed=45, estimator="SVRG", p=0.3)]
+    for q, k in enumerate(s3):
+        reqs.insert(1 + 2 * q, serve.Request(key="cone", b=b3, arrival=0.002 + 0.004 * q, alpha=0.01,
+                                             gamma=1 / (3 * L3), fgp_iters=10, max_iters=40, **k))
+    srv = serve.MixedServer({i: [probs[i][1]] for i in (0, 1, 3)}, {"cone": g3}, 1 << 36)
     st = srv.run(reqs)
     srv.close()
     assert st.completed == len(reqs)
-    x, _, _ = vr.solve(b3, g3, 0.01, "VR_PROXSKIP", p=0.2, gamma=1 / (3 * L3), seed=44, estimator="SAGA",
-                       fgp_iters=10, max_iters=40)
-    torch.cuda.synchronize()
-    assert torch.equal(reqs[1].x, x)
-    g3.close()
+    got = [r for r in reqs if r.key == "cone"]
+    for r, k in zip(got, s3):
+        x, _, _ = vr.solve(b3, g3[0], 0.01, "VR_PROXSKIP", gamma=1 / (3 * L3), fgp_iters=10, max_iters=40, **k)
+        torch.cuda.synchronize()
+        assert torch.equal(r.x, x), k
+    for g in g3:
+        g.close()
