@@ -234,7 +234,6 @@ static int build_cone3d(vrps_geom* g) {
   const double cv = 0.5 * (g->nv - 1);
   const double vmax = std::fabs((0 - cv) * g->dv);
   std::vector<RayInfo3D> rays((size_t)g->n_angles * g->nu);
-  double qz_min = 1e300;
   g->view3d_host.assign(g->n_angles, ViewInfo3D());
   for (int a = 0; a < g->n_angles; ++a) {
     const double b = g->angles[a];
@@ -271,13 +270,6 @@ static int build_cone3d(vrps_geom* g) {
       }
       RayInfo3D& r = rays[(size_t)a * g->nu + iu];
       r.pad = 0;
-      {
-        // smallest z-index step per detector row over the volume's planes (adjoint window)
-        const bool ax0 = std::fabs(dx) >= std::fabs(dy);
-        const double Sa = ax0 ? Sx : Sy, da = ax0 ? dx : dy;
-        const double half = 0.5 * ((ax0 ? g->nx : g->ny) - 1) * vox;
-        for (double X : {-half, half}) qz_min = std::fmin(qz_min, g->dv * ((X - Sa) / da) / vox);
-      }
       // transverse index P0 + P1 (l - lc) and z step per row Q0 + Q1 (l - lc) on plane l
       double P0, P1, Q0, Q1, lc;
       if (std::fabs(dx) >= std::fabs(dy)) {
@@ -305,9 +297,6 @@ static int build_cone3d(vrps_geom* g) {
       r.R = (float)Q1;
     }
   }
-  // rows within one voxel of a voxel's centre in z: an open window of 2/qz rows
-  g->adj3_ncv = (int)std::ceil(2.0 / qz_min);
-  if (g->adj3_ncv < 2) g->adj3_ncv = 2;
   VRPS_CUDA(cudaMalloc((void**)&g->ray3d, sizeof(RayInfo3D) * rays.size()));
   VRPS_CUDA(cudaMemcpy(g->ray3d, rays.data(), sizeof(RayInfo3D) * rays.size(), cudaMemcpyHostToDevice));
   VRPS_CUDA(cudaMalloc((void**)&g->view3d, sizeof(ViewInfo3D) * g->n_angles));

@@ -139,21 +139,42 @@ __global__ void __launch_bounds__(256) prescale3d_kernel(const float* __restrict
 // column.  For each view and each dominant axis it projects the voxel's plane points at
 // +-1 voxel onto the detector to bound the candidate columns iu; for every column whose ray
 // meets the voxel's plane within one voxel (transverse weight wt, the same for the whole z
-// column) it adds, voxel by voxel, wt * wz * r over the detector rows iv whose ray passes
-// within one voxel in z.  r arrives pre-multiplied by the ray length factors.
-template <int NCV>
+// column) it walks the detector rows whose ray crosses the column's z range.  On the
+// column's plane the ray of row iv has z position fz(iv) = base + iv * 2 qf in the forward's
+// 2^-33 fixed point, so every row reproduces the forward's tap exactly: z index fz >> 33
+// gets weight 1 - g and the next voxel g, g the low 32 bits of fz >> 1.  The row range is
+// found from a float estimate corrected by exact integer comparisons; rows add into the
+// thread's own shared-memory slots (index = z index - z0 + 1, two spill slots).  r arrives
+// pre-multiplied by the ray length factors.
+constexpr float TWO_M33 = 1.16415321826934814453125e-10f;   // 2^-33
+constexpr int ADJ3_SLOTS = ADJ3_ZC + 2;
+
+// First row in [0, nv] whose fixed-point z position base + iv * step reaches t (step > 0).
+__device__ __forceinline__ int first_row(long long base, long long step, long long t, float iq, int nv) {
+  float est = ceilf(__ll2float_rn(t - base) * TWO_M33 * iq);
+  est = fminf(fmaxf(est, 0.f), (float)nv);
+  int iv = (int)est;
+  const long long f = base + (long long)iv * step;
+  if (iv < nv && f < t) ++iv;
+  else if (iv > 0 && f - step >= t) --iv;
+  return iv;
+}
+
 __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by, int bz) {
+  __shared__ float acc[ADJ3_SLOTS][256];   // [slot][thread]: each thread owns one column
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   const int gx = bx * 32 + threadIdx.x;
   const int gy = by * 8 + threadIdx.y;
   const int z0 = bz * ADJ3_ZC;
   if (gx >= P.nx || gy >= P.ny) return;
-  const float X = ((float)gx - P.cx) * P.vox, Y = ((float)gy - P.cy) * P.vox;
-  float acc[ADJ3_ZC];
 #pragma unroll
-  for (int z = 0; z < ADJ3_ZC; ++z) acc[z] = 0.f;
+  for (int q = 0; q < ADJ3_SLOTS; ++q) acc[q][tid] = 0.f;
+  const float X = ((float)gx - P.cx) * P.vox, Y = ((float)gy - P.cy) * P.vox;
   const float lim = (float)P.nu + 2.f;
-  const float kmax = (float)(P.nv - NCV - 1);   // first candidate row clamped to [0, nv - NCV]
-  const float czg0 = P.cz - (float)z0;          // exact
+  const long long lo_t = (long long)(z0 - 1) << 33;         // rows with z index >= z0 - 1 ...
+  const long long hi_t = (long long)(z0 + ADJ3_ZC) << 33;   // ... and < z0 + ADJ3_ZC
+  const long long zc32 = (long long)(P.nz - 1) << 32;
+  float* const a0 = &acc[0][tid];
   for (int q = 0; q < P.rows; ++q) {
     const int view = P.ids[q];
     const ViewInfo3D vi = P.views[view];
@@ -174,31 +195,21 @@ __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by,
         const long long dt = ri.PF0 + ri.PF1 * gl - tt32;   // (transverse - tt) 2^32, exact
         if (dt <= -(1LL << 32) || dt >= (1LL << 32)) continue;
         const float wt = 1.f - fabsf(__ll2float_rn(dt) * TWO_M32);
-        // z-index step per detector row (> 0) as an unevaluated sum qh + ql
-        const long long qf = ri.QF0 + ri.QF1 * gl;
-        const float qh = __ll2float_rn(qf) * TWO_M32;
-        const float ql = __ll2float_rn(qf - __float2ll_rn(qh * 4294967296.f)) * TWO_M32;
-        const float iq = 1.f / qh;
-        const float* col = rr + iu;
-        // row window of voxel z: rows above klo(z) = (z0 + z - 1 - cz) / qz + cv; its first
-        // row is clamped into the detector, so every candidate row exists and rows outside
-        // the window get weight max(0, 1 - |e|) = 0
-        const float klo0 = fmaf(-1.f - czg0, iq, P.cv);
-#pragma unroll
-        for (int z = 0; z < ADJ3_ZC; ++z) {
-          const float klo = fminf(fmaxf(fmaf((float)z, iq, klo0), -1.f), kmax);
-          const float fl = floorf(klo);
-          const float ks = fl + (1.f - P.cv);                  // first row - cv (exact)
-          const int ivs = (int)fl + 1;
-          float e = fmaf(ks, ql, fmaf(ks, qh, czg0 - (float)z));   // fz(first row) - gz
-          const float* rp = col + ivs * P.nu;
-          float a = 0.f;
-#pragma unroll
-          for (int c = 0; c < NCV; ++c) {
-            a = fmaf(fmaxf(1.f - fabsf(e), 0.f), __ldg(rp + c * P.nu), a);
-            e += qh;
-          }
-          acc[z] = fmaf(wt, a, acc[z]);
+        const long long qf = ri.QF0 + ri.QF1 * gl;            // z voxels per row, 2^-32 (> 0)
+        const long long step = 2 * qf;
+        const long long base = zc32 - (long long)(P.nv - 1) * qf;
+        const float iq = 1.f / (__ll2float_rn(qf) * TWO_M32);
+        const int iv0 = first_row(base, step, lo_t, iq, P.nv);
+        const int iv1 = first_row(base, step, hi_t, iq, P.nv);
+        long long f = base + (long long)iv0 * step;
+        const float* rp = rr + (size_t)iv0 * P.nu + iu;
+        for (int iv = iv0; iv < iv1; ++iv, f += step, rp += P.nu) {
+          const float wr = wt * __ldg(rp);
+          const int sl = (int)(f >> 33) - z0 + 1;                  // 0 .. ADJ3_ZC + 1
+          const float g = (float)(unsigned)(f >> 1) * TWO_M32;
+          const float hi = g * wr;
+          a0[sl * 256] += wr - hi;
+          a0[(sl + 1) * 256] += hi;
         }
       }
     }
@@ -209,7 +220,7 @@ __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by,
     const int gz = z0 + z;
     if (gz >= P.nz) break;
     const size_t p = ((size_t)gz * P.ny + gy) * P.nx + gx;
-    const float g = acc[z];
+    const float g = acc[z + 1][tid];
     if (!u.enabled) {
       u.out[p] = g;
       continue;
@@ -218,9 +229,8 @@ __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by,
   }
 }
 
-template <int NCV>
 __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
-  adj3d_item<NCV>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+  adj3d_item(P, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace
@@ -285,9 +295,6 @@ int adj3d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, co
   P.vox = (float)g->pixel;
   P.u = u;
   P.r = r;
-  if (g->adj3_ncv > g->nv)
-    return fail(VRPS_ERR_UNSUPPORTED, "detector of %d rows is shorter than the %d-row adjoint window", g->nv,
-                g->adj3_ncv);
   return VRPS_OK;
 }
 
@@ -308,16 +315,7 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   }
   dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + ADJ3_ZC - 1) / ADJ3_ZC), block(32, 8);
   LaunchScope _ls("adj3d_kernel", s, 4.0 * rows * g->nu * g->nv + update_bytes(u, (size_t)g->n));
-  switch (g->adj3_ncv) {
-    case 2: VRPS_CUDA(launch_kernel(adj3d_kernel<2>, grid, block, (size_t)0, s, P)); break;
-    case 3: VRPS_CUDA(launch_kernel(adj3d_kernel<3>, grid, block, (size_t)0, s, P)); break;
-    case 4: VRPS_CUDA(launch_kernel(adj3d_kernel<4>, grid, block, (size_t)0, s, P)); break;
-    case 5: VRPS_CUDA(launch_kernel(adj3d_kernel<5>, grid, block, (size_t)0, s, P)); break;
-    case 6: VRPS_CUDA(launch_kernel(adj3d_kernel<6>, grid, block, (size_t)0, s, P)); break;
-    case 7: VRPS_CUDA(launch_kernel(adj3d_kernel<7>, grid, block, (size_t)0, s, P)); break;
-    case 8: VRPS_CUDA(launch_kernel(adj3d_kernel<8>, grid, block, (size_t)0, s, P)); break;
-    default: return fail(VRPS_ERR_UNSUPPORTED, "detector rows much finer than voxels (%d candidates)", g->adj3_ncv);
-  }
+  VRPS_CUDA(launch_kernel(adj3d_kernel, grid, block, (size_t)0, s, P));
   VRPS_LAUNCHED("adj3d");
   return VRPS_OK;
 }
@@ -409,7 +407,7 @@ __global__ void __launch_bounds__(256) fwd3d_batched_kernel(char* __restrict__ s
   }
 }
 
-__global__ void __launch_bounds__(256) adj3d_batched_kernel(char* __restrict__ slot) {
+__global__ void __launch_bounds__(256, 4) adj3d_batched_kernel(char* __restrict__ slot) {
   __shared__ int pre[BATCH_MAX_JOBS + 1];
   __shared__ int s_item;
   const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
@@ -426,15 +424,7 @@ __global__ void __launch_bounds__(256) adj3d_batched_kernel(char* __restrict__ s
     const int per = J.tiles_x * J.tiles_y;
     const int bz = local / per, tl = local - bz * per;
     const int bx = tl % J.tiles_x, by = tl / J.tiles_x;
-    switch (J.ncv) {
-      case 2: adj3d_item<2>(J.P, bx, by, bz); break;
-      case 3: adj3d_item<3>(J.P, bx, by, bz); break;
-      case 4: adj3d_item<4>(J.P, bx, by, bz); break;
-      case 5: adj3d_item<5>(J.P, bx, by, bz); break;
-      case 6: adj3d_item<6>(J.P, bx, by, bz); break;
-      case 7: adj3d_item<7>(J.P, bx, by, bz); break;
-      default: adj3d_item<8>(J.P, bx, by, bz); break;
-    }
+    adj3d_item(J.P, bx, by, bz);
   }
 }
 
@@ -485,10 +475,7 @@ int fwd3d_batch_entry(const vrps_geom* g, const float* x, const float* xT, const
 int adj3d_batch_entry(const vrps_geom* g, const float* r, const int* ids, int rows, const UpdateArgs& u,
                       BatchAdj3* e, int* items) {
   if (!u.prescaled) return fail(VRPS_ERR_UNSUPPORTED, "the batched 3D adjoint reads prescaled residuals");
-  if (g->adj3_ncv < 2 || g->adj3_ncv > 8)
-    return fail(VRPS_ERR_UNSUPPORTED, "detector rows much finer than voxels (%d candidates)", g->adj3_ncv);
   VRPS_TRY(adj3d_setup(g, r, ids, rows, u, &e->P));
-  e->ncv = g->adj3_ncv;
   e->tiles_x = (g->nx + 31) / 32;
   e->tiles_y = (g->ny + 7) / 8;
   e->chunks = (g->nz + ADJ3_ZC - 1) / ADJ3_ZC;

@@ -200,7 +200,6 @@ struct vrps_geom {
   vrps::RayInfo3D* ray3d = nullptr;     // [n_views][nu]
   vrps::ViewInfo3D* view3d = nullptr;   // [n_views]
   std::vector<vrps::ViewInfo3D> view3d_host;
-  int adj3_ncv = 0;                     // detector-row candidates per voxel of the 3D adjoint
   // angle orders
   int* order_natural = nullptr;   // [n_angles] 0..n_angles-1
   int* order_subset = nullptr;    // [n_angles] subset-major for n_subsets
@@ -533,7 +532,7 @@ struct BatchFwd3 {           // items tiles_u * rows * bands_v
 };
 struct BatchAdj3 {           // items tiles_x * tiles_y * chunks
   Adj3DParams P;
-  int ncv, tiles_x, tiles_y, chunks;
+  int tiles_x, tiles_y, chunks;
 };
 struct BatchFgp3 {           // iteration it: items tiles_x * tiles_y * chunks when it < iters
   const float* v;
