@@ -114,15 +114,17 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
  * added in share order by the last share) are timed with the pixels per thread, and the 2D FGP
  * output tile (32 x 32, 32 x 16 or 16 x 16) on a 16-iteration prox call (see vrps_launch_shape).
  * 3D geometries: times three iterations of the streaming FGP prox for chunks of 4 ... 128 z
- * planes and keeps the fastest (out4: chunk, 0, time in microseconds, 0); untuned, the chunk
- * is the longest of 64, 32, 16, 8 planes giving at least 8 CTAs per SM, else 4.  Chunking
- * does not change the results.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+ * planes, and subset 0's adjoint with 16 and 32 voxels per thread along z, and keeps the
+ * fastest of each (out4: FGP chunk, adjoint voxels per thread, FGP time and adjoint time in
+ * microseconds); untuned, the FGP chunk is the longest of 64, 32, 16, 8 planes giving at least
+ * 8 CTAs per SM, else 4, and the adjoint takes 16 voxels.  Neither changes the results.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
 int vrps_autotune(vrps_geom* g, int reps, double* out4, vrps_stream_t stream);
 
 /* Sets the launch shapes by hand (0 = built-in default for each): forward band bytes, forward
- * bands per CTA, adjoint pixels per thread (1 or 2), 3D FGP planes per chunk, 2D FGP output
- * tile (0: 32 x 32, 1: 32 x 16, 2: 16 x 16), adjoint angle shares per tile.  Errors:
- * INVALID_ARG. */
+ * bands per CTA, adjoint pixels per thread (2D: 1 or 2; 3D: voxels per thread along z, 16 or
+ * 32), 3D FGP planes per chunk, 2D FGP output tile (0: 32 x 32, 1: 32 x 16, 2: 16 x 16),
+ * adjoint angle shares per tile.  Errors: INVALID_ARG. */
 int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread,
                           int fgp3_chunk, int fgp_tile, int adj_split);
 /* Current launch shapes of the handle in the same order (HOST int[6]; 0 = default; the 3D FGP

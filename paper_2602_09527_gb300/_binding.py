@@ -242,7 +242,8 @@ def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
     out = (ctypes.c_double * 4)()
     _check(lib.vrps_autotune(g.handle, int(reps), out, _stream(stream)))
     if g.dims == 3:
-        return {"fgp3d_chunk_planes": int(out[0]), "fgp3_iterations_us": float(out[2])}
+        return {"fgp3d_chunk_planes": int(out[0]), "fgp3_iterations_us": float(out[2]),
+                "adj3d_voxels_per_thread": int(out[1]), "adj3d_subset_us": float(out[3])}
     shape = launch_shape(g)
     return {"fwd_band_bytes": int(out[0]), "fwd_bands_per_cta": int(out[3]), "adj_pixels_per_thread": int(out[1]),
             "adj_angle_shares": max(1, shape[5]), "fgp_tile": ["32x32", "32x16", "16x16"][shape[4]],

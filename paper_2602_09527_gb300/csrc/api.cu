@@ -549,13 +549,40 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
       }
     }
     g->tune_f3_zc = best_zc;
+    // adjoint voxels per thread along z (16 or 32; same results), timed on subset 0
+    const int* ids = g->order_subset + g->subset_off[0];
+    const int rows = g->subset_off[1] - g->subset_off[0];
+    VRPS_TRY(ensure(&w.sino, (size_t)g->m));
+    VRPS_TRY(fill(w.sino, 0.5f, (int64_t)rows * g->row_len, s));
+    UpdateArgs ua;
+    std::memset(&ua, 0, sizeof(ua));
+    ua.prescaled = 1;
+    ua.out = w.img2;
+    int best_az = 16;
+    float best_a = 1e30f;
+    for (int az : {16, 32}) {
+      g->tune_adj3_zc = az;
+      for (int r = 0; r <= reps; ++r) {
+        VRPS_CUDA(cudaEventRecord(e0, s));
+        VRPS_TRY(proj_adjoint(g, w.sino, ids, rows, ua, s));
+        VRPS_CUDA(cudaEventRecord(e1, s));
+        VRPS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VRPS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0 && ms < best_a) {
+          best_a = ms;
+          best_az = az;
+        }
+      }
+    }
+    g->tune_adj3_zc = best_az;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out3) {
       out3[0] = best_zc;
-      out3[1] = 0;
+      out3[1] = best_az;
       out3[2] = 1e3 * (double)best;
-      out3[3] = 0;
+      out3[3] = 1e3 * (double)best_a;
     }
     return VRPS_OK;
   }
@@ -678,7 +705,7 @@ int vrps_launch_shape(const vrps_geom* g, int* out6) {
   if (!out6) return fail(VRPS_ERR_INVALID_ARG, "out6 is NULL");
   out6[0] = g->tune_fwd_bytes;
   out6[1] = g->tune_fwd_group;
-  out6[2] = g->tune_adj_two < 0 ? 0 : (g->tune_adj_two ? 2 : 1);
+  out6[2] = g->dims == 3 ? (g->tune_adj3_zc == 32 ? 32 : 16) : (g->tune_adj_two < 0 ? 0 : (g->tune_adj_two ? 2 : 1));
   out6[3] = g->dims == 3 ? fgp3_zc(g) : 0;
   out6[4] = g->tune_fgp_tile;
   out6[5] = g->tune_adj_split;
@@ -688,10 +715,16 @@ int vrps_launch_shape(const vrps_geom* g, int* out6) {
 int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread, int fgp3_chunk,
                           int fgp_tile, int adj_split) {
   VRPS_TRY(check_geom(g));
-  if (fwd_band_bytes < 0 || fwd_band_bytes > (200 << 10) || fwd_group < 0 || fwd_group > 64 ||
-      adj_pixels_per_thread < 0 || adj_pixels_per_thread > 2 || fgp3_chunk < 0 || fgp_tile < 0 || fgp_tile > 2 ||
-      adj_split < 0 || adj_split > 64)
+  const bool adj_ok = g->dims == 3 ? (adj_pixels_per_thread == 0 || adj_pixels_per_thread == 16 ||
+                                      adj_pixels_per_thread == 32)
+                                   : (adj_pixels_per_thread >= 0 && adj_pixels_per_thread <= 2);
+  if (fwd_band_bytes < 0 || fwd_band_bytes > (200 << 10) || fwd_group < 0 || fwd_group > 64 || !adj_ok ||
+      fgp3_chunk < 0 || fgp_tile < 0 || fgp_tile > 2 || adj_split < 0 || adj_split > 64)
     return fail(VRPS_ERR_INVALID_ARG, "launch shape out of range");
+  if (g->dims == 3) {
+    g->tune_adj3_zc = adj_pixels_per_thread;
+    adj_pixels_per_thread = 0;
+  }
   g->tune_fgp_tile = fgp_tile;
   g->tune_adj_split = adj_split;
   g->tune_fwd_bytes = fwd_band_bytes;

@@ -120,7 +120,7 @@ __device__ __forceinline__ float column_of(const ViewInfo3D& vi, float qx, float
   return fmaf(vi.sdd * num / den, vi.inv_du, vi.cu);
 }
 
-constexpr int ADJ3_ZC = 16;   // voxels of one z column handled by a thread
+constexpr int ADJ3_ZC = 16;   // voxels of one z column handled by a thread (default; 32 tunable)
 
 // r[row][iv][iu] <- r times the ray length factor voxel |d|/|d_a| (input of adj3d_kernel)
 __global__ void __launch_bounds__(256) prescale3d_kernel(const float* __restrict__ r, float* __restrict__ out,
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) prescale3d_kernel(const float* __restrict
   out[idx] = r[idx] * ray_factor(vox, ri.P1, ((float)iv - cv) * ri.R);
 }
 
-// Voxel-driven transpose of the 3D Joseph projector.  A thread owns ADJ3_ZC voxels of one z
+// Voxel-driven transpose of the 3D Joseph projector.  A thread owns ZC voxels of one z
 // column.  For each view and each dominant axis it projects the voxel's plane points at
 // +-1 voxel onto the detector to bound the candidate columns iu; for every column whose ray
 // meets the voxel's plane within one voxel (transverse weight wt, the same for the whole z
@@ -147,7 +147,6 @@ __global__ void __launch_bounds__(256) prescale3d_kernel(const float* __restrict
 // thread's own shared-memory slots (index = z index - z0 + 1, two spill slots).  r arrives
 // pre-multiplied by the ray length factors.
 constexpr float TWO_M33 = 1.16415321826934814453125e-10f;   // 2^-33
-constexpr int ADJ3_SLOTS = ADJ3_ZC + 2;
 
 // First row in [0, nv] whose fixed-point z position base + iv * step reaches t (step > 0).
 __device__ __forceinline__ int first_row(long long base, long long step, long long t, float iq, int nv) {
@@ -160,21 +159,24 @@ __device__ __forceinline__ int first_row(long long base, long long step, long lo
   return iv;
 }
 
-__device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by, int bz) {
-  __shared__ float acc[ADJ3_SLOTS][256];   // [slot][thread]: each thread owns one column
+// acc: shared [ZC + 2][256] (slot-major, one column per thread).  A voxel's contributions
+// arrive in the same order (views, columns, rows ascending) whatever ZC is, so the result
+// does not depend on the chunk length.
+template <int ZC>
+__device__ __forceinline__ void adj3d_item(const Adj3DParams& P, float* __restrict__ acc, int bx, int by, int bz) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const int gx = bx * 32 + threadIdx.x;
   const int gy = by * 8 + threadIdx.y;
-  const int z0 = bz * ADJ3_ZC;
+  const int z0 = bz * ZC;
   if (gx >= P.nx || gy >= P.ny) return;
+  float* const a0 = acc + tid;
 #pragma unroll
-  for (int q = 0; q < ADJ3_SLOTS; ++q) acc[q][tid] = 0.f;
+  for (int q = 0; q < ZC + 2; ++q) a0[q * 256] = 0.f;
   const float X = ((float)gx - P.cx) * P.vox, Y = ((float)gy - P.cy) * P.vox;
   const float lim = (float)P.nu + 2.f;
   const long long lo_t = (long long)(z0 - 1) << 33;         // rows with z index >= z0 - 1 ...
-  const long long hi_t = (long long)(z0 + ADJ3_ZC) << 33;   // ... and < z0 + ADJ3_ZC
+  const long long hi_t = (long long)(z0 + ZC) << 33;   // ... and < z0 + ZC
   const long long zc32 = (long long)(P.nz - 1) << 32;
-  float* const a0 = &acc[0][tid];
   for (int q = 0; q < P.rows; ++q) {
     const int view = P.ids[q];
     const ViewInfo3D vi = P.views[view];
@@ -203,9 +205,10 @@ __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by,
         const int iv1 = first_row(base, step, hi_t, iq, P.nv);
         long long f = base + (long long)iv0 * step;
         const float* rp = rr + (size_t)iv0 * P.nu + iu;
+#pragma unroll 2
         for (int iv = iv0; iv < iv1; ++iv, f += step, rp += P.nu) {
           const float wr = wt * __ldg(rp);
-          const int sl = (int)(f >> 33) - z0 + 1;                  // 0 .. ADJ3_ZC + 1
+          const int sl = (int)(f >> 33) - z0 + 1;                  // 0 .. ZC + 1
           const float g = (float)(unsigned)(f >> 1) * TWO_M32;
           const float hi = g * wr;
           a0[sl * 256] += wr - hi;
@@ -216,11 +219,11 @@ __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by,
   }
   const UpdateArgs& u = P.u;
 #pragma unroll
-  for (int z = 0; z < ADJ3_ZC; ++z) {
+  for (int z = 0; z < ZC; ++z) {
     const int gz = z0 + z;
     if (gz >= P.nz) break;
     const size_t p = ((size_t)gz * P.ny + gy) * P.nx + gx;
-    const float g = acc[z + 1][tid];
+    const float g = a0[(z + 1) * 256];
     if (!u.enabled) {
       u.out[p] = g;
       continue;
@@ -229,8 +232,10 @@ __device__ __forceinline__ void adj3d_item(const Adj3DParams& P, int bx, int by,
   }
 }
 
+template <int ZC>
 __global__ void __launch_bounds__(256) adj3d_kernel(Adj3DParams P) {
-  adj3d_item(P, blockIdx.x, blockIdx.y, blockIdx.z);
+  __shared__ float acc[(ZC + 2) * 256];
+  adj3d_item<ZC>(P, acc, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace
@@ -313,9 +318,11 @@ int adj3d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
     VRPS_LAUNCHED("prescale3d");
     P.r = gm->ws.sino2;
   }
-  dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + ADJ3_ZC - 1) / ADJ3_ZC), block(32, 8);
+  const int zc = g->tune_adj3_zc == 32 ? 32 : ADJ3_ZC;
+  dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + zc - 1) / zc), block(32, 8);
   LaunchScope _ls("adj3d_kernel", s, 4.0 * rows * g->nu * g->nv + update_bytes(u, (size_t)g->n));
-  VRPS_CUDA(launch_kernel(adj3d_kernel, grid, block, (size_t)0, s, P));
+  if (zc == 32) VRPS_CUDA(launch_kernel(adj3d_kernel<32>, grid, block, (size_t)0, s, P));
+  else VRPS_CUDA(launch_kernel(adj3d_kernel<ADJ3_ZC>, grid, block, (size_t)0, s, P));
   VRPS_LAUNCHED("adj3d");
   return VRPS_OK;
 }
@@ -408,6 +415,7 @@ __global__ void __launch_bounds__(256) fwd3d_batched_kernel(char* __restrict__ s
 }
 
 __global__ void __launch_bounds__(256, 4) adj3d_batched_kernel(char* __restrict__ slot) {
+  __shared__ float acc[(ADJ3_ZC + 2) * 256];   // batched jobs keep the default chunk (same results)
   __shared__ int pre[BATCH_MAX_JOBS + 1];
   __shared__ int s_item;
   const TickHeader3& H = *reinterpret_cast<const TickHeader3*>(slot);
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(256, 4) adj3d_batched_kernel(char* __restrict_
     const int per = J.tiles_x * J.tiles_y;
     const int bz = local / per, tl = local - bz * per;
     const int bx = tl % J.tiles_x, by = tl / J.tiles_x;
-    adj3d_item(J.P, bx, by, bz);
+    adj3d_item<ADJ3_ZC>(J.P, acc, bx, by, bz);
   }
 }
 

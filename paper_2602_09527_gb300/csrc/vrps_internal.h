@@ -194,6 +194,7 @@ struct vrps_geom {
   int tune_fwd_group = 0;   // bands per forward CTA item (0: one)
   int tune_adj_two = -1;    // 2D adjoint: two pixels per thread (1) or one (0)
   int tune_f3_zc = 0;       // 3D FGP: z planes per streaming chunk
+  int tune_adj3_zc = 0;     // 3D adjoint: voxels per thread along z (0 = 16, or 32)
   int tune_fgp_tile = 0;    // 2D FGP output tile: 0 32x32, 1 32x16, 2 16x16
   int tune_adj_split = 0;   // 2D adjoint: angle shares per pixel tile (0: one)
   // 3D tables

@@ -161,3 +161,23 @@ def test_cone_solver_short_run():
     ref = solvers.run(op, b, 0.01, "VR_PROXSKIP", 1 / L, 12, 10, p=0.3, seed=8, estimator="SVRG")
     assert rel(host(x), ref.x) < 1e-4
     assert rep["prox_calls"] == ref.prox_calls
+
+
+def test_adjoint_z_chunk_same_bits():
+    """16 or 32 voxels per thread along z: a voxel's contributions arrive in the same order, so
+    the adjoint is bit-identical (and matches the oracle); other values are rejected."""
+    vr, g, og = _pair(RAGGED)
+    rng = np.random.default_rng(31)
+    r = dev(rng.standard_normal((4, 52, 61)))
+    outs = []
+    for zc in (16, 32):
+        vr.set_launch_shape(g, adj_pixels_per_thread=zc)
+        assert vr.launch_shape(g)[2] == zc
+        outs.append(host(vr.proj_adj(g, 0, r)))
+    vr.set_launch_shape(g)
+    assert np.array_equal(outs[0], outs[1])
+    assert rel(outs[0], J.adjoint(og, host(r).reshape(4, 52, 61), list(range(0, 8, 2)))) < TOL
+    with pytest.raises(vr.VrpsError):
+        vr.set_launch_shape(g, adj_pixels_per_thread=8)
+    t = vr.autotune(g, reps=1)
+    assert t["adj3d_voxels_per_thread"] in (16, 32)
