@@ -57,23 +57,29 @@ WORKLOADS_3D = {
 
 # Batched uneven 2D jobs (optional): 64 parallel-beam problems with sides drawn uniformly
 # from {128, 256, 384, 512, 1024}, angles = bins = 1.5 x side, N uniform in [10, 30], ellipse
-# phantoms with Gaussian 1 % noise, ProxSAGASkip p = 0.1, 50 FGP iterations, 20 epochs per
-# job; sinograms and SAGA tables stored as float16 (power-of-two scaled) with one final
-# float32 epoch.  Metric: wall seconds from the first admission to the last result for all 64
-# jobs, against the same jobs run one after another through vrps_solve in float32.
+# phantoms with Gaussian 1 % noise, TV weight 0.02 on a unit-radius field of view (0.02 (side/2)^2
+# in pixel units), ProxSAGASkip p = 0.1, 50 FGP iterations; sinograms and SAGA tables stored
+# as float16 (power-of-two scaled) with one final float32 epoch (20 epochs per job when no gap
+# target is set).  Metric: wall seconds from the first admission to the last result for all 64
+# jobs, each run for the iterations it needs to reach a 1e-4 relative objective gap (found
+# beforehand from a 300-epoch per-job float32 replay that evaluates the objective once per
+# epoch; F* = the lowest value seen), against the same jobs run one after another through
+# vrps_solve in float32 (bit-identical trajectories, so the same accuracy).
 #
 # Batched 3D jobs (optional): 16 cone-beam problems with sides drawn uniformly from {64, 96, 128},
 # each the 256^3 geometry scaled to side s (same field of view, voxel 128 / s, 1.4 s views, a
 # 1.5 s square detector, SOD 500, SDD 1000), N = 30, ellipsoid phantoms (two per size) with
-# Gaussian 1 % noise, ProxSVRGSkip p = 0.1, 50 FGP iterations, 3 epochs per job, float32.
-# Metric: wall seconds for all 16 jobs, against the same jobs one after another through
-# vrps_solve.
+# Gaussian 1 % noise, TV weight 0.01 on a unit-radius field of view (0.01 x 64^2 in the
+# geometry's units), ProxSVRGSkip p = 0.1, 50 FGP iterations, float32, each job run to a 1e-4
+# relative objective gap (from a 150-epoch replay, as for the 2D batch).  Metric: wall seconds
+# for all 16 jobs, against the same jobs one after another through vrps_solve.
 WORKLOADS_BATCH = {
     "batch64": dict(jobs=64, sides=(128, 256, 384, 512, 1024), n_min=10, n_max=30, p=0.1, fgp_iters=50,
-                    alpha=0.02, epochs=20, estimator="SAGA", storage="FP16", correction_epochs=1, seed=20260209),
+                    alpha=0.02, alpha_fov=True, epochs=20, estimator="SAGA", storage="FP16", correction_epochs=1,
+                    seed=20260209, target_gap=1e-4, max_epochs=300),
     "batch3d_16": dict(dims=3, jobs=16, sides=(64, 96, 128), n_min=30, n_max=30, p=0.1, fgp_iters=50,
-                       alpha=0.01, epochs=3, estimator="SVRG", storage="FP32", correction_epochs=0, pool=2,
-                       seed=20260209),
+                       alpha=0.01, alpha_fov=True, epochs=3, estimator="SVRG", storage="FP32", correction_epochs=0,
+                       pool=2, seed=20260209, target_gap=1e-4, max_epochs=150),
 }
 
 # Served stream (optional): Poisson arrivals at `rate` per second for `seconds`; each request a
@@ -425,6 +431,16 @@ def bench_3d(args, rank, world, local):
 
 
 # --------------------------------------------------------------------------- batched jobs
+def job_alpha(w, J):
+    """TV weight of a batched job.  With alpha_fov the weight is stated on a unit-radius field of
+    view: scaling lengths by the radius R scales A and b by R and the data term by R^2, so the
+    same minimiser in pixel units has alpha R^2 (and the same relative objective gaps)."""
+    if not w.get("alpha_fov"):
+        return w["alpha"]
+    radius = J["side"] / 2.0 if w.get("dims", 2) == 2 else 64.0   # 3D: the 256^3 geometry's 128-unit field
+    return w["alpha"] * radius * radius
+
+
 def make_batch_jobs(w, rank):
     rng = np.random.default_rng(w["seed"] + rank)
     jobs = []
@@ -472,9 +488,29 @@ def bench_batch(args, rank, world, local):
     for j, (J, g) in enumerate(zip(jobs, geoms)):
         L = vr.power_iteration(g, 50, seed=w["seed"] + j)
         fac = 1.0 / 3.0 if w["estimator"] == "SAGA" else 1.0
-        kws.append(dict(alpha=w["alpha"], p=w["p"], gamma=fac / L, seed=w["seed"] + j, job=j,
+        kws.append(dict(alpha=job_alpha(w, J), p=w["p"], gamma=fac / L, seed=w["seed"] + j, job=j,
                         estimator=w["estimator"], fgp_iters=w["fgp_iters"], max_iters=w["epochs"] * J["N"]))
     xs = [torch.empty(g.n, device="cuda") for g in geoms]
+    gap_target = w.get("target_gap")
+    replay = None
+    if gap_target and not args.profile_once:
+        # iterations to the target gap, per job: a float32 replay evaluating F once per epoch
+        replay = []
+        for j, (J, g, b, kw) in enumerate(zip(jobs, geoms, bs, kws)):
+            N, E = J["N"], w["max_epochs"]
+            k = dict(kw, max_iters=E * N)
+            _, _, hist = vr.solve(b, g, k.pop("alpha"), "VR_PROXSKIP", p=k.pop("p"), gamma=k.pop("gamma"),
+                                  seed=k.pop("seed"), eval_every=N, history_cap=E + 1, x_out=xs[j], **k)
+            F = [h[1] for h in hist]
+            f_star = min(F)
+            e_star = next(e for e, f in enumerate(F) if (f - f_star) / abs(f_star) <= gap_target) + 1
+            # F was evaluated at the last prox output before iteration e* N: stop the job right
+            # after that prox step, so that its final iterate is that point
+            theta = vr.philox_schedule(kw["seed"], kw["job"], 0, e_star * N, N, kw["p"])[:, 1].cpu().numpy()
+            hits = np.nonzero(theta)[0]
+            kw["max_iters"] = int(hits[-1]) + 1 if len(hits) else e_star * N
+            replay.append(dict(f_star=f_star, epochs=e_star))
+        torch.cuda.synchronize()
     B = vr.Batch()
     if args.profile_once:
         # profiling driver: one batched run of all jobs, then exit
@@ -486,10 +522,11 @@ def bench_batch(args, rank, world, local):
         B.close()
         return
 
-    def run_batched(storage, corr):
+    def run_batched(storage, corr, scale=1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ids = [B.submit(g, b, x_out=x, storage=storage, correction_epochs=corr, **kw)
+        ids = [B.submit(g, b, x_out=x, storage=storage, correction_epochs=corr,
+                        **dict(kw, max_iters=kw["max_iters"] * scale))
                for g, b, x, kw in zip(geoms, bs, xs, kws)]
         while B.step(16):
             pass
@@ -511,7 +548,7 @@ def bench_batch(args, rank, world, local):
         return time.perf_counter() - t0
 
     def objectives():
-        return [vr.objective(g, x, b, w["alpha"])[0] for g, x, b in zip(geoms, xs, bs)]
+        return [vr.objective(g, x, b, kw["alpha"])[0] for g, x, b, kw in zip(geoms, xs, bs, kws)]
 
     # reference: the plain per-job float32 solver, one job after another
     run_sequential()
@@ -533,6 +570,15 @@ def bench_batch(args, rank, world, local):
             times.append(t)
     launches = (vr.kernel_launches() - launches0) // args.steps
     F_b16 = objectives()
+    # accuracy of the returned iterates against F* (the replay's lowest objective, or the lowest
+    # seen in a float32 run with 5x the iterations when no target gap is set)
+    if replay is not None:
+        F_star = [min(r_["f_star"], a, b) for r_, a, b in zip(replay, F_seq, F_b16)]
+    else:
+        run_batched("FP32", 0, scale=5)
+        F_star = [min(v) for v in zip(objectives(), F_seq, F_b16, F_oth)]
+    gap32 = [(a - f) / abs(f) for a, f in zip(F_seq, F_star)]
+    gap16 = [(a - f) / abs(f) for a, f in zip(F_b16, F_star)]
     dF32 = max(abs(a - b) / abs(b) for a, b in zip(F_b32, F_seq))
     dF16 = max(abs(a - b) / abs(b) for a, b in zip(F_b16, F_seq))
     dFo = max(abs(a - b) / abs(b) for a, b in zip(F_oth, F_seq))
@@ -547,7 +593,8 @@ def bench_batch(args, rank, world, local):
     vr.profile_enable(False)
     sides = [j["side"] for j in jobs]
     three = w.get("dims", 2) == 3
-    metric = (f"s for {w['jobs']} uneven {'3D' if three else '2D'} reconstructions ({w['epochs']} epochs each)")
+    metric = (f"s for {w['jobs']} uneven {'3D' if three else '2D'} reconstructions "
+              + (f"to a {gap_target:g} relative objective gap" if replay is not None else f"({w['epochs']} epochs each)"))
     algo = {"SAGA": "ProxSAGASkip", "SVRG": "ProxSVRGSkip"}.get(w["estimator"], w["estimator"])
     storage = (f"{w['storage'].lower()} + {w['correction_epochs']} float32 correction epoch"
                if w["storage"] != "FP32" else "float32")
@@ -569,8 +616,11 @@ def bench_batch(args, rank, world, local):
                    "angles_bins": ("views 1.4 x side, detector 1.5 x side squared, 256^3 field of view" if three
                                    else "1.5 x side"),
                    "subsets": f"U[{w['n_min']}, {w['n_max']}]",
-                   "algo": algo, "p": w["p"], "fgp_iters": w["fgp_iters"], "alpha": w["alpha"],
-                   "epochs": w["epochs"], "storage": storage,
+                   "algo": algo, "p": w["p"], "fgp_iters": w["fgp_iters"],
+                   "alpha": (f"{w['alpha']} on a unit-radius field of view ({w['alpha']} x R^2 in pixel units, "
+                             f"R = field-of-view radius in pixels)" if w.get("alpha_fov") else w["alpha"]),
+                   "epochs": (f"to a {gap_target:g} gap (replay cap {w['max_epochs']})" if replay is not None
+                              else w["epochs"]), "storage": storage,
                    "timing": "host wall clock, device synchronised at both ends (the batch runs on its own stream)",
                    "l2": f"working set of {w['jobs']} jobs > L2", "parallelism": f"replicas x{world}"},
         "baseline_per_job_fp32_s": round(t_seq, 6),
@@ -579,6 +629,16 @@ def bench_batch(args, rank, world, local):
         "objective_rel_diff_vs_per_job_fp32": {"batched_fp32": dF32, f"batched_{w['storage'].lower()}": dF16,
                                                f"batched_{other.lower()}": dFo},
         f"batched_{other.lower()}_s": round(t_oth, 6),
+        "final_iterate_gap": {
+            "per_job_fp32_max": max(gap32), f"batched_{w['storage'].lower()}_max": max(gap16),
+            "jobs_within_1e-4": {"per_job_fp32": sum(g_ <= 1e-4 for g_ in gap32),
+                                 f"batched_{w['storage'].lower()}": sum(g_ <= 1e-4 for g_ in gap16)},
+            "f_star": (f"lowest objective of a {w.get('max_epochs')}-epoch float32 replay per job" if replay is not None
+                       else f"min over runs incl. {5 * w['epochs']} epochs batched float32"),
+            "note": "each job stops right after the prox step whose output reached the target in the replay"},
+        "epochs_to_gap": ({"min": min(r_["epochs"] for r_ in replay), "max": max(r_["epochs"] for r_ in replay),
+                           "mean": round(float(np.mean([r_["epochs"] for r_ in replay])), 2),
+                           "cap": w["max_epochs"]} if replay is not None else None),
         "reconstructions_per_s": round(w["jobs"] * world / sec, 3),
         "ticks_per_run": ticks // (args.steps + args.warmup + 4),
         "e2e": {"value": round(sec, 6), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
