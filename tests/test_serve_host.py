@@ -17,3 +17,94 @@ def test_percentile_interpolates_order_statistics():
 def test_request_defaults():
     r = serve.Request(key=1, b=None, arrival=0.5, alpha=0.01, gamma=1.0, seed=3)
     assert r.admitted is None and r.finished is None and r.n_subsets == 0 and r.storage == "FP32"
+
+
+class _FakeBatch:
+    """Stands in for the device batch: a job finishes after max_iters ticks."""
+    live = []
+
+    def __init__(self, graphs=True):
+        self.left, self.next_id, self.running_max = {}, 0, 0
+        _FakeBatch.live.append(self)
+
+    def submit(self, g, b, *, max_iters, x_out, **kw):
+        jid = self.next_id
+        self.next_id += 1
+        self.left[jid] = max_iters
+        self.running_max = max(self.running_max, sum(v > 0 for v in self.left.values()))
+        return jid
+
+    def step(self, ticks=1):
+        for j in self.left:
+            self.left[j] = max(0, self.left[j] - ticks)
+        return sum(v > 0 for v in self.left.values())
+
+    def poll(self, jid):
+        done = self.left[jid] == 0
+        return done, ({"iterations": 1} if done else None)
+
+    def release(self, jid):
+        del self.left[jid]
+
+    def close(self):
+        pass
+
+
+class _G:
+    def __init__(self, n, nbytes):
+        self.n, self.nbytes = n, nbytes
+
+
+@pytest.fixture
+def fake_engine(monkeypatch):
+    import torch
+    from paper_2602_09527_gb300 import _binding as vb
+    _FakeBatch.live = []
+    monkeypatch.setattr(vb, "Batch", _FakeBatch)
+    monkeypatch.setattr(vb, "job_footprint", lambda g, max_iters, storage="FP32": g.nbytes)
+    return torch
+
+
+def _reqs(torch, keys, iters):
+    return [serve.Request(key=k, b=torch.zeros(4), arrival=0.0, alpha=0.01, gamma=1.0, seed=i, max_iters=it)
+            for i, (k, it) in enumerate(zip(keys, iters))]
+
+
+def test_admission_by_footprint_and_handles(fake_engine):
+    """Admission in arrival order while a handle of the request's class is free and the summed
+    footprint stays within the budget; memory and handles return when a job finishes."""
+    torch = fake_engine
+    pools = {"a": [_G(4, 100), _G(4, 100), _G(4, 100)], "b": [_G(4, 250)]}
+    srv = serve.BatchServer(pools, budget_bytes=300, ticks_per_step=1)
+    reqs = _reqs(torch, ["a", "a", "b", "a", "b", "a"], [3, 5, 2, 4, 1, 2])
+    st = srv.run(reqs)
+    assert st.completed == len(reqs)
+    assert st.peak_bytes <= 300
+    assert _FakeBatch.live[0].running_max <= 3
+    assert all(r.admitted is not None and r.finished >= r.admitted for r in reqs)
+    # arrival order: a request is never admitted before an earlier one
+    adm = [r.admitted for r in reqs]
+    assert adm == sorted(adm)
+    assert srv.used == 0 and len(srv.free["a"]) == 3 and len(srv.free["b"]) == 1
+
+
+def test_single_job_larger_than_budget_still_runs(fake_engine):
+    """A job whose footprint alone exceeds the budget is admitted when nothing else runs."""
+    torch = fake_engine
+    srv = serve.BatchServer({"big": [_G(4, 10_000)]}, budget_bytes=10, ticks_per_step=2)
+    st = srv.run(_reqs(torch, ["big", "big"], [3, 3]))
+    assert st.completed == 2 and st.peak_jobs == 1
+
+
+def test_mixed_server_splits_and_merges(fake_engine):
+    """2D and 3D requests go to two batch servers (the 3D one in a worker thread) sharing one
+    clock; the merged statistics count every request."""
+    torch = fake_engine
+    srv = serve.MixedServer({"2d": [_G(4, 10), _G(4, 10)]}, {"3d": [_G(8, 10)]}, budget_bytes=100)
+    reqs = _reqs(torch, ["2d", "3d", "2d", "3d", "2d"], [4, 6, 2, 3, 5])
+    st = srv.run(reqs)
+    srv.close()
+    assert st.completed == 5 and len(st.latencies) == 5
+    assert len(_FakeBatch.live) == 2
+    assert sum(b.next_id for b in _FakeBatch.live) == 5
+    assert all(r.finished is not None for r in reqs)
