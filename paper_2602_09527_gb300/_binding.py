@@ -238,7 +238,8 @@ def vrps_geom_cone3d(*a, **k):
 
 
 def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
-    """vrps_autotune: 2D forward band and adjoint pixels per thread, or the 3D FGP chunk, by timing."""
+    """vrps_autotune: 2D forward band and adjoint pixels per thread, or the 3D FGP chunk and
+    adjoint voxels per thread, by timing."""
     out = (ctypes.c_double * 4)()
     _check(lib.vrps_autotune(g.handle, int(reps), out, _stream(stream)))
     if g.dims == 3:
@@ -252,14 +253,15 @@ def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
 
 def set_launch_shape(g: Geometry, fwd_band_bytes: int = 0, fwd_group: int = 0, adj_pixels_per_thread: int = 0,
                      fgp3_chunk: int = 0, fgp_tile: int = 0, adj_split: int = 0):
-    """vrps_set_launch_shape (0 = built-in default for each)."""
+    """vrps_set_launch_shape (0 = built-in default for each).  adj_pixels_per_thread: 1 or 2
+    for 2D geometries, voxels per thread along z (16 or 32) for 3D ones."""
     _check(lib.vrps_set_launch_shape(g.handle, int(fwd_band_bytes), int(fwd_group), int(adj_pixels_per_thread),
                                      int(fgp3_chunk), int(fgp_tile), int(adj_split)))
 
 
 def launch_shape(g: Geometry) -> list:
-    """vrps_launch_shape: [fwd band bytes, bands per CTA, adjoint pixels per thread, 3D FGP chunk,
-    2D FGP tile, adjoint angle shares]."""
+    """vrps_launch_shape: [fwd band bytes, bands per CTA, adjoint pixels per thread (3D: voxels
+    per thread along z), 3D FGP chunk, 2D FGP tile, adjoint angle shares]."""
     out = (ctypes.c_int * 6)()
     _check(lib.vrps_launch_shape(g.handle, out))
     return list(out)
