@@ -106,7 +106,7 @@ WORKLOADS_OPS = {"ops": dict(base="par2d_512", ks=(10, 100), ns=(10, 20, 50, 100
 # by the CPU oracle legs to scale a bounded sample up to a whole reconstruction.  Recorded from
 # the GPU replay of this workload; the GPU arm recomputes them every run.
 TRAJECTORY = {
-    "par2d_512": dict(iterations=1920, prox_calls=180, snapshots=96),
+    "par2d_512": dict(iterations=1901, prox_calls=180, snapshots=96),
     "par2d_64": dict(iterations=None, prox_calls=None, snapshots=None),
 }
 
@@ -937,6 +937,14 @@ def main():
     reached = k_star is not None
     if not reached:
         k_star = max_it
+    k_eval = k_star
+    if reached:
+        # F was evaluated at the last prox output before iteration k_eval: the reconstruction is
+        # done right after that prox step, whose output is the returned iterate
+        theta = vr.philox_schedule(w["seed"], 0, 0, k_eval, N, w["p"])[:, 1].cpu().numpy()
+        hits = np.nonzero(theta)[0]
+        if len(hits):
+            k_star = int(hits[-1]) + 1
 
     def run_once(host=False):
         bb = b_host if host else b_dev
@@ -1034,7 +1042,8 @@ def main():
         "data": "synthetic (seeded ellipse phantom, analytic sinogram, Poisson 1e4 photons)",
         "config": {"workload": wl, "image": f"{w['n']}x{w['n']}", "angles": w["n_angles"], "bins": w["n_bins"],
                    "subsets": N, "algo": "ProxSVRGSkip", "p": w["p"], "fgp_iters": w["fgp_iters"],
-                   "alpha": w["alpha"], "gamma": "1/L", "k_star": k_star, "target_reached": reached,
+                   "alpha": w["alpha"], "gamma": "1/L", "k_star": k_star, "gap_evaluated_at": k_eval,
+                   "target_reached": reached,
                    "f_star": f_star, "f_star_sources": {"fista_4000": min(h[1] for h in hist_ref),
                                                         "pdhg_6000": f_pdhg,
                                                         "trajectory": min(h[1] for h in hist)},
