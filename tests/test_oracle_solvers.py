@@ -147,3 +147,22 @@ def test_skip_variant_prox_count_follows_coins(small):
     tr = solvers.run(op, b, alpha, "VR_PROXSKIP", 1.0 / L, K, 10, p=p, seed=seed)
     _, theta, _ = philox.schedule(seed, K, op.N, p)
     assert tr.prox_calls == int(theta.sum())
+
+
+def test_stopping_after_last_prox_returns_evaluated_point(small):
+    """The time-to-gap measurements evaluate F at the last prox output before iteration k and
+    stop a run right after that prox step (iteration j, the last with theta_j = 1 below k):
+    the run's final iterate x_{j+1} is exactly the point that was evaluated."""
+    op, b, alpha, L = small
+    p, seed, N = 0.2, 9, op.N
+    k = 6 * N
+    tr = solvers.run(op, b, alpha, "VR_PROXSKIP", 1.0 / L, k, 10, p=p, seed=seed, estimator="SAGA",
+                     eval_every=N)
+    _, theta, _ = philox.schedule(seed, k, N, p)
+    j = int(np.nonzero(theta)[0][-1])
+    short = solvers.run(op, b, alpha, "VR_PROXSKIP", 1.0 / L, j + 1, 10, p=p, seed=seed, estimator="SAGA")
+    assert np.array_equal(short.x, tr.last_prox)
+    assert solvers.objective(op, b, short.x, alpha) == tr.objective[k]
+    if j + 1 < k:
+        # the iterate at k itself is a gradient step past the prox point
+        assert not np.array_equal(tr.x, tr.last_prox)
