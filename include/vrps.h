@@ -112,7 +112,9 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
  * doubles): chosen band bytes, pixels per thread, tuned forward + adjoint time in
  * microseconds, bands per CTA; the adjoint's angle shares per pixel tile (1, 2, 4: partial sums
  * added in share order by the last share) are timed with the pixels per thread, and the 2D FGP
- * output tile (32 x 32, 32 x 16 or 16 x 16) on a 16-iteration prox call (see vrps_launch_shape).
+ * output tile (32 x 32, 32 x 16 or 16 x 16) on a 16-iteration prox call (see vrps_launch_shape);
+ * with more than one subset the all-angle forward and adjoint get their own band / bands per
+ * CTA and angle shares, timed on the full sinogram (see vrps_launch_shape_full).
  * 3D geometries: times three iterations of the streaming FGP prox for chunks of 4 ... 128 z
  * planes, and subset 0's adjoint with 16 and 32 voxels per thread along z, and keeps the
  * fastest of each (out4: FGP chunk, adjoint voxels per thread, FGP time and adjoint time in
@@ -130,6 +132,11 @@ int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int a
 /* Current launch shapes of the handle in the same order (HOST int[6]; 0 = default; the 3D FGP
  * chunk is reported as the effective one for 3D geometries). */
 int vrps_launch_shape(const vrps_geom* g, int* out6);
+/* 2D geometries: launch shapes of the all-angle passes (SVRG snapshots, full gradients,
+ * full-sinogram projections), which vrps_autotune times separately on the full sinogram
+ * (HOST int[3]: forward band bytes, forward bands per CTA, adjoint angle shares; 0 = as for
+ * subsets; vrps_set_launch_shape resets them to 0).  Errors: INVALID_ARG. */
+int vrps_launch_shape_full(const vrps_geom* g, int* out3);
 
 /* ---------------------------------------------------------------- operators
  * y = A_i x  (Section 1.2: the forward operator of subset i; i = -1 for A).

@@ -94,6 +94,7 @@ def _load():
         "vrps_power_iteration": (i, [vp, i, u64, P(d), vp]),
         "vrps_objective": (i, [vp, vp, vp, d, P(d), vp]),
         "vrps_philox_schedule": (i, [u64, u32, i64, i, i, d, vp, vp]),
+        "vrps_launch_shape_full": (i, [vp, P(i)]),
         "vrps_solve_opts_default": (None, [P(SolveOpts)]),
         "vrps_solve": (i, [vp, vp, d, i, d, d, u64, P(SolveOpts), vp, P(Report), vp]),
         "vrps_kernel_launches": (u64, []),
@@ -246,9 +247,11 @@ def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
         return {"fgp3d_chunk_planes": int(out[0]), "fgp3_iterations_us": float(out[2]),
                 "adj3d_voxels_per_thread": int(out[1]), "adj3d_subset_us": float(out[3])}
     shape = launch_shape(g)
+    full = launch_shape_full(g)
     return {"fwd_band_bytes": int(out[0]), "fwd_bands_per_cta": int(out[3]), "adj_pixels_per_thread": int(out[1]),
             "adj_angle_shares": max(1, shape[5]), "fgp_tile": ["32x32", "32x16", "16x16"][shape[4]],
-            "fwd_adj_us": float(out[2])}
+            "fwd_adj_us": float(out[2]),
+            "all_angles": {"fwd_band_bytes": full[0], "fwd_bands_per_cta": full[1], "adj_angle_shares": full[2]}}
 
 
 def set_launch_shape(g: Geometry, fwd_band_bytes: int = 0, fwd_group: int = 0, adj_pixels_per_thread: int = 0,
@@ -264,6 +267,14 @@ def launch_shape(g: Geometry) -> list:
     per thread along z), 3D FGP chunk, 2D FGP tile, adjoint angle shares]."""
     out = (ctypes.c_int * 6)()
     _check(lib.vrps_launch_shape(g.handle, out))
+    return list(out)
+
+
+def launch_shape_full(g: Geometry) -> list:
+    """vrps_launch_shape_full: [fwd band bytes, bands per CTA, adjoint angle shares] of the 2D
+    all-angle passes (0 = as for subsets)."""
+    out = (ctypes.c_int * 3)()
+    _check(lib.vrps_launch_shape_full(g.handle, out))
     return list(out)
 
 

@@ -613,6 +613,7 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
     return VRPS_OK;
   };
   FwdOut fo{w.sino, nullptr, nullptr};
+  g->tune_full_fwd_bytes = g->tune_full_fwd_group = g->tune_full_adj_split = 0;   // subsets first
   const int cand[] = {16 << 10, 24 << 10, 32 << 10, 48 << 10, 64 << 10, 96 << 10};
   const int groups[] = {1, 2, 4, 8};
   int best_bytes = 0, best_group = 1;
@@ -663,6 +664,50 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
   }
   g->tune_adj_two = best_two;
   g->tune_adj_split = best_split;
+  // all-angle passes (SVRG snapshots, full gradients): their own forward band / bands per CTA
+  // and adjoint angle shares, timed on the full sinogram
+  if (g->n_subsets > 1) {
+    const int* all = g->order_natural;
+    const int nall = g->n_angles;
+    int fb = best_bytes, fg = best_group;
+    float bf = 1e30f;
+    for (int c : cand) {
+      for (int grp : groups) {
+        if (grp > 1 && (c > (64 << 10) || g->n_bins > 1536)) continue;
+        g->tune_full_fwd_bytes = c;
+        g->tune_full_fwd_group = grp;
+        float t = 0.f;
+        const int rc = timed([&]() { return fwd2d(g, w.img, w.img2, all, nall, FWD_PLAIN, fo, s); }, &t);
+        if (rc != VRPS_OK) {
+          g->tune_full_fwd_bytes = g->tune_full_fwd_group = 0;
+          return rc;
+        }
+        if (t < bf) {
+          bf = t;
+          fb = c;
+          fg = grp;
+        }
+      }
+    }
+    g->tune_full_fwd_bytes = fb;
+    g->tune_full_fwd_group = fg;
+    int fs = 1;
+    float ba = 1e30f;
+    for (int split : {1, 2, 4, 8}) {
+      g->tune_full_adj_split = split;
+      float t = 0.f;
+      const int rc = timed([&]() { return adj2d(g, w.sino, all, nall, ua, s); }, &t);
+      if (rc != VRPS_OK) {
+        g->tune_full_adj_split = 0;
+        return rc;
+      }
+      if (t < ba) {
+        ba = t;
+        fs = split;
+      }
+    }
+    g->tune_full_adj_split = fs;
+  }
   // 2D FGP output tile, timed on one 16-iteration prox call
   {
     VRPS_TRY(ensure(&w.dual, 2 * (size_t)g->n));
@@ -712,6 +757,15 @@ int vrps_launch_shape(const vrps_geom* g, int* out6) {
   return VRPS_OK;
 }
 
+int vrps_launch_shape_full(const vrps_geom* g, int* out3) {
+  VRPS_TRY(check_geom(g));
+  if (!out3) return fail(VRPS_ERR_INVALID_ARG, "out3 is NULL");
+  out3[0] = g->tune_full_fwd_bytes;
+  out3[1] = g->tune_full_fwd_group;
+  out3[2] = g->tune_full_adj_split;
+  return VRPS_OK;
+}
+
 int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread, int fgp3_chunk,
                           int fgp_tile, int adj_split) {
   VRPS_TRY(check_geom(g));
@@ -727,6 +781,7 @@ int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int a
   }
   g->tune_fgp_tile = fgp_tile;
   g->tune_adj_split = adj_split;
+  g->tune_full_fwd_bytes = g->tune_full_fwd_group = g->tune_full_adj_split = 0;   // all passes alike
   g->tune_fwd_bytes = fwd_band_bytes;
   g->tune_fwd_group = fwd_group;
   g->tune_adj_two = adj_pixels_per_thread == 0 ? -1 : (adj_pixels_per_thread == 2 ? 1 : 0);

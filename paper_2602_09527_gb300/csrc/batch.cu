@@ -255,30 +255,35 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
     VRPS_CUDA(cudaEventRecord(J->ev_start, s));
     return VRPS_OK;
   }
-  // launch constants for the batch's shared-memory maxima
-  Fwd2DParams fp;
-  size_t fs = 0;
-  bool bulk = false;
-  FwdOut fo{w.res, w.b_perm, w.tab};
-  VRPS_TRY(fwd2d_setup(g, w.x, w.xfT, J->order, g->n_angles, fo, &fp, &fs, &bulk));
-  Adj2DParams ap;
-  size_t as = 0;
-  int var = 0, tx = 0, ty = 0;
-  UpdateArgs ua;
-  std::memset(&ua, 0, sizeof(ua));
-  VRPS_TRY(adj2d_setup(g, w.res, J->order, g->n_angles, ua, &ap, &as, &var, &tx, &ty));
+  // launch constants for the batch's shared-memory maxima, over the all-angle and the subset
+  // passes (their launch shapes can differ) -- this also sizes the job's partial-sum buffers
   bool regrid = false;
-  if (fs > B->fwd_smem) {
-    B->fwd_smem = fs;
-    regrid = true;
-  }
-  if (fp.group > 1 && bulk && !B->fwd_grouped) {
-    B->fwd_grouped = true;
-    regrid = true;
-  }
-  if (as > B->adj_smem) {
-    B->adj_smem = as;
-    regrid = true;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int* ids = pass == 0 ? J->order : J->order + J->off[0];
+    const int rows = pass == 0 ? g->n_angles : J->off[1] - J->off[0];
+    Fwd2DParams fp;
+    size_t fs = 0;
+    bool bulk = false;
+    FwdOut fo{w.res, w.b_perm, w.tab};
+    VRPS_TRY(fwd2d_setup(g, w.x, w.xfT, ids, rows, fo, &fp, &fs, &bulk));
+    Adj2DParams ap;
+    size_t as = 0;
+    int var = 0, tx = 0, ty = 0;
+    UpdateArgs ua;
+    std::memset(&ua, 0, sizeof(ua));
+    VRPS_TRY(adj2d_setup(g, w.res, ids, rows, ua, &ap, &as, &var, &tx, &ty));
+    if (fs > B->fwd_smem) {
+      B->fwd_smem = fs;
+      regrid = true;
+    }
+    if (fp.group > 1 && bulk && !B->fwd_grouped) {
+      B->fwd_grouped = true;
+      regrid = true;
+    }
+    if (as > B->adj_smem) {
+      B->adj_smem = as;
+      regrid = true;
+    }
   }
   const int nb = (J->fgp_iters + FB_T - 1) / FB_T;
   if (nb > B->max_blocks) B->max_blocks = nb;
@@ -431,11 +436,16 @@ int job_tick(vrps_batch* B, Job* J, Entries* E) {
   size_t sm = 0;
   bool bulk = false;
   VRPS_TRY(fwd2d_setup(g, w.x, w.xfT, P.ids, P.rows, P.fo, &E->f.P, &sm, &bulk));
+  // the batch's launches were sized at admission; a launch shape changed since cannot run
+  if (sm > B->fwd_smem || (E->f.P.group > 1 && bulk && !B->fwd_grouped))
+    return fail(VRPS_ERR_INVALID_ARG, "job %d: its geometry's launch shape changed while the job runs", J->id);
   E->f.mode = P.mode;
   E->f.bulk = bulk ? 1 : 0;
   E->f_items = E->f.P.bands * P.rows;
   int var = 0, tx = 0, ty = 0;
   VRPS_TRY(adj2d_setup(g, w.res, P.ids, P.rows, P.ua, &E->a.P, &sm, &var, &tx, &ty));
+  if (sm > B->adj_smem)
+    return fail(VRPS_ERR_INVALID_ARG, "job %d: its geometry's launch shape changed while the job runs", J->id);
   E->a.variant = var;
   E->a.tiles_x = tx;
   E->a_items = tx * ty * E->a.P.split;

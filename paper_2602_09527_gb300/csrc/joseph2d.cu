@@ -530,7 +530,10 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   P.o = o;
   const int maxw = g->nx > g->ny ? g->nx : g->ny;   // widest line (row of x or of x^T)
   const int maxl = maxw;
-  const int band_bytes = g->tune_fwd_bytes > 0 ? g->tune_fwd_bytes : FWD_BAND_BYTES;
+  // all-angle passes take their own tuned shape when there is one
+  const bool full = rows >= g->n_angles && g->tune_full_fwd_bytes > 0;
+  const int band_bytes = full ? g->tune_full_fwd_bytes : (g->tune_fwd_bytes > 0 ? g->tune_fwd_bytes : FWD_BAND_BYTES);
+  const int want_group = full ? g->tune_full_fwd_group : g->tune_fwd_group;
   int band = band_bytes / (int)(sizeof(float) * (maxw + 2 * FWD_PAD));
   if (band < 1) band = 1;
   if (band > maxl) band = maxl;
@@ -539,16 +542,18 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   // the bulk copy needs 16-byte aligned rows: line lengths that are multiples of 4 floats
   *bulk = (g->nx % 4 == 0) && (g->ny % 4 == 0) && (((uintptr_t)x | (uintptr_t)xT) % 16 == 0);
   // band groups: bulk copies only (the plain-load path walks one band per item)
-  P.group = *bulk && g->tune_fwd_group > 1 && g->n_bins <= FWD_RPT * FWD_THREADS ? g->tune_fwd_group : 1;
+  P.group = *bulk && want_group > 1 && g->n_bins <= FWD_RPT * FWD_THREADS ? want_group : 1;
   if (P.group > P.nbands) P.group = P.nbands;
   P.bands = (P.nbands + P.group - 1) / P.group;
   vrps_geom* gm = const_cast<vrps_geom*>(g);
   Workspace& ws = gm->ws;
-  if (!ws.fwd_part || ws.fwd_bands != P.bands) {
+  const size_t part_need = (size_t)g->n_angles * P.bands * g->n_bins;
+  if (ws.fwd_part_cap < part_need) {
     if (ws.fwd_part) cudaFree(ws.fwd_part);
     ws.fwd_part = nullptr;
-    VRPS_CUDA(cudaMalloc((void**)&ws.fwd_part, sizeof(float) * (size_t)g->n_angles * P.bands * g->n_bins));
-    ws.fwd_bands = P.bands;
+    ws.fwd_part_cap = 0;
+    VRPS_CUDA(cudaMalloc((void**)&ws.fwd_part, sizeof(float) * part_need));
+    ws.fwd_part_cap = part_need;
   }
   if (!ws.fwd_count) {
     VRPS_CUDA(cudaMalloc((void**)&ws.fwd_count, sizeof(unsigned) * (size_t)g->n_angles));
@@ -562,7 +567,6 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   P.count = ws.fwd_count;
   P.err = ws.dev_error;
   *smem = sizeof(float) * (size_t)band * (maxw + 2 * FWD_PAD) * (P.group > 1 ? 2 : 1);
-  (void)rows;
   return VRPS_OK;
 }
 
@@ -623,7 +627,8 @@ int adj2d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, co
   *tiles_y = (g->ny + ty - 1) / ty;
   P.tiles_x = *tiles_x;
   // angle shares per tile (at least 4 angles each)
-  int split = g->tune_adj_split > 1 ? g->tune_adj_split : 1;
+  int split = (rows >= g->n_angles && g->tune_full_adj_split > 0) ? g->tune_full_adj_split
+                                                                  : (g->tune_adj_split > 1 ? g->tune_adj_split : 1);
   while (split > 1 && rows / split < 4) --split;
   P.split = split;
   P.part = nullptr;

@@ -143,7 +143,7 @@ struct Workspace {
   double* partials = nullptr;   // reduction partials
   float* fwd_part = nullptr;      // 2D forward: per-band partial ray sums
   unsigned* fwd_count = nullptr;  // 2D forward: band arrival counters (one per angle row)
-  int fwd_bands = 0;              // bands the partial buffer was sized for
+  size_t fwd_part_cap = 0;        // floats the partial buffer holds
   unsigned* dev_error = nullptr;  // device-side error word (bounded waits that expired)
   double* scalars = nullptr;    // [16] device scalars
   float* sino = nullptr;        // [m] sinogram scratch
@@ -195,6 +195,9 @@ struct vrps_geom {
   int tune_adj_two = -1;    // 2D adjoint: two pixels per thread (1) or one (0)
   int tune_f3_zc = 0;       // 3D FGP: z planes per streaming chunk
   int tune_adj3_zc = 0;     // 3D adjoint: voxels per thread along z (0 = 16, or 32)
+  // 2D all-angle passes (snapshots, full gradients): own forward band / bands per CTA and
+  // adjoint angle shares when tuned (0 = as for subsets)
+  int tune_full_fwd_bytes = 0, tune_full_fwd_group = 0, tune_full_adj_split = 0;
   int tune_fgp_tile = 0;    // 2D FGP output tile: 0 32x32, 1 32x16, 2 16x16
   int tune_adj_split = 0;   // 2D adjoint: angle shares per pixel tile (0: one)
   // 3D tables

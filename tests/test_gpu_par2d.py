@@ -158,6 +158,29 @@ def test_autotuned_shapes_keep_parity():
     assert rel(y, J.forward(og, x, rows)) < TOL
     r = rng.standard_normal((len(rows), 300))
     assert rel(host(vr.proj_adj(g, 2, dev(r))), J.adjoint(og, r, rows)) < TOL
+    # the all-angle passes got their own shapes, timed on the full sinogram
+    full = t["all_angles"]
+    assert full["fwd_band_bytes"] in (16 << 10, 24 << 10, 32 << 10, 48 << 10, 64 << 10, 96 << 10)
+    assert full["fwd_bands_per_cta"] in (1, 2, 4, 8) and full["adj_angle_shares"] in (1, 2, 4, 8)
+    yf = host(vr.proj_fwd(g, -1, dev(x))).reshape(120, 300)
+    assert rel(yf, J.forward(og, x, list(range(120)))) < TOL
+    rf = rng.standard_normal((120, 300))
+    assert rel(host(vr.proj_adj(g, -1, dev(rf))), J.adjoint(og, rf, list(range(120)))) < TOL
+    # a batched job on the tuned geometry (snapshot passes with the all-angle shapes) equals
+    # vrps_solve on it, bit for bit
+    b = dev(J.forward(og, x, list(range(120))))
+    L = vr.power_iteration(g, 30, seed=1)
+    kw = dict(p=0.3, gamma=1 / L, seed=12, estimator="SVRG", fgp_iters=9, max_iters=20)
+    xs, _, _ = vr.solve(b, g, 0.01, "VR_PROXSKIP", **kw)
+    xs = xs.clone()
+    B = vr.Batch()
+    jid = B.submit(g, b, alpha=0.01, **kw)
+    B.wait(jid)
+    assert torch.equal(B.result(jid), xs)
+    B.close()
+    # setting shapes by hand applies them to every pass again
+    vr.set_launch_shape(g)
+    assert vr.launch_shape_full(g) == [0, 0, 0]
 
 
 @pytest.mark.parametrize("shape", [(16 << 10, 1, 1, 1), (16 << 10, 3, 2, 2), (24 << 10, 4, 1, 3), (48 << 10, 8, 2, 4),
