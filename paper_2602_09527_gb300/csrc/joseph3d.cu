@@ -6,10 +6,11 @@
 // fz = cz + (iv - cv)(Q0 + Q1 l), both carried in 64-bit fixed point, bilinearly
 // interpolated; each plane adds voxel * |d| / |d_a|.  Rays marched over x planes read the
 // volume transposed in (x, y), so that for either axis the 32 lanes of a warp (adjacent
-// detector columns) read along a contiguous row.  The adjoint visits, for every voxel and view, the detector
-// columns whose rays cross the voxel's dominant plane within one voxel (found by projecting
-// the two plane points at +-1 voxel onto the detector) and the rows whose z index is within
-// one voxel, and accumulates the identical bilinear weight.
+// detector columns) read along a contiguous row.  The adjoint visits, for every column of
+// voxels and view, the detector columns whose rays cross the voxels' dominant plane within
+// one voxel (found by projecting the two plane points at +-1 voxel onto the detector) and
+// walks their detector rows in the forward's own fixed point, so that every row adds the
+// identical bilinear weights to the two voxels its ray interpolates.
 #include "vrps_internal.h"
 
 namespace vrps {
