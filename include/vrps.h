@@ -334,8 +334,7 @@ int vrps_batch_set_graphs(vrps_batch* batch, int on);
 /* Admits a job before the next tick: allocates its state in the geometry's workspace,
  * reorders b subset-major, draws its Philox schedule and (SAGA) builds its table.  *id is
  * the job's handle.  Errors: INVALID_ARG (bad field, geometry busy, 2D job in a 3D batch or
- * the reverse), UNSUPPORTED (more than 256 running jobs, a 3D detector with rows much finer
- * than the voxels), OUT_OF_MEMORY, CUDA. */
+ * the reverse), UNSUPPORTED (more than 256 running jobs), OUT_OF_MEMORY, CUDA. */
 int vrps_batch_submit(vrps_batch* batch, const vrps_job* job, int* id);
 /* Enqueues up to `ticks` ticks (fewer when every job finishes); *active = jobs still
  * running.  Returns once the work is enqueued (the host may block on a work-list slot that
