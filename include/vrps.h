@@ -338,7 +338,8 @@ int vrps_batch_set_graphs(vrps_batch* batch, int on);
 int vrps_batch_submit(vrps_batch* batch, const vrps_job* job, int* id);
 /* Enqueues up to `ticks` ticks (fewer when every job finishes); *active = jobs still
  * running.  Returns once the work is enqueued (the host may block on a work-list slot that
- * the device still reads). */
+ * the device still reads).  Errors: INVALID_ARG (NULL batch, or a running job's geometry was
+ * given a launch shape after admission that the batch's launches were not sized for), CUDA. */
 int vrps_batch_step(vrps_batch* batch, int ticks, int* active);
 /* *done = 1 once job `id` has finished on the device, with its report (seconds = device
  * time from admission to completion).  Errors: INVALID_ARG, TIMEOUT (a bounded device wait
