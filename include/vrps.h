@@ -83,8 +83,9 @@ int vrps_geom_par2d(int nx, int ny, double pixel, int n_angles, const double* an
  * -(sdd-sod)(cos b, sin b, 0); detector axes e_u = (-sin b, cos b, 0), e_v = (0,0,1);
  * pixel (iu,iv) centre (iu-(nu-1)/2) du, (iv-(nv-1)/2) dv.  Voxel (ix,iy,iz) centre
  * ((i-(n-1)/2) voxel).  betas_rad: HOST array of n_views float64 source angles, copied.
- * Errors: INVALID_ARG as above, or when the source lies inside the volume's bounding
- * circle; UNSUPPORTED when a ray would be marched along z (cone angle above 45 degrees). */
+ * Errors: INVALID_ARG as above, more than 65535 views or 65536 detector columns or rows, or
+ * when the source lies inside the volume's bounding circle; UNSUPPORTED when a ray would be
+ * marched along z (cone angle above 45 degrees). */
 int vrps_geom_cone3d(int nx, int ny, int nz, double voxel, int n_views, const double* betas_rad,
                      int nu, int nv, double du, double dv, double sod, double sdd,
                      int n_subsets, vrps_geom** out);

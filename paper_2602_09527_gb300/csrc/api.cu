@@ -370,6 +370,8 @@ int vrps_geom_cone3d(int nx, int ny, int nz, double voxel, int n_views, const do
   if (nx <= 0 || ny <= 0 || nz <= 0 || n_views <= 0 || nu <= 0 || nv <= 0)
     return fail(VRPS_ERR_INVALID_ARG, "sizes must be positive");
   if (n_views > 65535) return fail(VRPS_ERR_INVALID_ARG, "at most 65535 views");
+  // detector rows / columns: the adjoint's float row-range estimate stays within one row
+  if (nu > 65536 || nv > 65536) return fail(VRPS_ERR_INVALID_ARG, "at most 65536 detector columns and rows");
   if ((int64_t)nx * ny * nz > ((int64_t)1 << 31) - 1) return fail(VRPS_ERR_INVALID_ARG, "volume too large");
   if ((int64_t)nu * nv * n_views > ((int64_t)1 << 31) - 1) return fail(VRPS_ERR_INVALID_ARG, "sinogram too large");
   if (!(voxel > 0) || !(du > 0) || !(dv > 0)) return fail(VRPS_ERR_INVALID_ARG, "spacings must be > 0");
