@@ -434,6 +434,23 @@ def bench_3d(args, rank, world, local):
 
 
 # --------------------------------------------------------------------------- batched jobs
+def first_within(hist, f_star, target):
+    """Iteration of the first evaluation (rows [k, F, ...]) whose F is within `target` of f_star
+    (relative gap), or None."""
+    for h in hist:
+        if (h[1] - f_star) / abs(f_star) <= target:
+            return int(h[0])
+    return None
+
+
+def stop_after_last_prox(k_eval, theta):
+    """Iterations to run so that the final iterate is the prox output F was evaluated at: the
+    solver evaluates F at the last prox output before iteration k_eval, which is x after the
+    last iteration j < k_eval with theta_j = 1 (k_eval itself when there is none)."""
+    hits = np.nonzero(np.asarray(theta)[:k_eval])[0]
+    return int(hits[-1]) + 1 if len(hits) else k_eval
+
+
 def job_alpha(w, J):
     """TV weight of a batched job.  With alpha_fov the weight is stated on a unit-radius field of
     view: scaling lengths by the radius R scales A and b by R and the data term by R^2, so the
@@ -506,12 +523,11 @@ def bench_batch(args, rank, world, local):
                                   seed=k.pop("seed"), eval_every=N, history_cap=E + 1, x_out=xs[j], **k)
             F = [h[1] for h in hist]
             f_star = min(F)
-            e_star = next(e for e, f in enumerate(F) if (f - f_star) / abs(f_star) <= gap_target) + 1
-            # F was evaluated at the last prox output before iteration e* N: stop the job right
-            # after that prox step, so that its final iterate is that point
-            theta = vr.philox_schedule(kw["seed"], kw["job"], 0, e_star * N, N, kw["p"])[:, 1].cpu().numpy()
-            hits = np.nonzero(theta)[0]
-            kw["max_iters"] = int(hits[-1]) + 1 if len(hits) else e_star * N
+            k_eval = first_within(hist, f_star, gap_target)
+            e_star = k_eval // N
+            # stop the job right after the prox step whose output reached the target
+            theta = vr.philox_schedule(kw["seed"], kw["job"], 0, k_eval, N, kw["p"])[:, 1].cpu().numpy()
+            kw["max_iters"] = stop_after_last_prox(k_eval, theta)
             replay.append(dict(f_star=f_star, epochs=e_star))
         torch.cuda.synchronize()
     B = vr.Batch()
@@ -932,22 +948,15 @@ def main():
                                estimator=w["estimator"], fgp_iters=w["fgp_iters"], max_iters=max_it,
                                eval_every=N, history_cap=max_it // N + 1)
     f_star = min(f_ref, min(h[1] for h in hist))
-    k_star = None
-    for h in hist:
-        if (h[1] - f_star) / abs(f_star) <= w["target_gap"]:
-            k_star = int(h[0])
-            break
-    reached = k_star is not None
+    k_eval = first_within(hist, f_star, w["target_gap"])
+    reached = k_eval is not None
     if not reached:
-        k_star = max_it
-    k_eval = k_star
+        k_eval = max_it
+    k_star = k_eval
     if reached:
-        # F was evaluated at the last prox output before iteration k_eval: the reconstruction is
-        # done right after that prox step, whose output is the returned iterate
+        # the reconstruction is done right after the prox step whose output met the target
         theta = vr.philox_schedule(w["seed"], 0, 0, k_eval, N, w["p"])[:, 1].cpu().numpy()
-        hits = np.nonzero(theta)[0]
-        if len(hits):
-            k_star = int(hits[-1]) + 1
+        k_star = stop_after_last_prox(k_eval, theta)
 
     def run_once(host=False):
         bb = b_host if host else b_dev
