@@ -102,6 +102,7 @@ class Trace:
     prox_calls: int = 0
     snapshots: int = 0
     iterates: dict = field(default_factory=dict)     # k -> x_k (after iteration k-1)
+    snapshot_iters: list = field(default_factory=list)   # iterations k at which x~ was taken
     objective: dict = field(default_factory=dict)    # k -> F at the last prox output
     draws: tuple = ()
     last_prox: np.ndarray | None = None
@@ -110,8 +111,11 @@ class Trace:
 
 def run(op: Operator, b, alpha: float, algo: str, gamma: float, iters: int, fgp_iters: int,
         p: float = 1.0, seed: int = 0, estimator: str = "SVRG", nonneg: bool = True,
-        x0=None, job: int = 0, keep=(), eval_every: int = 0) -> Trace:
-    """Run `iters` outer iterations of the chosen member of Algorithm 1's family."""
+        x0=None, job: int = 0, keep=(), eval_every: int = 0, draws=None) -> Trace:
+    """Run `iters` outer iterations of the chosen member of Algorithm 1's family.
+
+    draws: optional (i_k, theta_k, coin_k) arrays of at least `iters` entries that replace
+    the Philox schedule (used by tests to drive a run along chosen draws)."""
     algo = algo.upper()
     if algo not in ALGOS:
         raise ValueError(algo)
@@ -125,7 +129,10 @@ def run(op: Operator, b, alpha: float, algo: str, gamma: float, iters: int, fgp_
     x = np.zeros(op.shape) if x0 is None else np.asarray(x0, dtype=np.float64).reshape(op.shape).copy()
     h = np.zeros(op.shape)
     dual = np.zeros(len(op.shape) * x.size)
-    i_k, theta_k, coin_k = philox.schedule(seed, iters, N, p, job)
+    if draws is None:
+        i_k, theta_k, coin_k = philox.schedule(seed, iters, N, p, job)
+    else:
+        i_k, theta_k, coin_k = (np.asarray(d) for d in draws)
     tr = Trace(x=x, h=h, dual=dual, draws=(i_k, theta_k, coin_k))
 
     def prox(v, scale):
@@ -161,6 +168,7 @@ def run(op: Operator, b, alpha: float, algo: str, gamma: float, iters: int, fgp_
                 x_snap = x.copy()
                 g_snap = grad_f(op, b, x_snap)
                 tr.snapshots += 1
+                tr.snapshot_iters.append(k)
             G = N * (grad_fi(op, b, x, i) - grad_fi(op, b, x_snap, i)) + g_snap
         # ---- update
         if algo == "FISTA":
