@@ -145,6 +145,15 @@ int vrps_launch_shape_full(const vrps_geom* g, int* out3);
  * Ray-driven gather; no atomics.  Errors: INVALID_ARG (NULL, subset out of range). */
 int vrps_proj_fwd(const vrps_geom* g, int subset, const float* x, float* y, vrps_stream_t stream);
 
+/* Synchronises `stream`, then reads and clears the handle's device error word: returns
+ * VRPS_ERR_TIMEOUT when a bounded device-side wait of an earlier call on this handle expired
+ * since the last check (the 2D forward projector waits, with an iteration limit, for its
+ * bulk copies; an expired wait leaves that projection incomplete), VRPS_OK otherwise.
+ * vrps_solve, vrps_power_iteration and vrps_objective check the word themselves; callers of
+ * the asynchronous vrps_proj_fwd / vrps_proj_adj / vrps_prox_tv check it with this call.
+ * No counterpart in the paper.  Errors: INVALID_ARG, CUDA, TIMEOUT. */
+int vrps_check_error(const vrps_geom* g, vrps_stream_t stream);
+
 /* x = A_i^T r, the exact transpose of vrps_proj_fwd for the same subset, computed
  * pixel (voxel) by pixel as a gather over the rays that touch it; no atomics.
  * r: [rows(i) * row_len]; x: [n], overwritten.  Errors as vrps_proj_fwd. */
@@ -167,13 +176,16 @@ int vrps_prox_tv(const vrps_geom* g, const float* v, float* x, float tau, int it
  * Same operation and arguments as vrps_prox_tv on an nx x ny image (v, x: [nx*ny], dual:
  * NULL or [2*nx*ny], caller-owned device buffers), but no geometry handle and no
  * allocation: the scratch lives in a fixed array in device global memory of
- * VRPS_NOALLOC_MAX_PIXELS x 10 floats (about 10 MB), which every GPU that calls this keeps
- * until the process exits.  nx*ny above VRPS_NOALLOC_MAX_PIXELS is rejected with
- * INVALID_ARG.  The first call on each device looks up the array's device address (with
- * that device current) and caches it; make that first call before any stream capture.
- * All calls share the array, which keeps the last call's contents (a cold start clears
- * its dual): calls that overlap on the GPU -- on different streams, or from different host
- * threads -- race with each other and must be serialised by the caller. */
+ * VRPS_NOALLOC_MAX_PIXELS x 10 floats (about 10 MB).  With CUDA's default lazy module loading
+ * a GPU reserves that array when this entry point first runs on it (with
+ * CUDA_MODULE_LOADING=EAGER, every GPU that loads the library reserves it) and keeps it until
+ * the process exits.  nx*ny above VRPS_NOALLOC_MAX_PIXELS is rejected with INVALID_ARG.
+ * The first call on each device looks up the array's device address (with that device
+ * current) and caches it for the process; make that first call before any stream capture,
+ * and do not use the entry point on a device after cudaDeviceReset (the cached address would
+ * be stale).  All calls share the array, which keeps the last call's contents (a cold start
+ * clears its dual): calls that overlap on the GPU -- on different streams, or from different
+ * host threads -- race with each other and must be serialised by the caller. */
 #define VRPS_NOALLOC_MAX_PIXELS (512 * 512)
 int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, float tau, int iters, int nonneg,
                            float* dual, vrps_stream_t stream);

@@ -93,6 +93,7 @@ def _load():
         "vrps_prox_tv2d_noalloc": (i, [i, i, vp, vp, ctypes.c_float, i, i, vp, vp]),
         "vrps_power_iteration": (i, [vp, i, u64, P(d), vp]),
         "vrps_objective": (i, [vp, vp, vp, d, P(d), vp]),
+        "vrps_check_error": (i, [vp, vp]),
         "vrps_philox_schedule": (i, [u64, u32, i64, i, i, d, vp, vp]),
         "vrps_launch_shape_full": (i, [vp, P(i)]),
         "vrps_solve_opts_default": (None, [P(SolveOpts)]),
@@ -330,6 +331,12 @@ def objective(g: Geometry, x: torch.Tensor, b: torch.Tensor, alpha: float, strea
     _check(lib.vrps_objective(g.handle, _dev_ptr(x, "x", g.n), _dev_ptr(b, "b", g.m), float(alpha), out,
                               _stream(stream)))
     return out[0], out[1], out[2]
+
+
+def check_error(g: Geometry, stream=None):
+    """vrps_check_error: synchronises the stream; raises VrpsError (TIMEOUT) when a bounded
+    device-side wait of an earlier call on this geometry had expired."""
+    _check(lib.vrps_check_error(g.handle, _stream(stream)))
 
 
 def philox_schedule(seed: int, job: int, k0: int, count: int, n_subsets: int, p: float, stream=None):

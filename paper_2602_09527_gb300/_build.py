@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libvrps.so")
-SOURCES = ["api.cu", "joseph2d.cu", "joseph3d.cu", "fgp.cu", "reduce.cu", "solver.cu", "batch.cu", "pdhg.cu"]
+SOURCES = ["api.cu", "joseph2d.cu", "joseph3d.cu", "fgp.cu", "fgp_noalloc.cu", "reduce.cu", "solver.cu", "batch.cu",
+           "pdhg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I" + INCLUDE, "-I" + CSRC]

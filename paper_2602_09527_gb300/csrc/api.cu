@@ -310,6 +310,16 @@ static int fgp_dual_size(const vrps_geom* g, size_t* count) {
   return VRPS_OK;
 }
 
+int take_device_error(vrps_geom* g) {
+  Workspace& w = g->ws;
+  if (!w.dev_error) return VRPS_OK;
+  unsigned err = 0;
+  VRPS_CUDA(cudaMemcpy(&err, w.dev_error, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (!err) return VRPS_OK;
+  VRPS_CUDA(cudaMemset(w.dev_error, 0, sizeof(unsigned)));
+  return fail(VRPS_ERR_TIMEOUT, "a bounded device-side wait expired (error word %u)", err);
+}
+
 }  // namespace vrps
 
 using namespace vrps;
@@ -867,6 +877,7 @@ int vrps_power_iteration(const vrps_geom* g, int iters, uint64_t seed, double* L
   double lam = 0.0;
   VRPS_CUDA(cudaMemcpyAsync(&lam, w.scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   VRPS_CUDA(cudaStreamSynchronize(s));
+  VRPS_TRY(take_device_error(gm));
   *L_out = lam;
   return VRPS_OK;
 }
@@ -886,10 +897,17 @@ int vrps_objective(const vrps_geom* g, const float* x, const float* b, double al
   double h[2];
   VRPS_CUDA(cudaMemcpyAsync(h, w.scalars + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   VRPS_CUDA(cudaStreamSynchronize(s));
+  VRPS_TRY(take_device_error(gm));
   out3[1] = 0.5 * h[0];
   out3[2] = h[1];
   out3[0] = out3[1] + alpha * out3[2];
   return VRPS_OK;
+}
+
+int vrps_check_error(const vrps_geom* g, vrps_stream_t stream) {
+  VRPS_TRY(check_geom(g));
+  VRPS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return take_device_error(const_cast<vrps_geom*>(g));
 }
 
 int vrps_philox_schedule(uint64_t seed, uint32_t job, int64_t k0, int count, int n_subsets, double p,

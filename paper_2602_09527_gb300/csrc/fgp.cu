@@ -529,6 +529,59 @@ int fgp_prepare(vrps_geom* g) {
   return VRPS_OK;
 }
 
+int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int nx, int ny, float tau, int iters,
+                  int nonneg, int tile, cudaStream_t s, const float** w_final) {
+  // blocks of FB_T iterations; the (w, z) state alternates between pairs[0] and pairs[1].  The
+  // first block starts from z = w0 (iteration 0 does not extrapolate).
+  const float step = (float)(1.0 / (8.0 * (double)tau));
+  const float* rw = w0;
+  const float* rz = w0;
+  int which = 0;
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLarge>, TileLarge::SMEM));
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileWide>, TileWide::SMEM));
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileSmall>, TileSmall::SMEM));
+  const std::vector<MomBlock> moms = fgp_momentum(iters);
+  const double n = (double)nx * ny;
+  for (int k0 = 0; k0 < iters; k0 += FB_T) {
+    const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
+    const MomBlock& mb = moms[k0 / FB_T];
+    float* wn = pairs[which][0];
+    float* zn = pairs[which][1];
+    {
+      // read v, w and z (one array when z = w), write w and z
+      LaunchScope _ls("fgp2d_block", s, 4.0 * n * (rz == rw ? 7 : 9));
+      const FgpBlockArgs A{v, rw, rz, wn, zn, nx, ny, tau, step, mb, ns, nonneg};
+      auto launch = [&](auto kern, auto tl) -> cudaError_t {
+        using TL = decltype(tl);
+        dim3 grid((nx + TL::TX - 1) / TL::TX, (ny + TL::TY - 1) / TL::TY);
+        return launch_kernel(kern, grid, dim3(TL::NT), (size_t)TL::SMEM, s, A);
+      };
+      if (tile == 1) VRPS_CUDA(launch(fgp2d_block<TileWide>, TileWide{}));
+      else if (tile == 2) VRPS_CUDA(launch(fgp2d_block<TileSmall>, TileSmall{}));
+      else VRPS_CUDA(launch(fgp2d_block<TileLarge>, TileLarge{}));
+    }
+    VRPS_LAUNCHED("fgp2d_block");
+    rw = wn;
+    rz = zn;
+    which ^= 1;
+  }
+  *w_final = rw;
+  return VRPS_OK;
+}
+
+int fgp2d_output(const float* v, const float* w, float* wdst, int nx, int ny, float tau, int nonneg,
+                 const ProxTail& t, cudaStream_t s) {
+  dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
+  {
+    const double n = (double)nx * ny;
+    LaunchScope _ls("fgp2d_out", s, 4.0 * n * (wdst ? 5 : 3) + tail_bytes(t, (size_t)nx * ny));
+    const FgpOutArgs A{v, w, wdst, nx, ny, tau, nonneg, t};
+    VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, A));
+  }
+  VRPS_LAUNCHED("fgp_out");
+  return VRPS_OK;
+}
+
 int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg, float* dual,
             const ProxTail& tail, cudaStream_t s) {
   vrps_geom* gm = const_cast<vrps_geom*>(g);
@@ -538,42 +591,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   const float step = (float)(1.0 / (4.0 * g->dims * (double)tau));
   const float* w_final = dual;
   if (g->dims == 2) {
-    // blocks of FB_T iterations; state (w, z) pairs alternate (s1,s2) <-> (s3,s4).  The
-    // first block starts from z = w (iteration 0 does not extrapolate).
-    const float* rw = dual;
-    const float* rz = dual;
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
-    int which = 0;
-    const int tile = g->tune_fgp_tile;   // 0 large, 1 wide, 2 small
-    VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLarge>, TileLarge::SMEM));
-    VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileWide>, TileWide::SMEM));
-    VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileSmall>, TileSmall::SMEM));
-    const std::vector<MomBlock> moms = fgp_momentum(iters);
-    for (int k0 = 0; k0 < iters; k0 += FB_T) {
-      const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
-      const MomBlock& mb = moms[k0 / FB_T];
-      float* wn = pairs[which][0];
-      float* zn = pairs[which][1];
-      {
-        // read v, w and z (one array when z = w), write w and z
-        LaunchScope _ls("fgp2d_block", s, 4.0 * g->n * (rz == rw ? 7 : 9));
-        const FgpBlockArgs A{v, rw, rz, wn, zn, g->nx, g->ny, tau, step, mb, ns, nonneg};
-        auto launch = [&](auto kern, auto tl) -> cudaError_t {
-          using TL = decltype(tl);
-          dim3 grid((g->nx + TL::TX - 1) / TL::TX, (g->ny + TL::TY - 1) / TL::TY);
-          return launch_kernel(kern, grid, dim3(TL::NT), (size_t)TL::SMEM, s, A);
-        };
-        if (tile == 1) VRPS_CUDA(launch(fgp2d_block<TileWide>, TileWide{}));
-        else if (tile == 2) VRPS_CUDA(launch(fgp2d_block<TileSmall>, TileSmall{}));
-        else VRPS_CUDA(launch(fgp2d_block<TileLarge>, TileLarge{}));
-      }
-      VRPS_LAUNCHED("fgp2d_block");
-      rw = wn;
-      rz = zn;
-      which ^= 1;
-    }
-    const float* rc = rw;
-    w_final = rc;
+    VRPS_TRY(fgp2d_iterate(v, dual, pairs, g->nx, g->ny, tau, iters, nonneg, g->tune_fgp_tile, s, &w_final));
   } else {
     float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};
     const Fgp3Schedule sch = fgp3_schedule(iters);
@@ -594,12 +613,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   }
   float* wdst = (w_final != dual) ? dual : nullptr;
   if (g->dims == 2) {
-    dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32), block(32, 8);
-    {
-      LaunchScope _ls("fgp2d_out", s, 4.0 * g->n * (wdst ? 5 : 3) + tail_bytes(tail, (size_t)g->n));
-      const FgpOutArgs A{v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail};
-      VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, A));
-    }
+    VRPS_TRY(fgp2d_output(v, w_final, wdst, g->nx, g->ny, tau, nonneg, tail, s));
+    return VRPS_OK;
   } else {
     Dims3 D{g->nx, g->ny, g->nz, (size_t)g->n};
     dim3 grid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), block(32, 8);
@@ -842,115 +857,3 @@ int batched_grid_3d(int which, int* grid) {
 }
 
 }  // namespace vrps
-
-// ---------------------------------------------------------------- allocation-free 2D prox
-// Some callers cannot let this library call cudaMalloc: an application that owns the whole
-// device-memory budget through its own pool, or a latency-critical loop in which the implicit
-// device synchronisation of an allocation is not acceptable.  vrps_prox_tv2d_noalloc serves
-// them with scratch held in a fixed array in device global memory instead of allocations.
-// The array belongs to the loaded library: every GPU that uses the entry point keeps it until
-// the process exits, and every call shares it.
-namespace vrps {
-namespace {
-
-constexpr long long NOALLOC_MAX_PIXELS = 512LL * 512LL;   // VRPS_NOALLOC_MAX_PIXELS
-// five dual-sized regions of 2 * NOALLOC_MAX_PIXELS floats: cold-start dual + four rotation
-// buffers of the temporally blocked iterations
-__device__ __align__(256) float g_noalloc_scratch[5 * 2 * NOALLOC_MAX_PIXELS];
-
-constexpr int NOALLOC_MAX_DEVICES = 64;
-float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
-std::mutex g_noalloc_mu;
-
-// Device address of the scratch array on the current device.  In host code the array's name
-// only stands for a host-side shadow, so the address is looked up once per device (with that
-// device current) and cached.
-int noalloc_scratch(int dev, float** out) {
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(VRPS_ERR_UNSUPPORTED, "device index %d too large", dev);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
-    g_noalloc_ptr[dev] = static_cast<float*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
-  return VRPS_OK;
-}
-
-}  // namespace
-}  // namespace vrps
-
-extern "C" int vrps_prox_tv2d_noalloc(int nx, int ny, const float* v, float* x, float tau, int iters, int nonneg,
-                                      float* dual, vrps_stream_t stream) {
-  using namespace vrps;
-  if (nx <= 0 || ny <= 0) return fail(VRPS_ERR_INVALID_ARG, "sizes must be positive (nx=%d ny=%d)", nx, ny);
-  if ((long long)nx * ny > NOALLOC_MAX_PIXELS)
-    return fail(VRPS_ERR_INVALID_ARG, "nx*ny = %lld exceeds the fixed scratch capacity of %lld pixels",
-                (long long)nx * ny, NOALLOC_MAX_PIXELS);
-  if (!v || !x) return fail(VRPS_ERR_INVALID_ARG, "v or x is NULL");
-  if (v == x) return fail(VRPS_ERR_INVALID_ARG, "v and x must not alias");
-  if (!(tau > 0.f) || !std::isfinite(tau)) return fail(VRPS_ERR_INVALID_ARG, "tau must be > 0");
-  if (iters < 0) return fail(VRPS_ERR_INVALID_ARG, "iters must be >= 0");
-  int dev = -1;
-  VRPS_CUDA(cudaGetDevice(&dev));
-  float* base = nullptr;
-  VRPS_TRY(noalloc_scratch(dev, &base));
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = (size_t)nx * ny, dn = 2 * n;
-  const size_t cap = 2 * (size_t)NOALLOC_MAX_PIXELS;
-  float* cold = base;
-  float* pairs[2][2] = {{base + cap, base + 2 * cap}, {base + 3 * cap, base + 4 * cap}};
-  float* d = dual;
-  if (!d) {
-    // the shared array keeps the previous call's contents: a cold start clears its dual
-    VRPS_CUDA(cudaMemsetAsync(cold, 0, dn * sizeof(float), s));
-    d = cold;
-  }
-  const float step = (float)(1.0 / (8.0 * (double)tau));
-  VRPS_CUDA(cudaFuncSetAttribute(fgp2d_block<TileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)TileLarge::SMEM));
-  // FGP momentum t_0 = 1, t_{k+1} = (1+sqrt(1+4 t_k^2))/2; the z formed after iteration k
-  // uses (t_k - 1)/t_{k+1}
-  double t_cur = 1.0;
-  const float* rw = d;
-  const float* rz = d;
-  int which = 0;
-  for (int k0 = 0; k0 < iters; k0 += FB_T) {
-    const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
-    MomBlock mb;
-    for (int q = 0; q <= FB_T; ++q) {
-      mb.c[q] = 0.f;
-      if (q < ns) {
-        const double t_next = (1.0 + std::sqrt(1.0 + 4.0 * t_cur * t_cur)) / 2.0;
-        if (k0 + q + 1 < iters) mb.c[q] = (float)((t_cur - 1.0) / t_next);
-        t_cur = t_next;
-      }
-    }
-    float* wn = pairs[which][0];
-    float* zn = pairs[which][1];
-    {
-      LaunchScope _ls("fgp2d_block", s, 4.0 * nx * ny * (rz == rw ? 7 : 9));
-      dim3 grid((nx + TileLarge::TX - 1) / TileLarge::TX, (ny + TileLarge::TY - 1) / TileLarge::TY);
-      const FgpBlockArgs A{v, rw, rz, wn, zn, nx, ny, tau, step, mb, ns, nonneg ? 1 : 0};
-      VRPS_CUDA(launch_kernel(fgp2d_block<TileLarge>, dim3(grid), dim3(TileLarge::NT), (size_t)(TileLarge::SMEM), s, A));
-    }
-    VRPS_LAUNCHED("fgp2d_block");
-    rw = wn;
-    rz = zn;
-    which ^= 1;
-  }
-  ProxTail t;
-  std::memset(&t, 0, sizeof(t));
-  t.mode = 0;
-  t.out = x;
-  float* wdst = (rw != d && dual) ? dual : nullptr;
-  {
-    dim3 grid((nx + 31) / 32, (ny + 31) / 32), block(32, 8);
-    LaunchScope _ls("fgp2d_out", s, 4.0 * nx * ny * (wdst ? 5 : 3) + tail_bytes(t, (size_t)nx * ny));
-    const FgpOutArgs A{v, rw, wdst, nx, ny, tau, nonneg ? 1 : 0, t};
-    VRPS_CUDA(launch_kernel(fgp2d_out, dim3(grid), dim3(block), (size_t)(0), s, A));
-  }
-  VRPS_LAUNCHED("fgp2d_out");
-  return VRPS_OK;
-}

@@ -397,13 +397,9 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
     VRPS_CUDA(cudaMemcpyAsync(x_out, x, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s));
   }
   VRPS_CUDA(cudaStreamSynchronize(s));
-  if (w.dev_error) {
-    unsigned err = 0;
-    VRPS_CUDA(cudaMemcpy(&err, w.dev_error, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (err) {
-      VRPS_CUDA(cudaMemset(w.dev_error, 0, sizeof(unsigned)));
-      status = fail(VRPS_ERR_TIMEOUT, "a bounded device-side wait expired (error word %u)", err);
-    }
+  {
+    const int e = take_device_error(g);
+    if (e != VRPS_OK) status = e;
   }
   if (rep) *rep = r;
   return status;

@@ -71,6 +71,9 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
 // Opt a kernel into `bytes` of dynamic shared memory on the current device (cached: the
 // runtime call is made once per kernel, device and size).
 int smem_opt_in(const void* kern, size_t bytes);
+// Reads and clears the handle's device error word (the caller has synchronised the work that
+// could set it); VRPS_ERR_TIMEOUT when a bounded device-side wait had expired.
+int take_device_error(vrps_geom* g);
 
 // ------------------------------------------------------------------ geometry tables
 // Per-angle constants of the 2D Joseph projector, derived in float64 on the host.
@@ -476,6 +479,14 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
             const ProxTail& tail, cudaStream_t s);
 // Momentum coefficients of the blocked 2D FGP launches of one prox call (t restarts at 1).
 std::vector<MomBlock> fgp_momentum(int iters);
+// 2D: `iters` FGP iterations from the dual w0 ([2][nx*ny]) in blocked launches whose (w, z)
+// state alternates between the buffer pairs pairs[0] and pairs[1] (each [2][nx*ny]); *w_final
+// receives the buffer holding w_K (w0 itself when iters = 0).  tile: 0 32x32, 1 32x16, 2 16x16.
+int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int nx, int ny, float tau, int iters,
+                  int nonneg, int tile, cudaStream_t s, const float** w_final);
+// 2D: x+ = P_+(v + tau div w) with the fused tail t; wdst (nullable) receives a copy of w.
+int fgp2d_output(const float* v, const float* w, float* wdst, int nx, int ny, float tau, int nonneg,
+                 const ProxTail& t, cudaStream_t s);
 // Allocates the dual rotation buffers of the geometry's prox.
 int fgp_prepare(vrps_geom* g);
 

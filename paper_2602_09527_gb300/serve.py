@@ -1,9 +1,12 @@
 """Request loop over the batched engine (vrps_batch_*): continuous batching of reconstruction
 jobs with admission by device-memory footprint.
 
-Requests wait in arrival order.  Before every group of ticks the loop admits waiting
-requests while a geometry handle of their size is free and the admitted jobs' state fits the
-memory budget; admitted jobs join the running batch at the next tick, and a job's handle and
+Requests wait in arrival order.  Before every group of ticks the loop scans the waiting
+requests in that order and admits each one whose geometry class has a free handle and whose
+state fits the memory budget.  A request waiting for a handle of its own class does not hold
+up requests of other classes behind it (handles are per class); a request waiting for memory
+does (memory is shared: admitting later, smaller jobs past it could starve it), so the scan
+stops there.  Admitted jobs join the running batch at the next tick, and a job's handle and
 memory are released as soon as its last iteration has finished on the device.  All device
 work (job setup, every tick, the result copy) happens in the library; this module only
 schedules.
@@ -11,7 +14,6 @@ schedules.
 from __future__ import annotations
 
 import time
-from collections import deque
 from dataclasses import dataclass, field
 
 import torch
@@ -67,14 +69,16 @@ class BatchServer:
         self.running = {}            # job id -> (request, geometry, bytes)
         self.used = 0
 
-    def _try_admit(self, r: Request, now: float) -> bool:
+    ADMITTED, NO_HANDLE, NO_MEMORY = 0, 1, 2
+
+    def _try_admit(self, r: Request, now: float) -> int:
         pool = self.free.get(r.key)
         if not pool:
-            return False
+            return self.NO_HANDLE
         g = pool[-1]
         need = vb.job_footprint(g, max_iters=r.max_iters, storage=r.storage)
         if self.running and self.used + need > self.budget:
-            return False
+            return self.NO_MEMORY
         pool.pop()
         r.x = torch.empty(g.n, device=r.b.device, dtype=torch.float32)
         jid = self.batch.submit(g, r.b, alpha=r.alpha, p=r.p, gamma=r.gamma, seed=r.seed, estimator=r.estimator,
@@ -83,13 +87,26 @@ class BatchServer:
         r.admitted = now
         self.running[jid] = (r, g, need)
         self.used += need
-        return True
+        return self.ADMITTED
+
+    def _admit_waiting(self, waiting: list, now: float):
+        """Admits waiting requests in arrival order: past requests whose class has no free
+        handle, up to the first that does not fit the memory budget."""
+        keep = []
+        for q, r in enumerate(waiting):
+            got = self._try_admit(r, now)
+            if got == self.NO_MEMORY:
+                keep.extend(waiting[q:])
+                break
+            if got == self.NO_HANDLE:
+                keep.append(r)
+        waiting[:] = keep
 
     def run(self, requests: list, clock=time.perf_counter, t0: float | None = None) -> ServerStats:
         """Serves `requests` (sorted by arrival) in real time; returns latency statistics.
         t0: the clock reading that arrival times count from (default: now)."""
         st = ServerStats()
-        waiting = deque()
+        waiting = []
         i = 0
         t0 = clock() if t0 is None else t0
         while i < len(requests) or waiting or self.running:
@@ -97,8 +114,8 @@ class BatchServer:
             while i < len(requests) and requests[i].arrival <= now:
                 waiting.append(requests[i])
                 i += 1
-            while waiting and self._try_admit(waiting[0], now):
-                waiting.popleft()
+            if waiting:
+                self._admit_waiting(waiting, now)
             st.peak_jobs = max(st.peak_jobs, len(self.running))
             st.peak_bytes = max(st.peak_bytes, self.used)
             if self.running:

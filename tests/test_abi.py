@@ -84,3 +84,8 @@ def test_null_handles_rejected(lib):
                                          ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.vrps_philox_schedule(1, 0, 0, -1, 4, 0.5, None, None) == -1
     assert lib.vrps_geom_free(None) == 0
+
+
+def test_check_error_rejects_null_handle(lib):
+    lib.vrps_check_error.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.vrps_check_error(None, None) == -1

@@ -108,6 +108,16 @@ def test_degenerate_sizes():
         assert np.max(np.abs(a - ref.ravel())) < 1e-5 * max(1.0, np.abs(ref).max())
 
 
+def test_check_error_clear_after_projections():
+    """The forward's bounded bulk-copy waits never expire in normal work: after projections of
+    every subset the handle's device error word reads clear (vrps_check_error)."""
+    vr, g, og = _pair("par2d_64")
+    x = dev(np.random.default_rng(3).uniform(size=(og.ny, og.nx)))
+    for i in list(range(og.n_subsets)) + [-1]:
+        vr.proj_fwd(g, i, x)
+    vr.check_error(g)
+
+
 def test_bad_subset_raises():
     vr, g, og = _pair("par2d_64")
     x = torch.zeros(og.n, device="cuda")

@@ -82,9 +82,10 @@ def test_admission_by_footprint_and_handles(fake_engine):
     assert st.peak_bytes <= 300
     assert _FakeBatch.live[0].running_max <= 3
     assert all(r.admitted is not None and r.finished >= r.admitted for r in reqs)
-    # arrival order: a request is never admitted before an earlier one
-    adm = [r.admitted for r in reqs]
-    assert adm == sorted(adm)
+    # arrival order within a class: a request is never admitted before an earlier one of its class
+    for key in ("a", "b"):
+        adm = [r.admitted for r in reqs if r.key == key]
+        assert adm == sorted(adm)
     assert srv.used == 0 and len(srv.free["a"]) == 3 and len(srv.free["b"]) == 1
 
 
@@ -108,3 +109,43 @@ def test_mixed_server_splits_and_merges(fake_engine):
     assert len(_FakeBatch.live) == 2
     assert sum(b.next_id for b in _FakeBatch.live) == 5
     assert all(r.finished is not None for r in reqs)
+
+
+class _Clock:
+    """Deterministic clock: every reading advances time by `dt` seconds."""
+
+    def __init__(self, dt=0.001):
+        self.t, self.dt = 0.0, dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+def test_later_request_of_free_class_admitted_past_blocked_head(fake_engine):
+    """The head request waits for a handle of its class (the only one is busy); a later request
+    of another class with a free handle and room in the budget is admitted at once instead of
+    queueing behind it."""
+    torch = fake_engine
+    pools = {"big": [_G(4, 100)], "small": [_G(4, 10)]}
+    srv = serve.BatchServer(pools, budget_bytes=1000, ticks_per_step=1)
+    reqs = _reqs(torch, ["big", "big", "small"], [50, 5, 3])
+    st = srv.run(reqs, clock=_Clock())
+    assert st.completed == 3
+    first_big, second_big, small = reqs
+    assert small.admitted < second_big.admitted          # went past the blocked head
+    assert small.finished < first_big.finished
+    assert second_big.admitted >= first_big.finished      # waited for the class's only handle
+
+
+def test_request_waiting_for_memory_holds_later_ones(fake_engine):
+    """Memory is shared: a request that does not fit the budget is not overtaken (no starvation
+    of large jobs by a stream of small ones)."""
+    torch = fake_engine
+    pools = {"big": [_G(4, 600), _G(4, 600)], "small": [_G(4, 10), _G(4, 10)]}
+    srv = serve.BatchServer(pools, budget_bytes=1000, ticks_per_step=1)
+    reqs = _reqs(torch, ["big", "big", "small"], [20, 5, 3])
+    st = srv.run(reqs, clock=_Clock())
+    assert st.completed == 3
+    _, second_big, small = reqs
+    assert small.admitted >= second_big.admitted
