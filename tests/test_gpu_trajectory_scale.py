@@ -8,9 +8,12 @@ same Philox draws (subset i_k, skip coin theta_k), in the launch shapes the benc
   pitch 4, SOD 500, SDD 1000, 30 subsets, Gaussian 1 %): ProxSVRGSkip p = 0.1, 50 3D FGP
   iterations, one epoch (30 iterations).  Iterates within 1e-4.
 * One size class of the batched workload (256^2, 384 angles, 384 bins, 20 subsets, Gaussian 1 %,
-  TV weight 0.02 on a unit-radius field of view): ProxSAGASkip p = 0.1 with sinogram and SAGA
-  table stored in bfloat16 (and float16), three epochs, the last one in float32 after an exact
-  full gradient.  Objective within 1e-3 relative of the oracle's.
+  TV weight 0.02 on a unit-radius field of view): ProxSAGASkip p = 0.1 run to just after its
+  ninth prox step (46 iterations).  Float32 storage: iterates within 1e-4.  Sinogram and SAGA
+  table stored in bfloat16 (and float16): the objective of that prox output within 1e-3
+  relative of the oracle's.  (The float32 correction epoch that ends a reduced-storage run
+  rebuilds the SAGA table at the current point, so after it the trajectory is a different one
+  by design; the correction is checked at convergence on the 64^2 problem.)
 
 The step is 1 / L_up with L_up = max row sum x max column sum of A (Schur's bound on ||A||_2^2,
 computed by the oracle from A 1 and A^T 1), so that no input comes from the CUDA path."""
@@ -86,22 +89,30 @@ def c4_class():
     g = vr.Geometry.from_spec(P.spec)
     op = solvers.Operator(joseph2d.Geometry2D.from_spec(P.spec))
     gamma = 1.0 / (3.0 * _schur_bound(op))
-    K = 60
+    K = 46                                # prox steps at k = 6, 17, 19, 22, 24, 32, 35, 44, 45
     ref = solvers.run(op, P.b, P.alpha, "VR_PROXSKIP", gamma, K, 50, p=0.1, seed=SEED + 1, estimator="SAGA")
+    assert ref.prox_calls == 9 and np.array_equal(ref.x, ref.last_prox)
     Fr = solvers.objective(op, P.b, ref.x, P.alpha)
     return vr, P, g, op, gamma, K, ref, Fr
+
+
+def _saga(c, **kw):
+    vr, P, g, op, gamma, K, ref, Fr = c
+    x, rep, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", p=0.1, gamma=gamma, seed=SEED + 1, estimator="SAGA",
+                         fgp_iters=50, max_iters=K, **kw)
+    assert rep["prox_calls"] == ref.prox_calls
+    return x
+
+
+def test_batched_size_class_fp32_saga_trajectory(c4_class):
+    x = _saga(c4_class)
+    err = rel(host(x), c4_class[6].x)
+    assert err < TOL_X, err
 
 
 @pytest.mark.parametrize("storage", ["BF16", "FP16"])
 def test_batched_size_class_reduced_storage_saga(c4_class, storage):
     vr, P, g, op, gamma, K, ref, Fr = c4_class
-    assert ref.prox_calls == 9
-    x, rep, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", p=0.1, gamma=gamma, seed=SEED + 1,
-                         estimator="SAGA", fgp_iters=50, max_iters=K, storage=storage, correction_epochs=1)
+    x = _saga(c4_class, storage=storage)
     F = solvers.objective(op, P.b, host(x), P.alpha)
     assert abs(F - Fr) / Fr < TOL_F, (storage, F, Fr)
-    assert rep["prox_calls"] == ref.prox_calls
-    # float32 storage on the same draws follows the float64 trajectory to 1e-4
-    x32, _, _ = vr.solve(dev(P.b), g, P.alpha, "VR_PROXSKIP", p=0.1, gamma=gamma, seed=SEED + 1,
-                         estimator="SAGA", fgp_iters=50, max_iters=K)
-    assert rel(host(x32), ref.x) < TOL_X
