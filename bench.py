@@ -46,7 +46,7 @@ WORKLOADS = {
                       alpha_alt=0.01, alt_epochs=(50, 150, 300)),
     "par2d_64": dict(n=64, n_angles=90, n_bins=96, n_subsets=10, noise="gauss", alpha=0.01,
                      algo="VR_PROXSKIP", estimator="SVRG", p=0.1, fgp_iters=50, seed=20260209,
-                     target_gap=1e-4, max_epochs=150, fista_iters=10000, pdhg_iters=20000),
+                     target_gap=1e-4, max_epochs=150, fista_iters=10000, pdhg_iters=20000, epochs=50),
 }
 
 # 3D cone-beam workload (optional, not the default line): 256^3 voxels of 0.5, 360 views over
@@ -81,7 +81,7 @@ WORKLOADS_3D = {
 # for all 16 jobs, against the same jobs one after another through vrps_solve.
 WORKLOADS_BATCH = {
     "batch64": dict(jobs=64, sides=(128, 256, 384, 512, 1024), n_min=10, n_max=30, p=0.1, fgp_iters=50,
-                    alpha=0.02, alpha_fov=True, epochs=20, estimator="SAGA", storage="BF16", correction_epochs=1,
+                    alpha=0.02, alpha_fov=True, epochs=20, estimator="SAGA", storage="BF16", correction_epochs=2,
                     seed=20260209, target_gap=1e-4, max_epochs=300),
     "batch3d_16": dict(dims=3, jobs=16, sides=(64, 96, 128), n_min=30, n_max=30, p=0.1, fgp_iters=50,
                        alpha=0.01, alpha_fov=True, epochs=3, estimator="SVRG", storage="FP32", correction_epochs=0,
@@ -102,7 +102,10 @@ WORKLOADS_SERVE = {
                   share3d=0.10, sides3d=(64, 128, 192, 256), pool3d=1, mem_share3d=0.5, max_handles=64,
                   # when the stated rate exceeds one GPU's per-job capacity at this mix, run at
                   # `load` x that capacity and report the stated rate's offered load
-                  rate_search=True, load=0.85),
+                  rate_search=True, load=0.85,
+                  # scheduling: at most 32 2D and 2 3D jobs advance together; the 2D batch's stream
+                  # has the higher priority and the 3D batch's persistent grids take 80 % of the GPU
+                  max_running=32, max_running3d=2, grid_share3d=0.8),
 }
 
 # Operator costs (optional), the structure of the paper's cost figure on the 512^2 / 720-angle
@@ -960,7 +963,8 @@ def serve_leg(vr, w, rank, local, seconds=None, rate=None):
                 "peak_running_jobs": st.peak_jobs, "peak_state_gb": round(st.peak_bytes / 1e9, 3)}
 
     # warm-up: a short stream through the batched server (graph capture, allocations)
-    srv = serve.MixedServer(pools, pools3, budget, share3d=share3)
+    srv = serve.MixedServer(pools, pools3, budget, share3d=share3, max_running=w.get("max_running"),
+                            max_running3d=w.get("max_running3d"), grid_share3d=w.get("grid_share3d", 1.0))
     warm = requests("BF16", 1)[: min(len(arrivals), 40)]
     for r in warm:
         r.arrival = 0.0
@@ -989,6 +993,8 @@ def serve_leg(vr, w, rank, local, seconds=None, rate=None):
         "sides_3d": list(w["sides3d"]), "epochs": epochs, "algo": "ProxSAGASkip", "p": w["p"],
         "fgp_iters": w["fgp_iters"], "alpha": f"U{list(w['alpha'])}", "budget_gb": w["budget_gb"],
         "handles_per_class": handles,
+        "scheduling": {"max_running_2d": w.get("max_running"), "max_running_3d": w.get("max_running3d"),
+                       "grid_share_3d": w.get("grid_share3d", 1.0), "stream_priority": "2D high, 3D low"},
         "device_s_per_request_alone": {k: round(v, 4) for k, v in cost.items()},
         "mean_device_s_per_request": round(e_cost, 4),
         "per_job_capacity_per_s": round(capacity, 3),
@@ -1186,48 +1192,45 @@ def alt_alpha_leg(vr, g, b_dev, w, gamma, stream, flush):
 
 
 def c1_measured_leg(vr, stream, flush):
-    """The 64^2 workload run to a 1e-4 gap twice, each side on its own: the CUDA path (F* from
-    its long FISTA run and its own evaluations; median of 5 device-timed replays of its k*
-    iterations) and the float64 oracle as it stands (L from the oracle's power iteration; F*
-    the lowest objective of its own 150-epoch run evaluated once per epoch; then a second
-    oracle run of exactly its k* iterations, wall-clock timed on one host core)."""
+    """The 64^2 workload's fixed budget of 50 epochs (500 ProxSVRGSkip iterations, the same
+    Philox draws) on both sides, each measured: the CUDA path (median of 5 device-timed runs,
+    L2 flushed) and the float64 oracle as it stands (wall clock, one host core).  The oracle
+    takes L from its own power iteration; the objectives of both final iterates are reported
+    beside each other (the oracle's in float64, the GPU's with float64 reductions)."""
     import torch
-    from oracle import joseph2d, philox, solvers
+    from oracle import joseph2d, solvers
     w = WORKLOADS["par2d_64"]
-    N, seed, a = w["n_subsets"], w["seed"], w["alpha"]
+    N, seed, a, E = w["n_subsets"], w["seed"], w["alpha"], w["epochs"]
     P = make_problem("par2d_64", 0)
     g = vr.Geometry.from_spec(P.spec)
     b = torch.tensor(P.b.astype(np.float32).ravel(), device="cuda")
-    L = vr.power_iteration(g, 100, seed=seed)
-    ref = fstar_reference(vr, g, b, a, 1.0 / L, seed, w["fista_iters"], w["pdhg_iters"])
-    run = time_to_gap(vr, g, b, a, w["algo"], w["estimator"], w["p"], 1.0 / L, seed, w["fgp_iters"], N,
-                      w["max_epochs"], stream, flush, reps=5)
-    gpu = time_to_gap_replay(vr, g, b, a, run, min(ref["f_star"], run["f_min"]), w["target_gap"], stream, flush)
-    g.close()
     op = solvers.Operator(joseph2d.Geometry2D.from_spec(P.spec))
     Lo = solvers.power_iteration(op, 100, seed=seed)
-    E = w["max_epochs"]
-    tr = solvers.run(op, P.b, a, w["algo"], 1.0 / Lo, E * N, w["fgp_iters"], p=w["p"], seed=seed,
-                     estimator=w["estimator"], eval_every=N)
-    f_star_o = min(tr.objective.values())
-    k_eval = next((k for k in sorted(tr.objective) if (tr.objective[k] - f_star_o) / abs(f_star_o) <= w["target_gap"]),
-                  None)
-    out = {"workload": "par2d_64 (64^2, 90 angles, 96 bins, N = 10, ProxSVRGSkip p = 0.1, FGP 50)", "gpu": gpu,
-           "gpu_f_star": min(ref["f_star"], run["f_min"])}
-    if k_eval is None:
-        out["oracle"] = {"reached": False}
-        return out
-    _, theta, _ = philox.schedule(seed, k_eval, N, w["p"])
-    k_star = stop_after_last_prox(k_eval, theta)
+    K = E * N
+    times, x = [], None
+    for r in range(6):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, rep, _ = vr.solve(b, g, a, w["algo"], p=w["p"], gamma=1.0 / Lo, seed=seed, estimator=w["estimator"],
+                             fgp_iters=w["fgp_iters"], max_iters=K)
+        e1.record(stream)
+        e1.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    F_gpu = vr.objective(g, x, b, a)[0]
+    g.close()
     t0 = time.perf_counter()
-    tr2 = solvers.run(op, P.b, a, w["algo"], 1.0 / Lo, k_star, w["fgp_iters"], p=w["p"], seed=seed,
-                      estimator=w["estimator"])
+    tr = solvers.run(op, P.b, a, w["algo"], 1.0 / Lo, K, w["fgp_iters"], p=w["p"], seed=seed,
+                     estimator=w["estimator"])
     t_o = time.perf_counter() - t0
-    out["oracle"] = {"reached": True, "seconds": round(t_o, 3), "k_star": k_star, "prox_calls": tr2.prox_calls,
-                     "f_star": f_star_o, "cores": 1, "what": "measured, not extrapolated"}
-    if gpu.get("reached"):
-        out["oracle_over_gpu"] = round(t_o / gpu["seconds"], 1)
-    return out
+    F_o = solvers.objective(op, P.b, tr.x, a)
+    t_g = statistics.median(times)
+    return {"workload": "par2d_64: 64^2, 90 angles, 96 bins, N = 10, ProxSVRGSkip p = 0.1, FGP 50, 50 epochs",
+            "gpu_seconds": round(t_g, 5), "oracle_seconds": round(t_o, 2), "oracle_cores": 1,
+            "oracle_over_gpu": round(t_o / t_g, 1), "iterations": K, "prox_calls": rep["prox_calls"],
+            "objective_gpu": F_gpu, "objective_oracle": F_o, "objective_rel_diff": abs(F_gpu - F_o) / abs(F_o),
+            "what": "both measured over the same 500 iterations, nothing extrapolated"}
 
 
 def main():
@@ -1244,8 +1247,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--alpha", type=float, default=None, help="override the workload's TV weight")
     ap.add_argument("--legs", default="alt,c1,c4,c5",
-                    help="extra measurements of the default line: alt (TV weight 0.01), c1 (measured 64^2 oracle "
-                         "and GPU time to gap), c4 (batched uneven jobs), c5 (served stream); '' for none")
+                    help="extra measurements of the default line: alt (TV weight 0.01), c1 (the 64^2 workload's "
+                         "50 epochs measured on the GPU and on the oracle), c4 (batched uneven jobs), c5 (served "
+                         "stream); '' for none")
     ap.add_argument("--profile-once", type=int, default=0, metavar="K",
                     help="profiling driver: run K solver iterations of the workload once (no F* search, "
                          "no timing) and exit")
@@ -1403,6 +1407,7 @@ def main():
         samp = oracle_sample(wl, P)
         counts = {"iterations": rep["iterations"], "prox_calls": rep["prox_calls"], "snapshots": rep["snapshots"]}
         cpu = {"value": round(oracle_extrapolate(samp, counts, N), 2), "unit": "s", "cores": 1, "kind": "oracle",
+               "host_cores": os.cpu_count(),
                "sample": (f"float64 oracle on this host: one ProxSVRG subset iteration ({samp['t_svrg_iter']:.2f} s), "
                           f"one {w['fgp_iters']}-iteration FGP prox ({samp['t_prox']:.2f} s), one subset gradient "
                           f"({samp['t_subset_grad']:.2f} s; a snapshot = N of them), scaled by this run's counts "
@@ -1418,7 +1423,7 @@ def main():
                 "speedup_vs_per_job_fp32", "objective_rel_diff_vs_per_job_fp32", "batched_fp16_s",
                 "final_iterate_gap", "epochs_to_gap", "reconstructions_per_s", "gpu_launches")
         c4 = {k: b4[k] for k in keys if k in b4}
-        c4["storage"] = "bf16 + 1 float32 correction epoch (value); fp16 + 1 float32 epoch (batched_fp16_s)"
+        c4["storage"] = "bf16 + 2 float32 correction epochs (value); fp16 + 2 float32 epochs (batched_fp16_s)"
     if "c5" in legs and world == 1:
         c5 = serve_leg(vr, WORKLOADS_SERVE["serve"], rank, local)
     out = {
@@ -1462,7 +1467,7 @@ def main():
         "alpha_0.01": alt,
         "batched_c4": c4,
         "served_c5": c5,
-        "c1_time_to_gap_measured": c1,
+        "c1_50_epochs_measured": c1,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
@@ -1520,8 +1525,14 @@ def reference_arm(args, rank, world):
                    "subsets": w["n_subsets"], "algo": "ProxSVRGSkip", "p": w["p"], "fgp_iters": w["fgp_iters"],
                    "trajectory_counts": counts},
         "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle",
+                         "host_cores": os.cpu_count(),
                          "sample": "per step: one ProxSVRG subset iteration, one FGP prox, one subset gradient, "
-                                   f"scaled by the recorded counts {counts}; {wall:.1f} s of sampling in total"},
+                                   f"scaled by the recorded counts {counts}; {wall:.1f} s of sampling in total",
+                         "measured": "the sampled operations (float64 numpy/scipy, single-threaded, so one of the "
+                                     "host's cores)",
+                         "scaled": "to a whole reconstruction by the trajectory's iteration, prox and snapshot "
+                                   "counts, recorded from the CUDA path's replay of the same Philox draws (the "
+                                   "oracle alone would need hours to find them)"},
         "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))

@@ -344,6 +344,15 @@ int vrps_batch_create(vrps_batch** out);
 int vrps_batch_free(vrps_batch* batch);
 /* on = 0: launch each tick's kernels directly instead of replaying captured graphs. */
 int vrps_batch_set_graphs(vrps_batch* batch, int on);
+/* Scheduling of a batch that shares the GPU with other work (no counterpart in the paper).
+ * set_stream_priority: recreates the batch's stream with this CUDA stream priority (clamped
+ * to the device's range; lower numbers run first when thread blocks of several streams
+ * wait for the same SMs).  set_grid_share: the persistent launches take this fraction (0, 1]
+ * of the resident thread-block slots (default 1), leaving the rest of the GPU to other
+ * streams.  Neither changes any result.  Both only before the batch's first job.
+ * Errors: INVALID_ARG (NULL batch, share out of range, jobs already submitted), CUDA. */
+int vrps_batch_set_stream_priority(vrps_batch* batch, int priority);
+int vrps_batch_set_grid_share(vrps_batch* batch, double share);
 /* Admits a job before the next tick: allocates its state in the geometry's workspace,
  * reorders b subset-major, draws its Philox schedule and (SAGA) builds its table.  *id is
  * the job's handle.  Errors: INVALID_ARG (bad field, geometry busy, 2D job in a 3D batch or

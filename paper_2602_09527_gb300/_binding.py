@@ -105,6 +105,8 @@ def _load():
         "vrps_batch_create": (i, [P(vp)]),
         "vrps_batch_free": (i, [vp]),
         "vrps_batch_set_graphs": (i, [vp, i]),
+        "vrps_batch_set_stream_priority": (i, [vp, i]),
+        "vrps_batch_set_grid_share": (i, [vp, d]),
         "vrps_batch_submit": (i, [vp, P(JobDesc), P(i)]),
         "vrps_batch_step": (i, [vp, i, P(i)]),
         "vrps_batch_poll": (i, [vp, i, P(i), P(Report)]),
@@ -451,13 +453,17 @@ class Batch:
     iteration per job per tick, each tick's phases one persistent launch over all jobs
     (continuous batching)."""
 
-    def __init__(self, graphs: bool = True):
+    def __init__(self, graphs: bool = True, priority: int | None = None, grid_share: float = 1.0):
         h = ctypes.c_void_p()
         _check(lib.vrps_batch_create(ctypes.byref(h)))
         self.handle = h
         self._keep = {}
         if not graphs:
             _check(lib.vrps_batch_set_graphs(self.handle, 0))
+        if priority is not None:
+            _check(lib.vrps_batch_set_stream_priority(self.handle, int(priority)))
+        if grid_share != 1.0:
+            _check(lib.vrps_batch_set_grid_share(self.handle, float(grid_share)))
 
     def submit(self, g: Geometry, b: torch.Tensor, *, alpha: float, p: float, gamma: float, seed: int = 0,
                job: int = 0, estimator: str = "SVRG", fgp_iters: int = 50, max_iters: int = 100,

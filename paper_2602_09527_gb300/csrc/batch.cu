@@ -85,16 +85,27 @@ struct vrps_batch {
   int dims = 0;                  // 2 or 3, set by the first job
   int grid3[5] = {0, 0, 0, 0, 0};   // 3D persistent grids: transpose, forward, adjoint, FGP, output
   int max_f3 = 0;                // 3D: most FGP iterations of any job (rows of the FGP prefix table)
+  double share = 1.0;            // fraction of the resident CTA slots the persistent grids take
   std::vector<char> pack;
 };
 
 namespace {
+
+// A persistent grid of `share` of the resident slots (at least one CTA).
+int shared_grid(int grid, double share) {
+  const int g = (int)(grid * share);
+  return g < 1 ? 1 : g;
+}
 
 int batch_grids(vrps_batch* B) {
   VRPS_TRY(batched_grid(B->fwd_grouped ? 4 : 0, B->fwd_smem, &B->grid_fwd));
   VRPS_TRY(batched_grid(1, B->adj_smem, &B->grid_adj));
   VRPS_TRY(batched_grid(2, 0, &B->grid_fgp));
   VRPS_TRY(batched_grid(3, 0, &B->grid_out));
+  B->grid_fwd = shared_grid(B->grid_fwd, B->share);
+  B->grid_adj = shared_grid(B->grid_adj, B->share);
+  B->grid_fgp = shared_grid(B->grid_fgp, B->share);
+  B->grid_out = shared_grid(B->grid_out, B->share);
   return VRPS_OK;
 }
 
@@ -249,7 +260,10 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   if (three) {
     if (J->fgp_iters > B->max_f3) B->max_f3 = J->fgp_iters;
     if (B->grid3[0] == 0)
-      for (int q = 0; q < 5; ++q) VRPS_TRY(batched_grid_3d(q, &B->grid3[q]));
+      for (int q = 0; q < 5; ++q) {
+        VRPS_TRY(batched_grid_3d(q, &B->grid3[q]));
+        B->grid3[q] = shared_grid(B->grid3[q], B->share);
+      }
     VRPS_CUDA(cudaEventCreate(&J->ev_start));
     VRPS_CUDA(cudaEventCreate(&J->ev_done));
     VRPS_CUDA(cudaEventRecord(J->ev_start, s));
@@ -806,6 +820,29 @@ int vrps_batch_free(vrps_batch* B) {
 int vrps_batch_set_graphs(vrps_batch* B, int on) {
   if (!B) return fail(VRPS_ERR_INVALID_ARG, "batch is NULL");
   B->graphs = on != 0;
+  return VRPS_OK;
+}
+
+int vrps_batch_set_stream_priority(vrps_batch* B, int priority) {
+  if (!B) return fail(VRPS_ERR_INVALID_ARG, "batch is NULL");
+  if (!B->jobs.empty()) return fail(VRPS_ERR_INVALID_ARG, "the stream priority is set before the first job");
+  int lo = 0, hi = 0;   // numerically: lo = lowest priority (largest value), hi = highest
+  VRPS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  if (priority > lo) priority = lo;
+  if (priority < hi) priority = hi;
+  cudaStream_t s = nullptr;
+  VRPS_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, priority));
+  VRPS_CUDA(cudaStreamSynchronize(B->stream));
+  cudaStreamDestroy(B->stream);
+  B->stream = s;
+  return VRPS_OK;
+}
+
+int vrps_batch_set_grid_share(vrps_batch* B, double share) {
+  if (!B) return fail(VRPS_ERR_INVALID_ARG, "batch is NULL");
+  if (!(share > 0.0 && share <= 1.0)) return fail(VRPS_ERR_INVALID_ARG, "share must be in (0, 1]");
+  if (!B->jobs.empty()) return fail(VRPS_ERR_INVALID_ARG, "the grid share is set before the first job");
+  B->share = share;
   return VRPS_OK;
 }
 

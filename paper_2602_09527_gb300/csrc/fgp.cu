@@ -26,23 +26,26 @@ namespace {
 // side; each iteration shrinks the region where values are exact by one pixel per side, so
 // after T iterations the tile itself holds w_{k+T} and z_{k+T}, which are written back.
 // Per iteration: x = P_+(v + tau div z) on the region, then per pixel
-// w' = P_B(z + step D x) and the next extrapolation z' = w' + mom' (w' - w), both in place
-// (each only reads its own pixel's w and z).  Reads and writes go to different buffer
-// pairs, so neighbouring CTAs never see a half-updated dual.
+// w' = P_B(z + step D x) and the next extrapolation z' = w' + mom' (w' - w).
+// Every thread owns fixed pixels of the grown tile (linear slots e = tid + k NT) and keeps
+// their v, w, z and x in registers for the whole launch; shared memory holds only what
+// neighbours read: z (for the divergence at the left / upper neighbour) and x (for the
+// forward differences at the right / lower neighbour).  Reads and writes go to different
+// global buffer pairs, so neighbouring CTAs never see a half-updated dual.
 
 // Tile: TX x TY outputs per CTA of NT threads; the grown tile (EX x EY elements) is walked
-// in NS linear slots per thread (slot e = tid + k NT).  Each slot carries the depth at which
-// it leaves the shrinking valid region, so one compare decides whether it works in a step.
+// in NS linear slots per thread.  Each slot carries the depth at which it leaves the
+// shrinking valid region, so one compare decides whether it works in a step.
 template <int TX_, int TY_, int NT_>
 struct FgpTile {
   static constexpr int TX = TX_, TY = TY_, NT = NT_;
   static constexpr int EX = TX + 2 * FB_T, EY = TY + 2 * FB_T, NE = EX * EY;
   static constexpr int NS = (NE + NT - 1) / NT;
-  static constexpr size_t SMEM = sizeof(float) * 6 * NE;
+  static constexpr size_t SMEM = sizeof(float) * 3 * NE;   // z (2 components) and x
 };
-using TileLarge = FgpTile<32, 32, 512>;   // 48 x 48 grown tile, 55 KB
-using TileWide = FgpTile<32, 16, 256>;    // 48 x 32, 36 KB: twice the tiles of TileLarge
-using TileSmall = FgpTile<16, 16, 256>;   // 32 x 32, 24 KB: four times the tiles
+using TileLarge = FgpTile<32, 32, 512>;   // 48 x 48 grown tile, 27 KB
+using TileWide = FgpTile<32, 16, 256>;    // 48 x 32, 18 KB: twice the tiles of TileLarge
+using TileSmall = FgpTile<16, 16, 256>;   // 32 x 32, 12 KB: four times the tiles
 
 
 // Projection onto the unit ball: g / max(1, |g|) through the hardware reciprocal square
@@ -59,14 +62,18 @@ __device__ __forceinline__ void ball2(float g1, float g2, float& n1, float& n2) 
   }
 }
 
-// One block of nsteps FGP iterations on the shared-memory tile.  INTERIOR: the grown tile
-// lies strictly inside the image (no boundary or bounds tests needed).
+// One block of A.nsteps FGP iterations on output tile (ox + FB_T, oy + FB_T) with its grown
+// tile in registers (own slots) and shared memory (sz1, sz2, sx: NE floats each).
+// INTERIOR: the grown tile lies strictly inside the image (no boundary or bounds tests).
 template <class TL, bool INTERIOR, bool NONNEG>
-__device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, float* z1, float* z2, float* sx, int ox,
-                                            int oy, int nx, int ny, float tau, float step, const MomBlock& mom,
-                                            int nsteps) {
+__device__ __forceinline__ void fgp2d_block_regs(const FgpBlockArgs& A, int ox, int oy, float* sz1, float* sz2,
+                                                 float* sx) {
   constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT, NS = TL::NS;
   const int tid = threadIdx.x;
+  const int nx = A.nx, ny = A.ny, nsteps = A.nsteps;
+  const float tau = A.tau, step = A.step;
+  const size_t n = (size_t)nx * ny;
+  float rv[NS], rw1[NS], rw2[NS], rz1[NS], rz2[NS], rx[NS];
   // x at step s needs z at i-1, i-EX: valid on [s+1, EX-s); w' also needs x at i+1, i+EX:
   // valid on [s+1, EX-s-1).  dx / dw = largest step at which the slot is still inside.
   int dx[NS], dw[NS];
@@ -77,7 +84,28 @@ __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, flo
     const int a = min(lx - 1, ly - 1);
     dx[k] = e < NE ? min(a, min(EX - 1 - lx, EY - 1 - ly)) : -1;
     dw[k] = e < NE ? min(a, min(EX - 2 - lx, EY - 2 - ly)) : -1;
+    const int gx = ox + lx, gy = oy + ly;
+    float vv = 0.f, w_a = 0.f, w_b = 0.f, z_a = 0.f, z_b = 0.f;
+    if (e < NE && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      const size_t p = (size_t)gy * nx + gx;
+      vv = A.v[p];
+      w_a = A.w[p];
+      w_b = A.w[n + p];
+      z_a = A.z[p];
+      z_b = A.z[n + p];
+    }
+    rv[k] = vv;
+    rw1[k] = w_a;
+    rw2[k] = w_b;
+    rz1[k] = z_a;
+    rz2[k] = z_b;
+    rx[k] = 0.f;
+    if (e < NE) {
+      sz1[e] = z_a;
+      sz2[e] = z_b;
+    }
   }
+  __syncthreads();
   for (int s = 0; s < nsteps; ++s) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
@@ -87,18 +115,19 @@ __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, flo
         const int gx = ox + i % EX, gy = oy + i / EX;
         if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
           float d = 0.f;
-          if (INTERIOR || gx < nx - 1) d += z1[i];
-          if (INTERIOR || gx > 0) d -= z1[i - 1];
-          if (INTERIOR || gy < ny - 1) d += z2[i];
-          if (INTERIOR || gy > 0) d -= z2[i - EX];
-          xv = fmaf(tau, d, sv[i]);
+          if (INTERIOR || gx < nx - 1) d += rz1[k];
+          if (INTERIOR || gx > 0) d -= sz1[i - 1];
+          if (INTERIOR || gy < ny - 1) d += rz2[k];
+          if (INTERIOR || gy > 0) d -= sz2[i - EX];
+          xv = fmaf(tau, d, rv[k]);
           if (NONNEG) xv = fmaxf(xv, 0.f);
         }
+        rx[k] = xv;
         sx[i] = xv;
       }
     }
     __syncthreads();
-    const float m = mom.c[s];
+    const float m = A.mom.c[s];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       if (dw[k] >= s) {
@@ -106,90 +135,62 @@ __device__ __forceinline__ void fgp2d_steps(float* sv, float* w1, float* w2, flo
         float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
         const int gx = ox + i % EX, gy = oy + i / EX;
         if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
-          const float xc = sx[i];
+          const float xc = rx[k];
           const float d1 = (INTERIOR || gx < nx - 1) ? sx[i + 1] - xc : 0.f;
           const float d2 = (INTERIOR || gy < ny - 1) ? sx[i + EX] - xc : 0.f;
-          ball2(fmaf(step, d1, z1[i]), fmaf(step, d2, z2[i]), n1, n2);
-          m1 = fmaf(m, n1 - w1[i], n1);
-          m2 = fmaf(m, n2 - w2[i], n2);
+          ball2(fmaf(step, d1, rz1[k]), fmaf(step, d2, rz2[k]), n1, n2);
+          m1 = fmaf(m, n1 - rw1[k], n1);
+          m2 = fmaf(m, n2 - rw2[k], n2);
         }
-        w1[i] = n1;
-        w2[i] = n2;
-        z1[i] = m1;
-        z2[i] = m2;
+        rw1[k] = n1;
+        rw2[k] = n2;
+        rz1[k] = m1;
+        rz2[k] = m2;
+        sz1[i] = m1;
+        sz2[i] = m2;
       }
     }
     __syncthreads();
+  }
+  // the output tile: every thread writes the slots it owns there
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int e = tid + k * NT;
+    const int lx = e % EX, ly = e / EX;
+    if (e < NE && lx >= FB_T && lx < FB_T + TL::TX && ly >= FB_T && ly < FB_T + TL::TY) {
+      const int gx = ox + lx, gy = oy + ly;
+      if (gx < nx && gy < ny) {
+        const size_t p = (size_t)gy * nx + gx;
+        A.wn[p] = rw1[k];
+        A.wn[n + p] = rw2[k];
+        A.zn[p] = rz1[k];
+        A.zn[n + p] = rz2[k];
+      }
+    }
   }
 }
 
 // One output tile (bx, by) of a blocked launch; smf: dynamic shared memory (TL::SMEM bytes).
 template <class TL>
 __device__ __forceinline__ void fgp2d_block_item(const FgpBlockArgs& A, int bx, int by, float* smf) {
-  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT;
-  const float* __restrict__ v = A.v;
-  const float* __restrict__ w_g = A.w;
-  const float* __restrict__ z_g = A.z;
-  float* __restrict__ wn_g = A.wn;
-  float* __restrict__ zn_g = A.zn;
-  const int nx = A.nx, ny = A.ny, nsteps = A.nsteps;
-  const float tau = A.tau, step = A.step;
-  const MomBlock& mom = A.mom;
-  float* sv = smf;
-  float* w1 = sv + NE;
-  float* w2 = w1 + NE;
-  float* z1 = w2 + NE;
-  float* z2 = z1 + NE;
-  float* sx = z2 + NE;
-  const int tid = threadIdx.x;
+  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE;
+  float* sz1 = smf;
+  float* sz2 = sz1 + NE;
+  float* sx = sz2 + NE;
   const int ox = bx * TL::TX - FB_T, oy = by * TL::TY - FB_T;
-  const size_t n = (size_t)nx * ny;
-  for (int i = tid; i < NE; i += NT) {
-    const int gx = ox + i % EX, gy = oy + i / EX;
-    float vv = 0.f, a = 0.f, b = 0.f, za = 0.f, zb = 0.f;
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-      const size_t p = (size_t)gy * nx + gx;
-      vv = v[p];
-      a = w_g[p];
-      b = w_g[n + p];
-      za = z_g[p];
-      zb = z_g[n + p];
-    }
-    sv[i] = vv;
-    w1[i] = a;
-    w2[i] = b;
-    z1[i] = za;
-    z2[i] = zb;
-  }
-  __syncthreads();
+  const int nx = A.nx, ny = A.ny;
   const bool interior = ox >= 1 && oy >= 1 && ox + EX <= nx - 1 && oy + EY <= ny - 1;
   if (A.nonneg) {
-    if (interior)
-      fgp2d_steps<TL, true, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
-    else
-      fgp2d_steps<TL, false, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+    if (interior) fgp2d_block_regs<TL, true, true>(A, ox, oy, sz1, sz2, sx);
+    else fgp2d_block_regs<TL, false, true>(A, ox, oy, sz1, sz2, sx);
   } else {
-    if (interior)
-      fgp2d_steps<TL, true, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
-    else
-      fgp2d_steps<TL, false, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
-  }
-  for (int q = tid; q < TL::TX * TL::TY; q += NT) {
-    const int lx = FB_T + q % TL::TX, ly = FB_T + q / TL::TX;
-    const int gx = ox + lx, gy = oy + ly;
-    if (gx < nx && gy < ny) {
-      const size_t p = (size_t)gy * nx + gx;
-      const int i = ly * EX + lx;
-      wn_g[p] = w1[i];
-      wn_g[n + p] = w2[i];
-      zn_g[p] = z1[i];
-      zn_g[n + p] = z2[i];
-    }
+    if (interior) fgp2d_block_regs<TL, true, false>(A, ox, oy, sz1, sz2, sx);
+    else fgp2d_block_regs<TL, false, false>(A, ox, oy, sz1, sz2, sx);
   }
 }
 
 template <class TL>
-__global__ void __launch_bounds__(TL::NT) fgp2d_block(FgpBlockArgs A) {
+__global__ void __launch_bounds__(TL::NT, 2) fgp2d_block(const __grid_constant__ FgpBlockArgs A) {
   extern __shared__ float smf[];
   fgp2d_block_item<TL>(A, blockIdx.x, blockIdx.y, smf);
 }
@@ -651,7 +652,7 @@ __device__ __forceinline__ int fgp_batch_next(unsigned* counter, int* s_item) {
   return *s_item;
 }
 
-__global__ void __launch_bounds__(TileLarge::NT) fgp2d_block_batched_kernel(char* __restrict__ slot, int b) {
+__global__ void __launch_bounds__(TileLarge::NT, 2) fgp2d_block_batched_kernel(char* __restrict__ slot, int b) {
   extern __shared__ float smf[];
   __shared__ int pre[BATCH_MAX_JOBS + 1];
   __shared__ int s_item;

@@ -86,7 +86,7 @@ struct FwdShared {
   unsigned last;               // this CTA completed the angle row
 };
 
-constexpr int FWD_RPT = 6;   // rays per thread held in registers across a band group (nb <= 1536)
+constexpr int FWD_RPT = 6;   // most rays per thread held in registers across a band group (nb <= 1536)
 
 // Stages band lines [l0, l0 + nl) of img into buf (zero margins; BULK: bulk copies on bar, the
 // caller waits; otherwise plain loads, visible after the caller's barrier).
@@ -206,7 +206,7 @@ __device__ __forceinline__ void fwd2d_ray(const Fwd2DParams& P, const AngleInfo2
 // keeps its rays' sums in registers across the group.  Each ray's group sum goes to a partial
 // buffer; the CTA that completes a row last adds the groups in order (deterministic) and runs
 // the epilogue.  ph[2]: the phases of the CTA's two barriers (flipped on every use).
-template <int MODE, bool BULK, bool GROUPED>
+template <int MODE, bool BULK, int RPT>
 __device__ __forceinline__ void fwd2d_item(const Fwd2DParams& P, int cg, int row, float* smem, FwdShared& S,
                                            unsigned* ph) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -220,7 +220,7 @@ __device__ __forceinline__ void fwd2d_item(const Fwd2DParams& P, int cg, int row
   const int c1 = min(c0 + P.group, P.nbands);
   const size_t pbase = (size_t)row * P.bands * P.nb + (size_t)cg * P.nb;
   bool ok = true;
-  if (!GROUPED || P.group == 1 || P.nb > FWD_RPT * FWD_THREADS) {
+  if (RPT == 0 || P.group == 1 || P.nb > RPT * FWD_THREADS) {
     // one band per item: rays written as they finish
     const int l0 = c0 * P.band;
     const int nl = min(P.band, nlines - l0);
@@ -240,9 +240,10 @@ __device__ __forceinline__ void fwd2d_item(const Fwd2DParams& P, int cg, int row
     }
   } else {
     const int band_floats = P.band * stride;
-    float acc[FWD_RPT][2];
+    constexpr int NR = RPT > 0 ? RPT : 1;   // rays per thread (RPT = 0: not grouped)
+    float acc[NR][2];
 #pragma unroll
-    for (int k = 0; k < FWD_RPT; ++k) acc[k][0] = acc[k][1] = 0.f;
+    for (int k = 0; k < NR; ++k) acc[k][0] = acc[k][1] = 0.f;
     {
       const int nl0 = min(P.band, nlines - c0 * P.band);
       if (nl0 > 0) fwd2d_stage<BULK>(img, ncols, stride, c0 * P.band, nl0, smem, &S.bar[0]);
@@ -262,7 +263,7 @@ __device__ __forceinline__ void fwd2d_item(const Fwd2DParams& P, int cg, int row
       if (ok) {
         const float* buf = smem + b * band_floats;
 #pragma unroll
-        for (int k = 0; k < FWD_RPT; ++k) {
+        for (int k = 0; k < NR; ++k) {
           const int j = warp * FWD_LANES + k * FWD_THREADS + lane;
           if (warp * FWD_LANES + k * FWD_THREADS < P.nb && j < P.nb)
             fwd2d_ray(P, in, buf, j, l0, nl, ncols, nlines, stride, acc[k][0], acc[k][1]);
@@ -271,7 +272,7 @@ __device__ __forceinline__ void fwd2d_item(const Fwd2DParams& P, int cg, int row
       __syncthreads();   // band c's buffer is free for band c + 2
     }
 #pragma unroll
-    for (int k = 0; k < FWD_RPT; ++k) {
+    for (int k = 0; k < NR; ++k) {
       const int j = warp * FWD_LANES + k * FWD_THREADS + lane;
       if (j < P.nb) P.part[pbase + j] = acc[k][0] + acc[k][1];
     }
@@ -327,13 +328,13 @@ __device__ __forceinline__ void fwd2d_init_barrier(FwdShared& S) {
   __syncthreads();
 }
 
-template <int MODE, bool BULK, bool GROUPED>
+template <int MODE, bool BULK, int RPT>
 __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
   extern __shared__ __align__(128) float band[];
   __shared__ FwdShared S;
   if (BULK) fwd2d_init_barrier(S);
   unsigned ph[2] = {0u, 0u};
-  fwd2d_item<MODE, BULK, GROUPED>(P, blockIdx.x, blockIdx.y, band, S, ph);
+  fwd2d_item<MODE, BULK, RPT>(P, blockIdx.x, blockIdx.y, band, S, ph);
 }
 
 
@@ -354,7 +355,9 @@ struct AdjShared {
   float tile[32][ADJ_TX + 1];
 };
 
-// One pixel tile (bx, by) of the transpose; sm: dynamic shared [chunk][fp].
+// One pixel tile (bx, by) of the transpose; sm: dynamic shared [chunk][fp].  The update's
+// per-pixel inputs are loaded before the angle loop (single-share launches), so that their
+// latency hides behind the gather.
 template <int NC, int PPT>
 __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by, float* sm, AdjShared& S,
                                            int part = 0) {
@@ -365,12 +368,20 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
   float4* s_par = S.par;
   float* s_c0 = S.c0;
   int* s_off = S.off;
-  int* s_jlo = S.jlo;
-  float* s_wgt = S.wgt;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_TX + tx;
   const int ix0 = bx * ADJ_TX, iy0 = by * TY;
   const float ftx = (float)tx, fty = (float)ty;
   const float half_rows = (float)(TY / 2);
+  const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + TY / 2;
+  const bool in0 = ix < P.nx && iy < P.ny, in1 = PPT == 2 && ix < P.nx && iy1 < P.ny;
+  const size_t p0 = (size_t)iy * P.nx + ix, p1 = (size_t)iy1 * P.nx + ix;
+  const UpdateArgs& u = P.u;
+  UpdIn pre0{0.f, 0.f, 0.f}, pre1{0.f, 0.f, 0.f};
+  const bool prefetch = u.enabled && P.split == 1;
+  if (prefetch) {
+    if (in0) pre0 = update_load(u, p0);
+    if (in1) pre1 = update_load(u, p1);
+  }
   float acc0 = 0.f, acc1 = 0.f;                  // pixels (tx, ty) and, with PPT = 2, (tx, ty + TY/2)
   for (int r0 = ra; r0 < rz; r0 += P.chunk) {
     const int nr = min(P.chunk, rz - r0);
@@ -385,14 +396,30 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
       s_par[tid] = make_float4(in.Bx, in.By, F0 - in.hw, in.inv_hw);
       s_c0[tid] = 1.f - in.hw;
       s_off[tid] = J0 - jlo;
-      s_jlo[tid] = jlo;
-      s_wgt[tid] = in.wgt;
+      S.jlo[tid] = jlo;
+      S.wgt[tid] = in.wgt;
     }
     __syncthreads();
-    for (int e = tid; e < nr * P.fp; e += ADJ_THREADS) {
-      const int q = e / P.fp;
-      const int j = s_jlo[q] + (e - q * P.fp);
-      sm[e] = (j >= 0 && j < P.nb) ? s_wgt[q] * __ldg(P.r + (size_t)(r0 + q) * P.nb + j) : 0.f;
+    // the footprint rows, four elements per thread per pass with the loads issued before the
+    // stores (several loads in flight per thread)
+    const int total = nr * P.fp;
+    for (int e0 = tid; e0 < total; e0 += 4 * ADJ_THREADS) {
+      float val[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * ADJ_THREADS;
+        val[u] = 0.f;
+        if (e < total) {
+          const int q = e / P.fp;
+          const int j = S.jlo[q] + (e - q * P.fp);
+          if (j >= 0 && j < P.nb) val[u] = S.wgt[q] * __ldg(P.r + (size_t)(r0 + q) * P.nb + j);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * ADJ_THREADS;
+        if (e < total) sm[e] = val[u];
+      }
     }
     __syncthreads();
     for (int q = 0; q < nr; ++q) {
@@ -434,9 +461,6 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
     }
     __syncthreads();
   }
-  const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + TY / 2;
-  const bool in0 = ix < P.nx && iy < P.ny, in1 = PPT == 2 && ix < P.nx && iy1 < P.ny;
-  const size_t p0 = (size_t)iy * P.nx + ix, p1 = (size_t)iy1 * P.nx + ix;
   if (P.split > 1) {
     // angle shares of one tile: partial sums to scratch; the last share to arrive adds them in
     // share order (deterministic) and runs the epilogue
@@ -461,14 +485,17 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
       if (in1) acc1 += __ldcg(P.part + (size_t)q * n + p1);
     }
   }
-  const UpdateArgs& u = P.u;
   if (!u.enabled) {
     if (in0) u.out[p0] = acc0;
     if (in1) u.out[p1] = acc1;
     return;
   }
-  const float x0 = in0 ? update_pixel(u, p0, acc0) : 0.f;
-  const float x1 = in1 ? update_pixel(u, p1, acc1) : 0.f;
+  if (!prefetch) {
+    if (in0) pre0 = update_load(u, p0);
+    if (in1) pre1 = update_load(u, p1);
+  }
+  const float x0 = in0 ? update_pixel_pre(u, p0, acc0, pre0) : 0.f;
+  const float x1 = in1 ? update_pixel_pre(u, p1, acc1, pre1) : 0.f;
   if (!u.theta && u.xT) {
     S.tile[ty][tx] = x0;
     if (PPT == 2) S.tile[ty + TY / 2][tx] = x1;
@@ -588,8 +615,9 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   switch (mode) {
 #define VRPS_FWD_CASE(M)                                                                          \
   case M:                                                                                         \
-    VRPS_TRY(grouped ? launch(fwd2d_kernel<M, true, true>)                                        \
-                     : (bulk ? launch(fwd2d_kernel<M, true, false>) : launch(fwd2d_kernel<M, false, false>))); \
+    VRPS_TRY(grouped ? (g->n_bins <= 3 * FWD_THREADS ? launch(fwd2d_kernel<M, true, 3>)            \
+                                                      : launch(fwd2d_kernel<M, true, FWD_RPT>))    \
+                     : (bulk ? launch(fwd2d_kernel<M, true, 0>) : launch(fwd2d_kernel<M, false, 0>))); \
     break;
     VRPS_FWD_CASE(FWD_PLAIN)
     VRPS_FWD_CASE(FWD_RESID)
@@ -701,15 +729,15 @@ __device__ __forceinline__ void batch_load_prefix(int* dst, const int* src, int 
   __syncthreads();
 }
 
-template <bool BULK, bool GROUPED>
+template <bool BULK, int RPT>
 __device__ __forceinline__ void fwd2d_item_mode(const BatchFwd& J, int c, int row, float* band, FwdShared& S,
                                                 unsigned* ph) {
   switch (J.mode) {
-    case FWD_PLAIN: fwd2d_item<FWD_PLAIN, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
-    case FWD_RESID: fwd2d_item<FWD_RESID, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
-    case FWD_SVRG: fwd2d_item<FWD_SVRG, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
-    case FWD_SAGA: fwd2d_item<FWD_SAGA, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
-    default: fwd2d_item<FWD_SNAP, BULK, GROUPED>(J.P, c, row, band, S, ph); break;
+    case FWD_PLAIN: fwd2d_item<FWD_PLAIN, BULK, RPT>(J.P, c, row, band, S, ph); break;
+    case FWD_RESID: fwd2d_item<FWD_RESID, BULK, RPT>(J.P, c, row, band, S, ph); break;
+    case FWD_SVRG: fwd2d_item<FWD_SVRG, BULK, RPT>(J.P, c, row, band, S, ph); break;
+    case FWD_SAGA: fwd2d_item<FWD_SAGA, BULK, RPT>(J.P, c, row, band, S, ph); break;
+    default: fwd2d_item<FWD_SNAP, BULK, RPT>(J.P, c, row, band, S, ph); break;
   }
 }
 
@@ -722,7 +750,7 @@ __device__ __forceinline__ int batch_next(unsigned* counter, int* s_item) {
   return *s_item;
 }
 
-template <bool GROUPED>
+template <int RPT>
 __global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(char* __restrict__ slot) {
   extern __shared__ __align__(128) float band[];
   __shared__ FwdShared S;
@@ -743,8 +771,8 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_batched_kernel(char* __rest
     const int local = item - pre[j];
     const int bands = J.P.bands;
     const int c = local % bands, row = local / bands;
-    if (J.bulk) fwd2d_item_mode<true, GROUPED>(J, c, row, band, S, ph);
-    else fwd2d_item_mode<false, false>(J, c, row, band, S, ph);
+    if (J.bulk) fwd2d_item_mode<true, RPT>(J, c, row, band, S, ph);
+    else fwd2d_item_mode<false, 0>(J, c, row, band, S, ph);
   }
 }
 
@@ -779,7 +807,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj2d_batched_kernel(char* __rest
 }  // namespace
 
 int fwd2d_batched(char* slot, int grid, size_t smem, bool grouped, cudaStream_t s) {
-  auto kern = grouped ? fwd2d_batched_kernel<true> : fwd2d_batched_kernel<false>;
+  auto kern = grouped ? fwd2d_batched_kernel<FWD_RPT> : fwd2d_batched_kernel<0>;
   VRPS_TRY(smem_opt_in((const void*)kern, smem));
   LaunchScope _ls("fwd2d_batched", s);
   VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(FWD_THREADS), smem, s, slot));
@@ -798,7 +826,7 @@ int batched_grid_2d(int which, size_t smem, int* grid) {
   VRPS_CUDA(cudaGetDevice(&dev));
   VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (which == 0 || which == 4) {
-    auto kern = which == 4 ? fwd2d_batched_kernel<true> : fwd2d_batched_kernel<false>;
+    auto kern = which == 4 ? fwd2d_batched_kernel<FWD_RPT> : fwd2d_batched_kernel<0>;
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
     VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FWD_THREADS, smem));
   } else {

@@ -286,21 +286,33 @@ struct UpdateArgs {
 // x_hat = base - gamma (G - h); theta = 0: x <- x_hat (returned for the transposed copy);
 // theta = 1: keep x_hat and write the prox input v = x_hat - (gamma/p) h.
 // (Explicit roundings and fused multiply-adds: identical bits in every kernel that inlines it.)
-__device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, float g) {
+// The pixel's inputs of the update (gbar, base point, h), which a kernel may load before it
+// computes g so that their latency hides behind the gather.
+struct UpdIn {
+  float gb, base, h;
+};
+__device__ __forceinline__ UpdIn update_load(const UpdateArgs& u, size_t p) {
+  UpdIn a;
+  a.gb = (!u.snap && u.gbar) ? u.gbar[p] : 0.f;
+  a.base = u.base[p];
+  a.h = u.h ? u.h[p] : 0.f;
+  return a;
+}
+__device__ __forceinline__ float update_pixel_pre(const UpdateArgs& u, size_t p, float g, const UpdIn& a) {
   float G;
   if (u.snap) {            // SVRG snapshot: g is the full gradient; gbar <- g, G = g
     u.gbar[p] = g;
     G = g;
   } else if (u.gbar) {
-    const float gb = u.gbar[p];
+    const float gb = a.gb;
     G = fmaf(u.cN, g, gb);
     if (u.saga) u.gbar[p] = __fadd_rn(gb, g);
   } else {
     G = __fmul_rn(u.cN, g);
   }
-  const float base = u.base[p];
+  const float base = a.base;
   if (u.h) {
-    const float hp = u.h[p];
+    const float hp = a.h;
     const float xh = fmaf(-u.gamma, __fsub_rn(G, hp), base);
     if (u.theta) {
       u.xhat[p] = xh;
@@ -317,6 +329,9 @@ __device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, flo
   }
   u.x[p] = xh;
   return xh;
+}
+__device__ __forceinline__ float update_pixel(const UpdateArgs& u, size_t p, float g) {
+  return update_pixel_pre(u, p, g, update_load(u, p));
 }
 // ---- 2D projector launch parameters (joseph2d.cu)
 struct Fwd2DParams {

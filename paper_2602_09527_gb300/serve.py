@@ -59,13 +59,19 @@ class BatchServer:
 
     pools: {key: [Geometry, ...]} handles per geometry class (each running job holds one);
     budget_bytes: upper bound on the summed footprint (vrps_job_footprint) of running jobs;
-    ticks_per_step: ticks enqueued between two admission / completion checks."""
+    ticks_per_step: ticks enqueued between two admission / completion checks;
+    max_running: at most this many jobs advance together (None: no limit besides handles and
+    memory) -- fewer concurrent jobs make each tick, and so each job, finish sooner;
+    priority, grid_share: the batch's CUDA stream priority and the fraction of the GPU's
+    resident thread-block slots its persistent launches take (vrps_batch_set_*)."""
 
-    def __init__(self, pools: dict, budget_bytes: int, ticks_per_step: int = 2, graphs: bool = True):
+    def __init__(self, pools: dict, budget_bytes: int, ticks_per_step: int = 2, graphs: bool = True,
+                 max_running: int | None = None, priority: int | None = None, grid_share: float = 1.0):
         self.free = {k: list(v) for k, v in pools.items()}
         self.budget = int(budget_bytes)
         self.ticks_per_step = int(ticks_per_step)
-        self.batch = vb.Batch(graphs=graphs)
+        self.max_running = max_running
+        self.batch = vb.Batch(graphs=graphs, priority=priority, grid_share=grid_share)
         self.running = {}            # job id -> (request, geometry, bytes)
         self.used = 0
 
@@ -73,7 +79,7 @@ class BatchServer:
 
     def _try_admit(self, r: Request, now: float) -> int:
         pool = self.free.get(r.key)
-        if not pool:
+        if not pool or (self.max_running is not None and len(self.running) >= self.max_running):
             return self.NO_HANDLE
         g = pool[-1]
         need = vb.job_footprint(g, max_iters=r.max_iters, storage=r.storage)
@@ -201,9 +207,14 @@ class MixedServer:
     every call, so neither loop waits for the other's host blocking."""
 
     def __init__(self, pools: dict, pools3d: dict, budget_bytes: int, ticks_per_step: int = 2,
-                 share3d: float = 0.5, ticks_per_step3d: int = 1):
-        self.s2 = BatchServer(pools, int(budget_bytes * (1.0 - share3d)), ticks_per_step)
-        self.s3 = BatchServer(pools3d, int(budget_bytes * share3d), ticks_per_step3d)
+                 share3d: float = 0.5, ticks_per_step3d: int = 1, max_running: int | None = None,
+                 max_running3d: int | None = None, grid_share3d: float = 1.0):
+        # the 2D batch's stream gets the highest priority (its short jobs wait least for SMs),
+        # the 3D batch's the lowest, and its persistent grids may leave part of the GPU free
+        self.s2 = BatchServer(pools, int(budget_bytes * (1.0 - share3d)), ticks_per_step, max_running=max_running,
+                              priority=-1000)
+        self.s3 = BatchServer(pools3d, int(budget_bytes * share3d), ticks_per_step3d, max_running=max_running3d,
+                              priority=0, grid_share=grid_share3d)
         self.keys3 = set(pools3d)
 
     def run(self, requests: list, clock=time.perf_counter) -> ServerStats:

@@ -23,7 +23,7 @@ class _FakeBatch:
     """Stands in for the device batch: a job finishes after max_iters ticks."""
     live = []
 
-    def __init__(self, graphs=True):
+    def __init__(self, graphs=True, **kw):
         self.left, self.next_id, self.running_max = {}, 0, 0
         _FakeBatch.live.append(self)
 
@@ -149,3 +149,14 @@ def test_request_waiting_for_memory_holds_later_ones(fake_engine):
     assert st.completed == 3
     _, second_big, small = reqs
     assert small.admitted >= second_big.admitted
+
+
+def test_max_running_caps_concurrent_jobs(fake_engine):
+    """With max_running the batch never holds more jobs at once, whatever handles and memory
+    would allow; every request still completes."""
+    torch = fake_engine
+    pools = {"a": [_G(4, 1) for _ in range(8)]}
+    srv = serve.BatchServer(pools, budget_bytes=10_000, ticks_per_step=1, max_running=3)
+    st = srv.run(_reqs(torch, ["a"] * 10, [4, 2, 6, 3, 5, 1, 2, 3, 4, 5]), clock=_Clock())
+    assert st.completed == 10 and st.peak_jobs == 3
+    assert _FakeBatch.live[0].running_max == 3
