@@ -103,9 +103,11 @@ WORKLOADS_SERVE = {
                   # when the stated rate exceeds one GPU's per-job capacity at this mix, run at
                   # `load` x that capacity and report the stated rate's offered load
                   rate_search=True, load=0.85,
-                  # scheduling: at most 32 2D and 2 3D jobs advance together; the 2D batch's stream
-                  # has the higher priority and the 3D batch's persistent grids take 80 % of the GPU
-                  max_running=32, max_running3d=2, grid_share3d=0.8),
+                  # scheduling: at most 32 2D jobs advance together in a batch whose stream has the
+                  # highest priority; 3D requests run one vrps_solve at a time in arrival order on a
+                  # lowest-priority stream (mode3d "solve"), or in a 3D batch of at most 2 jobs whose
+                  # persistent grids take 80 % of the GPU (mode3d "batch")
+                  max_running=32, mode3d="batch", max_running3d=2, grid_share3d=0.8),
 }
 
 # Operator costs (optional), the structure of the paper's cost figure on the 512^2 / 720-angle
@@ -346,11 +348,15 @@ def cone_gap_leg(vr, g, b, w, gamma, stream, flush, reps=2):
     run = time_to_gap(vr, g, b, w["alpha"], w["algo"], w["estimator"], w["p"], gamma, w["seed"], w["fgp_iters"],
                       w["n_subsets"], w["max_epochs"], stream, flush, reps=reps)
     f_star = min(min(Ff), run["f_min"])
-    out = time_to_gap_replay(vr, g, b, w["alpha"], run, f_star, w["target_gap"], stream, flush)
-    out.update(f_star=f_star, f_star_source=f"min(FISTA {fi} iterations, solver evaluations)",
-               fista_rel_change_last_half=(min(Ff[: len(Ff) // 2]) - min(Ff)) / abs(f_star))
-    if out.get("reached"):
-        out["epochs"] = round(out["k_star"] / w["n_subsets"], 2)
+    out = {"f_star": f_star, "f_star_source": f"min(FISTA {fi} iterations, solver evaluations)",
+           "fista_rel_change_last_half": (min(Ff[: len(Ff) // 2]) - min(Ff)) / abs(f_star),
+           "gap_after_search": (run["hist"][-1][1] - f_star) / abs(f_star), "search_epochs": w["max_epochs"],
+           "targets": {}}
+    for tgt in (1e-2, 1e-3, w["target_gap"]):
+        o = time_to_gap_replay(vr, g, b, w["alpha"], run, f_star, tgt, stream, flush)
+        if o.get("reached"):
+            o["epochs"] = round(o["k_star"] / w["n_subsets"], 2)
+        out["targets"][f"{tgt:g}"] = o
     return out
 
 
@@ -377,10 +383,11 @@ def cone64_leg(vr, w, stream, flush):
                 estimator=w["estimator"])
     t_epoch = time.perf_counter() - t0
     out = {"geometry": "64^3 voxel 2, 90 views, 96^2 detector pitch 4, SOD 500, SDD 1000, N = 30", "gpu": gpu,
-           "oracle_seconds_per_epoch": round(t_epoch, 2), "oracle_cores": 1}
-    if gpu.get("reached"):
-        out["oracle_seconds_to_gap"] = round(t_epoch * gpu["k_star"] / w["n_subsets"], 1)
-        out["oracle_note"] = "one oracle epoch measured, scaled by the epochs the trajectory needs (same draws)"
+           "oracle_seconds_per_epoch": round(t_epoch, 2), "oracle_cores": 1, "oracle_seconds_to_gap": {},
+           "oracle_note": "one oracle epoch measured, scaled by the epochs the trajectory needs (same draws)"}
+    for tgt, o in gpu["targets"].items():
+        if o.get("reached"):
+            out["oracle_seconds_to_gap"][tgt] = round(t_epoch * o["k_star"] / w["n_subsets"], 1)
     return out
 
 
@@ -751,6 +758,7 @@ def batch_leg(vr, wl, rank, world, local, steps, warmup, profile_once=0, dist=No
         F_star = [min(v) for v in zip(objectives(), F_seq, F_b16, F_oth)]
     gap32 = [(a - f) / abs(f) for a, f in zip(F_seq, F_star)]
     gap16 = [(a - f) / abs(f) for a, f in zip(F_b16, F_star)]
+    gapo = [(a - f) / abs(f) for a, f in zip(F_oth, F_star)]
     dF32 = max(abs(a - b) / abs(b) for a, b in zip(F_b32, F_seq))
     dF16 = max(abs(a - b) / abs(b) for a, b in zip(F_b16, F_seq))
     dFo = max(abs(a - b) / abs(b) for a, b in zip(F_oth, F_seq))
@@ -803,8 +811,10 @@ def batch_leg(vr, wl, rank, world, local, steps, warmup, profile_once=0, dist=No
         f"batched_{other.lower()}_s": round(t_oth, 6),
         "final_iterate_gap": {
             "per_job_fp32_max": max(gap32), f"batched_{w['storage'].lower()}_max": max(gap16),
+            f"batched_{other.lower()}_max": max(gapo),
             "jobs_within_1e-4": {"per_job_fp32": sum(g_ <= 1e-4 for g_ in gap32),
-                                 f"batched_{w['storage'].lower()}": sum(g_ <= 1e-4 for g_ in gap16)},
+                                 f"batched_{w['storage'].lower()}": sum(g_ <= 1e-4 for g_ in gap16),
+                                 f"batched_{other.lower()}": sum(g_ <= 1e-4 for g_ in gapo)},
             "f_star": (f"lowest objective of a {w.get('max_epochs')}-epoch float32 replay per job" if replay is not None
                        else f"min over runs incl. {5 * w['epochs']} epochs batched float32"),
             "note": "each job stops right after the prox step whose output reached the target in the replay"},
@@ -843,7 +853,7 @@ def bench_batch(args, rank, world, local):
 
 
 # --------------------------------------------------------------------------- served stream
-def serve_leg(vr, w, rank, local, seconds=None, rate=None):
+def serve_leg(vr, w, rank, local, seconds=None, rate=None, compare_3d_modes=False):
     """The served stream: pools of geometry handles sized from the memory budget, one seeded
     arrival sequence, and three runs of it (batched with bfloat16 storage + one float32 epoch,
     batched float32, and the per-job float32 solver one request after another).
@@ -963,8 +973,12 @@ def serve_leg(vr, w, rank, local, seconds=None, rate=None):
                 "peak_running_jobs": st.peak_jobs, "peak_state_gb": round(st.peak_bytes / 1e9, 3)}
 
     # warm-up: a short stream through the batched server (graph capture, allocations)
-    srv = serve.MixedServer(pools, pools3, budget, share3d=share3, max_running=w.get("max_running"),
-                            max_running3d=w.get("max_running3d"), grid_share3d=w.get("grid_share3d", 1.0))
+    def mixed(mode3d):
+        return serve.MixedServer(pools, pools3, budget, share3d=share3, max_running=w.get("max_running"),
+                                 max_running3d=w.get("max_running3d"), grid_share3d=w.get("grid_share3d", 1.0),
+                                 mode3d=mode3d)
+
+    srv = mixed(w.get("mode3d", "batch"))
     warm = requests("BF16", 1)[: min(len(arrivals), 40)]
     for r in warm:
         r.arrival = 0.0
@@ -978,6 +992,12 @@ def serve_leg(vr, w, rank, local, seconds=None, rate=None):
     reqs32 = requests("FP32", 0)
     results["batched_fp32"] = summary(srv.run(reqs32), reqs32)
     srv.close()
+    if compare_3d_modes:
+        other = "batch" if w.get("mode3d", "batch") == "solve" else "solve"
+        srv = mixed(other)
+        reqso = requests("BF16", 1)
+        results[f"batched_bf16_3d_{other}"] = summary(srv.run(reqso), reqso)
+        srv.close()
     seq = serve.SequentialServer({**pools, **pools3})
     reqsq = requests("FP32", 0)
     results["per_job_fp32"] = summary(seq.run(reqsq), reqsq)
@@ -993,8 +1013,9 @@ def serve_leg(vr, w, rank, local, seconds=None, rate=None):
         "sides_3d": list(w["sides3d"]), "epochs": epochs, "algo": "ProxSAGASkip", "p": w["p"],
         "fgp_iters": w["fgp_iters"], "alpha": f"U{list(w['alpha'])}", "budget_gb": w["budget_gb"],
         "handles_per_class": handles,
-        "scheduling": {"max_running_2d": w.get("max_running"), "max_running_3d": w.get("max_running3d"),
-                       "grid_share_3d": w.get("grid_share3d", 1.0), "stream_priority": "2D high, 3D low"},
+        "scheduling": {"max_running_2d": w.get("max_running"), "mode_3d": w.get("mode3d", "batch"),
+                       "max_running_3d": w.get("max_running3d"), "grid_share_3d": w.get("grid_share3d", 1.0),
+                       "stream_priority": "2D high, 3D low"},
         "device_s_per_request_alone": {k: round(v, 4) for k, v in cost.items()},
         "mean_device_s_per_request": round(e_cost, 4),
         "per_job_capacity_per_s": round(capacity, 3),
@@ -1010,7 +1031,7 @@ def bench_serve(args, rank, world, local):
     import paper_2602_09527_gb300 as vr
     w = WORKLOADS_SERVE[args.workload]
     with ClockSampler(local) as clk:
-        res = serve_leg(vr, w, rank, local, seconds=args.serve_seconds or None)
+        res = serve_leg(vr, w, rank, local, seconds=args.serve_seconds or None, compare_3d_modes=True)
     head = res["variants"]["batched_bf16"]
     out = {
         "metric": "served p99 latency",

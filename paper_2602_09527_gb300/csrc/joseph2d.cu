@@ -368,20 +368,12 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
   float4* s_par = S.par;
   float* s_c0 = S.c0;
   int* s_off = S.off;
+  int* s_jlo = S.jlo;
+  float* s_wgt = S.wgt;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_TX + tx;
   const int ix0 = bx * ADJ_TX, iy0 = by * TY;
   const float ftx = (float)tx, fty = (float)ty;
   const float half_rows = (float)(TY / 2);
-  const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + TY / 2;
-  const bool in0 = ix < P.nx && iy < P.ny, in1 = PPT == 2 && ix < P.nx && iy1 < P.ny;
-  const size_t p0 = (size_t)iy * P.nx + ix, p1 = (size_t)iy1 * P.nx + ix;
-  const UpdateArgs& u = P.u;
-  UpdIn pre0{0.f, 0.f, 0.f}, pre1{0.f, 0.f, 0.f};
-  const bool prefetch = u.enabled && P.split == 1;
-  if (prefetch) {
-    if (in0) pre0 = update_load(u, p0);
-    if (in1) pre1 = update_load(u, p1);
-  }
   float acc0 = 0.f, acc1 = 0.f;                  // pixels (tx, ty) and, with PPT = 2, (tx, ty + TY/2)
   for (int r0 = ra; r0 < rz; r0 += P.chunk) {
     const int nr = min(P.chunk, rz - r0);
@@ -396,30 +388,14 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
       s_par[tid] = make_float4(in.Bx, in.By, F0 - in.hw, in.inv_hw);
       s_c0[tid] = 1.f - in.hw;
       s_off[tid] = J0 - jlo;
-      S.jlo[tid] = jlo;
-      S.wgt[tid] = in.wgt;
+      s_jlo[tid] = jlo;
+      s_wgt[tid] = in.wgt;
     }
     __syncthreads();
-    // the footprint rows, four elements per thread per pass with the loads issued before the
-    // stores (several loads in flight per thread)
-    const int total = nr * P.fp;
-    for (int e0 = tid; e0 < total; e0 += 4 * ADJ_THREADS) {
-      float val[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = e0 + u * ADJ_THREADS;
-        val[u] = 0.f;
-        if (e < total) {
-          const int q = e / P.fp;
-          const int j = S.jlo[q] + (e - q * P.fp);
-          if (j >= 0 && j < P.nb) val[u] = S.wgt[q] * __ldg(P.r + (size_t)(r0 + q) * P.nb + j);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = e0 + u * ADJ_THREADS;
-        if (e < total) sm[e] = val[u];
-      }
+    for (int e = tid; e < nr * P.fp; e += ADJ_THREADS) {
+      const int q = e / P.fp;
+      const int j = s_jlo[q] + (e - q * P.fp);
+      sm[e] = (j >= 0 && j < P.nb) ? s_wgt[q] * __ldg(P.r + (size_t)(r0 + q) * P.nb + j) : 0.f;
     }
     __syncthreads();
     for (int q = 0; q < nr; ++q) {
@@ -461,6 +437,9 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
     }
     __syncthreads();
   }
+  const int ix = ix0 + tx, iy = iy0 + ty, iy1 = iy + TY / 2;
+  const bool in0 = ix < P.nx && iy < P.ny, in1 = PPT == 2 && ix < P.nx && iy1 < P.ny;
+  const size_t p0 = (size_t)iy * P.nx + ix, p1 = (size_t)iy1 * P.nx + ix;
   if (P.split > 1) {
     // angle shares of one tile: partial sums to scratch; the last share to arrive adds them in
     // share order (deterministic) and runs the epilogue
@@ -485,17 +464,14 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
       if (in1) acc1 += __ldcg(P.part + (size_t)q * n + p1);
     }
   }
+  const UpdateArgs& u = P.u;
   if (!u.enabled) {
     if (in0) u.out[p0] = acc0;
     if (in1) u.out[p1] = acc1;
     return;
   }
-  if (!prefetch) {
-    if (in0) pre0 = update_load(u, p0);
-    if (in1) pre1 = update_load(u, p1);
-  }
-  const float x0 = in0 ? update_pixel_pre(u, p0, acc0, pre0) : 0.f;
-  const float x1 = in1 ? update_pixel_pre(u, p1, acc1, pre1) : 0.f;
+  const float x0 = in0 ? update_pixel(u, p0, acc0) : 0.f;
+  const float x1 = in1 ? update_pixel(u, p1, acc1) : 0.f;
   if (!u.theta && u.xT) {
     S.tile[ty][tx] = x0;
     if (PPT == 2) S.tile[ty + TY / 2][tx] = x1;

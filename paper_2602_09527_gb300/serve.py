@@ -151,14 +151,16 @@ class BatchServer:
 
 
 class SequentialServer:
-    """The per-job baseline: requests in arrival order, one vrps_solve at a time."""
+    """The per-job baseline: requests in arrival order, one vrps_solve at a time (on `stream`,
+    default the current stream)."""
 
-    def __init__(self, pools: dict):
+    def __init__(self, pools: dict, stream=None):
         self.geom = {k: v[0] for k, v in pools.items()}
+        self.stream = stream
 
-    def run(self, requests: list, clock=time.perf_counter) -> ServerStats:
+    def run(self, requests: list, clock=time.perf_counter, t0: float | None = None) -> ServerStats:
         st = ServerStats()
-        t0 = clock()
+        t0 = clock() if t0 is None else t0
         for r in requests:
             now = clock() - t0
             if r.arrival > now:
@@ -167,7 +169,8 @@ class SequentialServer:
             g = self.geom[r.key]
             x, rep, _ = vb.solve(r.b, g, r.alpha, "VR_PROXSKIP", p=r.p, gamma=r.gamma, seed=r.seed,
                                  estimator=r.estimator, fgp_iters=r.fgp_iters, max_iters=r.max_iters,
-                                 n_subsets=r.n_subsets, storage=r.storage, correction_epochs=r.correction_epochs)
+                                 n_subsets=r.n_subsets, storage=r.storage, correction_epochs=r.correction_epochs,
+                                 stream=self.stream)
             r.finished = clock() - t0
             r.report, r.x = rep, x
             st.completed += 1
@@ -201,20 +204,25 @@ def merge_stats(parts: list, wall: float) -> ServerStats:
 
 
 class MixedServer:
-    """2D and 3D requests: a 2D BatchServer and a 3D BatchServer, each with its own batch (and
-    CUDA stream, so that the two batches' kernels overlap) and its own share of the memory
-    budget.  The 3D server's loop runs in a worker thread; the library releases the GIL in
-    every call, so neither loop waits for the other's host blocking."""
+    """2D and 3D requests: a 2D BatchServer and, for the 3D requests, either a 3D BatchServer
+    (mode3d "batch": its own batch, share of the memory budget and persistent grids taking
+    grid_share3d of the GPU) or one vrps_solve at a time in arrival order (mode3d "solve":
+    ordinary launches, so that the 2D batch's thread blocks interleave with them block by
+    block).  Each side runs on its own CUDA stream, the 2D one with the highest priority (its
+    short jobs wait least for SMs) and the 3D one with the lowest.  The 3D loop runs in a
+    worker thread; the library releases the GIL in every call, so neither loop waits for the
+    other's host blocking."""
 
     def __init__(self, pools: dict, pools3d: dict, budget_bytes: int, ticks_per_step: int = 2,
                  share3d: float = 0.5, ticks_per_step3d: int = 1, max_running: int | None = None,
-                 max_running3d: int | None = None, grid_share3d: float = 1.0):
-        # the 2D batch's stream gets the highest priority (its short jobs wait least for SMs),
-        # the 3D batch's the lowest, and its persistent grids may leave part of the GPU free
+                 max_running3d: int | None = None, grid_share3d: float = 1.0, mode3d: str = "batch"):
         self.s2 = BatchServer(pools, int(budget_bytes * (1.0 - share3d)), ticks_per_step, max_running=max_running,
                               priority=-1000)
-        self.s3 = BatchServer(pools3d, int(budget_bytes * share3d), ticks_per_step3d, max_running=max_running3d,
-                              priority=0, grid_share=grid_share3d)
+        if mode3d == "solve":
+            self.s3 = SequentialServer(pools3d, stream=torch.cuda.Stream(priority=0))   # 0: the lowest
+        else:
+            self.s3 = BatchServer(pools3d, int(budget_bytes * share3d), ticks_per_step3d, max_running=max_running3d,
+                                  priority=0, grid_share=grid_share3d)
         self.keys3 = set(pools3d)
 
     def run(self, requests: list, clock=time.perf_counter) -> ServerStats:
@@ -237,4 +245,5 @@ class MixedServer:
 
     def close(self):
         self.s2.close()
-        self.s3.close()
+        if hasattr(self.s3, "close"):
+            self.s3.close()
