@@ -81,7 +81,7 @@ WORKLOADS_3D = {
 # for all 16 jobs, against the same jobs one after another through vrps_solve.
 WORKLOADS_BATCH = {
     "batch64": dict(jobs=64, sides=(128, 256, 384, 512, 1024), n_min=10, n_max=30, p=0.1, fgp_iters=50,
-                    alpha=0.02, alpha_fov=True, epochs=20, estimator="SAGA", storage="BF16", correction_epochs=2,
+                    alpha=0.02, alpha_fov=True, epochs=20, estimator="SAGA", storage="BF16", correction_epochs=4,
                     seed=20260209, target_gap=1e-4, max_epochs=300),
     "batch3d_16": dict(dims=3, jobs=16, sides=(64, 96, 128), n_min=30, n_max=30, p=0.1, fgp_iters=50,
                        alpha=0.01, alpha_fov=True, epochs=3, estimator="SVRG", storage="FP32", correction_epochs=0,
@@ -1444,7 +1444,7 @@ def main():
                 "speedup_vs_per_job_fp32", "objective_rel_diff_vs_per_job_fp32", "batched_fp16_s",
                 "final_iterate_gap", "epochs_to_gap", "reconstructions_per_s", "gpu_launches")
         c4 = {k: b4[k] for k in keys if k in b4}
-        c4["storage"] = "bf16 + 2 float32 correction epochs (value); fp16 + 2 float32 epochs (batched_fp16_s)"
+        c4["storage"] = "bf16 + 4 float32 correction epochs (value); fp16 + 4 float32 epochs (batched_fp16_s)"
     if "c5" in legs and world == 1:
         c5 = serve_leg(vr, WORKLOADS_SERVE["serve"], rank, local)
     out = {
