@@ -40,7 +40,8 @@ WORKLOADS = {
     # (sweep 0.002 .. 10 with long FISTA runs); the workload's description leaves it open
     "par2d_512": dict(n=512, n_angles=720, n_bins=768, n_subsets=20, noise="poisson", alpha=1.0,
                       algo="VR_PROXSKIP", estimator="SVRG", p=0.1, fgp_iters=100, seed=20260209,
-                      target_gap=1e-4, max_epochs=150, fista_iters=10000, pdhg_iters=200000,
+                      # the paper's 2e5 PDHG iterations run in the sweep workload; 2e4 here as a check
+                      target_gap=1e-4, max_epochs=150, fista_iters=10000, pdhg_iters=20000,
                       # the same problem at the survey's proposed TV weight (reported beside the
                       # headline: its gap after a fixed epoch budget)
                       alpha_alt=0.01, alt_epochs=(50, 150, 300)),
@@ -1331,7 +1332,10 @@ def main():
 
     # F*: the lowest objective of two independent long reference runs (FISTA, and the paper's
     # preconditioned PDHG for its reference solution) and of every value the solver evaluates
+    t_leg = time.perf_counter()
+    legs_s = {}
     ref = fstar_reference(vr, g, b_dev, w["alpha"], gamma, w["seed"], w["fista_iters"], w["pdhg_iters"])
+    legs_s["f_star_reference"] = round(time.perf_counter() - t_leg, 1)
     f_ref = ref["f_star"]
     max_it = w["max_epochs"] * N
     _, rep_tr, hist = vr.solve(b_dev, g, w["alpha"], w["algo"], p=w["p"], gamma=gamma, seed=w["seed"],
@@ -1418,12 +1422,16 @@ def main():
     t_adj = pp["adj2d_kernel"][1] / pp["adj2d_kernel"][0] / 1e3
     gvox = 2 * samples_sub / (t_fwd + t_adj) / 1e9
 
+    t_leg = time.perf_counter()
     alt = alt_alpha_leg(vr, g, b_dev, w, gamma, stream, flush) if w.get("alpha_alt") and "alt" in legs else None
+    legs_s["alpha_0.01"] = round(time.perf_counter() - t_leg, 1)
 
     cpu = None
     c1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and "c1" in legs:
+        t_leg = time.perf_counter()
         c1 = c1_measured_leg(vr, stream, flush)
+        legs_s["c1"] = round(time.perf_counter() - t_leg, 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         samp = oracle_sample(wl, P)
         counts = {"iterations": rep["iterations"], "prox_calls": rep["prox_calls"], "snapshots": rep["snapshots"]}
@@ -1439,14 +1447,18 @@ def main():
     # the served stream, measured in this run beside the headline
     c4 = c5 = None
     if "c4" in legs:
+        t_leg = time.perf_counter()
         b4 = batch_leg(vr, "batch64", rank, world, local, steps=1, warmup=1, dist=dist)
+        legs_s["c4"] = round(time.perf_counter() - t_leg, 1)
         keys = ("metric", "value", "unit", "config", "baseline_per_job_fp32_s", "batched_fp32_s",
                 "speedup_vs_per_job_fp32", "objective_rel_diff_vs_per_job_fp32", "batched_fp16_s",
                 "final_iterate_gap", "epochs_to_gap", "reconstructions_per_s", "gpu_launches")
         c4 = {k: b4[k] for k in keys if k in b4}
         c4["storage"] = "bf16 + 4 float32 correction epochs (value); fp16 + 4 float32 epochs (batched_fp16_s)"
     if "c5" in legs and world == 1:
+        t_leg = time.perf_counter()
         c5 = serve_leg(vr, WORKLOADS_SERVE["serve"], rank, local)
+        legs_s["c5"] = round(time.perf_counter() - t_leg, 1)
     out = {
         "metric": "s to 1e-4 rel. objective gap",
         "value": round(sec_per, 6),
@@ -1489,6 +1501,7 @@ def main():
         "batched_c4": c4,
         "served_c5": c5,
         "c1_50_epochs_measured": c1,
+        "leg_wall_s": legs_s,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
