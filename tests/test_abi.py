@@ -89,3 +89,10 @@ def test_null_handles_rejected(lib):
 def test_check_error_rejects_null_handle(lib):
     lib.vrps_check_error.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.vrps_check_error(None, None) == -1
+
+
+def test_batch_scheduling_knobs_reject_bad_input(lib):
+    lib.vrps_batch_set_grid_share.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    lib.vrps_batch_set_stream_priority.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.vrps_batch_set_grid_share(None, 0.5) == -1
+    assert lib.vrps_batch_set_stream_priority(None, 0) == -1

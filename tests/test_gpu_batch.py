@@ -89,6 +89,23 @@ def test_mix_bit_identical_to_solo(mix, graphs):
     B.close()
 
 
+def test_priority_and_grid_share_keep_bits(mix):
+    """A batch on a highest-priority stream whose persistent grids take a third of the GPU gives
+    the same bits (scheduling knobs only); both knobs are refused once a job was submitted."""
+    vr, probs, solo = mix
+    B = vr.Batch(priority=-100, grid_share=1.0 / 3.0)
+    ids = [B.submit(probs[i][1], dev(probs[i][2]), **_kw(MIX[i], probs[i][3], i)) for i in range(len(MIX))]
+    while B.step(4):
+        pass
+    for i, jid in enumerate(ids):
+        B.wait(jid)
+        assert torch.equal(B.result(jid), solo[i][0]), i
+    import ctypes
+    assert vr.lib.vrps_batch_set_grid_share(B.handle, ctypes.c_double(0.5)) == -1
+    assert vr.lib.vrps_batch_set_stream_priority(B.handle, 0) == -1
+    B.close()
+
+
 def test_staggered_admission_and_alone(mix):
     """Jobs joining while others run, and a job running alone, give the same bits."""
     vr, probs, solo = mix
