@@ -42,6 +42,7 @@ struct FgpTile {
   static constexpr int EX = TX + 2 * FB_T, EY = TY + 2 * FB_T, NE = EX * EY;
   static constexpr int NS = (NE + NT - 1) / NT;
   static constexpr size_t SMEM = sizeof(float) * 3 * NE;   // z (2 components) and x
+  static constexpr size_t SMEM_SHARED = sizeof(float) * 6 * NE;   // v, w, z, x: the batched variant
 };
 using TileLarge = FgpTile<32, 32, 512>;   // 48 x 48 grown tile, 27 KB
 using TileWide = FgpTile<32, 16, 256>;    // 48 x 32, 18 KB: twice the tiles of TileLarge
@@ -186,6 +187,139 @@ __device__ __forceinline__ void fgp2d_block_item(const FgpBlockArgs& A, int bx, 
   } else {
     if (interior) fgp2d_block_regs<TL, true, false>(A, ox, oy, sz1, sz2, sx);
     else fgp2d_block_regs<TL, false, false>(A, ox, oy, sz1, sz2, sx);
+  }
+}
+
+// The batched launches' variant of the block: v, w, z and x of the grown tile all in shared
+// memory (17 shared accesses per pixel-iteration, but few registers, so three or four CTAs of
+// the persistent grid share an SM).  Same operations in the same order as fgp2d_block_regs:
+// the same bits.  One block of nsteps FGP iterations.  INTERIOR: the grown tile
+// lies strictly inside the image (no boundary or bounds tests needed).
+template <class TL, bool INTERIOR, bool NONNEG>
+__device__ __forceinline__ void fgp2d_steps_smem(float* sv, float* w1, float* w2, float* z1, float* z2, float* sx, int ox,
+                                            int oy, int nx, int ny, float tau, float step, const MomBlock& mom,
+                                            int nsteps) {
+  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT, NS = TL::NS;
+  const int tid = threadIdx.x;
+  // x at step s needs z at i-1, i-EX: valid on [s+1, EX-s); w' also needs x at i+1, i+EX:
+  // valid on [s+1, EX-s-1).  dx / dw = largest step at which the slot is still inside.
+  int dx[NS], dw[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const int e = tid + k * NT;
+    const int lx = e % EX, ly = e / EX;
+    const int a = min(lx - 1, ly - 1);
+    dx[k] = e < NE ? min(a, min(EX - 1 - lx, EY - 1 - ly)) : -1;
+    dw[k] = e < NE ? min(a, min(EX - 2 - lx, EY - 2 - ly)) : -1;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (dx[k] >= s) {
+        const int i = tid + k * NT;
+        float xv = 0.f;
+        const int gx = ox + i % EX, gy = oy + i / EX;
+        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+          float d = 0.f;
+          if (INTERIOR || gx < nx - 1) d += z1[i];
+          if (INTERIOR || gx > 0) d -= z1[i - 1];
+          if (INTERIOR || gy < ny - 1) d += z2[i];
+          if (INTERIOR || gy > 0) d -= z2[i - EX];
+          xv = fmaf(tau, d, sv[i]);
+          if (NONNEG) xv = fmaxf(xv, 0.f);
+        }
+        sx[i] = xv;
+      }
+    }
+    __syncthreads();
+    const float m = mom.c[s];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (dw[k] >= s) {
+        const int i = tid + k * NT;
+        float n1 = 0.f, n2 = 0.f, m1 = 0.f, m2 = 0.f;
+        const int gx = ox + i % EX, gy = oy + i / EX;
+        if (INTERIOR || (gx >= 0 && gx < nx && gy >= 0 && gy < ny)) {
+          const float xc = sx[i];
+          const float d1 = (INTERIOR || gx < nx - 1) ? sx[i + 1] - xc : 0.f;
+          const float d2 = (INTERIOR || gy < ny - 1) ? sx[i + EX] - xc : 0.f;
+          ball2(fmaf(step, d1, z1[i]), fmaf(step, d2, z2[i]), n1, n2);
+          m1 = fmaf(m, n1 - w1[i], n1);
+          m2 = fmaf(m, n2 - w2[i], n2);
+        }
+        w1[i] = n1;
+        w2[i] = n2;
+        z1[i] = m1;
+        z2[i] = m2;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One output tile (bx, by) of a blocked launch with the whole grown tile in shared memory;
+// smf: dynamic shared memory (TL::SMEM_SHARED bytes).
+template <class TL>
+__device__ __forceinline__ void fgp2d_block_item_smem(const FgpBlockArgs& A, int bx, int by, float* smf) {
+  constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT;
+  const float* __restrict__ v = A.v;
+  const float* __restrict__ w_g = A.w;
+  const float* __restrict__ z_g = A.z;
+  float* __restrict__ wn_g = A.wn;
+  float* __restrict__ zn_g = A.zn;
+  const int nx = A.nx, ny = A.ny, nsteps = A.nsteps;
+  const float tau = A.tau, step = A.step;
+  const MomBlock& mom = A.mom;
+  float* sv = smf;
+  float* w1 = sv + NE;
+  float* w2 = w1 + NE;
+  float* z1 = w2 + NE;
+  float* z2 = z1 + NE;
+  float* sx = z2 + NE;
+  const int tid = threadIdx.x;
+  const int ox = bx * TL::TX - FB_T, oy = by * TL::TY - FB_T;
+  const size_t n = (size_t)nx * ny;
+  for (int i = tid; i < NE; i += NT) {
+    const int gx = ox + i % EX, gy = oy + i / EX;
+    float vv = 0.f, a = 0.f, b = 0.f, za = 0.f, zb = 0.f;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      const size_t p = (size_t)gy * nx + gx;
+      vv = v[p];
+      a = w_g[p];
+      b = w_g[n + p];
+      za = z_g[p];
+      zb = z_g[n + p];
+    }
+    sv[i] = vv;
+    w1[i] = a;
+    w2[i] = b;
+    z1[i] = za;
+    z2[i] = zb;
+  }
+  __syncthreads();
+  const bool interior = ox >= 1 && oy >= 1 && ox + EX <= nx - 1 && oy + EY <= ny - 1;
+  if (A.nonneg) {
+    if (interior)
+      fgp2d_steps_smem<TL, true, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+    else
+      fgp2d_steps_smem<TL, false, true>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+  } else {
+    if (interior)
+      fgp2d_steps_smem<TL, true, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+    else
+      fgp2d_steps_smem<TL, false, false>(sv, w1, w2, z1, z2, sx, ox, oy, nx, ny, tau, step, mom, nsteps);
+  }
+  for (int q = tid; q < TL::TX * TL::TY; q += NT) {
+    const int lx = FB_T + q % TL::TX, ly = FB_T + q / TL::TX;
+    const int gx = ox + lx, gy = oy + ly;
+    if (gx < nx && gy < ny) {
+      const size_t p = (size_t)gy * nx + gx;
+      const int i = ly * EX + lx;
+      wn_g[p] = w1[i];
+      wn_g[n + p] = w2[i];
+      zn_g[p] = z1[i];
+      zn_g[n + p] = z2[i];
+    }
   }
 }
 
@@ -652,7 +786,7 @@ __device__ __forceinline__ int fgp_batch_next(unsigned* counter, int* s_item) {
   return *s_item;
 }
 
-__global__ void __launch_bounds__(TileLarge::NT, 2) fgp2d_block_batched_kernel(char* __restrict__ slot, int b) {
+__global__ void __launch_bounds__(TileLarge::NT) fgp2d_block_batched_kernel(char* __restrict__ slot, int b) {
   extern __shared__ float smf[];
   __shared__ int pre[BATCH_MAX_JOBS + 1];
   __shared__ int s_item;
@@ -669,7 +803,7 @@ __global__ void __launch_bounds__(TileLarge::NT, 2) fgp2d_block_batched_kernel(c
     const int j = fgp_batch_job(pre, n, item);
     const BatchFgp& J = jobs[j];
     const int local = item - pre[j];
-    fgp2d_block_item<TileLarge>(J.A[b], local % J.tiles_x, local / J.tiles_x, smf);
+    fgp2d_block_item_smem<TileLarge>(J.A[b], local % J.tiles_x, local / J.tiles_x, smf);
   }
 }
 
@@ -697,9 +831,9 @@ __global__ void __launch_bounds__(256) fgp2d_out_batched_kernel(char* __restrict
 }  // namespace
 
 int fgp2d_block_batched(char* slot, int b, int grid, cudaStream_t s) {
-  VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM));
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM_SHARED));
   LaunchScope _ls("fgp2d_block_batched", s);
-  VRPS_CUDA(launch_kernel(fgp2d_block_batched_kernel, dim3(grid), dim3(TileLarge::NT), (size_t)TileLarge::SMEM, s,
+  VRPS_CUDA(launch_kernel(fgp2d_block_batched_kernel, dim3(grid), dim3(TileLarge::NT), (size_t)TileLarge::SMEM_SHARED, s,
                           slot, b));
   return VRPS_OK;
 }
@@ -716,9 +850,9 @@ int batched_grid(int which, size_t smem, int* grid) {
   VRPS_CUDA(cudaGetDevice(&dev));
   VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (which == 2) {
-    VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM));
+    VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM_SHARED));
     VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_block_batched_kernel, TileLarge::NT,
-                                                             TileLarge::SMEM));
+                                                             TileLarge::SMEM_SHARED));
   } else {
     VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_out_batched_kernel, 256, 0));
   }
