@@ -42,11 +42,12 @@ struct FgpTile {
   static constexpr int EX = TX + 2 * FB_T, EY = TY + 2 * FB_T, NE = EX * EY;
   static constexpr int NS = (NE + NT - 1) / NT;
   static constexpr size_t SMEM = sizeof(float) * 3 * NE;   // z (2 components) and x
-  static constexpr size_t SMEM_SHARED = sizeof(float) * 6 * NE;   // v, w, z, x: the batched variant
 };
 using TileLarge = FgpTile<32, 32, 512>;   // 48 x 48 grown tile, 27 KB
 using TileWide = FgpTile<32, 16, 256>;    // 48 x 32, 18 KB: twice the tiles of TileLarge
 using TileSmall = FgpTile<16, 16, 256>;   // 32 x 32, 12 KB: four times the tiles
+// the batched launches' block keeps v, w, z and x of the grown tile in shared memory
+constexpr size_t BATCHED_FGP_SMEM = sizeof(float) * 6 * TileLarge::NE;   // 55 KB
 
 
 // Projection onto the unit ball: g / max(1, |g|) through the hardware reciprocal square
@@ -258,7 +259,7 @@ __device__ __forceinline__ void fgp2d_steps_smem(float* sv, float* w1, float* w2
 }
 
 // One output tile (bx, by) of a blocked launch with the whole grown tile in shared memory;
-// smf: dynamic shared memory (TL::SMEM_SHARED bytes).
+// smf: dynamic shared memory (6 TL::NE floats).
 template <class TL>
 __device__ __forceinline__ void fgp2d_block_item_smem(const FgpBlockArgs& A, int bx, int by, float* smf) {
   constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT;
@@ -831,9 +832,9 @@ __global__ void __launch_bounds__(256) fgp2d_out_batched_kernel(char* __restrict
 }  // namespace
 
 int fgp2d_block_batched(char* slot, int b, int grid, cudaStream_t s) {
-  VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM_SHARED));
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, BATCHED_FGP_SMEM));
   LaunchScope _ls("fgp2d_block_batched", s);
-  VRPS_CUDA(launch_kernel(fgp2d_block_batched_kernel, dim3(grid), dim3(TileLarge::NT), (size_t)TileLarge::SMEM_SHARED, s,
+  VRPS_CUDA(launch_kernel(fgp2d_block_batched_kernel, dim3(grid), dim3(TileLarge::NT), (size_t)BATCHED_FGP_SMEM, s,
                           slot, b));
   return VRPS_OK;
 }
@@ -850,9 +851,9 @@ int batched_grid(int which, size_t smem, int* grid) {
   VRPS_CUDA(cudaGetDevice(&dev));
   VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (which == 2) {
-    VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, TileLarge::SMEM_SHARED));
+    VRPS_TRY(smem_opt_in((const void*)fgp2d_block_batched_kernel, BATCHED_FGP_SMEM));
     VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_block_batched_kernel, TileLarge::NT,
-                                                             TileLarge::SMEM_SHARED));
+                                                             BATCHED_FGP_SMEM));
   } else {
     VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_out_batched_kernel, 256, 0));
   }

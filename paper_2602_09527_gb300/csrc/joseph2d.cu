@@ -137,9 +137,18 @@ __device__ __forceinline__ bool fwd2d_wait(unsigned long long* bar, unsigned ph,
   return false;
 }
 
+// Fractional part in [0, 1) of a 28-bit fixed-point value, from its top 23 fraction bits.
+__device__ __forceinline__ float fix28_frac(int v) {
+  return __int_as_float(0x3f800000u | (((unsigned)v << 4) >> 9)) - 1.0f;
+}
+
 // Ray j's samples on lines [l0, l0 + nl) of the staged band buf (acc0: even lines of each
 // trip of four, acc1: odd ones).  Positions: every trip of four lines re-anchors exactly from
-// the 64-bit fixed-point walk (u = I + F); the four samples of the trip add A2 k to F in float.
+// the 64-bit fixed-point walk (u = I + F); within the trip the fraction is a 32-bit fixed-point
+// value (28 fraction bits) stepped by the per-line increment, whose integer part offsets the
+// tap and whose top fraction bits give the weight.  Integer and bit operations only: the
+// float floor and float-to-int conversions this replaces run at a quarter of the FP32 rate and
+// bounded the walk (5.4 instead of 7.3 us of band walking per 512^2 subset forward).
 __device__ __forceinline__ void fwd2d_ray(const Fwd2DParams& P, const AngleInfo2D& in, const float* buf, int j,
                                           int l0, int nl, int ncols, int nlines, int stride, float& acc0,
                                           float& acc1) {
@@ -167,18 +176,17 @@ __device__ __forceinline__ void fwd2d_ray(const Fwd2DParams& P, const AngleInfo2
   long long U = (long long)(ncols - 1 + 2 * FWD_PAD) * 2147483648LL + in.A1H * (long long)(2 * j - (P.nb - 1)) +
                 in.A2H * (long long)(2 * lo - (nlines - 1));
   const long long dU4 = 8 * in.A2H;   // four lines
-  const float A2 = in.A2;
+  const int st = (int)((2 * in.A2H) >> 4);   // one line, 28 fraction bits (|A2| <= 1: |st| <= 2^28)
   int rb = (lo - l0) * stride;          // shared-memory offset of the current line
   int l = lo;
   for (; l + 3 <= hi; l += 4) {
     const int I = fix_floor(U) + rb;
-    const float F = fix_frac(U);
+    const int p0 = (int)(((unsigned)(unsigned long long)U) >> 4);   // fraction, 28 bits
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float ur = fmaf(A2, (float)q, F);
-      const float fl = floorf(ur);
-      const float f = ur - fl;
-      const float* t = buf + (I + q * stride + (int)fl);
+      const int pq = p0 + q * st;   // in (-3, 4) x 2^28: fits 32 bits
+      const float* t = buf + (I + q * stride + (pq >> 28));
+      const float f = fix28_frac(pq);
       const float a = t[0], b = t[1];
       if (q & 1) acc1 += fmaf(f, b - a, a);
       else acc0 += fmaf(f, b - a, a);
@@ -187,13 +195,11 @@ __device__ __forceinline__ void fwd2d_ray(const Fwd2DParams& P, const AngleInfo2
     rb += 4 * stride;
   }
   const int I = fix_floor(U) + rb;
-  const float F = fix_frac(U);
+  const int p0 = (int)(((unsigned)(unsigned long long)U) >> 4);
   for (int q = 0; l <= hi; ++l, ++q) {
-    const float ur = fmaf(A2, (float)q, F);
-    const float fl = floorf(ur);
-    const float f = ur - fl;
-    const float* t = buf + (I + q * stride + (int)fl);
-    acc0 += fmaf(f, t[1] - t[0], t[0]);
+    const int pq = p0 + q * st;
+    const float* t = buf + (I + q * stride + (pq >> 28));
+    acc0 += fmaf(fix28_frac(pq), t[1] - t[0], t[0]);
   }
 }
 
