@@ -34,6 +34,17 @@ int cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? VRPS_ERR_OUT_OF_MEMORY : VRPS_ERR_CUDA;
 }
 
+int launch_fail(cudaError_t e, const char* name, const void* kern, dim3 grid, dim3 block, size_t smem) {
+  cudaGetLastError();   // a refused launch leaves no sticky error; clear the record of it
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, kern);
+  set_error("CUDA error %d (%s) launching %s: grid %u x %u, block %u x %u, %zu B dynamic shared memory "
+            "(kernel: %zu B static, at most %d B dynamic, %d registers)",
+            (int)e, cudaGetErrorString(e), name, grid.x, grid.y, block.x, block.y, smem, fa.sharedSizeBytes,
+            fa.maxDynamicSharedSizeBytes, fa.numRegs);
+  return e == cudaErrorMemoryAllocation ? VRPS_ERR_OUT_OF_MEMORY : VRPS_ERR_CUDA;
+}
+
 int smem_opt_in(const void* kern, size_t bytes) {
   if (bytes <= 48 * 1024) return VRPS_OK;
   static std::mutex mu;

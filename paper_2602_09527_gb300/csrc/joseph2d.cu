@@ -344,26 +344,32 @@ __global__ void __launch_bounds__(FWD_THREADS) fwd2d_kernel(Fwd2DParams P) {
 }
 
 
-// Pixel-driven transpose.  Per angle of a chunk, one thread stages the tile's detector
-// footprint: the tile origin's fractional bin t0 = J0 + F0 is exact (fixed point); the
-// footprint r[jlo .. jlo+fp) is copied to shared memory pre-multiplied by the angle's
-// length factor.  A pixel at tile offset (tx, ty) then has t - J0 = F0 + Bx tx + By ty (a
-// small float) and receives max(0, 1 - |j - t|/hw) r_j from the bins within hw of t.
-// NC = 2 covers hw <= 1 (bins not finer than pixels): two candidates, unrolled; NC = 0 is
-// the general loop over P.nc candidates.
+// Pixel-driven transpose.  Per angle of a chunk, one thread derives the tile's constants: the
+// tile origin's fractional bin t0 = J0 + F0 is exact (fixed point), and the footprint
+// r[jlo .. jlo+fp) is gathered into shared memory (asynchronous 4-byte copies, bins outside
+// [0, nb) zero-filled).  A pixel at tile offset (tx, ty) has t - J0 = F0 + Bx tx + By ty (a
+// small float) and receives wgt max(0, 1 - |j - t|/hw) r_j from the bins within hw of t; the
+// length factor wgt is folded into the per-angle weight constants.  NC = 2 covers hw <= 1
+// (bins not finer than pixels): only bins floor(t) and floor(t) + 1 can be within hw, with
+// weights wgt max(0, 1 - phi/hw) and wgt max(0, 1 - (1 - phi)/hw), phi = t - floor(t).  NC = 0
+// is the general loop over P.nc candidates from floor(t - hw) + 1 on.
 struct AdjShared {
   unsigned last;           // this CTA completed the tile (angle shares)
-  float4 par[ADJ_CHUNK];   // Bx, By, (F0 - hw), 1/hw
-  float c0[ADJ_CHUNK];     // 1 - hw
+  float4 par[ADJ_CHUNK];   // Bx, By, F0 (NC = 2) or F0 - hw (NC = 0), wgt/hw
+  float2 par2[ADJ_CHUNK];  // NC = 2: wgt, wgt (1 - 1/hw); NC = 0: wgt, hw
   int off[ADJ_CHUNK];      // J0 - jlo
   int jlo[ADJ_CHUNK];
-  float wgt[ADJ_CHUNK];
   float tile[32][ADJ_TX + 1];
 };
 
-// One pixel tile (bx, by) of the transpose; sm: dynamic shared [chunk][fp].  The update's
-// per-pixel inputs are loaded before the angle loop (single-share launches), so that their
-// latency hides behind the gather.
+// Asynchronous 4-byte global -> shared copy; ok = false zero-fills the destination instead.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(global_addr(src)),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+
+// One pixel tile (bx, by) of the transpose; sm: dynamic shared [chunk][fp].
 template <int NC, int PPT>
 __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by, float* sm, AdjShared& S,
                                            int part = 0) {
@@ -371,12 +377,8 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
   // angle range of this item: part `part` of P.split equal shares of the launch's rows
   const int ra = (int)(((long long)P.rows * part) / P.split);
   const int rz = (int)(((long long)P.rows * (part + 1)) / P.split);
-  float4* s_par = S.par;
-  float* s_c0 = S.c0;
-  int* s_off = S.off;
-  int* s_jlo = S.jlo;
-  float* s_wgt = S.wgt;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ADJ_TX + tx;
+  const int lane = tid & 31, warp = tid >> 5;
   const int ix0 = bx * ADJ_TX, iy0 = by * TY;
   const float ftx = (float)tx, fty = (float)ty;
   const float half_rows = (float)(TY / 2);
@@ -391,53 +393,66 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
       const float F0 = fix_frac(T0);
       const float tmin = F0 + fminf(0.f, in.Bx * (float)(ADJ_TX - 1)) + fminf(0.f, in.By * (float)(TY - 1));
       const int jlo = J0 + (int)floorf(tmin - in.hw) - 1;
-      s_par[tid] = make_float4(in.Bx, in.By, F0 - in.hw, in.inv_hw);
-      s_c0[tid] = 1.f - in.hw;
-      s_off[tid] = J0 - jlo;
-      s_jlo[tid] = jlo;
-      s_wgt[tid] = in.wgt;
+      const float wiw = in.wgt * in.inv_hw;
+      if (NC == 2) {
+        S.par[tid] = make_float4(in.Bx, in.By, F0, wiw);
+        S.par2[tid] = make_float2(in.wgt, in.wgt - wiw);
+      } else {
+        S.par[tid] = make_float4(in.Bx, in.By, F0 - in.hw, wiw);
+        S.par2[tid] = make_float2(in.wgt, in.hw);
+      }
+      S.off[tid] = J0 - jlo;
+      S.jlo[tid] = jlo;
     }
     __syncthreads();
-    for (int e = tid; e < nr * P.fp; e += ADJ_THREADS) {
-      const int q = e / P.fp;
-      const int j = s_jlo[q] + (e - q * P.fp);
-      sm[e] = (j >= 0 && j < P.nb) ? s_wgt[q] * __ldg(P.r + (size_t)(r0 + q) * P.nb + j) : 0.f;
+    // footprint gather: warp w copies the rows of angles w, w + 8, ...; every copy is issued
+    // before any is waited for
+    for (int q = warp; q < nr; q += ADJ_THREADS / 32) {
+      const int jl = S.jlo[q];
+      const float* __restrict__ rq = P.r + (size_t)(r0 + q) * P.nb;
+      float* dq = sm + q * P.fp;
+      for (int k = lane; k < P.fp; k += 32) {
+        const int j = jl + k;
+        const bool ok = j >= 0 && j < P.nb;
+        cp_async4(dq + k, rq + (ok ? j : 0), ok);
+      }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     for (int q = 0; q < nr; ++q) {
-      const float4 pr = s_par[q];
-      const float* row = sm + q * P.fp + s_off[q] + 1;   // row[floor(ua)] = first candidate
-      const float ua = fmaf(pr.y, fty, fmaf(pr.x, ftx, pr.z));   // (t - J0) - hw
+      const float4 pr = S.par[q];
+      const float2 p2 = S.par2[q];
+      const float* row = sm + q * P.fp + S.off[q];   // row[k] = bin J0 + k
+      const float ua = fmaf(pr.y, fty, fmaf(pr.x, ftx, pr.z));
       const float ub = fmaf(pr.y, half_rows, ua);
       if (NC == 2) {
-        const float c0 = s_c0[q];
         {
           const float fl = floorf(ua);
-          const float d0 = c0 - (ua - fl);
-          const float w0 = fmaxf(0.f, fmaf(-fabsf(d0), pr.w, 1.f));
-          const float w1 = fmaxf(0.f, fmaf(-(d0 + 1.f), pr.w, 1.f));
+          const float ph = ua - fl;
+          const float w0 = fmaxf(0.f, fmaf(-ph, pr.w, p2.x));
+          const float w1 = fmaxf(0.f, fmaf(ph, pr.w, p2.y));
           const float* rr = row + (int)fl;
           acc0 = fmaf(w0, rr[0], acc0);
           acc0 = fmaf(w1, rr[1], acc0);
         }
         if (PPT == 2) {
           const float fl = floorf(ub);
-          const float d0 = c0 - (ub - fl);
-          const float w0 = fmaxf(0.f, fmaf(-fabsf(d0), pr.w, 1.f));
-          const float w1 = fmaxf(0.f, fmaf(-(d0 + 1.f), pr.w, 1.f));
+          const float ph = ub - fl;
+          const float w0 = fmaxf(0.f, fmaf(-ph, pr.w, p2.x));
+          const float w1 = fmaxf(0.f, fmaf(ph, pr.w, p2.y));
           const float* rr = row + (int)fl;
           acc1 = fmaf(w0, rr[0], acc1);
           acc1 = fmaf(w1, rr[1], acc1);
         }
       } else {
-        const float hw = 1.f - s_c0[q];
+        const float hw = p2.y;
         const float fa = floorf(ua), fb = floorf(ub);
-        const float* ra = row + (int)fa;
-        const float* rb = row + (int)fb;
+        const float* ra_ = row + 1 + (int)fa;
+        const float* rb_ = row + 1 + (int)fb;
         const float da = fa + 1.f - (ua + hw), db = fb + 1.f - (ub + hw);   // first candidate - t
         for (int c = 0; c < P.nc; ++c) {
-          acc0 = fmaf(fmaxf(0.f, fmaf(-fabsf(da + (float)c), pr.w, 1.f)), ra[c], acc0);
-          if (PPT == 2) acc1 = fmaf(fmaxf(0.f, fmaf(-fabsf(db + (float)c), pr.w, 1.f)), rb[c], acc1);
+          acc0 = fmaf(fmaxf(0.f, fmaf(-fabsf(da + (float)c), pr.w, p2.x)), ra_[c], acc0);
+          if (PPT == 2) acc1 = fmaf(fmaxf(0.f, fmaf(-fabsf(db + (float)c), pr.w, p2.x)), rb_[c], acc1);
         }
       }
     }
@@ -590,7 +605,7 @@ int fwd2d(const vrps_geom* g, const float* x, const float* xT, const int* ids, i
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("fwd2d_kernel", s, 4.0 * g->n + fwd_mode_bytes(mode, (size_t)rows * g->n_bins, o.store));
-    VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
+    VRPS_LAUNCH("fwd2d_kernel", kern, dim3(grid), dim3(block), (size_t)(smem), s, P);
     return VRPS_OK;
   };
   const bool grouped = bulk && P.group > 1;
@@ -679,7 +694,7 @@ int adj2d(const vrps_geom* g, const float* r, const int* ids, int rows, const Up
   auto launch = [&](auto kern) -> int {
     VRPS_TRY(smem_opt_in((const void*)kern, smem));
     LaunchScope _ls("adj2d_kernel", s, 4.0 * rows * g->n_bins + update_bytes(u, (size_t)g->n));
-    VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(block), (size_t)(smem), s, P));
+    VRPS_LAUNCH("adj2d_kernel", kern, dim3(grid), dim3(block), (size_t)(smem), s, P);
     return VRPS_OK;
   };
   switch (variant) {
@@ -792,14 +807,14 @@ int fwd2d_batched(char* slot, int grid, size_t smem, bool grouped, cudaStream_t 
   auto kern = grouped ? fwd2d_batched_kernel<FWD_RPT> : fwd2d_batched_kernel<0>;
   VRPS_TRY(smem_opt_in((const void*)kern, smem));
   LaunchScope _ls("fwd2d_batched", s);
-  VRPS_CUDA(launch_kernel(kern, dim3(grid), dim3(FWD_THREADS), smem, s, slot));
+  VRPS_LAUNCH("fwd2d_batched", kern, dim3(grid), dim3(FWD_THREADS), smem, s, slot);
   return VRPS_OK;
 }
 
 int adj2d_batched(char* slot, int grid, size_t smem, cudaStream_t s) {
   VRPS_TRY(smem_opt_in((const void*)adj2d_batched_kernel, smem));
   LaunchScope _ls("adj2d_batched", s);
-  VRPS_CUDA(launch_kernel(adj2d_batched_kernel, dim3(grid), dim3(ADJ_TX, ADJ_THREADS / ADJ_TX), smem, s, slot));
+  VRPS_LAUNCH("adj2d_batched", adj2d_batched_kernel, dim3(grid), dim3(ADJ_TX, ADJ_THREADS / ADJ_TX), smem, s, slot);
   return VRPS_OK;
 }
 

@@ -18,6 +18,8 @@ namespace vrps {
 void set_error(const char* fmt, ...);
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+// A refused kernel launch: the error with the launch's configuration and the kernel's limits.
+int launch_fail(cudaError_t e, const char* name, const void* kern, dim3 grid, dim3 block, size_t smem);
 
 #define VRPS_CUDA(call)                                        \
   do {                                                         \
@@ -67,6 +69,13 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
   cfg.numAttrs = 0;
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
+
+// launch_kernel, returning launch_fail's status from the enclosing function when refused.
+#define VRPS_LAUNCH(name, kern, grid, block, smem, s, ...)                                      \
+  do {                                                                                          \
+    const cudaError_t _le = ::vrps::launch_kernel(kern, grid, block, smem, s, __VA_ARGS__);      \
+    if (_le != cudaSuccess) return ::vrps::launch_fail(_le, name, (const void*)(kern), grid, block, smem); \
+  } while (0)
 
 // Opt a kernel into `bytes` of dynamic shared memory on the current device (cached: the
 // runtime call is made once per kernel, device and size).
