@@ -113,7 +113,8 @@ int vrps_geom_samples(const vrps_geom* g, int subset, int64_t* samples);
  * doubles): chosen band bytes, pixels per thread, tuned forward + adjoint time in
  * microseconds, bands per CTA; the adjoint's angle shares per pixel tile (1, 2, 4: partial sums
  * added in share order by the last share) are timed with the pixels per thread, and the 2D FGP
- * output tile (32 x 32, 32 x 16 or 16 x 16) on a 16-iteration prox call (see vrps_launch_shape);
+ * output tile (32 wide with a balanced height, 32 x 16 or 16 x 16) on a 32-iteration prox call
+ * (see vrps_launch_shape);
  * with more than one subset the all-angle forward and adjoint get their own band / bands per
  * CTA and angle shares, timed on the full sinogram (see vrps_launch_shape_full).
  * 3D geometries: times three iterations of the streaming FGP prox for chunks of 4 ... 128 z
@@ -126,7 +127,9 @@ int vrps_autotune(vrps_geom* g, int reps, double* out4, vrps_stream_t stream);
 
 /* Sets the launch shapes by hand (0 = built-in default for each): forward band bytes, forward
  * bands per CTA, adjoint pixels per thread (2D: 1 or 2; 3D: voxels per thread along z, 16 or
- * 32), 3D FGP planes per chunk, 2D FGP output tile (0: 32 x 32, 1: 32 x 16, 2: 16 x 16),
+ * 32), 3D FGP planes per chunk, 2D FGP output tile (0: 32 columns by 32 or 27 rows, whichever
+ * gives the busiest SM less work when the tiles are spread over the SMs -- 27 at 512^2 and
+ * 1024^2 on 152 SMs; 1: 32 x 16; 2: 16 x 16; 3: 32 x 32; 4: 32 x 27; all give the same bits),
  * adjoint angle shares per tile.  Errors: INVALID_ARG. */
 int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int adj_pixels_per_thread,
                           int fgp3_chunk, int fgp_tile, int adj_split);

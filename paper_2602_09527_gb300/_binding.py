@@ -252,7 +252,7 @@ def autotune(g: Geometry, reps: int = 5, stream=None) -> dict:
     shape = launch_shape(g)
     full = launch_shape_full(g)
     return {"fwd_band_bytes": int(out[0]), "fwd_bands_per_cta": int(out[3]), "adj_pixels_per_thread": int(out[1]),
-            "adj_angle_shares": max(1, shape[5]), "fgp_tile": ["32x32", "32x16", "16x16"][shape[4]],
+            "adj_angle_shares": max(1, shape[5]), "fgp_tile": ["32x32|27", "32x16", "16x16", "32x32", "32x27"][shape[4]],
             "fwd_adj_us": float(out[2]),
             "all_angles": {"fwd_band_bytes": full[0], "fwd_bands_per_cta": full[1], "adj_angle_shares": full[2]}}
 

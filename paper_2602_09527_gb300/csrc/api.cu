@@ -731,9 +731,12 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
     }
     g->tune_full_adj_split = fs;
   }
-  // 2D FGP output tile, timed on one 16-iteration prox call
+  // 2D FGP output tile, timed on one 32-iteration prox call of a uniform random image with a
+  // TV weight that saturates most of the dual (as in reconstructions: the projection onto the
+  // unit ball is then active at most pixels)
   {
     VRPS_TRY(ensure(&w.dual, 2 * (size_t)g->n));
+    VRPS_TRY(philox_uniform(0x5eedULL, 0u, 7u, w.img, g->n, s));
     ProxTail t;
     std::memset(&t, 0, sizeof(t));
     t.out = w.img2;
@@ -744,7 +747,7 @@ int vrps_autotune(vrps_geom* g, int reps, double* out3, vrps_stream_t stream) {
       float tp = 0.f;
       const int rc = timed([&]() -> int {
         VRPS_CUDA(cudaMemsetAsync(w.dual, 0, sizeof(float) * 2 * (size_t)g->n, s));
-        return fgp_run(g, w.img, 0.01f, 16, 1, w.dual, t, s);
+        return fgp_run(g, w.img, 0.25f, 32, 1, w.dual, t, s);
       }, &tp);
       if (rc != VRPS_OK) {
         g->tune_fgp_tile = 0;
@@ -796,7 +799,7 @@ int vrps_set_launch_shape(vrps_geom* g, int fwd_band_bytes, int fwd_group, int a
                                       adj_pixels_per_thread == 32)
                                    : (adj_pixels_per_thread >= 0 && adj_pixels_per_thread <= 2);
   if (fwd_band_bytes < 0 || fwd_band_bytes > (200 << 10) || fwd_group < 0 || fwd_group > 64 || !adj_ok ||
-      fgp3_chunk < 0 || fgp_tile < 0 || fgp_tile > 2 || adj_split < 0 || adj_split > 64)
+      fgp3_chunk < 0 || fgp_tile < 0 || fgp_tile > 4 || adj_split < 0 || adj_split > 64)
     return fail(VRPS_ERR_INVALID_ARG, "launch shape out of range");
   if (g->dims == 3) {
     g->tune_adj3_zc = adj_pixels_per_thread;

@@ -46,6 +46,7 @@ struct FgpTile {
 using TileLarge = FgpTile<32, 32, 512>;   // 48 x 48 grown tile, 27 KB
 using TileWide = FgpTile<32, 16, 256>;    // 48 x 32, 18 KB: twice the tiles of TileLarge
 using TileSmall = FgpTile<16, 16, 256>;   // 32 x 32, 12 KB: four times the tiles
+using TileLow = FgpTile<32, 27, 512>;     // 48 x 43, 24 KB: 19 tile rows at 512 and 38 at 1024 rows
 // the batched launches' block keeps v, w, z and x of the grown tile in shared memory
 constexpr size_t BATCHED_FGP_SMEM = sizeof(float) * 6 * TileLarge::NE;   // 55 KB
 
@@ -665,6 +666,32 @@ int fgp_prepare(vrps_geom* g) {
   return VRPS_OK;
 }
 
+// The 32-wide tile for an nx x ny image: the busiest SM runs ceil(tiles / SMs) tiles, each
+// costing its grown tile's pixel-iterations over a block (the valid region shrinking one pixel
+// per side per iteration); the height (32 or 27 rows) with the least such work wins, 32 on
+// ties.  27 rows fill the resident slots evenly where 32 leave part of the last wave empty
+// (512^2: 304 tiles for 2 x 152 slots instead of 256).
+static bool fgp_low_tile(int nx, int ny) {
+  thread_local int last_dev = -1, last_nx = -1, last_ny = -1, sms = 0;
+  thread_local bool last_low = false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (dev == last_dev && nx == last_nx && ny == last_ny) return last_low;
+  if (dev != last_dev && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  auto cost = [&](int tx, int ty, int ex) {
+    const long long tiles = (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+    double work = 0.0;
+    for (int q = 0; q < FB_T; ++q) work += (double)(ex - 2 * q) * (double)(ty + 2 * FB_T - 2 * q);
+    return (double)((tiles + sms - 1) / sms) * work;
+  };
+  last_low = cost(TileLow::TX, TileLow::TY, TileLow::EX) < cost(TileLarge::TX, TileLarge::TY, TileLarge::EX);
+  last_dev = dev;
+  last_nx = nx;
+  last_ny = ny;
+  return last_low;
+}
+
 int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int nx, int ny, float tau, int iters,
                   int nonneg, int tile, cudaStream_t s, const float** w_final) {
   // blocks of FB_T iterations; the (w, z) state alternates between pairs[0] and pairs[1].  The
@@ -676,6 +703,7 @@ int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int
   VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLarge>, TileLarge::SMEM));
   VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileWide>, TileWide::SMEM));
   VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileSmall>, TileSmall::SMEM));
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLow>, TileLow::SMEM));
   const std::vector<MomBlock> moms = fgp_momentum(iters);
   const double n = (double)nx * ny;
   for (int k0 = 0; k0 < iters; k0 += FB_T) {
@@ -692,8 +720,11 @@ int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int
         dim3 grid((nx + TL::TX - 1) / TL::TX, (ny + TL::TY - 1) / TL::TY);
         return launch_kernel(kern, grid, dim3(TL::NT), (size_t)TL::SMEM, s, A);
       };
+      // tile 0: 32 x 32 or 32 x 27 by fgp_low_tile; 3: 32 x 32; 4: 32 x 27; 1, 2: smaller tiles
+      const bool low = tile == 4 || (tile == 0 && fgp_low_tile(nx, ny));
       if (tile == 1) VRPS_CUDA(launch(fgp2d_block<TileWide>, TileWide{}));
       else if (tile == 2) VRPS_CUDA(launch(fgp2d_block<TileSmall>, TileSmall{}));
+      else if (low) VRPS_CUDA(launch(fgp2d_block<TileLow>, TileLow{}));
       else VRPS_CUDA(launch(fgp2d_block<TileLarge>, TileLarge{}));
     }
     VRPS_LAUNCHED("fgp2d_block");

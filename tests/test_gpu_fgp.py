@@ -104,10 +104,11 @@ def test_fgp3d_after_autotune():
     assert rel(host(x), ref) < TOL
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
-@pytest.mark.parametrize("shape", [(70, 45), (16, 130)])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(70, 45), (16, 130), (300, 170)])
 def test_fgp2d_tiles(tile, shape):
-    """The three 2D output tiles the autotuner chooses from give the oracle's K-step FGP."""
+    """The 2D output tiles (the 32-wide one 32 or 27 rows high, chosen for the SM count, or
+    either by hand; 32 x 16; 16 x 16) give the oracle's K-step FGP."""
     vr, g = _geom2(shape[1], shape[0])
     vr.set_launch_shape(g, fgp_tile=tile)
     rng = np.random.default_rng(tile + shape[0])
@@ -119,3 +120,23 @@ def test_fgp2d_tiles(tile, shape):
     ref, wref = tv.fgp(v, 0.05, 21, w0=w0)
     assert rel(host(x), ref) < TOL
     assert rel(host(d), wref) < TOL
+
+
+@pytest.mark.parametrize("shape", [(512, 512), (1024, 1024), (200, 333)])
+def test_fgp2d_tiles_same_bits(shape):
+    """Temporal blocking recomputes the halo with the same operations, so every output tile
+    (and the balanced height the 32-wide tile takes at these sizes) gives identical bits,
+    dual included, and the result is the oracle's."""
+    vr, g = _geom2(shape[1], shape[0])
+    rng = np.random.default_rng(shape[0])
+    v = rng.uniform(-0.2, 4.0, size=shape)
+    outs = []
+    for tile in (0, 1, 2, 3, 4):
+        vr.set_launch_shape(g, fgp_tile=tile)
+        d = torch.zeros(2 * v.size, device="cuda")
+        x = vr.prox_tv(g, dev(v), 1.0, 20, dual=d)
+        outs.append((x.clone(), d.clone()))
+    for x, d in outs[1:]:
+        assert torch.equal(x, outs[0][0]) and torch.equal(d, outs[0][1])
+    ref, _ = tv.fgp(v, 1.0, 20)
+    assert rel(host(outs[0][0]), ref) < TOL
