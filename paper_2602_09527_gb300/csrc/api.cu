@@ -152,6 +152,8 @@ static void free_ws(Workspace& w) {
   if (w.fwd_part) cudaFree(w.fwd_part);
   if (w.fwd_count) cudaFree(w.fwd_count);
   if (w.dev_error) cudaFree(w.dev_error);
+  if (w.fgp_bar) cudaFree(w.fgp_bar);
+  w.fgp_bar = nullptr;
   if (w.adj_part) cudaFree(w.adj_part);
   if (w.adj_count) cudaFree(w.adj_count);
   if (w.scalars) cudaFree(w.scalars);

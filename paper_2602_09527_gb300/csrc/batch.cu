@@ -859,7 +859,7 @@ int vrps_batch_submit(vrps_batch* B, const vrps_job* d, int* id) {
   if (!(d->p > 0.0 && d->p <= 1.0)) return fail(VRPS_ERR_INVALID_ARG, "p must be in (0, 1]");
   if (!(d->gamma > 0.0) || !std::isfinite(d->gamma)) return fail(VRPS_ERR_INVALID_ARG, "gamma must be > 0");
   if (d->max_iters <= 0) return fail(VRPS_ERR_INVALID_ARG, "max_iters must be > 0");
-  const int max_fgp = g->dims == 3 ? BATCH3_MAX_ITERS : FB_T * BATCH_MAX_BLOCKS;
+  const int max_fgp = g->dims == 3 ? BATCH3_MAX_ITERS : BATCH_MAX_FGP_ITERS;
   if (d->fgp_iters < 0 || d->fgp_iters > max_fgp)
     return fail(VRPS_ERR_INVALID_ARG, "fgp_iters must be in [0, %d]", max_fgp);
   if (d->estimator < VRPS_EST_SVRG || d->estimator > VRPS_EST_SGD)

@@ -5,8 +5,9 @@
 //   x    = P_+( v + tau div z )            (D^T = -div, forward differences, Neumann)
 //   w'   = P_B( z + D x / (4 d tau) )      (d = 2 or 3)
 //   z'   = w' + mom_k (w' - w)             (mom from t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2)
-// Kernels store only w_k and w_{k-1} and rebuild z on the fly.  2D runs FB_T iterations
-// per launch on shared-memory tiles (temporal blocking); 3D runs one iteration per launch
+// Kernels store only w_k and w_{k-1} and rebuild z on the fly.  2D runs blocks of FB_T
+// iterations on shared-memory tiles (temporal blocking), all blocks of a prox call in one
+// cooperative launch where the tiles fit the resident slots; 3D runs one iteration per launch
 // (reads v, w_k, w_{k-1}, writes w_{k+1}: 10 floats per voxel) with three rotating buffers,
 // so that no launch writes a buffer another CTA still reads.
 // The output kernel forms x+ = P_+(v + tau div w_K) and applies the fused tail of the
@@ -43,12 +44,13 @@ struct FgpTile {
   static constexpr int NS = (NE + NT - 1) / NT;
   static constexpr size_t SMEM = sizeof(float) * 3 * NE;   // z (2 components) and x
 };
-using TileLarge = FgpTile<32, 32, 512>;   // 48 x 48 grown tile, 27 KB
-using TileWide = FgpTile<32, 16, 256>;    // 48 x 32, 18 KB: twice the tiles of TileLarge
-using TileSmall = FgpTile<16, 16, 256>;   // 32 x 32, 12 KB: four times the tiles
-using TileLow = FgpTile<32, 27, 512>;     // 48 x 43, 24 KB: 19 tile rows at 512 and 38 at 1024 rows
+// (grown tiles for FB_T = 6)
+using TileLarge = FgpTile<32, 32, 512>;   // 44 x 44 grown tile, 23 KB
+using TileWide = FgpTile<32, 16, 256>;    // 44 x 28, 15 KB: twice the tiles of TileLarge
+using TileSmall = FgpTile<16, 16, 256>;   // 28 x 28, 9 KB: four times the tiles
+using TileLow = FgpTile<32, 27, 512>;     // 44 x 39, 20 KB: 19 tile rows at 512 and 38 at 1024 rows
 // the batched launches' block keeps v, w, z and x of the grown tile in shared memory
-constexpr size_t BATCHED_FGP_SMEM = sizeof(float) * 6 * TileLarge::NE;   // 55 KB
+constexpr size_t BATCHED_FGP_SMEM = sizeof(float) * 6 * TileLarge::NE;   // 46 KB
 
 
 // Projection onto the unit ball: g / max(1, |g|) through the hardware reciprocal square
@@ -70,7 +72,7 @@ __device__ __forceinline__ void ball2(float g1, float g2, float& n1, float& n2) 
 // INTERIOR: the grown tile lies strictly inside the image (no boundary or bounds tests).
 template <class TL, bool INTERIOR, bool NONNEG>
 __device__ __forceinline__ void fgp2d_block_regs(const FgpBlockArgs& A, int ox, int oy, float* sz1, float* sz2,
-                                                 float* sx) {
+                                                 float* sx, const float* mom) {
   constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE, NT = TL::NT, NS = TL::NS;
   const int tid = threadIdx.x;
   const int nx = A.nx, ny = A.ny, nsteps = A.nsteps;
@@ -90,12 +92,14 @@ __device__ __forceinline__ void fgp2d_block_regs(const FgpBlockArgs& A, int ox, 
     const int gx = ox + lx, gy = oy + ly;
     float vv = 0.f, w_a = 0.f, w_b = 0.f, z_a = 0.f, z_b = 0.f;
     if (e < NE && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+      // the dual state through L2 only: within a cooperative launch other CTAs rewrite these
+      // buffers between blocks, after this SM may have cached them
       const size_t p = (size_t)gy * nx + gx;
       vv = A.v[p];
-      w_a = A.w[p];
-      w_b = A.w[n + p];
-      z_a = A.z[p];
-      z_b = A.z[n + p];
+      w_a = __ldcg(A.w + p);
+      w_b = __ldcg(A.w + n + p);
+      z_a = __ldcg(A.z + p);
+      z_b = __ldcg(A.z + n + p);
     }
     rv[k] = vv;
     rw1[k] = w_a;
@@ -130,7 +134,7 @@ __device__ __forceinline__ void fgp2d_block_regs(const FgpBlockArgs& A, int ox, 
       }
     }
     __syncthreads();
-    const float m = A.mom.c[s];
+    const float m = mom[s];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       if (dw[k] >= s) {
@@ -173,10 +177,14 @@ __device__ __forceinline__ void fgp2d_block_regs(const FgpBlockArgs& A, int ox, 
   }
 }
 
-// One output tile (bx, by) of a blocked launch; smf: dynamic shared memory (TL::SMEM bytes).
+// One output tile (bx, by) of a blocked launch; smf: dynamic shared memory (TL::SMEM bytes);
+// mom: the block's momentum coefficients (FB_T + 1), staged in shared memory here.
 template <class TL>
-__device__ __forceinline__ void fgp2d_block_item(const FgpBlockArgs& A, int bx, int by, float* smf) {
+__device__ __forceinline__ void fgp2d_block_item(const FgpBlockArgs& A, int bx, int by, float* smf,
+                                                 const float* mom) {
   constexpr int EX = TL::EX, EY = TL::EY, NE = TL::NE;
+  __shared__ float s_mom[FB_T + 1];
+  if (threadIdx.x <= FB_T) s_mom[threadIdx.x] = mom[threadIdx.x];   // visible after the load phase
   float* sz1 = smf;
   float* sz2 = sz1 + NE;
   float* sx = sz2 + NE;
@@ -184,11 +192,11 @@ __device__ __forceinline__ void fgp2d_block_item(const FgpBlockArgs& A, int bx, 
   const int nx = A.nx, ny = A.ny;
   const bool interior = ox >= 1 && oy >= 1 && ox + EX <= nx - 1 && oy + EY <= ny - 1;
   if (A.nonneg) {
-    if (interior) fgp2d_block_regs<TL, true, true>(A, ox, oy, sz1, sz2, sx);
-    else fgp2d_block_regs<TL, false, true>(A, ox, oy, sz1, sz2, sx);
+    if (interior) fgp2d_block_regs<TL, true, true>(A, ox, oy, sz1, sz2, sx, s_mom);
+    else fgp2d_block_regs<TL, false, true>(A, ox, oy, sz1, sz2, sx, s_mom);
   } else {
-    if (interior) fgp2d_block_regs<TL, true, false>(A, ox, oy, sz1, sz2, sx);
-    else fgp2d_block_regs<TL, false, false>(A, ox, oy, sz1, sz2, sx);
+    if (interior) fgp2d_block_regs<TL, true, false>(A, ox, oy, sz1, sz2, sx, s_mom);
+    else fgp2d_block_regs<TL, false, false>(A, ox, oy, sz1, sz2, sx, s_mom);
   }
 }
 
@@ -328,7 +336,75 @@ __device__ __forceinline__ void fgp2d_block_item_smem(const FgpBlockArgs& A, int
 template <class TL>
 __global__ void __launch_bounds__(TL::NT, 2) fgp2d_block(const __grid_constant__ FgpBlockArgs A) {
   extern __shared__ float smf[];
-  fgp2d_block_item<TL>(A, blockIdx.x, blockIdx.y, smf);
+  fgp2d_block_item<TL>(A, blockIdx.x, blockIdx.y, smf, A.mom.c);
+}
+
+// All blocks of one 2D prox call in one cooperative launch (every CTA resident): CTA (bx, by)
+// runs its tile's block, and the CTAs meet at a grid barrier before the next block reads the
+// halos its neighbours wrote.  Same item function, same buffers, same order as one launch per
+// block: the same bits, without the relaunch between blocks.
+constexpr int FGP_COOP_MAX_BLOCKS = (256 + FB_T - 1) / FB_T;   // up to 256 iterations per prox call
+constexpr unsigned FGP_BARRIER_LIMIT = 1u << 22;   // bounded polls of a grid barrier
+struct FgpCoopArgs {
+  const float* v;
+  const float* w0;            // initial dual (also the first block's extrapolated dual)
+  float* pair[2][2];          // (w, z) buffer pairs, alternating per block
+  int nx, ny, iters, nblocks, nonneg;
+  float tau, step;
+  unsigned long long* bar;    // arrival counter, zero at launch
+  unsigned* err;              // device error word (bit 4: a barrier wait expired)
+  MomBlock mom[FGP_COOP_MAX_BLOCKS];
+};
+
+// Grid barrier number b (0-based) of nctas CTAs on a counter that was zero at launch: thread 0
+// publishes the CTA's writes, arrives, and polls (bounded) until every CTA has arrived b + 1
+// times; an expired wait sets the error word and lets the CTA go on (its results are then not
+// used: the host reports the timeout).
+__device__ __forceinline__ void fgp_grid_barrier(unsigned long long* bar, unsigned long long target, unsigned* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1ull);
+    unsigned long long seen = 0;
+    unsigned it = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(bar) : "memory");
+      if (seen >= target || ++it >= FGP_BARRIER_LIMIT) break;
+      __nanosleep(32);
+    }
+    if (seen < target) atomicOr(err, 4u);
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <class TL>
+__global__ void __launch_bounds__(TL::NT, 2) fgp2d_coop(const __grid_constant__ FgpCoopArgs C) {
+  extern __shared__ float smf[];
+  const unsigned long long nctas = (unsigned long long)gridDim.x * gridDim.y;
+  const float* rw = C.w0;
+  const float* rz = C.w0;
+  for (int b = 0; b < C.nblocks; ++b) {
+    const int ns = min(FB_T, C.iters - b * FB_T);
+    float* wn = C.pair[b & 1][0];
+    float* zn = C.pair[b & 1][1];
+    FgpBlockArgs A;
+    A.v = C.v;
+    A.w = rw;
+    A.z = rz;
+    A.wn = wn;
+    A.zn = zn;
+    A.nx = C.nx;
+    A.ny = C.ny;
+    A.tau = C.tau;
+    A.step = C.step;
+    A.nsteps = ns;
+    A.nonneg = C.nonneg;
+    fgp2d_block_item<TL>(A, blockIdx.x, blockIdx.y, smf, C.mom[b].c);
+    rw = wn;
+    rz = zn;
+    if (b + 1 < C.nblocks) fgp_grid_barrier(C.bar, nctas * (unsigned long long)(b + 1), C.err);
+  }
 }
 
 // x+ = P_+(v + tau div w) and the fused tail.  32x32 tile, block 32x8 (4 rows per thread).
@@ -662,6 +738,14 @@ int fgp_prepare(vrps_geom* g) {
   if (g->dims == 2) {
     VRPS_TRY(ensure(&ws.dual_s3, dn));
     VRPS_TRY(ensure(&ws.dual_s4, dn));
+    if (!ws.fgp_bar) {
+      VRPS_CUDA(cudaMalloc((void**)&ws.fgp_bar, sizeof(unsigned long long)));
+      VRPS_CUDA(cudaMemset(ws.fgp_bar, 0, sizeof(unsigned long long)));
+    }
+    if (!ws.dev_error) {
+      VRPS_CUDA(cudaMalloc((void**)&ws.dev_error, sizeof(unsigned)));
+      VRPS_CUDA(cudaMemset(ws.dev_error, 0, sizeof(unsigned)));
+    }
   }
   return VRPS_OK;
 }
@@ -692,8 +776,43 @@ static bool fgp_low_tile(int nx, int ny) {
   return last_low;
 }
 
+// One cooperative launch of fgp2d_coop<TL> for all blocks; *done = false (and nothing launched)
+// when the tiles do not all fit the resident slots.
+template <class TL>
+static int fgp2d_coop_launch(const FgpCoopArgs& C, int ty, cudaStream_t s, bool* done) {
+  *done = false;
+  const int tiles_x = (C.nx + TL::TX - 1) / TL::TX, tiles_y = (C.ny + ty - 1) / ty;
+  int dev = 0, sms = 0, per = 0;
+  VRPS_CUDA(cudaGetDevice(&dev));
+  VRPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  VRPS_TRY(smem_opt_in((const void*)fgp2d_coop<TL>, TL::SMEM));
+  VRPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fgp2d_coop<TL>, TL::NT, TL::SMEM));
+  if ((long long)tiles_x * tiles_y > (long long)per * sms) return VRPS_OK;
+  VRPS_CUDA(cudaMemsetAsync(C.bar, 0, sizeof(unsigned long long), s));
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles_x, tiles_y);
+  cfg.blockDim = dim3(TL::NT);
+  cfg.dynamicSmemBytes = TL::SMEM;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  {
+    LaunchScope _ls("fgp2d_coop", s, 4.0 * (double)C.nx * C.ny * (7.0 + 9.0 * (C.nblocks - 1)));
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, fgp2d_coop<TL>, C);
+    if (e != cudaSuccess)
+      return launch_fail(e, "fgp2d_coop", (const void*)fgp2d_coop<TL>, cfg.gridDim, cfg.blockDim, TL::SMEM);
+  }
+  VRPS_LAUNCHED("fgp2d_coop");
+  *done = true;
+  return VRPS_OK;
+}
+
 int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int nx, int ny, float tau, int iters,
-                  int nonneg, int tile, cudaStream_t s, const float** w_final) {
+                  int nonneg, int tile, cudaStream_t s, const float** w_final, unsigned long long* coop_bar,
+                  unsigned* err) {
   // blocks of FB_T iterations; the (w, z) state alternates between pairs[0] and pairs[1].  The
   // first block starts from z = w0 (iteration 0 does not extrapolate).
   const float step = (float)(1.0 / (8.0 * (double)tau));
@@ -706,6 +825,34 @@ int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int
   VRPS_TRY(smem_opt_in((const void*)fgp2d_block<TileLow>, TileLow::SMEM));
   const std::vector<MomBlock> moms = fgp_momentum(iters);
   const double n = (double)nx * ny;
+  const int nblocks = (iters + FB_T - 1) / FB_T;
+  if (coop_bar && err && nblocks > 1 && nblocks <= FGP_COOP_MAX_BLOCKS && (tile == 0 || tile >= 3)) {
+    // the 32-wide tiles in one cooperative launch
+    FgpCoopArgs C;
+    std::memset(&C, 0, sizeof(C));
+    C.v = v;
+    C.w0 = w0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) C.pair[a][b] = pairs[a][b];
+    C.nx = nx;
+    C.ny = ny;
+    C.iters = iters;
+    C.nblocks = nblocks;
+    C.nonneg = nonneg;
+    C.tau = tau;
+    C.step = step;
+    C.bar = coop_bar;
+    C.err = err;
+    for (int b = 0; b < nblocks; ++b) C.mom[b] = moms[b];
+    const bool low = tile == 4 || (tile == 0 && fgp_low_tile(nx, ny));
+    bool done = false;
+    if (low) VRPS_TRY(fgp2d_coop_launch<TileLow>(C, TileLow::TY, s, &done));
+    else VRPS_TRY(fgp2d_coop_launch<TileLarge>(C, TileLarge::TY, s, &done));
+    if (done) {
+      *w_final = pairs[(nblocks - 1) & 1][0];
+      return VRPS_OK;
+    }
+  }
   for (int k0 = 0; k0 < iters; k0 += FB_T) {
     const int ns = iters - k0 < FB_T ? iters - k0 : FB_T;
     const MomBlock& mb = moms[k0 / FB_T];
@@ -759,7 +906,8 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
   const float* w_final = dual;
   if (g->dims == 2) {
     float* pairs[2][2] = {{ws.dual_s1, ws.dual_s2}, {ws.dual_s3, ws.dual_s4}};
-    VRPS_TRY(fgp2d_iterate(v, dual, pairs, g->nx, g->ny, tau, iters, nonneg, g->tune_fgp_tile, s, &w_final));
+    VRPS_TRY(fgp2d_iterate(v, dual, pairs, g->nx, g->ny, tau, iters, nonneg, g->tune_fgp_tile, s, &w_final,
+                           ws.fgp_bar, ws.dev_error));
   } else {
     float* buf[3] = {dual, ws.dual_s1, ws.dual_s2};
     const Fgp3Schedule sch = fgp3_schedule(iters);

@@ -157,6 +157,7 @@ struct Workspace {
   unsigned* fwd_count = nullptr;  // 2D forward: band arrival counters (one per angle row)
   size_t fwd_part_cap = 0;        // floats the partial buffer holds
   unsigned* dev_error = nullptr;  // device-side error word (bounded waits that expired)
+  unsigned long long* fgp_bar = nullptr;   // arrival counter of the cooperative 2D FGP launch
   double* scalars = nullptr;    // [16] device scalars
   float* sino = nullptr;        // [m] sinogram scratch
   float* sino2 = nullptr;       // [m] second sinogram scratch (3D adjoint prescaling)
@@ -469,7 +470,7 @@ Fgp3Schedule fgp3_schedule(int iters);
 int fgp3_zc(const vrps_geom* g);   // z planes per chunk of the streaming 3D FGP iteration
 constexpr int FGP3_TX = 32, FGP3_TY = 16, FGP3_ZC = 64;   // streaming tile and default chunk
 
-constexpr int FB_T = 8;   // iterations per launch (= halo width)
+constexpr int FB_T = 6;   // iterations per block (= halo width)
 
 struct MomBlock {
   float c[FB_T + 1];   // c[s]: extrapolation used when forming z for iteration s + 1
@@ -505,9 +506,14 @@ int fgp_run(const vrps_geom* g, const float* v, float tau, int iters, int nonneg
 std::vector<MomBlock> fgp_momentum(int iters);
 // 2D: `iters` FGP iterations from the dual w0 ([2][nx*ny]) in blocked launches whose (w, z)
 // state alternates between the buffer pairs pairs[0] and pairs[1] (each [2][nx*ny]); *w_final
-// receives the buffer holding w_K (w0 itself when iters = 0).  tile: 0 32x32, 1 32x16, 2 16x16.
+// receives the buffer holding w_K (w0 itself when iters = 0).  tile: 0 32 x 32 or 32 x 27 by the
+// SM count, 1 32x16, 2 16x16, 3 32x32, 4 32x27.  coop_bar (device counter, nullable): run all
+// blocks in one cooperative launch whose CTAs meet at a bounded grid barrier between blocks
+// (err: device error word, set when a barrier wait expires), when the tiles fit the resident
+// slots; otherwise, and with coop_bar null, one launch per block.
 int fgp2d_iterate(const float* v, const float* w0, float* const pairs[2][2], int nx, int ny, float tau, int iters,
-                  int nonneg, int tile, cudaStream_t s, const float** w_final);
+                  int nonneg, int tile, cudaStream_t s, const float** w_final,
+                  unsigned long long* coop_bar = nullptr, unsigned* err = nullptr);
 // 2D: x+ = P_+(v + tau div w) with the fused tail t; wdst (nullable) receives a copy of w.
 int fgp2d_output(const float* v, const float* w, float* wdst, int nx, int ny, float tau, int nonneg,
                  const ProxTail& t, cudaStream_t s);
@@ -517,7 +523,8 @@ int fgp_prepare(vrps_geom* g);
 // ---- batched persistent launches (a CTA walks items blockIdx.x, blockIdx.x + gridDim.x, ...
 // over the items of many problems; the same item functions as the single-problem kernels)
 constexpr int BATCH_MAX_JOBS = 256;
-constexpr int BATCH_MAX_BLOCKS = 16;   // FGP blocks per prox call: at most 128 inner iterations
+constexpr int BATCH_MAX_FGP_ITERS = 128;                                  // 2D inner iterations per prox call
+constexpr int BATCH_MAX_BLOCKS = (BATCH_MAX_FGP_ITERS + FB_T - 1) / FB_T;   // FGP blocks per prox call
 constexpr int FGP_TILE = 32;           // 2D FGP output tile (TileLarge)
 struct BatchFwd {
   Fwd2DParams P;

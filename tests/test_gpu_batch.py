@@ -183,7 +183,7 @@ def test_busy_geometry_and_bad_jobs_rejected(mix):
 
 
 def test_launch_count_per_tick(mix):
-    """A tick is 3 + (FGP blocks) launches however many jobs run."""
+    """A tick is 3 + (FGP blocks of 6 iterations) launches however many jobs run."""
     vr, probs, _ = mix
     B = vr.Batch()
     for i in (0, 1, 3):
@@ -194,7 +194,7 @@ def test_launch_count_per_tick(mix):
     B.step(5)
     B.sync()
     per_tick = (vr.kernel_launches() - n0) / 5
-    assert per_tick == 3 + math.ceil(50 / 8)
+    assert per_tick == 3 + math.ceil(50 / 6)
     B.close()
 
 
