@@ -45,7 +45,8 @@ enum vrps_status {
   VRPS_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed */
   VRPS_ERR_TIMEOUT = -4,       /* a bounded device-side wait expired */
   VRPS_ERR_DIVERGED = -5,      /* the objective became non-finite */
-  VRPS_ERR_UNSUPPORTED = -6    /* valid request outside what this build implements */
+  VRPS_ERR_UNSUPPORTED = -6,   /* valid request outside what this build implements */
+  VRPS_ERR_INTERNAL = -7       /* a self-test found the library misbehaving */
 };
 
 enum vrps_algo {               /* Algorithm 1 and its estimator table */
@@ -151,11 +152,21 @@ int vrps_proj_fwd(const vrps_geom* g, int subset, const float* x, float* y, vrps
 /* Synchronises `stream`, then reads and clears the handle's device error word: returns
  * VRPS_ERR_TIMEOUT when a bounded device-side wait of an earlier call on this handle expired
  * since the last check (the 2D forward projector waits, with an iteration limit, for its
- * bulk copies; an expired wait leaves that projection incomplete), VRPS_OK otherwise.
+ * bulk copies, and the CTAs of the 2D prox's cooperative launch wait, with a poll limit, at a
+ * grid barrier between blocks of iterations; an expired wait leaves that projection or prox
+ * incomplete), VRPS_OK otherwise.
  * vrps_solve, vrps_power_iteration and vrps_objective check the word themselves; callers of
  * the asynchronous vrps_proj_fwd / vrps_proj_adj / vrps_prox_tv check it with this call.
  * No counterpart in the paper.  Errors: INVALID_ARG, CUDA, TIMEOUT. */
 int vrps_check_error(const vrps_geom* g, vrps_stream_t stream);
+
+/* Self-test of the device-side bounded waits (no counterpart in the paper): one CTA arrives at
+ * the 2D prox's grid barrier on a fresh counter that needs two arrivals, so its wait can only
+ * end by its poll limit (`polls`, 1 ... 2^24); checks on the host that the wait gave up, set
+ * the error word and let the kernel return, and that the device still runs work afterwards.
+ * Synchronises `stream`.  Returns VRPS_OK when all of that held.  Errors: INVALID_ARG (polls
+ * outside the range), OUT_OF_MEMORY, CUDA, INTERNAL (the wait did not report its expiry). */
+int vrps_selftest_bounded_wait(unsigned polls, vrps_stream_t stream);
 
 /* x = A_i^T r, the exact transpose of vrps_proj_fwd for the same subset, computed
  * pixel (voxel) by pixel as a gather over the rays that touch it; no atomics.

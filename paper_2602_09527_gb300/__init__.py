@@ -9,8 +9,9 @@ this package is its thin ctypes binding.  Entry points keep the C names without 
 from ._binding import (ALGOS, ESTIMATORS, Batch, autotune, check_error, Geometry, Report, SolveOpts, VrpsError, job_footprint,
                        kernel_launches, lib, objective, pdhg, philox_schedule, power_iteration, profile_enable,
                        profile_read, prox_tv, prox_tv2d_noalloc, proj_adj, proj_fwd, set_launch_shape, launch_shape,
-                       launch_shape_full, solve)
+                       launch_shape_full, selftest_bounded_wait, solve)
 
 __all__ = ["ALGOS", "ESTIMATORS", "Batch", "autotune", "check_error", "Geometry", "job_footprint", "Report", "SolveOpts", "VrpsError", "kernel_launches", "lib",
            "objective", "pdhg", "philox_schedule", "power_iteration", "profile_enable", "profile_read", "prox_tv",
-           "prox_tv2d_noalloc", "proj_adj", "proj_fwd", "set_launch_shape", "launch_shape", "launch_shape_full", "solve"]
+           "prox_tv2d_noalloc", "proj_adj", "proj_fwd", "set_launch_shape", "launch_shape", "launch_shape_full",
+           "selftest_bounded_wait", "solve"]

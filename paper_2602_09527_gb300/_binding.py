@@ -21,7 +21,7 @@ ALGOS = {"ISTA": 0, "FISTA": 1, "SVRG": 2, "SAGA": 3, "PROXSKIP": 4, "VR_PROXSKI
 ESTIMATORS = {"SVRG": 0, "SAGA": 1, "LSVRG": 2, "SGD": 3}
 STORAGE = {"FP32": 0, "BF16": 1, "FP16": 2}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OUT_OF_MEMORY", -3: "CUDA", -4: "TIMEOUT",
-          -5: "DIVERGED", -6: "UNSUPPORTED"}
+          -5: "DIVERGED", -6: "UNSUPPORTED", -7: "INTERNAL"}
 
 
 class VrpsError(RuntimeError):
@@ -94,6 +94,7 @@ def _load():
         "vrps_power_iteration": (i, [vp, i, u64, P(d), vp]),
         "vrps_objective": (i, [vp, vp, vp, d, P(d), vp]),
         "vrps_check_error": (i, [vp, vp]),
+        "vrps_selftest_bounded_wait": (i, [u32, vp]),
         "vrps_philox_schedule": (i, [u64, u32, i64, i, i, d, vp, vp]),
         "vrps_launch_shape_full": (i, [vp, P(i)]),
         "vrps_solve_opts_default": (None, [P(SolveOpts)]),
@@ -333,6 +334,12 @@ def objective(g: Geometry, x: torch.Tensor, b: torch.Tensor, alpha: float, strea
     _check(lib.vrps_objective(g.handle, _dev_ptr(x, "x", g.n), _dev_ptr(b, "b", g.m), float(alpha), out,
                               _stream(stream)))
     return out[0], out[1], out[2]
+
+
+def selftest_bounded_wait(polls: int = 1000, stream=None):
+    """vrps_selftest_bounded_wait: a device-side wait that can only end by its poll limit gives
+    up, reports it in the error word, and leaves the device usable (raises VrpsError if not)."""
+    _check(lib.vrps_selftest_bounded_wait(int(polls), _stream(stream)))
 
 
 def check_error(g: Geometry, stream=None):

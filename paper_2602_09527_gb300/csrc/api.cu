@@ -46,7 +46,9 @@ int launch_fail(cudaError_t e, const char* name, const void* kern, dim3 grid, di
 }
 
 int smem_opt_in(const void* kern, size_t bytes) {
-  if (bytes <= 48 * 1024) return VRPS_OK;
+  // without the opt-in a kernel may use 48 KB of shared memory minus its static shared memory,
+  // so sizes just under 48 KB can need it too: every nonzero size goes through the cache
+  if (bytes == 0) return VRPS_OK;
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, size_t> done;
   int dev = 0;
@@ -81,15 +83,46 @@ int ensure_d(double** p, size_t count) {
 
 // Staggered subsets (Fig. 1 caption): subset i = {i, i+N, i+2N, ...}; subset-major order
 // concatenates the subsets, so subset i occupies rows off[i] .. off[i+1]-1.
-int build_order(int n_angles, int N, int** dev, std::vector<int>* off) {
+// Subset-major angle order: subset i holds angles i, i + N, i + 2N, ... (off: subset starts).
+static std::vector<int> subset_order(int n_angles, int N, std::vector<int>* off) {
   std::vector<int> order;
   order.reserve(n_angles);
-  off->assign(N + 1, 0);
+  if (off) off->assign(N + 1, 0);
   for (int i = 0; i < N; ++i) {
-    (*off)[i] = (int)order.size();
+    if (off) (*off)[i] = (int)order.size();
     for (int a = i; a < n_angles; a += N) order.push_back(a);
   }
-  (*off)[N] = (int)order.size();
+  if (off) (*off)[N] = (int)order.size();
+  return order;
+}
+
+int build_order_angles(const vrps_geom* g, int N, AngleInfo2D** dev) {
+  if (*dev) {
+    cudaFree(*dev);
+    *dev = nullptr;
+  }
+  if (g->dims != 2 || g->ang2d_host.empty()) return VRPS_OK;
+  const std::vector<int> order = subset_order(g->n_angles, N, nullptr);
+  std::vector<AngleInfo2D> rows(order.size());
+  for (size_t r = 0; r < order.size(); ++r) rows[r] = g->ang2d_host[order[r]];
+  VRPS_CUDA(cudaMalloc((void**)dev, sizeof(AngleInfo2D) * rows.size()));
+  VRPS_CUDA(cudaMemcpy(*dev, rows.data(), sizeof(AngleInfo2D) * rows.size(), cudaMemcpyHostToDevice));
+  return VRPS_OK;
+}
+
+const AngleInfo2D* angle_rows(const vrps_geom* g, const int* ids) {
+  const uintptr_t p = (uintptr_t)ids;
+  const size_t span = sizeof(int) * (size_t)g->n_angles;
+  auto within = [&](const int* base) { return base && p >= (uintptr_t)base && p < (uintptr_t)base + span; };
+  if (within(g->order_natural) && g->ang2d) return g->ang2d + (ids - g->order_natural);
+  if (within(g->order_subset) && g->ang2d_sub) return g->ang2d_sub + (ids - g->order_subset);
+  const Workspace& w = g->ws;
+  if (within(w.order_dev) && w.ang_order_dev) return w.ang_order_dev + (ids - w.order_dev);
+  return nullptr;
+}
+
+int build_order(int n_angles, int N, int** dev, std::vector<int>* off) {
+  const std::vector<int> order = subset_order(n_angles, N, off);
   if (*dev) {
     cudaFree(*dev);
     *dev = nullptr;
@@ -160,6 +193,8 @@ static void free_ws(Workspace& w) {
   if (w.sched_dev) cudaFree(w.sched_dev);
   if (w.sched_host) cudaFreeHost(w.sched_host);
   if (w.order_dev) cudaFree(w.order_dev);
+  if (w.ang_order_dev) cudaFree(w.ang_order_dev);
+  w.ang_order_dev = nullptr;
   w = Workspace();
 }
 
@@ -170,6 +205,7 @@ static void free_geom(vrps_geom* g) {
   cudaSetDevice(g->device);
   cudaDeviceSynchronize();
   if (g->ang2d) cudaFree(g->ang2d);
+  if (g->ang2d_sub) cudaFree(g->ang2d_sub);
   if (g->ray3d) cudaFree(g->ray3d);
   if (g->view3d) cudaFree(g->view3d);
   if (g->order_natural) cudaFree(g->order_natural);
@@ -235,6 +271,9 @@ static int build_par2d(vrps_geom* g) {
   g->adj_fp = (int)std::ceil(span_max) + g->adj_nc + 4;
   VRPS_CUDA(cudaMalloc((void**)&g->ang2d, sizeof(AngleInfo2D) * g->n_angles));
   VRPS_CUDA(cudaMemcpy(g->ang2d, tab.data(), sizeof(AngleInfo2D) * g->n_angles, cudaMemcpyHostToDevice));
+  g->ang2d_host = tab;
+  // the rows of a subset launch read their angle constants directly, without the id hop
+  VRPS_TRY(build_order_angles(g, g->n_subsets, &g->ang2d_sub));
   return VRPS_OK;
 }
 

@@ -213,6 +213,7 @@ int job_setup(vrps_batch* B, Job* J, const vrps_job* d) {
   if (J->N != g->n_subsets) {
     if (w.order_N != J->N) {
       VRPS_TRY(build_order(g->n_angles, J->N, &w.order_dev, &w.order_off));
+      VRPS_TRY(build_order_angles(g, J->N, &w.ang_order_dev));
       w.order_N = J->N;
     }
     J->order = w.order_dev;

@@ -360,7 +360,8 @@ struct FgpCoopArgs {
 // publishes the CTA's writes, arrives, and polls (bounded) until every CTA has arrived b + 1
 // times; an expired wait sets the error word and lets the CTA go on (its results are then not
 // used: the host reports the timeout).
-__device__ __forceinline__ void fgp_grid_barrier(unsigned long long* bar, unsigned long long target, unsigned* err) {
+__device__ __forceinline__ void fgp_grid_barrier(unsigned long long* bar, unsigned long long target, unsigned* err,
+                                                 unsigned limit = FGP_BARRIER_LIMIT) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -369,13 +370,18 @@ __device__ __forceinline__ void fgp_grid_barrier(unsigned long long* bar, unsign
     unsigned it = 0;
     for (;;) {
       asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(bar) : "memory");
-      if (seen >= target || ++it >= FGP_BARRIER_LIMIT) break;
+      if (seen >= target || ++it >= limit) break;
       __nanosleep(32);
     }
     if (seen < target) atomicOr(err, 4u);
     __threadfence();
   }
   __syncthreads();
+}
+
+// The barrier's expiry path: a single CTA waits for a second arrival that never comes.
+__global__ void bounded_wait_probe(unsigned long long* bar, unsigned* err, unsigned polls) {
+  fgp_grid_barrier(bar, 2ull, err, polls);
 }
 
 template <class TL>
@@ -1172,3 +1178,44 @@ int batched_grid_3d(int which, int* grid) {
 }
 
 }  // namespace vrps
+
+extern "C" int vrps_selftest_bounded_wait(unsigned polls, vrps_stream_t stream) {
+  using namespace vrps;
+  if (polls < 1 || polls > (1u << 24)) return fail(VRPS_ERR_INVALID_ARG, "polls must be in [1, 2^24]");
+  const cudaStream_t s = (cudaStream_t)stream;
+  char* buf = nullptr;   // [counter (8 bytes)][error word (4 bytes)]
+  cudaError_t e = cudaMalloc((void**)&buf, 16);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(self-test)");
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(buf);
+  unsigned* err = reinterpret_cast<unsigned*>(buf + 8);
+  unsigned word = 0;
+  unsigned long long arrived = 0;
+  int rc = VRPS_OK;
+  if ((e = cudaMemsetAsync(buf, 0, 16, s)) != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync(self-test)");
+  if (rc == VRPS_OK) {
+    e = launch_kernel(bounded_wait_probe, dim3(1), dim3(32), (size_t)0, s, bar, err, polls);
+    if (e != cudaSuccess) rc = launch_fail(e, "bounded_wait_probe", (const void*)bounded_wait_probe, dim3(1), dim3(32), 0);
+  }
+  if (rc == VRPS_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(e, "self-test wait");
+  if (rc == VRPS_OK && (e = cudaMemcpy(&word, err, sizeof(word), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    rc = cuda_fail(e, "self-test read");
+  if (rc == VRPS_OK && (e = cudaMemcpy(&arrived, bar, sizeof(arrived), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    rc = cuda_fail(e, "self-test read");
+  // the context survived the expired wait: a second probe launches, runs and expires the same way
+  if (rc == VRPS_OK && (e = cudaMemsetAsync(buf, 0, 16, s)) != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync(self-test)");
+  unsigned word2 = 1;
+  if (rc == VRPS_OK) {
+    e = launch_kernel(bounded_wait_probe, dim3(1), dim3(32), (size_t)0, s, bar, err, polls);
+    if (e != cudaSuccess) rc = launch_fail(e, "bounded_wait_probe", (const void*)bounded_wait_probe, dim3(1), dim3(32), 0);
+  }
+  if (rc == VRPS_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(e, "self-test wait");
+  if (rc == VRPS_OK && (e = cudaMemcpy(&word2, err, sizeof(word2), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    rc = cuda_fail(e, "self-test read");
+  cudaFree(buf);
+  if (rc != VRPS_OK) return rc;
+  if (!(word & 4u) || arrived != 1ull)
+    return fail(VRPS_ERR_INTERNAL, "bounded wait: error word %u, %llu arrivals (expected bit 4 and 1)", word,
+                arrived);
+  if (!(word2 & 4u)) return fail(VRPS_ERR_INTERNAL, "bounded wait: the second probe did not expire either");
+  return VRPS_OK;
+}

@@ -216,7 +216,7 @@ template <int MODE, bool BULK, int RPT>
 __device__ __forceinline__ void fwd2d_item(const Fwd2DParams& P, int cg, int row, float* smem, FwdShared& S,
                                            unsigned* ph) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const AngleInfo2D in = P.ang[P.ids[row]];
+  const AngleInfo2D in = P.ids ? P.ang[P.ids[row]] : P.ang[row];
   const bool tr = in.T != 0;
   const float* __restrict__ img = tr ? P.xT : P.x;
   const int ncols = tr ? P.ny : P.nx;
@@ -386,7 +386,7 @@ __device__ __forceinline__ void adj2d_item(const Adj2DParams& P, int bx, int by,
   for (int r0 = ra; r0 < rz; r0 += P.chunk) {
     const int nr = min(P.chunk, rz - r0);
     if (tid < nr) {
-      const AngleInfo2D in = P.ang[P.ids[r0 + tid]];
+      const AngleInfo2D in = P.ids ? P.ang[P.ids[r0 + tid]] : P.ang[r0 + tid];
       const long long T0 = (long long)(P.nb - 1) * 2147483648LL + in.BxH * (long long)(2 * ix0 - (P.nx - 1)) +
                            in.ByH * (long long)(2 * iy0 - (P.ny - 1));
       const int J0 = fix_floor(T0);
@@ -545,8 +545,10 @@ int fwd2d_setup(const vrps_geom* g, const float* x, const float* xT, const int* 
   Fwd2DParams& P = *out;
   P.x = x;
   P.xT = xT;
-  P.ang = g->ang2d;
-  P.ids = ids;
+  // row-indexed angle constants when ids is a subset of one of the geometry's orders
+  const AngleInfo2D* rows_tab = angle_rows(g, ids);
+  P.ang = rows_tab ? rows_tab : g->ang2d;
+  P.ids = rows_tab ? nullptr : ids;
   P.nx = g->nx;
   P.ny = g->ny;
   P.nb = g->n_bins;
@@ -632,8 +634,9 @@ int adj2d_setup(const vrps_geom* g, const float* r, const int* ids, int rows, co
                 Adj2DParams* out, size_t* smem, int* variant, int* tiles_x, int* tiles_y) {
   Adj2DParams& P = *out;
   P.r = r;
-  P.ang = g->ang2d;
-  P.ids = ids;
+  const AngleInfo2D* rows_tab = angle_rows(g, ids);
+  P.ang = rows_tab ? rows_tab : g->ang2d;
+  P.ids = rows_tab ? nullptr : ids;
   P.rows = rows;
   P.nx = g->nx;
   P.ny = g->ny;

@@ -148,6 +148,7 @@ extern "C" int vrps_solve(const float* b_in, const vrps_geom* gc, double alpha, 
   if (N != g->n_subsets) {
     if (w.order_N != N) {
       VRPS_TRY(build_order(g->n_angles, N, &w.order_dev, &w.order_off));
+      VRPS_TRY(build_order_angles(g, N, &w.ang_order_dev));
       w.order_N = N;
     }
     order = w.order_dev;

@@ -178,6 +178,7 @@ struct Workspace {
   int32_t* sched_host = nullptr;   // pinned
   int* order_dev = nullptr;        // subset-major angle order for the solver's N
   int order_N = 0;
+  AngleInfo2D* ang_order_dev = nullptr;   // 2D angle table in order_dev's order
   std::vector<int> order_off;      // N+1 row offsets of the subsets in subset-major order
 };
 
@@ -200,6 +201,8 @@ struct vrps_geom {
   std::vector<double> angles;
   // 2D tables
   vrps::AngleInfo2D* ang2d = nullptr;
+  vrps::AngleInfo2D* ang2d_sub = nullptr;         // the same rows in order_subset's order
+  std::vector<vrps::AngleInfo2D> ang2d_host;      // host copy (natural order)
   int adj_fp = 0;        // footprint slots per angle of the 2D adjoint tile
   int adj_nc = 0;        // candidate bins per pixel and angle
   // launch shapes chosen by vrps_autotune (0 / -1: built-in defaults)
@@ -229,6 +232,11 @@ namespace vrps {
 // subset -> (device id list, row count, row offset within the subset-major order)
 int subset_rows(const vrps_geom* g, int subset, const int** ids, int* rows);
 int build_order(int n_angles, int N, int** dev, std::vector<int>* off);
+// 2D: the angle table permuted into the subset-major order of N subsets (device, replacing *dev).
+int build_order_angles(const vrps_geom* g, int N, AngleInfo2D** dev);
+// 2D: the angle table indexed by launch row for the id list ids (a subset's rows of one of the
+// geometry's orders), or null when ids is none of them (the kernels then read ang[ids[row]]).
+const AngleInfo2D* angle_rows(const vrps_geom* g, const int* ids);
 int ensure(float** p, size_t count);
 int ensure_d(double** p, size_t count);
 

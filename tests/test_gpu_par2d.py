@@ -243,3 +243,21 @@ def test_largest_2d_size_sampled():
     lhs = float((vr.proj_fwd(g, -1, xa).double() * ya.double()).sum())
     rhs = float((xa.double() * vr.proj_adj(g, -1, ya).double()).sum())
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_bounded_wait_expires_and_device_stays_usable():
+    """The grid barrier of the cooperative prox gives up after its poll limit when a CTA never
+    arrives (a one-CTA probe on a counter that needs two arrivals), reports it in the error
+    word, and the context keeps working: a prox afterwards still matches the oracle."""
+    vr = _vr()
+    vr.selftest_bounded_wait(1000)
+    with pytest.raises(vr.VrpsError):
+        vr.selftest_bounded_wait(0)
+    g = vr.Geometry.par2d(40, 33, 1.0, [0.0], 4, 1.0, 1)
+    rng = np.random.default_rng(3)
+    v = rng.uniform(-0.2, 1.0, size=(33, 40))
+    x = vr.prox_tv(g, dev(v), 0.05, 13)
+    from oracle import tv
+    ref, _ = tv.fgp(v, 0.05, 13)
+    assert rel(host(x), ref) < 1e-5
+    vr.check_error(g)
