@@ -149,9 +149,10 @@ TRAJECTORY = {
 
 # dram bytes (read + write) per launch of the dominant kernel from one ncu capture, with the
 # profile summary it comes from; None when the kernel changed since the capture.
-# fwd2d_kernel: profiles/fwd2d_kernel_par2d_512.md (a subset launch in SVRG mode with the
-# tuned shape: 2.26 MB read, 0 written).
-NCU_TRAFFIC = {"fwd2d_kernel": 2256640}
+# fwd2d_kernel: profiles/fwd2d_kernel_par2d_512.md counted 2 256 640 bytes (a subset launch in
+# SVRG mode, 2.26 MB read, 0 written) before the kernel began reading its angle constants by
+# launch row, so no current figure.
+NCU_TRAFFIC = {"fwd2d_kernel": None}
 
 
 def _env_int(name, default):
