@@ -96,3 +96,18 @@ def test_batch_scheduling_knobs_reject_bad_input(lib):
     lib.vrps_batch_set_stream_priority.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert lib.vrps_batch_set_grid_share(None, 0.5) == -1
     assert lib.vrps_batch_set_stream_priority(None, 0) == -1
+
+
+def test_status_codes_match_header():
+    """The binding names every status code the header defines, and nothing else."""
+    src = open(os.path.join(ROOT, "include", "vrps.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"VRPS_(OK|ERR_[A-Z_]+)\s*=\s*(-?\d+)", src)}
+    from paper_2602_09527_gb300 import _binding
+    assert {c: n.replace("ERR_", "") for c, n in codes.items()} == _binding.STATUS
+
+
+def test_selftest_rejects_bad_poll_counts_on_host(lib):
+    lib.vrps_selftest_bounded_wait.argtypes = [ctypes.c_uint32, ctypes.c_void_p]
+    assert lib.vrps_selftest_bounded_wait(0, None) == -1
+    assert lib.vrps_selftest_bounded_wait((1 << 24) + 1, None) == -1
+    assert "polls" in _err(lib)
