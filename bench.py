@@ -273,6 +273,42 @@ def oracle_extrapolate(samp, counts, N):
     return it * samp["t_svrg_iter"] + pc * samp["t_prox"] + sn * N * samp["t_subset_grad"]
 
 
+_SINGLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _oracle_child(task):
+    """One oracle sample (oracle_sample) in a spawned, single-threaded process."""
+    wl, rank = task
+    return oracle_sample(wl, make_problem(wl, rank))
+
+
+def oracle_all_cores(wl, counts, n_subsets, procs=None):
+    """The oracle sample in one single-threaded process per host core at once (spawned, so
+    that no process is forked from one that holds a CUDA context): the throughput of
+    independent reconstructions on all cores.  The oracle's numerics are single-threaded, so
+    one reconstruction cannot use more than one core; this is what the whole host delivers."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in _SINGLE_THREAD_ENV}
+    os.environ.update({k: "1" for k in _SINGLE_THREAD_ENV})
+    try:
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(procs) as pool:
+            samples = pool.map(_oracle_child, [(wl, 0)] * procs)
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    per = statistics.mean(oracle_extrapolate(x, counts, n_subsets) for x in samples)
+    return {"processes": procs, "s_per_reconstruction": round(per, 2),
+            "reconstructions_per_hour": round(procs * 3600.0 / per, 3), "wall_s": round(wall, 1),
+            "sample": "each process: the single-core sample above (problem built in the process), "
+                      "scaled by the same counts"}
+
+
 # --------------------------------------------------------------------------- roofline
 def roofline_of(prof, peaks):
     """Roofline entry of the kernel family with the largest share of device time: achieved =
@@ -1443,6 +1479,7 @@ def main():
                           f"one {w['fgp_iters']}-iteration FGP prox ({samp['t_prox']:.2f} s), one subset gradient "
                           f"({samp['t_subset_grad']:.2f} s; a snapshot = N of them), scaled by this run's counts "
                           f"{counts}")}
+        cpu["all_cores"] = oracle_all_cores(wl, counts, N)
 
     clocks = clk.summary()
     # the batched uneven jobs (BF16 storage + one float32 epoch, FP16 as the second variant) and
@@ -1568,7 +1605,8 @@ def reference_arm(args, rank, world):
                                      "host's cores)",
                          "scaled": "to a whole reconstruction by the trajectory's iteration, prox and snapshot "
                                    "counts, recorded from the CUDA path's replay of the same Philox draws (the "
-                                   "oracle alone would need hours to find them)"},
+                                   "oracle alone would need hours to find them)",
+                         "all_cores": oracle_all_cores(wl, counts, w["n_subsets"])},
         "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))

@@ -1,5 +1,5 @@
-"""Host-side measurement logic of bench.py (no GPU): the time-to-gap stopping rule and the
-field-of-view scaling of the batched jobs' TV weight."""
+"""Host-side measurement logic of bench.py (no GPU): the time-to-gap stopping rule, the
+field-of-view scaling of the batched jobs' TV weight and the all-cores oracle figure."""
 import os
 import sys
 
@@ -8,6 +8,9 @@ import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import bench  # noqa: E402
+
+
+ORIG_ENV = {k for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS") if os.environ.get(k) == "1"}
 
 
 def test_first_within_takes_the_first_evaluation_inside_the_target():
@@ -33,3 +36,17 @@ def test_job_alpha_field_of_view():
     w3 = dict(alpha=0.01, alpha_fov=True, dims=3)
     assert bench.job_alpha(w3, dict(side=96)) == pytest.approx(0.01 * 64 ** 2)
     assert bench.job_alpha(dict(alpha=0.3), dict(side=128)) == 0.3
+
+
+def test_oracle_all_cores_runs_spawned_single_threaded_samples():
+    """The all-cores oracle figure: one spawned process per requested core, each timing the
+    single-core sample on its own copy of the problem; per-reconstruction seconds scale the
+    samples by the counts, and the throughput is processes / that time."""
+    import bench
+    counts = {"iterations": 10, "prox_calls": 2, "snapshots": 1}
+    out = bench.oracle_all_cores("par2d_64", counts, 10, procs=2)
+    assert out["processes"] == 2 and out["s_per_reconstruction"] > 0
+    assert abs(out["reconstructions_per_hour"] - 2 * 3600.0 / out["s_per_reconstruction"]) < 1e-3 * out[
+        "reconstructions_per_hour"] + 0.01
+    for k in bench._SINGLE_THREAD_ENV:   # the parent's environment is restored
+        assert os.environ.get(k) != "1" or k in ORIG_ENV
